@@ -1,0 +1,49 @@
+/*
+ * rearr_oracle.h -- declarations of the CPU oracle (test infrastructure only).
+ *
+ * This header belongs to the oracle alone; the CUDA library does not include it.
+ * See rearr_oracle.c for the conventions (row-major storage, numpy-style perm,
+ * gather reorder, element-granular interlace) and the paper passages each
+ * function follows.
+ */
+#ifndef REARR_ORACLE_H
+#define REARR_ORACLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#define ORACLE_MAX_RANK 8
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* N-D permute (Sec. III.B "3D Permute Kernel" / "Reorder Kernel"):
+ * out[lin(j)] = in[sum_i j_i * s[perm[i]]], s the row-major input strides. */
+int oracle_permute(void *dst, const void *src, size_t elem_bytes, int rank,
+                   const int64_t *dims, const int *perm);
+
+/* The same definition evaluated only at the output linear indices out_lin[0..count):
+ * vals[t] = out[out_lin[t]].  Used to check full-size results at sampled points. */
+int oracle_permute_sample(void *vals, const void *src, size_t elem_bytes,
+                          int rank, const int64_t *dims, const int *perm,
+                          const int64_t *out_lin, int64_t count);
+
+/* Reorder by an index sequence (Sec. III.A indexed access): dst[i] = src[idx[i]],
+ * src holding n elements; an index >= n is rejected with -1. */
+int oracle_reorder(void *dst, const void *src, const uint32_t *idx, size_t n,
+                   size_t elem_bytes);
+
+/* Interlace (Sec. III.C): dst[i*k + j] = srcs[j][i], i < n, j < k. */
+int oracle_interlace(void *dst, const void *const *srcs, int k, size_t n,
+                     size_t elem_bytes);
+
+/* De-interlace (Sec. III.C): dsts[j][i] = src[i*k + j], i < n, j < k. */
+int oracle_deinterlace(void *const *dsts, const void *src, int k, size_t n,
+                       size_t elem_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif
