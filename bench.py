@@ -1,0 +1,500 @@
+"""Benchmark of librearr on the generic-permute workload.
+
+One step = one pass over the workload, one library call (one kernel) per op,
+all on one stream, inputs resident in HBM:
+  * the 6 axis orders of a 512 x 512 x 512 fp32 tensor (512 MiB),
+  * the 24 axis orders of a 64 x 128 x 256 x 64 tensor at 2, 4 and 8 bytes per
+    element (256 MiB, 512 MiB, 1 GiB),
+  * a reorder of 2^28 fp32 elements by a uniform random permutation and by a
+    permutation of 65536 shuffled blocks of 4096 elements.
+Inputs are seeded random bit patterns (numpy PCG64), every op reads at least
+256 MiB, so every operand is larger than the 129 MB L2 and no flush is needed.
+
+Throughput is effective GB/s = (bytes read + bytes written) / time, GB = 1e9,
+index reads of the reorders included.  The roofline denominators are a
+cudaMemcpyAsync device-to-device copy measured in the same run and the
+measured copy bandwidth in MEASURED_PEAKS.json.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs the whole workload on its own GPU (independent
+replicas, no collective on the data path); the value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "permute GB/s (R+W) as % of GB300 D2D memcpy; batched ops/s & p99 vs plain"
+WORKLOAD = "generic permute: 6 orders of 512^3 fp32, 24 orders of 64x128x256x64 at 2/4/8 B, reorder 2^28 fp32 (random, 4096-block)"
+MIB = 1 << 20
+
+
+def workload_ops():
+    """The op list of one step (shapes only)."""
+    import itertools
+    ops = []
+    for perm in itertools.permutations(range(3)):
+        ops.append(dict(kind="permute", elem_bytes=4, dims=[512, 512, 512], perm=list(perm)))
+    for e in (2, 4, 8):
+        for perm in itertools.permutations(range(4)):
+            ops.append(dict(kind="permute", elem_bytes=e, dims=[64, 128, 256, 64], perm=list(perm)))
+    ops.append(dict(kind="reorder", elem_bytes=4, n=1 << 28, idx="random"))
+    ops.append(dict(kind="reorder", elem_bytes=4, n=1 << 28, idx="block4096"))
+    return ops
+
+
+def op_bytes(op) -> int:
+    if op["kind"] == "permute":
+        return 2 * int(np.prod(op["dims"])) * op["elem_bytes"]
+    return 2 * op["n"] * op["elem_bytes"] + 4 * op["n"]
+
+
+def op_in_bytes(op) -> int:
+    if op["kind"] == "permute":
+        return int(np.prod(op["dims"])) * op["elem_bytes"]
+    return op["n"] * op["elem_bytes"] + 4 * op["n"]
+
+
+def op_out_bytes(op) -> int:
+    if op["kind"] == "permute":
+        return int(np.prod(op["dims"])) * op["elem_bytes"]
+    return op["n"] * op["elem_bytes"]
+
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1011_3583_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[0]), smax=float(parts[1]), power=float(parts[2]),
+                                 hw=parts[4], hwt=parts[5], swt=parts[6], swp=parts[7]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        reasons = set()
+        for r in rows:
+            if r["hw"] == "Active":
+                reasons.add("hw_slowdown")
+            if r["hwt"] == "Active":
+                reasons.add("hw_thermal_slowdown")
+            if r["swt"] == "Active":
+                reasons.add("sw_thermal_slowdown")
+            if r["swp"] == "Active":
+                reasons.add("sw_power_cap")
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(r["power"] for r in rows)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+
+class Workload:
+    """Device buffers of the workload (inputs seeded, reused across ops)."""
+
+    def __init__(self, torch, ops, device):
+        import synth
+        self.torch = torch
+        self.ops = ops
+        max_in = max(int(np.prod(o["dims"])) * o["elem_bytes"] if o["kind"] == "permute" else o["n"] * o["elem_bytes"]
+                     for o in ops)
+        self.src_np = synth.random_elements(20260101, max_in // 4, 4)
+        self.src = torch.from_numpy(self.src_np).to(device)
+        self.dst = torch.empty(max_in, dtype=torch.uint8, device=device)
+        self.idx_np = {}
+        self.idx = {}
+        for o in ops:
+            if o["kind"] == "reorder" and o["idx"] not in self.idx:
+                n = o["n"]
+                a = (synth.random_permutation(7, n) if o["idx"] == "random"
+                     else synth.block_shuffled_permutation(8, n, 4096))
+                self.idx_np[o["idx"]] = a
+                self.idx[o["idx"]] = torch.from_numpy(a.view(np.uint8)).to(device)
+
+    def run_op(self, rr, o, stream, src=None, dst=None):
+        src = self.src if src is None else src
+        dst = self.dst if dst is None else dst
+        if o["kind"] == "permute":
+            rr.permute(dst, src, o["elem_bytes"], o["dims"], o["perm"], stream)
+        else:
+            rr.reorder(dst, src, self.idx[o["idx"]], o["n"], o["elem_bytes"], stream)
+
+
+def kernel_family(rr, o) -> str:
+    if o["kind"] == "reorder":
+        return "gather"
+    return rr.describe_permute(o["elem_bytes"], o["dims"], o["perm"])["kind"]
+
+
+def measure_memcpy(torch, rr, stream, nbytes=1 << 30, reps=10):
+    a = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    b = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    a.fill_(1)
+    times = []
+    with torch.cuda.stream(stream):
+        for i in range(3 + reps):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            rr.memcpy_d2d(b, a, nbytes, stream)
+            e.record(stream)
+            e.synchronize()
+            if i >= 3:
+                times.append(s.elapsed_time(e) / 1e3)
+    del a, b
+    t = statistics.median(times)
+    return 2 * nbytes / t / 1e9, min(times)
+
+
+def load_traffic_summary():
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("source_digest") != source_digest():
+        return None  # the kernels changed since the counters were taken
+    return d
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("hbm_gbs"):
+            return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+
+    from paper_1011_3583_gb300 import build as rbuild
+    if rank == 0:
+        rbuild.build()
+    if world > 1:
+        dist.barrier()
+    import paper_1011_3583_gb300 as rr
+    rr.load()
+
+    ops = workload_ops()
+    wl = Workload(torch, ops, device)
+    stream = torch.cuda.Stream(device)
+    step_bytes = sum(op_bytes(o) for o in ops)
+    fams = [kernel_family(rr, o) for o in ops]
+
+    def step():
+        for o in ops:
+            wl.run_op(rr, o, stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # warm-up
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    memcpy_gbs, _ = measure_memcpy(torch, rr, stream)
+
+    # timed region: K steps, one event between consecutive ops
+    n_ev = len(ops) * args.steps + 1
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(device).uuid)
+        gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
+    except Exception:
+        gpu_id = None
+    launches0 = rr.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_id) as clk:
+        evs[0].record(stream)
+        k = 1
+        for _ in range(args.steps):
+            for o in ops:
+                wl.run_op(rr, o, stream)
+                evs[k].record(stream)
+                k += 1
+        torch.cuda.synchronize()
+    barrier()
+    launches = rr.launch_count() - launches0
+    elapsed = evs[0].elapsed_time(evs[-1]) / 1e3
+    if world > 1:
+        t = torch.tensor([elapsed], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    per_op = np.zeros(len(ops))
+    k = 1
+    for _ in range(args.steps):
+        for i in range(len(ops)):
+            per_op[i] += evs[k - 1].elapsed_time(evs[k]) / 1e3
+            k += 1
+    value = world * step_bytes * args.steps / elapsed / 1e9
+
+    # roofline of the dominant kernel family
+    fam_time, fam_bytes, fam_launch = {}, {}, {}
+    for i, o in enumerate(ops):
+        f = fams[i]
+        fam_time[f] = fam_time.get(f, 0.0) + per_op[i]
+        fam_bytes[f] = fam_bytes.get(f, 0) + op_bytes(o) * args.steps
+        fam_launch[f] = fam_launch.get(f, 0) + args.steps
+    dom = max(fam_time, key=fam_time.get)
+    peak, peak_kind = measured_peak()
+    achieved = fam_bytes[dom] / fam_time[dom] / 1e9
+    traffic = load_traffic_summary()
+    roofline = {"bound": "hbm", "kernel": f"k_tile_fast family ({dom})" if dom == "tile" else dom,
+                "achieved": round(achieved, 1), "peak": peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "frac_of_memcpy": round(achieved / memcpy_gbs, 4),
+                "algorithmic_bytes_per_launch": int(fam_bytes[dom] / fam_launch[dom]),
+                "traffic": (traffic or {}).get("families", {}).get(dom)}
+    families = {f: {"gbs": round(fam_bytes[f] / fam_time[f] / 1e9, 1), "time_share": round(fam_time[f] / sum(fam_time.values()), 4),
+                    "launches_per_step": fam_launch[f] // args.steps} for f in fam_time}
+    per_op_gbs = [round(op_bytes(o) * args.steps / per_op[i] / 1e9, 1) for i, o in enumerate(ops)]
+
+    # end to end through the public API with pinned host buffers
+    t_e2e, e2e_steps, h2d, d2h = run_e2e(torch, rr, wl, ops, stream, args)
+    if world > 1:
+        t = torch.tensor([t_e2e], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": round(world * step_bytes * e2e_steps / t_e2e / 1e9, 1), "unit": "GB/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
+
+    result = None
+    if rank == 0:
+        cpu = None if (world > 1 or args.no_cpu_baseline) else cpu_baseline(wl)
+        result = {
+            "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bytes (u8/u16/u32/u64 words, bit-exact)",
+            "data": "synthetic (seeded PCG64 random bit patterns)",
+            "config": {"workload": WORKLOAD, "ops_per_step": len(ops), "bytes_per_step": step_bytes,
+                       "l2": "every operand >= 256 MiB, larger than the 129 MB L2; no flush",
+                       "parallelism": f"replicas x{world}"},
+            "memcpy_d2d_gbs": round(memcpy_gbs, 1), "frac_of_memcpy": round(value / world / memcpy_gbs, 4),
+            "frac_of_8tbs": round(value / world / 8000.0, 4),
+            "roofline": roofline, "families": families, "per_op_gbs": per_op_gbs,
+            "gpu_launches": int(launches), "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu,
+            "source_digest": source_digest(),
+        }
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return result
+
+
+def run_e2e(torch, rr, wl, ops, stream, args):
+    """Same step through the public API, inputs copied from pinned host memory
+    and outputs copied back inside the timed region."""
+    max_in = wl.dst.numel()
+    h_src = torch.empty(max_in, dtype=torch.uint8, pin_memory=True)
+    h_src.copy_(torch.from_numpy(wl.src_np.view(np.uint8)))
+    h_dst = torch.empty(max_in, dtype=torch.uint8, pin_memory=True)
+    h_idx = {k: torch.from_numpy(v.view(np.uint8)).pin_memory() for k, v in wl.idx_np.items()}
+    d_src = torch.empty(max_in, dtype=torch.uint8, device=wl.src.device)
+    d_idx = {k: torch.empty_like(v) for k, v in wl.idx.items()}
+    h2d = sum(op_in_bytes(o) for o in ops)
+    d2h = sum(op_out_bytes(o) for o in ops)
+
+    def step():
+        with torch.cuda.stream(stream):
+            for o in ops:
+                nin = (int(np.prod(o["dims"])) if o["kind"] == "permute" else o["n"]) * o["elem_bytes"]
+                d_src[:nin].copy_(h_src[:nin], non_blocking=True)
+                if o["kind"] == "reorder":
+                    d_idx[o["idx"]].copy_(h_idx[o["idx"]], non_blocking=True)
+                    rr.reorder(wl.dst, d_src, d_idx[o["idx"]], o["n"], o["elem_bytes"], stream)
+                else:
+                    rr.permute(wl.dst, d_src, o["elem_bytes"], o["dims"], o["perm"], stream)
+                h_dst[:op_out_bytes(o)].copy_(wl.dst[:op_out_bytes(o)], non_blocking=True)
+
+    steps = max(1, min(args.steps, args.e2e_steps))
+    step()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for _ in range(steps):
+        step()
+    e.record(stream)
+    e.synchronize()
+    t = s.elapsed_time(e) / 1e3
+    return t, steps, int(h2d), int(d2h)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs
+
+CPU_SAMPLE = [dict(kind="permute", elem_bytes=4, dims=[512, 512, 512], perm=[2, 0, 1]),
+              dict(kind="permute", elem_bytes=4, dims=[64, 128, 256, 64], perm=[3, 1, 2, 0]),
+              dict(kind="permute", elem_bytes=8, dims=[64, 128, 256, 64], perm=[0, 3, 2, 1]),
+              dict(kind="permute", elem_bytes=2, dims=[64, 128, 256, 64], perm=[2, 3, 0, 1]),
+              dict(kind="reorder", elem_bytes=4, n=1 << 28, idx="random")]
+
+
+def oracle_run(orc, o, src_np, idx_np):
+    if o["kind"] == "permute":
+        n = int(np.prod(o["dims"])) * o["elem_bytes"]
+        orc.permute(src_np.view(np.uint8)[:n], o["elem_bytes"], o["dims"], o["perm"])
+    else:
+        orc.reorder(src_np.view(np.uint8)[:o["n"] * o["elem_bytes"]], idx_np, o["elem_bytes"])
+
+
+def cpu_baseline(wl, sample=CPU_SAMPLE):
+    """The oracle (single-threaded C loop nest) on a bounded sample of the workload."""
+    import oracle
+    orc = oracle.get()
+    total_b, total_t = 0, 0.0
+    for o in sample:
+        idx = wl.idx_np.get(o.get("idx")) if o["kind"] == "reorder" else None
+        t0 = time.perf_counter()
+        oracle_run(orc, o, wl.src_np, idx)
+        total_t += time.perf_counter() - t0
+        total_b += op_bytes(o)
+    return {"value": round(total_b / total_t / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "one pass of: 512^3 fp32 order (2,0,1); 64x128x256x64 orders (3,1,2,0) at 4 B, (0,3,2,1) "
+                      "at 8 B, (2,3,0,1) at 2 B; reorder of 2^28 fp32 by a random permutation",
+            "seconds": round(total_t, 2), "cpu": cpu_model()}
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name"):
+                return ln.split(":", 1)[1].strip() + f" ({os.cpu_count()} cpus)"
+    except OSError:
+        pass
+    return f"{os.cpu_count()} cpus"
+
+
+class _HostWL:
+    def __init__(self):
+        import synth
+        self.src_np = synth.random_elements(20260101, (1 << 30) // 4, 4)
+        self.idx_np = {"random": synth.random_permutation(7, 1 << 28)}
+
+
+def run_reference(args):
+    """The oracle as it stands, timed on the host cores: each step runs one op
+    of a bounded sample of the workload (rotating)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import oracle
+    orc = oracle.get()
+    wl = _HostWL()
+    seq = CPU_SAMPLE
+    for i in range(args.warmup):
+        o = seq[i % len(seq)]
+        oracle_run(orc, o, wl.src_np, wl.idx_np.get(o.get("idx")))
+    total_b, total_t = 0, 0.0
+    for i in range(args.steps):
+        o = seq[i % len(seq)]
+        t0 = time.perf_counter()
+        oracle_run(orc, o, wl.src_np, wl.idx_np.get(o.get("idx")))
+        total_t += time.perf_counter() - t0
+        total_b += op_bytes(o)
+    value = total_b / total_t / 1e9
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_t / args.steps * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bytes (memcpy per element)",
+            "data": "synthetic (seeded PCG64 random bit patterns)",
+            "config": {"workload": WORKLOAD, "parallelism": "single CPU thread"},
+            "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": "each step runs one op of: 512^3 fp32 (2,0,1); 64x128x256x64 (3,1,2,0) 4 B, "
+                                       "(0,3,2,1) 8 B, (2,3,0,1) 2 B; reorder 2^28 fp32 random (rotating)",
+                             "cpu": cpu_model()},
+            "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="librearr", choices=["librearr", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl != "reference":
+        args.warmup = 3
+    res = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * librearr.h -- C ABI of librearr, GB300 (sm_103a) kernels for the data
+ * rearrangement operations of "Fast GPGPU Data Rearrangement Kernels using
+ * CUDA" (Bader, Bungartz, Mudigere, Narasimhan, Narayanan; arXiv:1011.3583).
+ *
+ * Common conventions
+ * ------------------
+ *  - Every data pointer (dst, src, idx, plane pointers) is a DEVICE pointer to
+ *    memory of the current CUDA device, owned by the caller.  Arrays of plane
+ *    pointers (srcs, dsts) and the dims / perm arrays are HOST arrays, read
+ *    during the call only.
+ *  - Elements are opaque: elem_bytes bytes are moved bit for bit, never
+ *    interpreted as numbers (NaN payloads and -0 survive).
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
+ *    default stream).  A call returns once its kernel is launched; completion
+ *    is observed with the usual stream / event synchronisation.
+ *  - Errors that can be detected on the host are returned synchronously and
+ *    launch nothing: invalid rank, dims, perm, k or elem_bytes, NULL pointers
+ *    with a nonzero size, destination overlapping a source (REARR_EINVAL).
+ *    A failed launch returns REARR_ECUDA.  Operations of zero elements return
+ *    REARR_OK and launch nothing.  In-place operation is not supported.
+ *  - rearr_last_error() gives a human-readable message for the most recent
+ *    failure on the calling thread.
+ */
+#ifndef LIBREARR_H
+#define LIBREARR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* The stream type: identical to cudaStream_t (struct CUstream_st *), declared
+ * here so that this header needs no CUDA header. */
+typedef struct CUstream_st *rearr_stream_t;
+
+typedef enum {
+    REARR_OK = 0,
+    REARR_EINVAL = 1,     /* invalid argument                                  */
+    REARR_ENOMEM = 2,     /* device or host allocation failed / over budget    */
+    REARR_ECUDA = 3,      /* a CUDA runtime call or kernel launch failed       */
+    REARR_ERANGE = 4,     /* an index was out of range (checked reorder)       */
+    REARR_ETIMEDOUT = 5,  /* a wait ran past its deadline                      */
+    REARR_EBUSY = 6       /* the object is in use (e.g. plan already final)    */
+} rearr_status;
+
+#define REARR_MAX_RANK 8
+#define REARR_MAX_K 256
+
+/* Name of a status code ("REARR_OK", ...).  Never NULL. */
+const char *rearr_status_str(rearr_status status);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *rearr_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * rearr_permute -- N-D axis permute (arXiv:1011.3583 Sec. III.B, "3D Permute
+ * Kernel" and the generic N-to-N "Reorder Kernel"; Tables 1 and 2).
+ *
+ *   src   : rank-dimensional array, row-major (dims[0] slowest), contiguous.
+ *   dst   : the permuted array, row-major over output extents dims[perm[i]].
+ *   Output axis i is input axis perm[i] (numpy transpose semantics):
+ *       dst[lin(j)] = src[sum_i j_i * s[perm[i]]],  s = row-major strides of src.
+ *   The paper's order vector o (fastest dimension first) corresponds to
+ *   perm[i] = rank-1-o[rank-1-i].
+ *   elem_bytes : any value >= 1.
+ *   rank       : 1..8; dims[i] >= 0; perm a permutation of 0..rank-1.
+ *   Every collapsed axis of a transposing permute must be < 2^31 elements.
+ * ------------------------------------------------------------------------- */
+rearr_status rearr_permute(void *dst, const void *src, size_t elem_bytes, int rank,
+                           const int64_t *dims, const int *perm, rearr_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * rearr_reorder -- reorder by an index sequence, the "accessing specified set
+ * of indices" pattern of arXiv:1011.3583 Sec. III.A:
+ *       dst[i] = src[idx[i]],  0 <= i < n.
+ *   src holds n elements of elem_bytes; idx holds n uint32 indices, each < n
+ *   (repeats allowed).  An index >= n is undefined behaviour in this call (it
+ *   is never written outside dst, but the value read is unspecified).
+ * ------------------------------------------------------------------------- */
+rearr_status rearr_reorder(void *dst, const void *src, const uint32_t *idx, size_t n,
+                           size_t elem_bytes, rearr_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * rearr_interlace -- join k arrays into one interlaced array
+ * (arXiv:1011.3583 Sec. III.C, Table 3):
+ *       dst[i*k + j] = srcs[j][i],  0 <= i < n, 0 <= j < k.
+ *   srcs : host array of k device pointers, each to n elements.
+ *   dst  : n*k elements.  1 <= k <= REARR_MAX_K.
+ * ------------------------------------------------------------------------- */
+rearr_status rearr_interlace(void *dst, const void *const *srcs, int k, size_t n,
+                             size_t elem_bytes, rearr_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * rearr_deinterlace -- split one interlaced array into k arrays
+ * (arXiv:1011.3583 Sec. III.C, Table 3):
+ *       dsts[j][i] = src[i*k + j],  0 <= i < n, 0 <= j < k.
+ *   dsts : host array of k device pointers, each to room for n elements.
+ *   src  : n*k elements.  1 <= k <= REARR_MAX_K.
+ * ------------------------------------------------------------------------- */
+rearr_status rearr_deinterlace(void *const *dsts, const void *src, int k, size_t n,
+                               size_t elem_bytes, rearr_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched execution.  The paper has no batching; these calls run many of the
+ * operations above in one persistent kernel launch driven by a device-side
+ * tile work list, captured once in a CUDA graph and replayed.
+ *
+ *   rearr_plan_create    : new empty plan (host object).
+ *   rearr_plan_add_*     : record one operation; same arguments and validation
+ *                          as the single calls, minus the stream.  Pointers are
+ *                          recorded, not data: the buffers must stay allocated
+ *                          and unchanged until the batch's stream work is done.
+ *   rearr_plan_finalize  : builds the work list, uploads it (one device
+ *                          allocation owned by the plan), picks tile shapes from
+ *                          the tuning table and captures the launch in a CUDA
+ *                          graph on `stream`.  No op can be added afterwards
+ *                          (REARR_EBUSY).
+ *   rearr_batch          : replays the captured graph on `stream`; every op of
+ *                          the plan is computed exactly as its single call
+ *                          would compute it.  Replays on one stream are ordered;
+ *                          overlapping replays of ONE plan on different streams
+ *                          race on the plan's work counter and are not allowed.
+ *   rearr_plan_destroy   : frees the plan (waits for nothing; the caller must
+ *                          make sure no replay is still running).
+ * ------------------------------------------------------------------------- */
+typedef struct rearr_plan rearr_plan;
+
+rearr_status rearr_plan_create(rearr_plan **plan);
+rearr_status rearr_plan_add_permute(rearr_plan *plan, void *dst, const void *src,
+                                    size_t elem_bytes, int rank, const int64_t *dims,
+                                    const int *perm);
+rearr_status rearr_plan_add_reorder(rearr_plan *plan, void *dst, const void *src,
+                                    const uint32_t *idx, size_t n, size_t elem_bytes);
+rearr_status rearr_plan_add_interlace(rearr_plan *plan, void *dst, const void *const *srcs,
+                                      int k, size_t n, size_t elem_bytes);
+rearr_status rearr_plan_add_deinterlace(rearr_plan *plan, void *const *dsts, const void *src,
+                                        int k, size_t n, size_t elem_bytes);
+rearr_status rearr_plan_finalize(rearr_plan *plan, rearr_stream_t stream);
+rearr_status rearr_batch(rearr_plan *plan, rearr_stream_t stream);
+void rearr_plan_destroy(rearr_plan *plan);
+
+/* Number of ops and of work-list tiles in a plan (after finalize), host only. */
+rearr_status rearr_plan_stats(const rearr_plan *plan, int64_t *n_ops, int64_t *n_tiles);
+
+/* ---------------------------------------------------------------------------
+ * Introspection of the permute plan compiler (host only; needs no GPU).
+ *
+ * The plan compiler drops extent-1 axes, merges output axes that are adjacent
+ * and in order in the input, folds an unmoved innermost run into a wider
+ * element, and classifies the op (the "offset/striding approach" and the 2-D
+ * plane of Sec. III.B: the plane of the input's fastest and the output's
+ * fastest dimension).
+ * ------------------------------------------------------------------------- */
+typedef enum {
+    REARR_KIND_NOOP = 0,        /* zero elements                                */
+    REARR_KIND_COPY = 1,        /* contiguous copy (identity after collapsing)  */
+    REARR_KIND_TILE = 2,        /* shared-memory tiled transpose, 1 word/cell   */
+    REARR_KIND_TILE_CELLS = 3,  /* tiled transpose of multi-word cells          */
+    REARR_KIND_RUNS = 4         /* copy of long contiguous runs                 */
+} rearr_kind;
+
+typedef struct {
+    int kind;                 /* rearr_kind                                      */
+    int rank;                 /* collapsed rank (after folding)                  */
+    int64_t dims[8];          /* collapsed output extents, slowest first         */
+    int64_t in_strides[8];    /* input stride of each output axis, in cells      */
+    int64_t cell_bytes;       /* bytes per cell after folding                    */
+    int word_bytes;           /* access word size (power of two, <= 16)          */
+    int plane_a;              /* output axis that is input-innermost (-1: none)  */
+    int vec_in, vec_out;      /* global access widths in bytes (TILE)            */
+    int tile_a, tile_b;       /* tile extents in cells (TILE, TILE_CELLS)        */
+    int64_t n_tiles;          /* work units (tiles, runs or copy blocks)         */
+} rearr_permute_info;
+
+rearr_status rearr_permute_describe(size_t elem_bytes, int rank, const int64_t *dims,
+                                    const int *perm, uintptr_t dst_addr, uintptr_t src_addr,
+                                    rearr_permute_info *info);
+
+/* ---------------------------------------------------------------------------
+ * Measurement helpers (not rearrangement operations).
+ *   rearr_memcpy_d2d   : cudaMemcpyAsync(dst, src, bytes, DeviceToDevice, stream),
+ *                        the roofline reference the paper measures against
+ *                        (Sec. I, Sec. III.A).
+ *   rearr_launch_count : number of kernels this library has launched in this
+ *                        process (graph replays count the kernels they run).
+ *   rearr_selftest_host: host-only checks of the plan compiler's integer
+ *                        helpers; returns REARR_OK when they all pass.
+ * ------------------------------------------------------------------------- */
+rearr_status rearr_memcpy_d2d(void *dst, const void *src, size_t bytes, rearr_stream_t stream);
+uint64_t rearr_launch_count(void);
+rearr_status rearr_selftest_host(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBREARR_H */

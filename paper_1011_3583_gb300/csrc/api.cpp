@@ -1,0 +1,129 @@
+// api.cpp -- the C ABI of librearr for single operations (include/librearr.h).
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <string>
+
+#include "../../include/librearr.h"
+#include "launch.h"
+#include "plan.h"
+
+namespace rearr {
+
+thread_local std::string t_last_error;
+
+rearr_status fail(rearr_status st, const std::string &msg)
+{
+    t_last_error = msg;
+    return st;
+}
+
+rearr_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(REARR_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace rearr
+
+using namespace rearr;
+
+extern "C" {
+
+const char *rearr_status_str(rearr_status status)
+{
+    switch (status) {
+        case REARR_OK: return "REARR_OK";
+        case REARR_EINVAL: return "REARR_EINVAL";
+        case REARR_ENOMEM: return "REARR_ENOMEM";
+        case REARR_ECUDA: return "REARR_ECUDA";
+        case REARR_ERANGE: return "REARR_ERANGE";
+        case REARR_ETIMEDOUT: return "REARR_ETIMEDOUT";
+        case REARR_EBUSY: return "REARR_EBUSY";
+        default: return "REARR_UNKNOWN";
+    }
+}
+
+const char *rearr_last_error(void) { return t_last_error.c_str(); }
+
+rearr_status rearr_permute(void *dst, const void *src, size_t elem_bytes, int rank, const int64_t *dims,
+                           const int *perm, rearr_stream_t stream)
+{
+    PermPlan pl;
+    std::string err;
+    rearr_status st = plan_permute(dst, src, elem_bytes, rank, dims, perm, pl, err);
+    if (st != REARR_OK) return fail(st, "rearr_permute: " + err);
+    cudaError_t e = launch_single(pl.op, nullptr, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "rearr_permute launch");
+    return REARR_OK;
+}
+
+rearr_status rearr_reorder(void *dst, const void *src, const uint32_t *idx, size_t n, size_t elem_bytes,
+                           rearr_stream_t stream)
+{
+    OpDesc op;
+    std::string err;
+    rearr_status st = plan_reorder(dst, src, idx, n, elem_bytes, op, err);
+    if (st != REARR_OK) return fail(st, "rearr_reorder: " + err);
+    cudaError_t e = launch_single(op, nullptr, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "rearr_reorder launch");
+    return REARR_OK;
+}
+
+rearr_status rearr_interlace(void *dst, const void *const *srcs, int k, size_t n, size_t elem_bytes,
+                             rearr_stream_t stream)
+{
+    InterlacePlan pl;
+    std::string err;
+    rearr_status st = plan_interlace(true, static_cast<char *>(dst), const_cast<char *const *>(
+                                         reinterpret_cast<const char *const *>(srcs)), k, n, elem_bytes, pl, err);
+    if (st != REARR_OK) return fail(st, "rearr_interlace: " + err);
+    cudaError_t e = launch_single(pl.op, pl.planes.data(), reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "rearr_interlace launch");
+    return REARR_OK;
+}
+
+rearr_status rearr_deinterlace(void *const *dsts, const void *src, int k, size_t n, size_t elem_bytes,
+                               rearr_stream_t stream)
+{
+    InterlacePlan pl;
+    std::string err;
+    rearr_status st = plan_interlace(false, static_cast<char *>(const_cast<void *>(src)),
+                                     reinterpret_cast<char *const *>(dsts), k, n, elem_bytes, pl, err);
+    if (st != REARR_OK) return fail(st, "rearr_deinterlace: " + err);
+    cudaError_t e = launch_single(pl.op, pl.planes.data(), reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "rearr_deinterlace launch");
+    return REARR_OK;
+}
+
+rearr_status rearr_permute_describe(size_t elem_bytes, int rank, const int64_t *dims, const int *perm,
+                                    uintptr_t dst_addr, uintptr_t src_addr, rearr_permute_info *info)
+{
+    if (!info) return fail(REARR_EINVAL, "rearr_permute_describe: info is NULL");
+    PermPlan pl;
+    std::string err;
+    rearr_status st = plan_permute(reinterpret_cast<void *>(dst_addr), reinterpret_cast<const void *>(src_addr),
+                                   elem_bytes, rank, dims, perm, pl, err);
+    if (st != REARR_OK) return fail(st, "rearr_permute_describe: " + err);
+    *info = pl.info;
+    return REARR_OK;
+}
+
+rearr_status rearr_memcpy_d2d(void *dst, const void *src, size_t bytes, rearr_stream_t stream)
+{
+    if (bytes == 0) return REARR_OK;
+    if (!dst || !src) return fail(REARR_EINVAL, "rearr_memcpy_d2d: NULL pointer");
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "rearr_memcpy_d2d");
+    return REARR_OK;
+}
+
+uint64_t rearr_launch_count(void) { return g_launches.load(); }
+
+rearr_status rearr_selftest_host(void)
+{
+    std::string err;
+    if (!selftest_host(err)) return fail(REARR_EINVAL, "selftest: " + err);
+    return REARR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,361 @@
+// batch.cu -- batched execution: one persistent kernel runs the tiles of many
+// independent ops from a device-side work list, captured once in a CUDA graph.
+//
+// Work list: the ops' descriptors and the prefix sum of their tile counts.
+// Every CTA repeatedly takes the next `grab` tiles with one atomicAdd on a
+// device counter, finds the op of the first by binary search over the prefix
+// array and runs the matching body (bodies.cuh) for each tile.  No CTA ever
+// waits for another: the only shared state is the counter.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/librearr.h"
+#include "batch.h"
+#include "bodies.cuh"
+#include "launch.h"
+#include "plan.h"
+
+namespace rearr {
+
+rearr_status fail(rearr_status st, const std::string &msg);
+rearr_status cuda_fail(cudaError_t e, const char *what);
+
+namespace {
+
+__device__ __forceinline__ char *const *planes_of(const InterlaceDesc &d)
+{
+    return d.k <= uint32_t(kInlineK) ? d.planes : d.planes_dev;
+}
+
+#define BT_CASE(E, VI, VO) \
+    case tile_variant(E, VI, VO): tile_fast_body<E, VI, VO>(d.tile, uint32_t(u), smem); return;
+
+__device__ __noinline__ void run_tile_fast(const OpDesc &d, uint64_t u, unsigned char *smem)
+{
+    switch (d.tile.variant) {
+        BT_CASE(1, 16, 4) BT_CASE(1, 4, 4) BT_CASE(1, 1, 4)
+        BT_CASE(1, 16, 1) BT_CASE(1, 4, 1) BT_CASE(1, 1, 1)
+        BT_CASE(2, 16, 8) BT_CASE(2, 4, 8) BT_CASE(2, 2, 8)
+        BT_CASE(2, 16, 4) BT_CASE(2, 4, 4) BT_CASE(2, 2, 4)
+        BT_CASE(2, 16, 2) BT_CASE(2, 4, 2) BT_CASE(2, 2, 2)
+        BT_CASE(4, 16, 16) BT_CASE(4, 4, 16) BT_CASE(4, 16, 4) BT_CASE(4, 4, 4)
+        BT_CASE(8, 16, 16) BT_CASE(8, 8, 16) BT_CASE(8, 16, 8) BT_CASE(8, 8, 8)
+        BT_CASE(16, 16, 16)
+        default: return;
+    }
+}
+#undef BT_CASE
+
+template <int W>
+__device__ __noinline__ void run_word_class(const OpDesc &d, uint64_t u, unsigned char *smem)
+{
+    switch (d.cls) {
+        case OC_TILE_CELLS: tile_cells_body<W>(d.tile, uint32_t(u), smem); return;
+        case OC_RUNS: runs_body<W>(d.runs, u); return;
+        case OC_COPY: copy_body<W>(d.copy, u); return;
+        case OC_GATHER: gather_body<W>(d.gather, u); return;
+        case OC_INTERLACE: interlace_generic_body<W>(d.inter, planes_of(d.inter), u, true); return;
+        case OC_DEINTERLACE: interlace_generic_body<W>(d.inter, planes_of(d.inter), u, false); return;
+        default: return;
+    }
+}
+
+template <int E>
+__device__ __noinline__ void run_inter_fast(const OpDesc &d, uint64_t u)
+{
+    char *const *pl = planes_of(d.inter);
+    const bool inter = d.cls == OC_INTERLACE;
+    switch (d.inter.k) {
+        case 1: inter ? interlace_fast_body<E, 1>(d.inter, pl, u, d.units) : deinterlace_fast_body<E, 1>(d.inter, pl, u, d.units); return;
+        case 2: inter ? interlace_fast_body<E, 2>(d.inter, pl, u, d.units) : deinterlace_fast_body<E, 2>(d.inter, pl, u, d.units); return;
+        case 3: inter ? interlace_fast_body<E, 3>(d.inter, pl, u, d.units) : deinterlace_fast_body<E, 3>(d.inter, pl, u, d.units); return;
+        case 4: inter ? interlace_fast_body<E, 4>(d.inter, pl, u, d.units) : deinterlace_fast_body<E, 4>(d.inter, pl, u, d.units); return;
+        default: return;
+    }
+}
+
+__device__ __forceinline__ void run_unit(const OpDesc &d, uint64_t u, unsigned char *smem)
+{
+    if (d.cls == OC_TILE) { run_tile_fast(d, u, smem); return; }
+    if ((d.cls == OC_INTERLACE || d.cls == OC_DEINTERLACE) && d.inter.fast) {
+        switch (d.inter.elem_bytes) {
+            case 1: run_inter_fast<1>(d, u); return;
+            case 2: run_inter_fast<2>(d, u); return;
+            case 4: run_inter_fast<4>(d, u); return;
+            case 8: run_inter_fast<8>(d, u); return;
+            case 16: run_inter_fast<16>(d, u); return;
+            default: return;
+        }
+    }
+    switch (d.word) {
+        case 1: run_word_class<1>(d, u, smem); return;
+        case 2: run_word_class<2>(d, u, smem); return;
+        case 4: run_word_class<4>(d, u, smem); return;
+        case 8: run_word_class<8>(d, u, smem); return;
+        case 16: run_word_class<16>(d, u, smem); return;
+        default: return;
+    }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kThreads) k_batch(const OpDesc *__restrict__ ops, const uint64_t *__restrict__ prefix,
+                                                    int n_ops, unsigned long long *counter, uint32_t grab)
+{
+    __shared__ __align__(16) unsigned char smem[kSmemBytes];
+    __shared__ unsigned long long s_start;
+    const uint64_t total = prefix[n_ops];
+    for (;;) {
+        if (threadIdx.x == 0) s_start = atomicAdd(counter, (unsigned long long)grab);
+        __syncthreads();
+        const uint64_t start = s_start;
+        __syncthreads();
+        if (start >= total) break;
+        const uint64_t end = min(total, start + grab);
+        // op containing `start`: last index with prefix[op] <= start
+        int lo = 0, hi = n_ops - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= start) lo = mid;
+            else hi = mid - 1;
+        }
+        int op = lo;
+        for (uint64_t t = start; t < end; ++t) {
+            while (t >= prefix[op + 1]) ++op;
+            run_unit(ops[op], t - prefix[op], smem);
+        }
+    }
+}
+
+}  // namespace rearr
+
+// ---------------------------------------------------------------------------
+// Host side of the batched plan.
+
+using namespace rearr;
+
+struct rearr_plan {
+    std::vector<OpDesc> ops;
+    std::vector<std::vector<char *>> plane_lists;  // per op (empty unless k > kInlineK)
+    bool finalized = false;
+    void *dev = nullptr;               // one allocation: ops | prefix | plane arrays | counter
+    OpDesc *d_ops = nullptr;
+    uint64_t *d_prefix = nullptr;
+    unsigned long long *d_counter = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t total_units = 0;
+    int n_launch_ops = 0;              // ops with at least one unit
+    uint32_t grab = 1;
+    int grid = 0;
+};
+
+namespace rearr {
+
+const BatchTuning &batch_tuning();
+
+}  // namespace rearr
+
+static rearr_status add_op(rearr_plan *p, const OpDesc &op, std::vector<char *> planes = {})
+{
+    if (op.units == 0) return REARR_OK;
+    p->ops.push_back(op);
+    p->plane_lists.push_back(std::move(planes));
+    return REARR_OK;
+}
+
+extern "C" {
+
+rearr_status rearr_plan_create(rearr_plan **plan)
+{
+    if (!plan) return fail(REARR_EINVAL, "rearr_plan_create: plan is NULL");
+    *plan = new (std::nothrow) rearr_plan();
+    if (!*plan) return fail(REARR_ENOMEM, "rearr_plan_create: out of host memory");
+    return REARR_OK;
+}
+
+rearr_status rearr_plan_add_permute(rearr_plan *plan, void *dst, const void *src, size_t elem_bytes, int rank,
+                                    const int64_t *dims, const int *perm)
+{
+    if (!plan) return fail(REARR_EINVAL, "rearr_plan_add_permute: plan is NULL");
+    if (plan->finalized) return fail(REARR_EBUSY, "rearr_plan_add_permute: plan is finalized");
+    PermPlan pl;
+    std::string err;
+    rearr_status st = plan_permute(dst, src, elem_bytes, rank, dims, perm, pl, err);
+    if (st != REARR_OK) return fail(st, "rearr_plan_add_permute: " + err);
+    return add_op(plan, pl.op);
+}
+
+rearr_status rearr_plan_add_reorder(rearr_plan *plan, void *dst, const void *src, const uint32_t *idx, size_t n,
+                                    size_t elem_bytes)
+{
+    if (!plan) return fail(REARR_EINVAL, "rearr_plan_add_reorder: plan is NULL");
+    if (plan->finalized) return fail(REARR_EBUSY, "rearr_plan_add_reorder: plan is finalized");
+    OpDesc op;
+    std::string err;
+    rearr_status st = plan_reorder(dst, src, idx, n, elem_bytes, op, err);
+    if (st != REARR_OK) return fail(st, "rearr_plan_add_reorder: " + err);
+    return add_op(plan, op);
+}
+
+static rearr_status plan_add_inter(rearr_plan *plan, bool inter, char *iv, char *const *planes, int k, size_t n,
+                                   size_t elem_bytes, const char *who)
+{
+    if (!plan) return fail(REARR_EINVAL, std::string(who) + ": plan is NULL");
+    if (plan->finalized) return fail(REARR_EBUSY, std::string(who) + ": plan is finalized");
+    InterlacePlan pl;
+    std::string err;
+    rearr_status st = plan_interlace(inter, iv, planes, k, n, elem_bytes, pl, err);
+    if (st != REARR_OK) return fail(st, std::string(who) + ": " + err);
+    if (pl.op.units == 0) return REARR_OK;
+    // The batched kernel instantiates the 16-byte group bodies for k <= 4 only.
+    if (pl.op.inter.fast && pl.op.inter.k > 4) {
+        const uint64_t al = 16;
+        const int W = pow2_align(al, elem_bytes);
+        InterlaceDesc &d = pl.op.inter;
+        d.fast = 0;
+        pl.op.word = uint32_t(W);
+        d.c = uint32_t(elem_bytes / W);
+        const uint64_t kc = uint64_t(k) * d.c;
+        d.unit_groups = std::max<uint64_t>(1, 8192 / kc);
+        d.kc_div = make_fastdiv(uint32_t(kc));
+        d.c_div = make_fastdiv(d.c);
+        pl.op.units = (uint64_t(n) + d.unit_groups - 1) / d.unit_groups;
+    }
+    std::vector<char *> lst;
+    if (k > kInlineK) lst = pl.planes;
+    return add_op(plan, pl.op, std::move(lst));
+}
+
+rearr_status rearr_plan_add_interlace(rearr_plan *plan, void *dst, const void *const *srcs, int k, size_t n,
+                                      size_t elem_bytes)
+{
+    return plan_add_inter(plan, true, static_cast<char *>(dst),
+                          const_cast<char *const *>(reinterpret_cast<const char *const *>(srcs)), k, n, elem_bytes,
+                          "rearr_plan_add_interlace");
+}
+
+rearr_status rearr_plan_add_deinterlace(rearr_plan *plan, void *const *dsts, const void *src, int k, size_t n,
+                                        size_t elem_bytes)
+{
+    return plan_add_inter(plan, false, static_cast<char *>(const_cast<void *>(src)),
+                          reinterpret_cast<char *const *>(dsts), k, n, elem_bytes, "rearr_plan_add_deinterlace");
+}
+
+rearr_status rearr_plan_finalize(rearr_plan *plan, rearr_stream_t stream)
+{
+    if (!plan) return fail(REARR_EINVAL, "rearr_plan_finalize: plan is NULL");
+    if (plan->finalized) return fail(REARR_EBUSY, "rearr_plan_finalize: plan is already finalized");
+    const size_t n = plan->ops.size();
+    plan->finalized = true;
+    if (n == 0) return REARR_OK;
+    // Host image of the device block.
+    size_t n_ptrs = 0;
+    for (auto &l : plan->plane_lists) n_ptrs += l.size();
+    const size_t off_ops = 0;
+    const size_t off_prefix = (n * sizeof(OpDesc) + 255) / 256 * 256;
+    const size_t off_planes = off_prefix + ((n + 1) * sizeof(uint64_t) + 255) / 256 * 256;
+    const size_t off_counter = off_planes + (n_ptrs * sizeof(char *) + 255) / 256 * 256;
+    const size_t total_bytes = off_counter + 256;
+    std::vector<unsigned char> host(total_bytes, 0);
+    std::vector<uint64_t> prefix(n + 1, 0);
+    for (size_t i = 0; i < n; ++i) prefix[i + 1] = prefix[i] + plan->ops[i].units;
+    plan->total_units = prefix[n];
+
+    cudaError_t e = cudaMalloc(&plan->dev, total_bytes);
+    if (e != cudaSuccess) {
+        plan->dev = nullptr;
+        return fail(REARR_ENOMEM, std::string("rearr_plan_finalize: cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    char *base = static_cast<char *>(plan->dev);
+    plan->d_ops = reinterpret_cast<OpDesc *>(base + off_ops);
+    plan->d_prefix = reinterpret_cast<uint64_t *>(base + off_prefix);
+    plan->d_counter = reinterpret_cast<unsigned long long *>(base + off_counter);
+    size_t pi = 0;
+    for (size_t i = 0; i < n; ++i) {
+        OpDesc &op = plan->ops[i];
+        auto &l = plan->plane_lists[i];
+        if (!l.empty()) {
+            char **dst = reinterpret_cast<char **>(host.data() + off_planes) + pi;
+            std::memcpy(dst, l.data(), l.size() * sizeof(char *));
+            op.inter.planes_dev = reinterpret_cast<char *const *>(base + off_planes + pi * sizeof(char *));
+            pi += l.size();
+        }
+    }
+    std::memcpy(host.data() + off_ops, plan->ops.data(), n * sizeof(OpDesc));
+    std::memcpy(host.data() + off_prefix, prefix.data(), (n + 1) * sizeof(uint64_t));
+    cudaStream_t us = reinterpret_cast<cudaStream_t>(stream);
+    e = cudaMemcpyAsync(plan->dev, host.data(), total_bytes, cudaMemcpyHostToDevice, us);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(us);
+    if (e != cudaSuccess) return cuda_fail(e, "rearr_plan_finalize: upload");
+
+    // Persistent grid: every SM filled to the kernel's occupancy.
+    int dev_id = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev_id);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kThreads, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "rearr_plan_finalize: occupancy");
+    const BatchTuning &tun = batch_tuning();
+    plan->grab = tun.grab_for(plan->total_units, uint64_t(sms) * uint64_t(std::max(per_sm, 1)));
+    uint64_t grid = uint64_t(sms) * uint64_t(std::max(per_sm, 1));
+    const uint64_t grabs = (plan->total_units + plan->grab - 1) / plan->grab;
+    if (grid > grabs) grid = grabs;
+    plan->grid = int(std::max<uint64_t>(grid, 1));
+    plan->n_launch_ops = int(n);
+
+    // Capture the counter reset and the launch in a graph on a private stream.
+    cudaStream_t cap;
+    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "rearr_plan_finalize: stream");
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaMemsetAsync(plan->d_counter, 0, sizeof(unsigned long long), cap);
+        k_batch<<<plan->grid, kThreads, 0, cap>>>(plan->d_ops, plan->d_prefix, int(n), plan->d_counter, plan->grab);
+        cudaError_t le = cudaGetLastError();
+        e = cudaStreamEndCapture(cap, &plan->graph);
+        if (e == cudaSuccess && le != cudaSuccess) e = le;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->exec, plan->graph, 0);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return cuda_fail(e, "rearr_plan_finalize: graph capture");
+    return REARR_OK;
+}
+
+rearr_status rearr_batch(rearr_plan *plan, rearr_stream_t stream)
+{
+    if (!plan) return fail(REARR_EINVAL, "rearr_batch: plan is NULL");
+    if (!plan->finalized) return fail(REARR_EINVAL, "rearr_batch: plan is not finalized");
+    if (!plan->exec) return REARR_OK;  // empty plan
+    cudaError_t e = cudaGraphLaunch(plan->exec, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "rearr_batch: graph launch");
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return REARR_OK;
+}
+
+void rearr_plan_destroy(rearr_plan *plan)
+{
+    if (!plan) return;
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    if (plan->dev) cudaFree(plan->dev);
+    delete plan;
+}
+
+rearr_status rearr_plan_stats(const rearr_plan *plan, int64_t *n_ops, int64_t *n_tiles)
+{
+    if (!plan) return fail(REARR_EINVAL, "rearr_plan_stats: plan is NULL");
+    if (n_ops) *n_ops = int64_t(plan->ops.size());
+    if (n_tiles) {
+        uint64_t t = 0;
+        for (auto &op : plan->ops) t += op.units;
+        *n_tiles = int64_t(t);
+    }
+    return REARR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,25 @@
+// batch.h -- tuning knobs of the batched persistent kernel.
+#pragma once
+
+#include <stdint.h>
+
+namespace rearr {
+
+struct BatchTuning {
+    // Tiles a CTA takes per atomicAdd on the work counter: enough work per
+    // grab to hide the atomic, few enough that the tail balances.
+    uint32_t min_grab = 1;
+    uint32_t max_grab = 8;
+    uint32_t grabs_per_cta = 8;  // target number of grabs per resident CTA
+
+    uint32_t grab_for(uint64_t total_units, uint64_t resident_ctas) const
+    {
+        if (resident_ctas == 0) resident_ctas = 1;
+        uint64_t g = total_units / (resident_ctas * grabs_per_cta);
+        if (g < min_grab) g = min_grab;
+        if (g > max_grab) g = max_grab;
+        return uint32_t(g);
+    }
+};
+
+}  // namespace rearr

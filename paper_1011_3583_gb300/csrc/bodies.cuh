@@ -1,0 +1,521 @@
+// bodies.cuh -- per-work-unit device bodies of every librearr op class.
+//
+// Each body moves one work unit (a tile, a block of runs, a copy block, ...)
+// with the whole CTA of kThreads threads.  The single-op kernels call a body
+// once per CTA; the batched persistent kernel calls the body that matches the
+// op of every tile it takes from the work list.  Bodies that use shared
+// memory end with a barrier so that the caller may reuse the buffer.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace rearr {
+
+// ---------------------------------------------------------------------------
+// Tiled transpose (arXiv:1011.3583 Sec. III.B): the 2-D plane spanned by the
+// input's fastest axis (A) and the output's fastest axis (B) is cut into
+// tiles; a tile is read along A (contiguous in the input), staged in shared
+// memory, and written along B (contiguous in the output), so both global
+// sides are coalesced.  The remaining axes batch the plane.
+
+// Fast-tile shape per element size: 16 KB of payload, input rows of 128-256 B.
+template <int E> struct FastTile;
+template <> struct FastTile<1> { static constexpr int TA = 128, TB = 128; };
+template <> struct FastTile<2> { static constexpr int TA = 128, TB = 64; };
+template <> struct FastTile<4> { static constexpr int TA = 64, TB = 64; };
+template <> struct FastTile<8> { static constexpr int TA = 32, TB = 64; };
+template <> struct FastTile<16> { static constexpr int TA = 16, TB = 64; };
+
+// Origin of tile t: (a0, b0) in the plane and the byte offsets of its batch.
+__device__ __forceinline__ void tile_origin(const TileDesc &d, uint32_t t, uint32_t &a0,
+                                            uint32_t &b0, int64_t &in_off, int64_t &out_off)
+{
+    uint32_t q, ta, tb;
+    fdivmod(t, d.ta_div, q, ta);
+    fdivmod(q, d.tb_div, q, tb);
+    a0 = ta * d.TA;
+    b0 = tb * d.TB;
+    in_off = 0;
+    out_off = 0;
+#pragma unroll
+    for (int i = kMaxBatch - 1; i >= 0; --i) {
+        if (i < d.nb) {
+            uint32_t r;
+            fdivmod(q, d.bdiv[i], q, r);
+            in_off += int64_t(r) * d.bin[i];
+            out_off += int64_t(r) * d.bout[i];
+        }
+    }
+}
+
+// Output piece m of a register block: rows r[0..VB) of the staged tile, each
+// a 16-byte chunk of 16/E elements along A, give for element m of the chunk
+// the VB consecutive B-elements as one word of VB*E bytes.
+template <int E, int VB>
+__device__ __forceinline__ typename Word<E * VB>::T piece(const uint4 (&r)[VB], int m)
+{
+    if constexpr (E >= 4) {
+        constexpr int EW = E / 4;  // words per element
+        uint32_t w[VB * EW];
+#pragma unroll
+        for (int i = 0; i < VB; ++i)
+#pragma unroll
+            for (int x = 0; x < EW; ++x) w[i * EW + x] = word_of(r[i], m * EW + x);
+        if constexpr (VB * EW == 4) return make_uint4(w[0], w[1], w[2], w[3]);
+        else if constexpr (VB * EW == 2) return make_uint2(w[0], w[1]);
+        else return w[0];
+    } else if constexpr (E == 2) {
+        const uint32_t sel = (m & 1) ? 0x7632u : 0x5410u;
+        if constexpr (VB == 4) {
+            return make_uint2(prmt(word_of(r[0], m >> 1), word_of(r[1], m >> 1), sel),
+                              prmt(word_of(r[2], m >> 1), word_of(r[3], m >> 1), sel));
+        } else if constexpr (VB == 2) {
+            return prmt(word_of(r[0], m >> 1), word_of(r[1], m >> 1), sel);
+        } else {
+            const uint32_t w = word_of(r[0], m >> 1);
+            return uint16_t((m & 1) ? (w >> 16) : (w & 0xFFFFu));
+        }
+    } else {  // E == 1
+        const uint32_t bp = uint32_t(m & 3);
+        const uint32_t sel = bp | ((4u + bp) << 4);
+        if constexpr (VB == 4) {
+            const uint32_t lo = prmt(word_of(r[0], m >> 2), word_of(r[1], m >> 2), sel);
+            const uint32_t hi = prmt(word_of(r[2], m >> 2), word_of(r[3], m >> 2), sel);
+            return prmt(lo, hi, 0x5410u);
+        } else if constexpr (VB == 2) {
+            return uint16_t(prmt(word_of(r[0], m >> 2), word_of(r[1], m >> 2), sel) & 0xFFFFu);
+        } else {
+            return uint8_t((word_of(r[0], m >> 2) >> (8 * bp)) & 0xFFu);
+        }
+    }
+}
+
+// Fast tile: cells are single E-byte elements (E a power of two <= 16).
+// VIN: width of the global loads along A; VOUT: width of the global stores
+// along B (VOUT/E = VB consecutive B-elements per store).  Shared memory holds
+// the tile row-major by B with 16-byte chunks XOR-swizzled by (row/VB)&7, so
+// the 16-byte row stores of the load phase and the 16-byte column-block loads
+// of the store phase are both free of bank conflicts.
+template <int E, int VIN, int VOUT>
+__device__ __forceinline__ void tile_fast_body(const TileDesc &d, uint32_t t, unsigned char *smem)
+{
+    constexpr int TA = FastTile<E>::TA, TB = FastTile<E>::TB;
+    constexpr int ROWB = TA * E;     // bytes per staged row
+    constexpr int V = 16 / E;        // elements per 16-byte chunk
+    constexpr int VB = VOUT / E;     // B-elements per output store
+    constexpr int PPR = ROWB / VIN;  // load pieces per row
+    constexpr int NP = TB * PPR;
+    constexpr int PT = NP / kThreads;
+    static_assert(NP % kThreads == 0, "tile must split evenly over the CTA");
+    static_assert(ROWB % 128 == 0, "swizzle works on groups of 8 chunks");
+    static_assert(VB >= 1 && VB <= 4, "output block of 1..4 rows");
+
+    uint32_t a0, b0;
+    int64_t ioff, ooff;
+    tile_origin(d, t, a0, b0, ioff, ooff);
+    const uint32_t na = min(uint32_t(TA), d.DA - a0);
+    const uint32_t nbv = min(uint32_t(TB), d.DB - b0);
+    const char *in = d.src + ioff + int64_t(a0) * E + int64_t(b0) * d.sb_in;
+    char *out = d.dst + ooff + int64_t(a0) * d.sa_out + int64_t(b0) * E;
+    const int tid = threadIdx.x;
+    const uint32_t row_valid_bytes = na * E;
+
+    typename Word<VIN>::T buf[PT];
+#pragma unroll
+    for (int k = 0; k < PT; ++k) {
+        const int f = k * kThreads + tid;
+        const int row = f / PPR, x = (f % PPR) * VIN;
+        if (uint32_t(row) < nbv && uint32_t(x) < row_valid_bytes)
+            buf[k] = ldg_stream<VIN>(in + int64_t(row) * d.sb_in + x);
+    }
+#pragma unroll
+    for (int k = 0; k < PT; ++k) {
+        const int f = k * kThreads + tid;
+        const int row = f / PPR, x = (f % PPR) * VIN;
+        if (uint32_t(row) < nbv && uint32_t(x) < row_valid_bytes) {
+            const int sw = (row / VB) & 7;
+            sts<VIN>(smem + row * ROWB + (((x >> 4) ^ sw) << 4) + (x & 15), buf[k]);
+        }
+    }
+    __syncthreads();
+
+    constexpr int UB = TB / VB, UQ = TA / V, NU = UB * UQ;
+    static_assert(NU % kThreads == 0, "store units must split evenly");
+#pragma unroll
+    for (int u0 = 0; u0 < NU; u0 += kThreads) {
+        const int u = u0 + tid;
+        const int bq = u % UB, q = u / UB;
+        const int b = bq * VB;
+        if (uint32_t(b) < nbv) {
+            uint4 r[VB];
+#pragma unroll
+            for (int i = 0; i < VB; ++i)
+                r[i] = lds<16>(smem + (b + i) * ROWB + ((q ^ (bq & 7)) << 4));
+#pragma unroll
+            for (int m = 0; m < V; ++m) {
+                const uint32_t a = uint32_t(q * V + m);
+                if (a < na) stg<VOUT>(out + int64_t(a) * d.sa_out + int64_t(b) * E, piece<E, VB>(r, m));
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Cells tile: each cell is c words of W bytes (any cell size; used for
+// element sizes that are not a power of two, unaligned element addresses and
+// permutes whose innermost axis is unmoved but short).  Rows are padded to a
+// pitch P = c (mod 32) words, which makes the column walk of the store phase
+// touch consecutive banks.
+template <int W>
+__device__ __forceinline__ void tile_cells_body(const TileDesc &d, uint32_t t, unsigned char *smem_raw)
+{
+    using T = typename Word<W>::T;
+    T *smem = reinterpret_cast<T *>(smem_raw);
+    uint32_t a0, b0;
+    int64_t ioff, ooff;
+    tile_origin(d, t, a0, b0, ioff, ooff);
+    const uint32_t c = d.c, P = d.pitch;
+    const uint32_t na = min(d.TA, d.DA - a0);
+    const uint32_t nbv = min(d.TB, d.DB - b0);
+    const char *in = d.src + ioff + int64_t(a0) * c * W + int64_t(b0) * d.sb_in;
+    char *out = d.dst + ooff + int64_t(a0) * d.sa_out + int64_t(b0) * c * W;
+    const int tid = threadIdx.x;
+    constexpr int U = 8;
+
+    const uint32_t RW = d.rowwords_div.d;  // TA*c
+    const uint32_t total_in = d.TB * RW;
+    const uint32_t rw_valid = na * c;
+    for (uint32_t base = 0; base < total_in; base += kThreads * U) {
+        T v[U];
+        uint32_t row[U], w[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const uint32_t f = base + k * kThreads + tid;
+            fdivmod(f, d.rowwords_div, row[k], w[k]);
+            if (f < total_in && row[k] < nbv && w[k] < rw_valid)
+                v[k] = ldg_stream<W>(in + int64_t(row[k]) * d.sb_in + int64_t(w[k]) * W);
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const uint32_t f = base + k * kThreads + tid;
+            if (f < total_in && row[k] < nbv && w[k] < rw_valid) smem[row[k] * P + w[k]] = v[k];
+        }
+    }
+    __syncthreads();
+
+    const uint32_t OW = d.outwords_div.d;  // TB*c
+    const uint32_t total_out = d.TA * OW;
+    const uint32_t ow_valid = nbv * c;
+    for (uint32_t base = 0; base < total_out; base += kThreads * U) {
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const uint32_t f = base + k * kThreads + tid;
+            uint32_t arow, w, b, kk;
+            fdivmod(f, d.outwords_div, arow, w);
+            if (f < total_out && arow < na && w < ow_valid) {
+                fdivmod(w, d.c_div, b, kk);
+                stg<W>(out + int64_t(arow) * d.sa_out + int64_t(w) * W, smem[b * P + arow * c + kk]);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Runs: permutes whose output is a sequence of long contiguous input runs
+// (an unmoved innermost axis of >= 256 bytes).  One warp per run.
+template <int W>
+__device__ __forceinline__ void runs_body(const RunsDesc &d, uint64_t unit)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = kThreads / 32;
+    const uint64_t r0 = unit * d.runs_per_unit;
+    const uint64_t r1 = min(d.n_runs, r0 + d.runs_per_unit);
+    const uint64_t words = uint64_t(d.run_bytes) / W;
+    for (uint64_t r = r0 + warp; r < r1; r += NW) {
+        uint32_t q = uint32_t(r), dig;
+        int64_t off = 0;
+#pragma unroll
+        for (int i = kMaxRank - 1; i >= 0; --i) {
+            if (i < d.nd) {
+                fdivmod(q, d.div[i], q, dig);
+                off += int64_t(dig) * d.in_stride[i];
+            }
+        }
+        const char *s = d.src + off;
+        char *o = d.dst + int64_t(r) * d.run_bytes;
+        constexpr int U = 4;
+        for (uint64_t w0 = 0; w0 < words; w0 += 32 * U) {
+            typename Word<W>::T v[U];
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const uint64_t w = w0 + k * 32 + lane;
+                if (w < words) v[k] = ldg_stream<W>(s + w * W);
+            }
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const uint64_t w = w0 + k * 32 + lane;
+                if (w < words) stg<W>(o + w * W, v[k]);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Contiguous copy (Sec. III.A, the sequential read/write kernel): each thread
+// moves U words of W bytes per unit, all loads issued before the stores.
+template <int W>
+__device__ __forceinline__ void copy_body(const CopyDesc &d, uint64_t unit)
+{
+    constexpr int U = 4;
+    const uint64_t base = unit * d.unit_bytes;
+    typename Word<W>::T v[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        const uint64_t off = base + uint64_t(k * kThreads + threadIdx.x) * W;
+        if (off < d.bytes) v[k] = ldg_stream<W>(d.src + off);
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        const uint64_t off = base + uint64_t(k * kThreads + threadIdx.x) * W;
+        if (off < d.bytes) stg<W>(d.dst + off, v[k]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reorder by an index sequence (Sec. III.A, indexed access): dst[i] = src[idx[i]].
+
+template <int W>
+__device__ __forceinline__ void store4(char *p, const typename Word<W>::T (&v)[4])
+{
+    if constexpr (W == 1) {
+        stg<4>(p, uint32_t(v[0]) | (uint32_t(v[1]) << 8) | (uint32_t(v[2]) << 16) | (uint32_t(v[3]) << 24));
+    } else if constexpr (W == 2) {
+        stg<8>(p, make_uint2(uint32_t(v[0]) | (uint32_t(v[1]) << 16), uint32_t(v[2]) | (uint32_t(v[3]) << 16)));
+    } else if constexpr (W == 4) {
+        stg<16>(p, make_uint4(v[0], v[1], v[2], v[3]));
+    } else if constexpr (W == 8) {
+        stg<16>(p, make_uint4(v[0].x, v[0].y, v[1].x, v[1].y));
+        stg<16>(p + 16, make_uint4(v[2].x, v[2].y, v[3].x, v[3].y));
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) stg<16>(p + 16 * k, v[k]);
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void gather_body(const GatherDesc &d, uint64_t unit)
+{
+    using T = typename Word<W>::T;
+    const uint64_t e0 = unit * d.unit_elems;
+    const uint64_t e1 = min(d.n, e0 + d.unit_elems);
+    if (d.vec) {
+        // Groups of 4 consecutive elements per thread: one 16-byte index load,
+        // four independent source loads, one store of 4*W bytes.
+        constexpr int G = 2;  // groups per thread in flight
+        for (uint64_t g0 = e0; g0 < e1; g0 += uint64_t(kThreads) * 4 * G) {
+            T v[G][4];
+            bool full[G];
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                const uint64_t i = g0 + (uint64_t(k) * kThreads + threadIdx.x) * 4;
+                full[k] = i + 3 < e1;
+                if (full[k]) {
+                    const uint4 ix = ldg_stream<16>(d.idx + i);
+                    v[k][0] = ldg_any<W>(d.src + uint64_t(ix.x) * W);
+                    v[k][1] = ldg_any<W>(d.src + uint64_t(ix.y) * W);
+                    v[k][2] = ldg_any<W>(d.src + uint64_t(ix.z) * W);
+                    v[k][3] = ldg_any<W>(d.src + uint64_t(ix.w) * W);
+                } else {
+                    for (uint64_t j = i; j < e1 && j < i + 4; ++j)
+                        stg<W>(d.dst + j * W, ldg_any<W>(d.src + uint64_t(d.idx[j]) * W));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                const uint64_t i = g0 + (uint64_t(k) * kThreads + threadIdx.x) * 4;
+                if (full[k]) store4<W>(d.dst + i * W, v[k]);
+            }
+        }
+    } else {
+        // Any element size: c words per element, U elements per thread in flight.
+        constexpr int U = 4;
+        const uint32_t c = d.c;
+        for (uint64_t b0 = e0; b0 < e1; b0 += uint64_t(kThreads) * U) {
+            uint32_t src_i[U];
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const uint64_t i = b0 + uint64_t(k) * kThreads + threadIdx.x;
+                src_i[k] = i < e1 ? ldg_stream<4>(d.idx + i) : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const uint64_t i = b0 + uint64_t(k) * kThreads + threadIdx.x;
+                if (i < e1) {
+                    const char *s = d.src + uint64_t(src_i[k]) * c * W;
+                    char *o = d.dst + i * c * W;
+                    for (uint32_t w = 0; w < c; ++w) stg<W>(o + w * W, ldg_any<W>(s + w * W));
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Interlace / de-interlace (Sec. III.C).  The fast form works on 16-byte
+// groups: a thread reads one 16-byte group from each of the K planes
+// (V = 16/E records) and writes the K*16 interleaved bytes of those records
+// contiguously, re-interleaving in registers; de-interlace is the inverse.
+// Every byte move is fixed at compile time (word moves for E >= 4, PRMT byte
+// selects below that), so no shared memory is needed.
+
+template <int E, int K>
+__device__ __forceinline__ void interleave_regs(const uint32_t (&in)[K][4], uint32_t (&out)[K * 4])
+{
+#pragma unroll
+    for (int ow = 0; ow < K * 4; ++ow) {
+        if constexpr (E >= 4) {
+            const int ob = ow * 4, oe = ob / E, bb = ob % E;
+            const int i = oe / K, j = oe % K;
+            out[ow] = in[j][(i * E + bb) / 4];
+        } else {
+            uint32_t w = 0;
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const int ob = ow * 4 + p, oe = ob / E, bb = ob % E;
+                const int i = oe / K, j = oe % K, sb = i * E + bb;
+                // insert byte (sb & 3) of the source word at byte p of w
+                const uint32_t sel = (0x3210u & ~(0xFu << (4 * p))) | (uint32_t(4 + (sb & 3)) << (4 * p));
+                w = prmt(w, in[j][sb / 4], sel);
+            }
+            out[ow] = w;
+        }
+    }
+}
+
+template <int E, int K>
+__device__ __forceinline__ void deinterleave_regs(const uint32_t (&in)[K * 4], uint32_t (&out)[K][4])
+{
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+#pragma unroll
+        for (int pw = 0; pw < 4; ++pw) {
+            if constexpr (E >= 4) {
+                const int sb = pw * 4, i = sb / E, bb = sb % E;
+                const int ob = (i * K + j) * E + bb;
+                out[j][pw] = in[ob / 4];
+            } else {
+                uint32_t w = 0;
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const int sb = pw * 4 + p, i = sb / E, bb = sb % E;
+                    const int ob = (i * K + j) * E + bb;
+                    const uint32_t sel = (0x3210u & ~(0xFu << (4 * p))) | (uint32_t(4 + (ob & 3)) << (4 * p));
+                    w = prmt(w, in[ob / 4], sel);
+                }
+                out[j][pw] = w;
+            }
+        }
+    }
+}
+
+// Element-wise tail of an interlace / de-interlace: records [r0, n).
+template <int E>
+__device__ __forceinline__ void interlace_tail(const InterlaceDesc &d, char *const *planes, uint64_t r0,
+                                               bool inter)
+{
+    const uint64_t cnt = (d.n - r0) * d.k;
+    for (uint64_t f = threadIdx.x; f < cnt; f += kThreads) {
+        const uint64_t i = r0 + f / d.k;
+        const uint32_t j = uint32_t(f % d.k);
+        char *iv = d.inter + (i * d.k + j) * E;
+        char *pl = planes[j] + i * E;
+        if (inter) stg<E>(iv, lds<E>(pl));  // plain (coherent) loads: tail is tiny
+        else stg<E>(pl, lds<E>(iv));
+    }
+}
+
+template <int E, int K>
+__device__ __forceinline__ void interlace_fast_body(const InterlaceDesc &d, char *const *planes, uint64_t unit,
+                                                    uint64_t n_units)
+{
+    const uint64_t groups = d.n * E / 16;
+    const uint64_t g0 = unit * d.unit_groups;
+    const uint64_t g1 = min(groups, g0 + d.unit_groups);
+    for (uint64_t g = g0 + threadIdx.x; g < g1; g += kThreads) {
+        uint32_t in[K][4], out[K * 4];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const uint4 v = ldg_stream<16>(planes[j] + g * 16);
+            in[j][0] = v.x; in[j][1] = v.y; in[j][2] = v.z; in[j][3] = v.w;
+        }
+        interleave_regs<E, K>(in, out);
+        char *o = d.inter + g * 16 * K;
+#pragma unroll
+        for (int x = 0; x < K; ++x)
+            stg<16>(o + 16 * x, make_uint4(out[4 * x], out[4 * x + 1], out[4 * x + 2], out[4 * x + 3]));
+    }
+    if (unit == n_units - 1 && groups * 16 / E < d.n) interlace_tail<E>(d, planes, groups * 16 / E, true);
+}
+
+template <int E, int K>
+__device__ __forceinline__ void deinterlace_fast_body(const InterlaceDesc &d, char *const *planes, uint64_t unit,
+                                                      uint64_t n_units)
+{
+    const uint64_t groups = d.n * E / 16;
+    const uint64_t g0 = unit * d.unit_groups;
+    const uint64_t g1 = min(groups, g0 + d.unit_groups);
+    for (uint64_t g = g0 + threadIdx.x; g < g1; g += kThreads) {
+        uint32_t in[K * 4], out[K][4];
+        const char *s = d.inter + g * 16 * K;
+#pragma unroll
+        for (int x = 0; x < K; ++x) {
+            const uint4 v = ldg_stream<16>(s + 16 * x);
+            in[4 * x] = v.x; in[4 * x + 1] = v.y; in[4 * x + 2] = v.z; in[4 * x + 3] = v.w;
+        }
+        deinterleave_regs<E, K>(in, out);
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            stg<16>(planes[j] + g * 16, make_uint4(out[j][0], out[j][1], out[j][2], out[j][3]));
+    }
+    if (unit == n_units - 1 && groups * 16 / E < d.n) interlace_tail<E>(d, planes, groups * 16 / E, false);
+}
+
+// Generic interlace / de-interlace: any k, any element size (c words of W
+// bytes).  A unit covers unit_groups records; within it the interlaced words
+// are walked in order (coalesced on the interlaced side).
+template <int W>
+__device__ __forceinline__ void interlace_generic_body(const InterlaceDesc &d, char *const *planes, uint64_t unit,
+                                                       bool inter)
+{
+    const uint64_t r0 = unit * d.unit_groups;
+    const uint64_t r1 = min(d.n, r0 + d.unit_groups);
+    if (r0 >= r1) return;
+    const uint32_t kc = d.kc_div.d, c = d.c;
+    const uint32_t total = uint32_t(r1 - r0) * kc;
+    char *ibase = d.inter + r0 * kc * W;
+    constexpr int U = 4;
+    for (uint32_t base = 0; base < total; base += kThreads * U) {
+        typename Word<W>::T v[U];
+        char *dstp[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const uint32_t f = base + k * kThreads + threadIdx.x;
+            dstp[k] = nullptr;
+            if (f < total) {
+                uint32_t i, rem, j, w;
+                fdivmod(f, d.kc_div, i, rem);
+                fdivmod(rem, d.c_div, j, w);
+                char *pl = planes[j] + ((r0 + i) * c + w) * W;
+                char *iv = ibase + uint64_t(f) * W;
+                if (inter) { v[k] = ldg_stream<W>(pl); dstp[k] = iv; }
+                else { v[k] = ldg_stream<W>(iv); dstp[k] = pl; }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+            if (dstp[k]) stg<W>(dstp[k], v[k]);
+    }
+}
+
+}  // namespace rearr

@@ -1,0 +1,195 @@
+// k_single.cu -- one-launch-per-call kernels of librearr and their launcher.
+//
+// Each kernel runs one op: CTA i handles work units i, i + gridDim.x, ...
+// with the body of the op's class (bodies.cuh).
+#include <atomic>
+
+#include "bodies.cuh"
+#include "launch.h"
+
+namespace rearr {
+
+std::atomic<uint64_t> g_launches{0};
+
+template <int E, int VIN, int VOUT>
+__global__ void __launch_bounds__(kThreads) k_tile_fast(const __grid_constant__ TileDesc d, uint32_t n)
+{
+    __shared__ __align__(16) unsigned char smem[kTileBytes];
+    for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) tile_fast_body<E, VIN, VOUT>(d, t, smem);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_tile_cells(const __grid_constant__ TileDesc d, uint32_t n)
+{
+    __shared__ __align__(16) unsigned char smem[kSmemBytes];
+    for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) tile_cells_body<W>(d, t, smem);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_runs(const __grid_constant__ RunsDesc d, uint64_t n)
+{
+    for (uint64_t u = blockIdx.x; u < n; u += gridDim.x) runs_body<W>(d, u);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_copy(const __grid_constant__ CopyDesc d, uint64_t n)
+{
+    for (uint64_t u = blockIdx.x; u < n; u += gridDim.x) copy_body<W>(d, u);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_gather(const __grid_constant__ GatherDesc d, uint64_t n)
+{
+    for (uint64_t u = blockIdx.x; u < n; u += gridDim.x) gather_body<W>(d, u);
+}
+
+// Interlace kernels take every plane pointer by value.
+struct InterlaceParams {
+    InterlaceDesc d;
+    char *planes[kMaxK];
+};
+
+template <int E, int K, bool INTER>
+__global__ void __launch_bounds__(kThreads) k_inter_fast(const __grid_constant__ InterlaceParams p, uint64_t n)
+{
+    for (uint64_t u = blockIdx.x; u < n; u += gridDim.x) {
+        if constexpr (INTER) interlace_fast_body<E, K>(p.d, p.planes, u, n);
+        else deinterlace_fast_body<E, K>(p.d, p.planes, u, n);
+    }
+}
+
+template <int W, bool INTER>
+__global__ void __launch_bounds__(kThreads) k_inter_generic(const __grid_constant__ InterlaceParams p, uint64_t n)
+{
+    for (uint64_t u = blockIdx.x; u < n; u += gridDim.x) interlace_generic_body<W>(p.d, p.planes, u, INTER);
+}
+
+namespace {
+
+inline unsigned grid_for(uint64_t units)
+{
+    return unsigned(units < 0x7FFFFFFFull ? units : 0x7FFFFFFFull);
+}
+
+template <typename K, typename P, typename N>
+cudaError_t go(K kernel, uint64_t units, const P &param, N n, cudaStream_t s)
+{
+    kernel<<<grid_for(units), kThreads, 0, s>>>(param, n);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
+#define RT_CASE(E, VI, VO)                                                                    \
+    case tile_variant(E, VI, VO):                                                             \
+        return go(k_tile_fast<E, VI, VO>, op.units, op.tile, uint32_t(op.units), s);
+
+cudaError_t launch_tile_fast(const OpDesc &op, cudaStream_t s)
+{
+    switch (op.tile.variant) {
+        RT_CASE(1, 16, 4) RT_CASE(1, 4, 4) RT_CASE(1, 1, 4)
+        RT_CASE(1, 16, 1) RT_CASE(1, 4, 1) RT_CASE(1, 1, 1)
+        RT_CASE(2, 16, 8) RT_CASE(2, 4, 8) RT_CASE(2, 2, 8)
+        RT_CASE(2, 16, 4) RT_CASE(2, 4, 4) RT_CASE(2, 2, 4)
+        RT_CASE(2, 16, 2) RT_CASE(2, 4, 2) RT_CASE(2, 2, 2)
+        RT_CASE(4, 16, 16) RT_CASE(4, 4, 16) RT_CASE(4, 16, 4) RT_CASE(4, 4, 4)
+        RT_CASE(8, 16, 16) RT_CASE(8, 8, 16) RT_CASE(8, 16, 8) RT_CASE(8, 8, 8)
+        RT_CASE(16, 16, 16)
+        default: return cudaErrorInvalidValue;
+    }
+}
+#undef RT_CASE
+
+template <template <int> class Fn, typename... A>
+cudaError_t by_word(int W, A &&...a)
+{
+    switch (W) {
+        case 1: return Fn<1>::run(a...);
+        case 2: return Fn<2>::run(a...);
+        case 4: return Fn<4>::run(a...);
+        case 8: return Fn<8>::run(a...);
+        case 16: return Fn<16>::run(a...);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int W> struct RunCells {
+    static cudaError_t run(const OpDesc &op, cudaStream_t s)
+    {
+        return go(k_tile_cells<W>, op.units, op.tile, uint32_t(op.units), s);
+    }
+};
+template <int W> struct RunRuns {
+    static cudaError_t run(const OpDesc &op, cudaStream_t s) { return go(k_runs<W>, op.units, op.runs, op.units, s); }
+};
+template <int W> struct RunCopy {
+    static cudaError_t run(const OpDesc &op, cudaStream_t s) { return go(k_copy<W>, op.units, op.copy, op.units, s); }
+};
+template <int W> struct RunGather {
+    static cudaError_t run(const OpDesc &op, cudaStream_t s)
+    {
+        return go(k_gather<W>, op.units, op.gather, op.units, s);
+    }
+};
+
+template <int E, bool INTER>
+cudaError_t launch_inter_fast_k(const InterlaceParams &p, uint64_t units, cudaStream_t s)
+{
+    switch (p.d.k) {
+        case 1: return go(k_inter_fast<E, 1, INTER>, units, p, units, s);
+        case 2: return go(k_inter_fast<E, 2, INTER>, units, p, units, s);
+        case 3: return go(k_inter_fast<E, 3, INTER>, units, p, units, s);
+        case 4: return go(k_inter_fast<E, 4, INTER>, units, p, units, s);
+        case 5: return go(k_inter_fast<E, 5, INTER>, units, p, units, s);
+        case 6: return go(k_inter_fast<E, 6, INTER>, units, p, units, s);
+        case 7: return go(k_inter_fast<E, 7, INTER>, units, p, units, s);
+        case 8: return go(k_inter_fast<E, 8, INTER>, units, p, units, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <bool INTER>
+cudaError_t launch_inter(const InterlaceParams &p, const OpDesc &op, cudaStream_t s)
+{
+    if (p.d.fast) {
+        switch (p.d.elem_bytes) {
+            case 1: return launch_inter_fast_k<1, INTER>(p, op.units, s);
+            case 2: return launch_inter_fast_k<2, INTER>(p, op.units, s);
+            case 4: return launch_inter_fast_k<4, INTER>(p, op.units, s);
+            case 8: return launch_inter_fast_k<8, INTER>(p, op.units, s);
+            case 16: return launch_inter_fast_k<16, INTER>(p, op.units, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (op.word) {
+        case 1: return go(k_inter_generic<1, INTER>, op.units, p, op.units, s);
+        case 2: return go(k_inter_generic<2, INTER>, op.units, p, op.units, s);
+        case 4: return go(k_inter_generic<4, INTER>, op.units, p, op.units, s);
+        case 8: return go(k_inter_generic<8, INTER>, op.units, p, op.units, s);
+        case 16: return go(k_inter_generic<16, INTER>, op.units, p, op.units, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_single(const OpDesc &op, char *const *planes_all, cudaStream_t s)
+{
+    if (op.units == 0) return cudaSuccess;
+    switch (op.cls) {
+        case OC_TILE: return launch_tile_fast(op, s);
+        case OC_TILE_CELLS: return by_word<RunCells>(int(op.word), op, s);
+        case OC_RUNS: return by_word<RunRuns>(int(op.word), op, s);
+        case OC_COPY: return by_word<RunCopy>(int(op.word), op, s);
+        case OC_GATHER: return by_word<RunGather>(int(op.word), op, s);
+        case OC_INTERLACE:
+        case OC_DEINTERLACE: {
+            InterlaceParams p;
+            p.d = op.inter;
+            for (uint32_t j = 0; j < kMaxK; ++j) p.planes[j] = j < op.inter.k ? planes_all[j] : nullptr;
+            return op.cls == OC_INTERLACE ? launch_inter<true>(p, op, s) : launch_inter<false>(p, op, s);
+        }
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace rearr

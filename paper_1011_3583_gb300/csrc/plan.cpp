@@ -1,0 +1,452 @@
+// plan.cpp -- host plan compiler of librearr.
+//
+// A permute is brought to canonical form in the spirit of the paper's
+// "offset/striding approach" (arXiv:1011.3583 Sec. III.B):
+//   1. extent-1 axes are dropped;
+//   2. output axes that are adjacent and in order in the input are merged
+//      (stride[i] == stride[i+1] * extent[i+1]);
+//   3. an unmoved innermost axis (input stride 1 on the output's last axis)
+//      is folded into a wider cell; after that the output's fastest axis
+//      always differs from the input's fastest axis;
+//   4. the op is classified: a plain copy, long contiguous runs, or a tiled
+//      transpose on the plane of the input's fastest and the output's fastest
+//      axes with the other axes as batch (Sec. III.B: the 2-D plane of the
+//      fastest dimensions of the original and the desired order).
+#include "plan.h"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+namespace rearr {
+
+namespace {
+
+constexpr int64_t kMaxExtent = (int64_t(1) << 31) - 1;
+constexpr uint64_t kMaxUnits = 0xFFFFFFFFull;
+
+bool mul_overflows(uint64_t a, uint64_t b, uint64_t &out)
+{
+    if (a != 0 && b > UINT64_MAX / a) return true;
+    out = a * b;
+    return false;
+}
+
+bool ranges_overlap(uintptr_t a, uint64_t na, uintptr_t b, uint64_t nb)
+{
+    if (na == 0 || nb == 0) return false;
+    return a < b + nb && b < a + na;
+}
+
+struct Axis {
+    int64_t extent;
+    int64_t stride;  // input stride in cells
+};
+
+}  // namespace
+
+int pow2_align(uint64_t a, uint64_t b, uint64_t c, uint64_t d)
+{
+    const uint64_t v = a | b | c | d | 16;
+    return int(v & (~v + 1));  // lowest set bit, at most 16
+}
+
+static void fill_tile_common(TileDesc &t, const std::vector<Axis> &ax, int p, int64_t cell, int64_t DA,
+                             int64_t DB, char *dst, const char *src)
+{
+    const int R = int(ax.size());
+    // Output strides (cells) of the canonical output axes, row-major.
+    std::vector<int64_t> os(R);
+    os[R - 1] = 1;
+    for (int i = R - 2; i >= 0; --i) os[i] = os[i + 1] * ax[i + 1].extent;
+    t.dst = dst;
+    t.src = src;
+    t.sb_in = ax[R - 1].stride * cell;
+    t.sa_out = os[p] * cell;
+    t.DA = uint32_t(DA);
+    t.DB = uint32_t(DB);
+    int nb = 0;
+    for (int i = 0; i < R; ++i) {
+        if (i == p || i == R - 1) continue;
+        t.bin[nb] = ax[i].stride * cell;
+        t.bout[nb] = os[i] * cell;
+        t.bdiv[nb] = make_fastdiv(uint32_t(ax[i].extent));
+        ++nb;
+    }
+    for (int i = nb; i < kMaxBatch; ++i) {
+        t.bin[i] = 0;
+        t.bout[i] = 0;
+        t.bdiv[i] = make_fastdiv(1);
+    }
+    t.nb = nb;
+}
+
+rearr_status plan_permute(void *dst, const void *src, size_t elem_bytes, int rank, const int64_t *dims,
+                          const int *perm, PermPlan &pl, std::string &err)
+{
+    std::memset(&pl, 0, sizeof(pl));
+    rearr_permute_info &info = pl.info;
+    info.plane_a = -1;
+    if (elem_bytes == 0) { err = "elem_bytes must be >= 1"; return REARR_EINVAL; }
+    if (rank < 1 || rank > kMaxRank) { err = "rank must be in [1, 8]"; return REARR_EINVAL; }
+    if (!dims || !perm) { err = "dims and perm must not be NULL"; return REARR_EINVAL; }
+    bool seen[kMaxRank] = {false};
+    for (int i = 0; i < rank; ++i) {
+        if (dims[i] < 0) { err = "dims must be >= 0"; return REARR_EINVAL; }
+        if (perm[i] < 0 || perm[i] >= rank || seen[perm[i]]) {
+            err = "perm is not a permutation of 0..rank-1";
+            return REARR_EINVAL;
+        }
+        seen[perm[i]] = true;
+    }
+    uint64_t total = 1;
+    for (int i = 0; i < rank; ++i)
+        if (mul_overflows(total, uint64_t(dims[i]), total)) { err = "element count overflows"; return REARR_EINVAL; }
+    uint64_t bytes;
+    if (mul_overflows(total, elem_bytes, bytes) || bytes > (uint64_t(1) << 62)) {
+        err = "byte count overflows";
+        return REARR_EINVAL;
+    }
+    if (total == 0) {
+        info.kind = REARR_KIND_NOOP;
+        pl.op.units = 0;
+        return REARR_OK;
+    }
+    if (!dst || !src) { err = "dst and src must not be NULL"; return REARR_EINVAL; }
+    if (ranges_overlap(uintptr_t(dst), bytes, uintptr_t(src), bytes)) {
+        err = "dst overlaps src (in-place permute is not supported)";
+        return REARR_EINVAL;
+    }
+
+    // Row-major input strides, in elements.
+    int64_t s[kMaxRank];
+    s[rank - 1] = 1;
+    for (int i = rank - 2; i >= 0; --i) s[i] = s[i + 1] * dims[i + 1];
+
+    // Output axes with extent > 1, merged where adjacent and in order.
+    std::vector<Axis> ax;
+    for (int i = 0; i < rank; ++i) {
+        const int a = perm[i];
+        if (dims[a] == 1) continue;
+        Axis cur{dims[a], s[a]};
+        if (!ax.empty() && ax.back().stride == cur.stride * cur.extent) {
+            ax.back().extent *= cur.extent;
+            ax.back().stride = cur.stride;
+        } else {
+            ax.push_back(cur);
+        }
+    }
+    int64_t cell = int64_t(elem_bytes);
+    const uintptr_t da = uintptr_t(dst), sa = uintptr_t(src);
+
+    auto set_copy = [&]() {
+        info.kind = REARR_KIND_COPY;
+        info.rank = 1;
+        info.dims[0] = int64_t(total);
+        info.in_strides[0] = 1;
+        info.cell_bytes = int64_t(elem_bytes);
+        const int W = pow2_align(da, sa, bytes);
+        info.word_bytes = W;
+        OpDesc &op = pl.op;
+        op.cls = OC_COPY;
+        op.word = uint32_t(W);
+        op.copy.dst = static_cast<char *>(dst);
+        op.copy.src = static_cast<const char *>(src);
+        op.copy.bytes = bytes;
+        op.copy.unit_bytes = uint64_t(kThreads) * 4 * W;
+        op.units = (bytes + op.copy.unit_bytes - 1) / op.copy.unit_bytes;
+        info.n_tiles = int64_t(op.units);
+    };
+
+    if (ax.size() <= 1) {  // identity after dropping / merging
+        set_copy();
+        return REARR_OK;
+    }
+    // Fold an unmoved innermost axis into the cell.
+    if (ax.back().stride == 1) {
+        const int64_t inner = ax.back().extent;
+        cell *= inner;
+        ax.pop_back();
+        for (Axis &a : ax) a.stride /= inner;  // every other stride is a multiple of inner
+        if (ax.size() == 1 && ax[0].stride == 1) {
+            set_copy();
+            return REARR_OK;
+        }
+    }
+    const int R = int(ax.size());
+    info.rank = R;
+    for (int i = 0; i < R; ++i) {
+        info.dims[i] = ax[i].extent;
+        info.in_strides[i] = ax[i].stride;
+    }
+    info.cell_bytes = cell;
+    int p = -1;
+    for (int i = 0; i < R; ++i)
+        if (ax[i].stride == 1) p = i;
+
+    // Long cells: one warp copies each cell as a contiguous run.
+    if (cell >= 256 || p < 0) {
+        const int W = pow2_align(da, sa, uint64_t(cell));
+        uint64_t n_runs = 1;
+        for (int i = 0; i < R; ++i) n_runs *= uint64_t(ax[i].extent);
+        if (n_runs > kMaxUnits) { err = "too many runs"; return REARR_EINVAL; }
+        info.kind = REARR_KIND_RUNS;
+        info.word_bytes = W;
+        OpDesc &op = pl.op;
+        op.cls = OC_RUNS;
+        op.word = uint32_t(W);
+        RunsDesc &r = op.runs;
+        r.dst = static_cast<char *>(dst);
+        r.src = static_cast<const char *>(src);
+        r.run_bytes = cell;
+        r.nd = R;
+        for (int i = 0; i < kMaxRank; ++i) {
+            r.in_stride[i] = i < R ? ax[i].stride * cell : 0;
+            r.div[i] = make_fastdiv(i < R ? uint32_t(ax[i].extent) : 1u);
+        }
+        r.n_runs = n_runs;
+        // about 16 KB per unit, at least one run per warp
+        r.runs_per_unit = uint32_t(std::max<int64_t>(kThreads / 32, 16384 / cell));
+        op.units = (n_runs + r.runs_per_unit - 1) / r.runs_per_unit;
+        info.n_tiles = int64_t(op.units);
+        return REARR_OK;
+    }
+
+    info.plane_a = p;
+    const int64_t DA = ax[p].extent, DB = ax[R - 1].extent;
+    for (int i = 0; i < R; ++i)
+        if (ax[i].extent > kMaxExtent) { err = "a collapsed axis has 2^31 or more elements"; return REARR_EINVAL; }
+
+    OpDesc &op = pl.op;
+    TileDesc &t = op.tile;
+    fill_tile_common(t, ax, p, cell, DA, DB, static_cast<char *>(dst), static_cast<const char *>(src));
+    const int W = pow2_align(da, sa, uint64_t(cell));
+    info.word_bytes = W;
+    uint64_t batch = 1;
+    for (int i = 0; i < t.nb; ++i) batch *= t.bdiv[i].d;
+
+    if (W == cell) {
+        // Fast tile: one power-of-two element per cell.
+        const int E = int(cell);
+        static const int TAs[17] = {0, 128, 128, 0, 64, 0, 0, 0, 32, 0, 0, 0, 0, 0, 0, 0, 16};
+        static const int TBs[17] = {0, 128, 64, 0, 64, 0, 0, 0, 64, 0, 0, 0, 0, 0, 0, 0, 64};
+        t.TA = uint32_t(TAs[E]);
+        t.TB = uint32_t(TBs[E]);
+        // Widest legal global access on each side: every input row starts at a
+        // multiple of DA*E bytes from src, every output row at a multiple of
+        // DB*E bytes from dst.
+        int vin = E;
+        for (int v : {16, 4}) {
+            if (v > E && (uint64_t(DA) * E) % v == 0 && sa % v == 0) { vin = v; break; }
+        }
+        int vout = E;
+        const int vmax = std::min(16, 4 * E);
+        for (int v : {vmax, 4}) {
+            if (v > E && (uint64_t(DB) * E) % v == 0 && da % v == 0) { vout = v; break; }
+        }
+        info.kind = REARR_KIND_TILE;
+        info.vec_in = vin;
+        info.vec_out = vout;
+        t.variant = tile_variant(E, vin, vout);
+        t.c = 1;
+        t.pitch = 0;
+        op.cls = OC_TILE;
+    } else {
+        const int64_t c = cell / W;
+        int64_t TA = std::max<int64_t>(1, std::min<int64_t>(DA, 256 / cell));
+        int64_t TB = std::max<int64_t>(1, std::min<int64_t>(DB, 16384 / (TA * cell)));
+        if (TB == DB) TA = std::max<int64_t>(1, std::min<int64_t>(DA, 16384 / (TB * cell)));
+        auto pitch_of = [&](int64_t ta) {
+            const int64_t rw = ta * c;
+            const int64_t pad = ((c - rw) % 32 + 32) % 32;
+            return rw + pad;
+        };
+        while (TB > 1 && TB * pitch_of(TA) * W > kSmemBytes) --TB;
+        while (TA > 1 && TB * pitch_of(TA) * W > kSmemBytes) --TA;
+        info.kind = REARR_KIND_TILE_CELLS;
+        t.TA = uint32_t(TA);
+        t.TB = uint32_t(TB);
+        t.c = uint32_t(c);
+        t.pitch = uint32_t(pitch_of(TA));
+        t.rowwords_div = make_fastdiv(uint32_t(TA * c));
+        t.outwords_div = make_fastdiv(uint32_t(TB * c));
+        t.c_div = make_fastdiv(uint32_t(c));
+        t.variant = uint32_t(W);
+        op.cls = OC_TILE_CELLS;
+    }
+    info.tile_a = int(t.TA);
+    info.tile_b = int(t.TB);
+    const uint64_t ta_tiles = (uint64_t(DA) + t.TA - 1) / t.TA;
+    const uint64_t tb_tiles = (uint64_t(DB) + t.TB - 1) / t.TB;
+    const uint64_t units = ta_tiles * tb_tiles * batch;
+    if (units > kMaxUnits || ta_tiles > kMaxUnits || tb_tiles > kMaxUnits) {
+        err = "too many tiles";
+        return REARR_EINVAL;
+    }
+    t.ta_div = make_fastdiv(uint32_t(ta_tiles));
+    t.tb_div = make_fastdiv(uint32_t(tb_tiles));
+    op.word = uint32_t(W);
+    op.units = units;
+    info.n_tiles = int64_t(units);
+    return REARR_OK;
+}
+
+rearr_status plan_reorder(void *dst, const void *src, const uint32_t *idx, size_t n, size_t elem_bytes,
+                          OpDesc &op, std::string &err)
+{
+    std::memset(&op, 0, sizeof(op));
+    if (elem_bytes == 0) { err = "elem_bytes must be >= 1"; return REARR_EINVAL; }
+    uint64_t bytes;
+    if (mul_overflows(n, elem_bytes, bytes) || bytes > (uint64_t(1) << 62)) {
+        err = "byte count overflows";
+        return REARR_EINVAL;
+    }
+    if (n > 0xFFFFFFFFull + 1) { err = "n exceeds the uint32 index range"; return REARR_EINVAL; }
+    if (n == 0) { op.units = 0; return REARR_OK; }
+    if (!dst || !src || !idx) { err = "dst, src and idx must not be NULL"; return REARR_EINVAL; }
+    const uintptr_t da = uintptr_t(dst), sa = uintptr_t(src), ia = uintptr_t(idx);
+    if (ranges_overlap(da, bytes, sa, bytes) || ranges_overlap(da, bytes, ia, uint64_t(n) * 4)) {
+        err = "dst overlaps src or idx";
+        return REARR_EINVAL;
+    }
+    if (ia % 4 != 0) { err = "idx must be 4-byte aligned"; return REARR_EINVAL; }
+    const int W = pow2_align(da, sa, elem_bytes);
+    op.cls = OC_GATHER;
+    op.word = uint32_t(W);
+    GatherDesc &g = op.gather;
+    g.dst = static_cast<char *>(dst);
+    g.src = static_cast<const char *>(src);
+    g.idx = idx;
+    g.n = n;
+    g.c = uint32_t(elem_bytes / W);
+    g.vec = (g.c == 1 && ia % 16 == 0 && da % uint64_t(std::min(16, 4 * W)) == 0) ? 1u : 0u;
+    g.unit_elems = g.vec ? uint32_t(kThreads) * 32 : uint32_t(kThreads) * 16;
+    op.units = (uint64_t(n) + g.unit_elems - 1) / g.unit_elems;
+    return REARR_OK;
+}
+
+rearr_status plan_interlace(bool inter, char *interlaced, char *const *planes, int k, size_t n,
+                            size_t elem_bytes, InterlacePlan &pl, std::string &err)
+{
+    std::memset(&pl.op, 0, sizeof(pl.op));
+    pl.planes.clear();
+    if (elem_bytes == 0) { err = "elem_bytes must be >= 1"; return REARR_EINVAL; }
+    if (k < 1 || k > kMaxK) { err = "k must be in [1, 256]"; return REARR_EINVAL; }
+    if (!planes) { err = "the plane pointer array must not be NULL"; return REARR_EINVAL; }
+    uint64_t pbytes, ibytes;
+    if (mul_overflows(n, elem_bytes, pbytes) || mul_overflows(pbytes, uint64_t(k), ibytes) ||
+        ibytes > (uint64_t(1) << 62)) {
+        err = "byte count overflows";
+        return REARR_EINVAL;
+    }
+    if (n == 0) { pl.op.units = 0; return REARR_OK; }
+    if (!interlaced) { err = "the interlaced array pointer must not be NULL"; return REARR_EINVAL; }
+    uint64_t align_or = uintptr_t(interlaced);
+    for (int j = 0; j < k; ++j) {
+        if (!planes[j]) { err = "a plane pointer is NULL"; return REARR_EINVAL; }
+        if (ranges_overlap(uintptr_t(planes[j]), pbytes, uintptr_t(interlaced), ibytes)) {
+            err = "a plane overlaps the interlaced array";
+            return REARR_EINVAL;
+        }
+        align_or |= uintptr_t(planes[j]);
+        pl.planes.push_back(planes[j]);
+    }
+    if (!inter) {  // de-interlace writes the planes: they must not overlap each other
+        std::vector<std::pair<uintptr_t, int>> order;
+        for (int j = 0; j < k; ++j) order.push_back({uintptr_t(planes[j]), j});
+        std::sort(order.begin(), order.end());
+        for (int j = 1; j < k; ++j)
+            if (order[j - 1].first + pbytes > order[j].first) {
+                err = "destination planes overlap";
+                return REARR_EINVAL;
+            }
+    }
+    OpDesc &op = pl.op;
+    InterlaceDesc &d = op.inter;
+    op.cls = inter ? OC_INTERLACE : OC_DEINTERLACE;
+    d.inter = interlaced;
+    for (int j = 0; j < kInlineK; ++j) d.planes[j] = j < k ? planes[j] : nullptr;
+    d.planes_dev = nullptr;
+    d.n = n;
+    d.k = uint32_t(k);
+    d.elem_bytes = uint32_t(elem_bytes);
+    const bool pow2e = elem_bytes == 1 || elem_bytes == 2 || elem_bytes == 4 || elem_bytes == 8 ||
+                       elem_bytes == 16;
+    d.fast = (pow2e && k <= 8 && align_or % 16 == 0) ? 1u : 0u;
+    if (d.fast) {
+        const uint64_t groups = uint64_t(n) * elem_bytes / 16;
+        op.word = uint32_t(elem_bytes);
+        d.c = 1;
+        d.unit_groups = uint64_t(kThreads) * 4;
+        op.units = std::max<uint64_t>(1, (groups + d.unit_groups - 1) / d.unit_groups);
+    } else {
+        const int W = pow2_align(align_or, elem_bytes);
+        op.word = uint32_t(W);
+        d.c = uint32_t(elem_bytes / W);
+        const uint64_t kc = uint64_t(k) * d.c;
+        if (kc > 0xFFFFFFFFull) { err = "k * elem_bytes too large"; return REARR_EINVAL; }
+        d.unit_groups = std::max<uint64_t>(1, 8192 / kc);
+        d.kc_div = make_fastdiv(uint32_t(kc));
+        d.c_div = make_fastdiv(d.c);
+        op.units = (uint64_t(n) + d.unit_groups - 1) / d.unit_groups;
+    }
+    return REARR_OK;
+}
+
+bool selftest_host(std::string &err)
+{
+    // Fast division against the hardware divide on divisors and dividends
+    // near powers of two, small values and pseudo-random values.
+    std::vector<uint32_t> ds, ns;
+    for (uint32_t v = 1; v < 300; ++v) ds.push_back(v);
+    for (int b = 1; b < 32; ++b) {
+        const uint32_t p = uint32_t(1) << b;
+        ds.push_back(p - 1); ds.push_back(p); ds.push_back(p + 1);
+    }
+    ds.push_back(0xFFFFFFFFu); ds.push_back(0xFFFFFFFEu); ds.push_back(0x80000001u);
+    uint64_t x = 0x9E3779B97F4A7C15ull;
+    for (int i = 0; i < 200; ++i) {
+        x ^= x << 13; x ^= x >> 7; x ^= x << 17;
+        ds.push_back(uint32_t(x) | 1u);
+        ds.push_back(uint32_t(x >> 40) + 1u);
+        ns.push_back(uint32_t(x >> 3));
+    }
+    for (uint32_t v = 0; v < 1000; ++v) ns.push_back(v);
+    for (int b = 1; b < 32; ++b) {
+        const uint32_t p = uint32_t(1) << b;
+        ns.push_back(p - 1); ns.push_back(p); ns.push_back(p + 1);
+    }
+    ns.push_back(0xFFFFFFFFu); ns.push_back(0xFFFFFFFEu);
+    for (uint32_t d : ds) {
+        const FastDiv f = make_fastdiv(d);
+        for (uint32_t n : ns) {
+            uint32_t q, r;
+            fdivmod(n, f, q, r);
+            if (q != n / d || r != n % d) {
+                char buf[128];
+                std::snprintf(buf, sizeof buf, "fastdiv %u / %u gave %u r %u", n, d, q, r);
+                err = buf;
+                return false;
+            }
+        }
+        // every multiple boundary of small quotients
+        for (uint64_t m = 1; m < 5; ++m) {
+            const uint64_t n = m * d;
+            if (n > 0xFFFFFFFFull) break;
+            for (int off = -1; off <= 1; ++off) {
+                const uint64_t nn = n + off;
+                if (nn > 0xFFFFFFFFull) continue;
+                uint32_t q, r;
+                fdivmod(uint32_t(nn), f, q, r);
+                if (q != uint32_t(nn / d) || r != uint32_t(nn % d)) { err = "fastdiv boundary"; return false; }
+            }
+        }
+    }
+    if (pow2_align(0) != 16 || pow2_align(12) != 4 || pow2_align(1024, 6) != 2 || pow2_align(3) != 1) {
+        err = "pow2_align";
+        return false;
+    }
+    return true;
+}
+
+}  // namespace rearr

@@ -1,0 +1,169 @@
+// rearr_internal.h -- descriptors shared by the host plan compiler and the
+// device kernels of librearr.  Plain structs, usable from host C++ and CUDA.
+#pragma once
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __CUDACC__
+#define RH_HD __host__ __device__ inline
+#else
+#define RH_HD inline
+#endif
+
+namespace rearr {
+
+constexpr int kMaxRank = 8;
+constexpr int kMaxBatch = 6;   // batch axes of a tiled transpose (rank - 2)
+constexpr int kMaxK = 256;     // planes of an interlace
+constexpr int kInlineK = 8;    // planes kept inline in a descriptor
+constexpr int kThreads = 256;  // threads per CTA of every tile kernel
+constexpr int kTileBytes = 16384;               // payload of one fast tile
+constexpr int kCellSmemBytes = 16384 + 4096;    // cells tile incl. padding
+constexpr int kSmemBytes = 20480;               // smem of any tile body
+
+// Unsigned 32-bit division by a run-time invariant divisor with one
+// multiply-high, a subtract, an add and two shifts (Granlund & Montgomery,
+// "Division by invariant integers using multiplication", PLDI 1994, Sec. 4):
+// with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+//     t = mulhi(m, n),  q = (t + ((n - t) >> min(l,1))) >> max(l-1,0)
+// is floor(n / d) for every 0 <= n < 2^32.
+struct FastDiv {
+    uint32_t d;
+    uint32_t m;
+    uint32_t s1;
+    uint32_t s2;
+};
+
+inline FastDiv make_fastdiv(uint32_t d)
+{
+    FastDiv f;
+    f.d = d ? d : 1;
+    uint32_t l = 0;
+    while (l < 32 && (uint64_t(1) << l) < f.d) ++l;
+    f.m = uint32_t(((uint64_t(1) << 32) * ((uint64_t(1) << l) - f.d)) / f.d + 1);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l > 0 ? l - 1 : 0;
+    return f;
+}
+
+RH_HD uint32_t mulhi32(uint32_t a, uint32_t b)
+{
+#ifdef __CUDA_ARCH__
+    return __umulhi(a, b);
+#else
+    return uint32_t((uint64_t(a) * b) >> 32);
+#endif
+}
+
+RH_HD uint32_t fdiv(uint32_t n, const FastDiv &f)
+{
+    uint32_t t = mulhi32(f.m, n);
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
+RH_HD void fdivmod(uint32_t n, const FastDiv &f, uint32_t &q, uint32_t &r)
+{
+    q = fdiv(n, f);
+    r = n - q * f.d;
+}
+
+// ---------------------------------------------------------------------------
+// Op classes of the work list.  Each maps to one device body.
+enum OpClass : uint32_t {
+    OC_COPY = 0,         // contiguous copy, W-byte words
+    OC_TILE = 1,         // fast tiled transpose (cell = one E-byte element)
+    OC_TILE_CELLS = 2,   // tiled transpose of cells of c W-byte words
+    OC_RUNS = 3,         // long contiguous runs, one warp per run
+    OC_GATHER = 4,       // dst[i] = src[idx[i]]
+    OC_INTERLACE = 5,    // dst[i*k+j] = src_j[i]
+    OC_DEINTERLACE = 6,  // dst_j[i] = src[i*k+j]
+    OC_COUNT = 7
+};
+
+// Plane of a tiled transpose: A = input-innermost axis (input stride one
+// cell), B = output-innermost axis (output stride one cell).  The remaining
+// collapsed axes are batch axes.  Strides are in bytes.
+struct TileDesc {
+    char *dst;
+    const char *src;
+    int64_t sb_in;        // input stride of B
+    int64_t sa_out;       // output stride of A
+    int64_t bin[kMaxBatch], bout[kMaxBatch];
+    FastDiv bdiv[kMaxBatch];   // batch extents, innermost batch axis last
+    FastDiv ta_div, tb_div;    // tile counts along A and B
+    uint32_t DA, DB;           // plane extents in cells
+    uint32_t TA, TB;           // tile extents in cells (cells path: run-time)
+    uint32_t c;                // words per cell (cells path)
+    uint32_t pitch;            // smem row pitch in words (cells path)
+    FastDiv rowwords_div;      // TA*c        (cells path)
+    FastDiv outwords_div;      // TB*c        (cells path)
+    FastDiv c_div;             // c           (cells path)
+    int32_t nb;                // number of batch axes
+    uint32_t variant;          // template variant id (fast path: E/VIN/VOUT)
+};
+
+// Long contiguous runs: the output is a sequence of runs of run_bytes, run r
+// comes from the input at sum_i digit_i(r) * in_stride_i.
+struct RunsDesc {
+    char *dst;
+    const char *src;
+    int64_t run_bytes;
+    int64_t in_stride[kMaxRank];  // bytes, per outer axis
+    FastDiv div[kMaxRank];        // outer extents, innermost last
+    int32_t nd;                   // number of outer axes
+    uint32_t runs_per_unit;       // runs handled per work unit
+    uint64_t n_runs;
+};
+
+struct CopyDesc {
+    char *dst;
+    const char *src;
+    uint64_t bytes;
+    uint64_t unit_bytes;   // bytes per work unit
+};
+
+struct GatherDesc {
+    char *dst;
+    const char *src;
+    const uint32_t *idx;
+    uint64_t n;
+    uint32_t c;            // words per element
+    uint32_t unit_elems;   // elements per work unit
+    uint32_t vec;          // 1: aligned 4-element groups with vector stores
+};
+
+struct InterlaceDesc {
+    char *inter;                       // interlaced array (dst of interlace, src of de-interlace)
+    char *planes[kInlineK];            // plane pointers when k <= kInlineK
+    char *const *planes_dev;           // device array of k plane pointers otherwise
+    uint64_t n;                        // records (elements per plane)
+    uint32_t k;
+    uint32_t c;                        // words per element
+    uint32_t fast;                     // 1: 16-byte group kernel for (E, k)
+    uint32_t elem_bytes;
+    uint64_t unit_groups;              // 16-byte groups (fast) or words (generic) per unit
+    FastDiv kc_div, c_div;             // k*c and c (generic path)
+};
+
+// One op of a batched work list.
+struct OpDesc {
+    uint32_t cls;       // OpClass
+    uint32_t word;      // word bytes W (1, 2, 4, 8, 16)
+    uint64_t units;     // work units (tiles) of this op
+    union {
+        TileDesc tile;
+        RunsDesc runs;
+        CopyDesc copy;
+        GatherDesc gather;
+        InterlaceDesc inter;
+    };
+};
+
+// Fast-tile variant ids: E in {1,2,4,8,16} x VIN x VOUT.
+constexpr RH_HD uint32_t tile_variant(int E, int vin, int vout)
+{
+    return uint32_t(E) | (uint32_t(vin) << 8) | (uint32_t(vout) << 16);
+}
+
+}  // namespace rearr

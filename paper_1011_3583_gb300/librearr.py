@@ -1,0 +1,232 @@
+"""Thin ctypes binding of the librearr C ABI (include/librearr.h).
+
+Argument marshalling only: every call goes straight to the C entry point of
+the same name, and every byte is moved by the library's CUDA kernels.
+Pointers may be given as integers or as objects with ``data_ptr()`` (torch
+tensors); streams as integers (cudaStream_t values), ``None`` (the legacy
+default stream) or objects with a ``cuda_stream`` attribute (torch streams).
+
+The library must have been built (``paper_1011_3583_gb300.build.build()``);
+importing this module without it raises, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+from .build import LIB
+
+MAX_RANK = 8
+MAX_K = 256
+
+STATUS = {0: "REARR_OK", 1: "REARR_EINVAL", 2: "REARR_ENOMEM", 3: "REARR_ECUDA", 4: "REARR_ERANGE",
+          5: "REARR_ETIMEDOUT", 6: "REARR_EBUSY"}
+OK, EINVAL, ENOMEM, ECUDA, ERANGE, ETIMEDOUT, EBUSY = range(7)
+KIND_NAMES = {0: "noop", 1: "copy", 2: "tile", 3: "tile_cells", 4: "runs"}
+
+
+class RearrError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class PermuteInfo(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("rank", ctypes.c_int), ("dims", ctypes.c_int64 * 8),
+                ("in_strides", ctypes.c_int64 * 8), ("cell_bytes", ctypes.c_int64), ("word_bytes", ctypes.c_int),
+                ("plane_a", ctypes.c_int), ("vec_in", ctypes.c_int), ("vec_out", ctypes.c_int),
+                ("tile_a", ctypes.c_int), ("tile_b", ctypes.c_int), ("n_tiles", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        r = self.rank
+        return dict(kind=KIND_NAMES.get(self.kind, self.kind), rank=r, dims=list(self.dims[:r]),
+                    in_strides=list(self.in_strides[:r]), cell_bytes=self.cell_bytes, word_bytes=self.word_bytes,
+                    plane_a=self.plane_a, vec_in=self.vec_in, vec_out=self.vec_out, tile_a=self.tile_a,
+                    tile_b=self.tile_b, n_tiles=self.n_tiles)
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load librearr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise ImportError(f"librearr is not built ({LIB} missing); run paper_1011_3583_gb300.build.build()")
+    L = ctypes.CDLL(LIB)
+    vp, sz, i64p, ip = ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int)
+    st = ctypes.c_int
+    sigs = {
+        "rearr_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+        "rearr_last_error": (ctypes.c_char_p, []),
+        "rearr_permute": (st, [vp, vp, sz, ctypes.c_int, i64p, ip, vp]),
+        "rearr_reorder": (st, [vp, vp, vp, sz, sz, vp]),
+        "rearr_interlace": (st, [vp, ctypes.POINTER(vp), ctypes.c_int, sz, sz, vp]),
+        "rearr_deinterlace": (st, [ctypes.POINTER(vp), vp, ctypes.c_int, sz, sz, vp]),
+        "rearr_plan_create": (st, [ctypes.POINTER(vp)]),
+        "rearr_plan_add_permute": (st, [vp, vp, vp, sz, ctypes.c_int, i64p, ip]),
+        "rearr_plan_add_reorder": (st, [vp, vp, vp, vp, sz, sz]),
+        "rearr_plan_add_interlace": (st, [vp, vp, ctypes.POINTER(vp), ctypes.c_int, sz, sz]),
+        "rearr_plan_add_deinterlace": (st, [vp, ctypes.POINTER(vp), vp, ctypes.c_int, sz, sz]),
+        "rearr_plan_finalize": (st, [vp, vp]),
+        "rearr_batch": (st, [vp, vp]),
+        "rearr_plan_destroy": (None, [vp]),
+        "rearr_plan_stats": (st, [vp, i64p, i64p]),
+        "rearr_permute_describe": (st, [sz, ctypes.c_int, i64p, ip, ctypes.c_size_t, ctypes.c_size_t,
+                                        ctypes.POINTER(PermuteInfo)]),
+        "rearr_memcpy_d2d": (st, [vp, vp, sz, vp]),
+        "rearr_launch_count": (ctypes.c_uint64, []),
+        "rearr_selftest_host": (st, []),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    raise TypeError(f"cannot take a device pointer from {type(x).__name__}")
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    if hasattr(s, "cuda_stream"):
+        return int(s.cuda_stream)
+    raise TypeError(f"cannot take a stream from {type(s).__name__}")
+
+
+def _check(status: int) -> None:
+    if status != OK:
+        msg = load().rearr_last_error().decode(errors="replace")
+        raise RearrError(status, msg)
+
+
+def _dims_perm(dims: Sequence[int], perm: Sequence[int]):
+    rank = len(dims)
+    d = (ctypes.c_int64 * max(rank, 1))(*[int(v) for v in dims])
+    p = (ctypes.c_int * max(len(perm), 1))(*[int(v) for v in perm])
+    return rank, d, p
+
+
+def _ptr_array(ptrs) -> ctypes.Array:
+    vals = [_ptr(p) for p in ptrs]
+    return (ctypes.c_void_p * max(len(vals), 1))(*vals)
+
+
+def status_str(status: int) -> str:
+    return load().rearr_status_str(status).decode()
+
+
+def permute(dst, src, elem_bytes: int, dims: Sequence[int], perm: Sequence[int], stream=None) -> None:
+    """rearr_permute: dst = src transposed by perm (numpy semantics, row-major)."""
+    rank, d, p = _dims_perm(dims, perm)
+    _check(load().rearr_permute(_ptr(dst), _ptr(src), int(elem_bytes), rank, d, p, _stream(stream)))
+
+
+def reorder(dst, src, idx, n: int, elem_bytes: int, stream=None) -> None:
+    """rearr_reorder: dst[i] = src[idx[i]]."""
+    _check(load().rearr_reorder(_ptr(dst), _ptr(src), _ptr(idx), int(n), int(elem_bytes), _stream(stream)))
+
+
+def interlace(dst, srcs: Sequence, n: int, elem_bytes: int, stream=None) -> None:
+    """rearr_interlace: dst[i*k + j] = srcs[j][i]."""
+    arr = _ptr_array(srcs)
+    _check(load().rearr_interlace(_ptr(dst), arr, len(srcs), int(n), int(elem_bytes), _stream(stream)))
+
+
+def deinterlace(dsts: Sequence, src, n: int, elem_bytes: int, stream=None) -> None:
+    """rearr_deinterlace: dsts[j][i] = src[i*k + j]."""
+    arr = _ptr_array(dsts)
+    _check(load().rearr_deinterlace(arr, _ptr(src), len(dsts), int(n), int(elem_bytes), _stream(stream)))
+
+
+def describe_permute(elem_bytes: int, dims: Sequence[int], perm: Sequence[int], dst_addr: int = 0,
+                     src_addr: int = 0) -> dict:
+    """rearr_permute_describe: the canonical plan of a permute (host only)."""
+    rank, d, p = _dims_perm(dims, perm)
+    info = PermuteInfo()
+    _check(load().rearr_permute_describe(int(elem_bytes), rank, d, p, int(dst_addr), int(src_addr),
+                                         ctypes.byref(info)))
+    return info.as_dict()
+
+
+def memcpy_d2d(dst, src, nbytes: int, stream=None) -> None:
+    """rearr_memcpy_d2d: cudaMemcpyAsync device to device (measurement reference)."""
+    _check(load().rearr_memcpy_d2d(_ptr(dst), _ptr(src), int(nbytes), _stream(stream)))
+
+
+def launch_count() -> int:
+    return int(load().rearr_launch_count())
+
+
+def selftest_host() -> None:
+    _check(load().rearr_selftest_host())
+
+
+class Plan:
+    """A batched plan (rearr_plan_*): add ops, finalize once, replay with run()."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check(load().rearr_plan_create(ctypes.byref(h)))
+        self._h = h
+        self._keep = []  # host arrays kept alive until finalize
+
+    @property
+    def handle(self) -> int:
+        return int(self._h.value or 0)
+
+    def add_permute(self, dst, src, elem_bytes: int, dims, perm) -> None:
+        rank, d, p = _dims_perm(dims, perm)
+        _check(load().rearr_plan_add_permute(self._h, _ptr(dst), _ptr(src), int(elem_bytes), rank, d, p))
+
+    def add_reorder(self, dst, src, idx, n: int, elem_bytes: int) -> None:
+        _check(load().rearr_plan_add_reorder(self._h, _ptr(dst), _ptr(src), _ptr(idx), int(n), int(elem_bytes)))
+
+    def add_interlace(self, dst, srcs, n: int, elem_bytes: int) -> None:
+        arr = _ptr_array(srcs)
+        _check(load().rearr_plan_add_interlace(self._h, _ptr(dst), arr, len(srcs), int(n), int(elem_bytes)))
+
+    def add_deinterlace(self, dsts, src, n: int, elem_bytes: int) -> None:
+        arr = _ptr_array(dsts)
+        _check(load().rearr_plan_add_deinterlace(self._h, arr, _ptr(src), len(dsts), int(n), int(elem_bytes)))
+
+    def finalize(self, stream=None) -> None:
+        _check(load().rearr_plan_finalize(self._h, _stream(stream)))
+
+    def run(self, stream=None) -> None:
+        _check(load().rearr_batch(self._h, _stream(stream)))
+
+    def stats(self) -> tuple[int, int]:
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().rearr_plan_stats(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def close(self) -> None:
+        if self._h is not None and self._h.value:
+            load().rearr_plan_destroy(self._h)
+        self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

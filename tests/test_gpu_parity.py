@@ -1,0 +1,335 @@
+"""GPU results of every librearr operation against the CPU oracle, bit for bit.
+
+Sizes are small enough for the oracle to finish in seconds but span several
+tiles with ragged tails; every call goes through the C ABI (ctypes binding).
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import DevBuf, sync, to_dev
+
+pytestmark = pytest.mark.gpu
+
+ELEMS = (1, 2, 3, 4, 6, 8, 12, 16, 24, 40, 300)
+
+
+@pytest.fixture(scope="module")
+def lr():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1011_3583_gb300 import build, librearr
+    build.build()
+    librearr.load()
+    return librearr
+
+
+@pytest.fixture(scope="module")
+def orc():
+    return oracle.get()
+
+
+def run_permute(lr, src_np, e, dims, perm, src_off=0, dst_off=0):
+    n = int(np.prod(dims, dtype=np.int64))
+    s = to_dev(src_np, src_off)
+    d = DevBuf(n * e, dst_off, fill=0xA5)
+    lr.permute(d.ptr, s.ptr, e, dims, perm)
+    sync()
+    return d.download()
+
+
+def check_permute(lr, orc, seed, e, dims, perm, src_off=0, dst_off=0):
+    n = int(np.prod(dims, dtype=np.int64))
+    src = synth.random_elements(seed, n, e)
+    got = run_permute(lr, src, e, dims, perm, src_off, dst_off)
+    want = orc.permute(src, e, dims, perm)
+    if not np.array_equal(got, want):
+        bad = np.flatnonzero(got != want)
+        raise AssertionError(f"permute dims={dims} perm={perm} e={e} offs=({src_off},{dst_off}): "
+                             f"{bad.size} bytes differ, first at byte {bad[0]}; "
+                             f"plan={lr.describe_permute(e, dims, perm, 0, 0)}")
+
+
+def test_permute_random_shapes(lr, orc):
+    g = synth.rng(101)
+    for t in range(160):
+        rank = int(g.integers(1, 9))
+        e = ELEMS[t % len(ELEMS)]
+        budget = 400_000 // e
+        dims = [int(g.integers(1, 80 if rank <= 3 else 12)) for _ in range(rank)]
+        while int(np.prod(dims)) > budget:
+            dims[int(np.argmax(dims))] //= 2
+        perm = [int(v) for v in g.permutation(rank)]
+        check_permute(lr, orc, 1000 + t, e, dims, perm)
+
+
+@pytest.mark.parametrize("e", [1, 2, 4, 8, 16])
+def test_permute_rank3_all_orders(lr, orc, e):
+    dims = [67, 130, 129] if e <= 4 else [33, 70, 65]
+    for perm in itertools.permutations(range(3)):
+        check_permute(lr, orc, 77 + e, e, dims, list(perm))
+
+
+@pytest.mark.parametrize("e", [1, 2, 4, 8])
+def test_permute_rank4_all_orders(lr, orc, e):
+    dims = [9, 33, 70, 17]
+    for perm in itertools.permutations(range(4)):
+        check_permute(lr, orc, 99 + e, e, dims, list(perm))
+
+
+@pytest.mark.parametrize("e", [1, 2, 4, 8])
+def test_permute_aligned_fast_paths(lr, orc, e):
+    # power-of-two extents: 16-byte vectors on both sides, several tiles
+    for dims, perm in [([256, 320], [1, 0]), ([16, 64, 96], [2, 0, 1]), ([8, 32, 16, 64], [3, 1, 0, 2]),
+                       ([4, 96, 128], [0, 2, 1]), ([2, 3, 64, 128], [1, 0, 3, 2])]:
+        check_permute(lr, orc, 5 + e, e, dims, perm)
+
+
+@pytest.mark.parametrize("src_off,dst_off", [(1, 0), (0, 1), (2, 6), (4, 0), (0, 4), (8, 8), (12, 4), (3, 5)])
+def test_permute_unaligned_pointers(lr, orc, src_off, dst_off):
+    for e in (1, 2, 4, 8, 16):
+        check_permute(lr, orc, 7 * e + src_off, e, [48, 136], [1, 0], src_off, dst_off)
+        check_permute(lr, orc, 9 * e + dst_off, e, [5, 40, 24], [2, 1, 0], src_off, dst_off)
+
+
+def test_permute_edge_cases(lr, orc):
+    check_permute(lr, orc, 1, 4, [1], [0])
+    check_permute(lr, orc, 2, 4, [1, 1, 1], [2, 0, 1])
+    check_permute(lr, orc, 3, 8, [65537, 3], [1, 0])
+    check_permute(lr, orc, 4, 1, [3, 65537], [1, 0])
+    check_permute(lr, orc, 5, 4, [2, 3, 2, 3, 2, 3, 2, 3], [7, 6, 5, 4, 3, 2, 1, 0])
+    check_permute(lr, orc, 6, 2, [3] * 8, [1, 0, 3, 2, 5, 4, 7, 6])
+    check_permute(lr, orc, 7, 4, [1000, 1, 1, 3], [3, 2, 1, 0])
+    check_permute(lr, orc, 8, 4, [7, 1024], [0, 1])          # identity -> copy
+    check_permute(lr, orc, 9, 1, [3, 5, 1001], [1, 0, 2])    # unmoved inner run, 1001 B
+    check_permute(lr, orc, 10, 4, [3, 5, 64], [1, 0, 2])     # runs of 256 B
+    check_permute(lr, orc, 11, 2, [40, 3, 7], [1, 0, 2])     # short unmoved runs -> cells
+    check_permute(lr, orc, 12, 5000, [3, 4], [1, 0])         # huge elements -> runs
+    # zero elements: no launch, dst untouched
+    before = lr.launch_count()
+    lr.permute(0, 0, 4, [5, 0, 3], [2, 1, 0])
+    assert lr.launch_count() == before
+
+
+def test_permute_tagged_bijection(lr):
+    """Tagged input: every output tag appears exactly once (catches stale or
+    overwritten shared-memory tiles as duplicates)."""
+    import torch
+    for dims, perm in [([256, 256, 33], [2, 0, 1]), ([129, 67, 31], [1, 2, 0]), ([64, 64, 64, 16], [3, 2, 1, 0])]:
+        n = int(np.prod(dims))
+        src = synth.tagged_elements(n, 4)
+        got = run_permute(lr, src, 4, dims, perm).view(np.uint32)
+        assert np.array_equal(np.sort(got), np.arange(n, dtype=np.uint32)), (dims, perm)
+
+
+# ---------------------------------------------------------------------------
+# reorder
+
+@pytest.mark.parametrize("e", [1, 2, 3, 4, 8, 12, 16])
+def test_reorder(lr, orc, e):
+    for t, n in enumerate([1, 3, 4, 5, 1000, 65537, (1 << 18) + 3]):
+        src = synth.random_elements(200 + t, n, e)
+        for kind in ("perm", "repeat", "block"):
+            if kind == "perm":
+                idx = synth.random_permutation(300 + t, n)
+            elif kind == "repeat":
+                idx = synth.random_indices(400 + t, n, n)
+            else:
+                if n % 64:
+                    continue
+                idx = synth.block_shuffled_permutation(500 + t, n, 64)
+            s, ix = to_dev(src), to_dev(idx)
+            d = DevBuf(n * e, fill=0x5A)
+            lr.reorder(d.ptr, s.ptr, ix.ptr, n, e)
+            sync()
+            assert np.array_equal(d.download(), orc.reorder(src, idx, e)), (n, e, kind)
+
+
+def test_reorder_unaligned(lr, orc):
+    n = 5003
+    for e, so, do, io in [(4, 0, 0, 4), (4, 2, 0, 0), (8, 8, 4, 8), (2, 1, 3, 12), (16, 4, 8, 0), (1, 3, 1, 4)]:
+        src = synth.random_elements(e + so, n, e)
+        idx = synth.random_permutation(e + io, n)
+        s, ix = to_dev(src, so), to_dev(idx, io)
+        d = DevBuf(n * e, do)
+        lr.reorder(d.ptr, s.ptr, ix.ptr, n, e)
+        sync()
+        assert np.array_equal(d.download(), orc.reorder(src, idx, e)), (e, so, do, io)
+
+
+# ---------------------------------------------------------------------------
+# interlace / de-interlace
+
+def check_interlace(lr, orc, k, n, e, offs=None, seed=0):
+    offs = offs or [0] * (k + 1)
+    planes = [synth.random_elements(seed + 10 * j, n, e) for j in range(k)]
+    pd = [to_dev(p, offs[j]) for j, p in enumerate(planes)]
+    d = DevBuf(n * k * e, offs[k], fill=0x11)
+    lr.interlace(d.ptr, [p.ptr for p in pd], n, e)
+    sync()
+    got = d.download()
+    want = orc.interlace(planes, n, e)
+    assert np.array_equal(got, want), ("interlace", k, n, e, offs)
+    # de-interlace of an independent interlaced array
+    arr = synth.random_elements(seed + 7, n * k, e)
+    s = to_dev(arr, offs[k])
+    outs = [DevBuf(n * e, offs[j], fill=0x22) for j in range(k)]
+    lr.deinterlace([o.ptr for o in outs], s.ptr, n, e)
+    sync()
+    want = orc.deinterlace(arr, k, n, e)
+    for j in range(k):
+        assert np.array_equal(outs[j].download(), want[j]), ("deinterlace", k, n, e, offs, j)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 7, 8, 9, 16])
+def test_interlace(lr, orc, k):
+    for e in (1, 2, 3, 4, 8, 16):
+        for n in (1, 7, 1000, 4099, 65536 + 5):
+            check_interlace(lr, orc, k, n, e, seed=k * 1000 + e * 10 + n % 7)
+
+
+def test_interlace_many_planes_and_unaligned(lr, orc):
+    check_interlace(lr, orc, 256, 37, 4, seed=1)
+    check_interlace(lr, orc, 100, 513, 1, seed=2)
+    for k in (2, 3, 4, 8):
+        offs = [(4 * j + 4) % 16 for j in range(k + 1)]
+        check_interlace(lr, orc, k, 3001, 4, offs, seed=3 + k)
+        offs = [(j + 1) % 16 for j in range(k + 1)]
+        check_interlace(lr, orc, k, 3001, 2, offs, seed=4 + k)
+
+
+# ---------------------------------------------------------------------------
+# batched execution
+
+def make_op_buffers(op, offset=0):
+    """Device inputs (from the op's data seed) and zeroed outputs for one op spec."""
+    e = op["elem_bytes"]
+    if op["kind"] == "permute":
+        n = int(np.prod(op["dims"]))
+        src = synth.random_elements(op["data_seed"], n, e)
+        return dict(src_np=src, src=to_dev(src, offset), dst=DevBuf(n * e, offset, fill=0))
+    if op["kind"] == "reorder":
+        n = op["n"]
+        src = synth.random_elements(op["data_seed"], n, e)
+        idx = synth.random_permutation(op["data_seed"] ^ 1, n)
+        return dict(src_np=src, idx_np=idx, src=to_dev(src, offset), idx=to_dev(idx), dst=DevBuf(n * e, offset, fill=0))
+    k, n = op["k"], op["n"]
+    if op["kind"] == "interlace":
+        planes = [synth.random_elements(op["data_seed"] + j, n, e) for j in range(k)]
+        return dict(planes_np=planes, planes=[to_dev(p, offset) for p in planes],
+                    dst=DevBuf(n * k * e, offset, fill=0))
+    arr = synth.random_elements(op["data_seed"], n * k, e)
+    return dict(src_np=arr, src=to_dev(arr, offset), dsts=[DevBuf(n * e, offset, fill=0) for _ in range(k)])
+
+
+def add_to_plan(plan, op, b):
+    e = op["elem_bytes"]
+    if op["kind"] == "permute":
+        plan.add_permute(b["dst"].ptr, b["src"].ptr, e, op["dims"], op["perm"])
+    elif op["kind"] == "reorder":
+        plan.add_reorder(b["dst"].ptr, b["src"].ptr, b["idx"].ptr, op["n"], e)
+    elif op["kind"] == "interlace":
+        plan.add_interlace(b["dst"].ptr, [p.ptr for p in b["planes"]], op["n"], e)
+    else:
+        plan.add_deinterlace([d.ptr for d in b["dsts"]], b["src"].ptr, op["n"], e)
+
+
+def oracle_of(orc, op, b):
+    e = op["elem_bytes"]
+    if op["kind"] == "permute":
+        return [orc.permute(b["src_np"], e, op["dims"], op["perm"])]
+    if op["kind"] == "reorder":
+        return [orc.reorder(b["src_np"], b["idx_np"], e)]
+    if op["kind"] == "interlace":
+        return [orc.interlace(b["planes_np"], op["n"], e)]
+    return orc.deinterlace(b["src_np"], op["k"], op["n"], e)
+
+
+def outputs_of(op, b):
+    if op["kind"] == "deinterlace":
+        return [d.download() for d in b["dsts"]]
+    return [b["dst"].download()]
+
+
+def test_batch_mix_matches_oracle(lr, orc):
+    ops = synth.batch_mix(seed=5, n_ops=160, hi_total=2 ** 15)
+    bufs = [make_op_buffers(op, offset=(i % 3) * 4) for i, op in enumerate(ops)]
+    plan = lr.Plan()
+    for op, b in zip(ops, bufs):
+        add_to_plan(plan, op, b)
+    plan.finalize()
+    for rep in range(2):  # the second replay must give the same bytes
+        for b in bufs:
+            for out in ([b["dst"]] if "dst" in b else b["dsts"]):
+                out.t.fill_(0)
+        plan.run()
+        sync()
+        for i, (op, b) in enumerate(zip(ops, bufs)):
+            want = oracle_of(orc, op, b)
+            got = outputs_of(op, b)
+            for w, gg in zip(want, got):
+                assert np.array_equal(gg, w), (rep, i, op)
+    plan.close()
+
+
+def test_batch_rereads_inputs_on_replay(lr, orc):
+    """A replay reads the buffers' current contents (the plan records pointers)."""
+    op = dict(kind="permute", elem_bytes=4, dims=[37, 70, 5], perm=[2, 0, 1], data_seed=1)
+    b = make_op_buffers(op)
+    plan = lr.Plan()
+    add_to_plan(plan, op, b)
+    plan.finalize()
+    plan.run()
+    sync()
+    assert np.array_equal(b["dst"].download(), orc.permute(b["src_np"], 4, op["dims"], op["perm"]))
+    new = synth.random_elements(999, 37 * 70 * 5, 4)
+    b["src"].upload(new)
+    plan.run()
+    sync()
+    assert np.array_equal(b["dst"].download(), orc.permute(new, 4, op["dims"], op["perm"]))
+    plan.close()
+
+
+def test_batch_equals_single_calls(lr, orc):
+    ops = synth.batch_mix(seed=9, n_ops=48, hi_total=2 ** 16)
+    b1 = [make_op_buffers(op) for op in ops]
+    b2 = [make_op_buffers(op) for op in ops]
+    plan = lr.Plan()
+    for op, b in zip(ops, b1):
+        add_to_plan(plan, op, b)
+    plan.finalize()
+    plan.run()
+    for op, b in zip(ops, b2):
+        e = op["elem_bytes"]
+        if op["kind"] == "permute":
+            lr.permute(b["dst"].ptr, b["src"].ptr, e, op["dims"], op["perm"])
+        elif op["kind"] == "reorder":
+            lr.reorder(b["dst"].ptr, b["src"].ptr, b["idx"].ptr, op["n"], e)
+        elif op["kind"] == "interlace":
+            lr.interlace(b["dst"].ptr, [p.ptr for p in b["planes"]], op["n"], e)
+        else:
+            lr.deinterlace([d.ptr for d in b["dsts"]], b["src"].ptr, op["n"], e)
+    sync()
+    for op, x, y in zip(ops, b1, b2):
+        for gx, gy in zip(outputs_of(op, x), outputs_of(op, y)):
+            assert np.array_equal(gx, gy), op
+    plan.close()
+
+
+def test_batch_many_planes(lr, orc):
+    op = dict(kind="interlace", elem_bytes=4, k=12, n=333, data_seed=3)
+    op2 = dict(kind="deinterlace", elem_bytes=2, k=9, n=1001, data_seed=4)
+    b, b2 = make_op_buffers(op), make_op_buffers(op2)
+    plan = lr.Plan()
+    add_to_plan(plan, op, b)
+    add_to_plan(plan, op2, b2)
+    plan.finalize()
+    plan.run()
+    sync()
+    assert np.array_equal(outputs_of(op, b)[0], oracle_of(orc, op, b)[0])
+    for g, w in zip(outputs_of(op2, b2), oracle_of(orc, op2, b2)):
+        assert np.array_equal(g, w)
+    plan.close()

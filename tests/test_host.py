@@ -1,0 +1,207 @@
+"""Host-side checks of librearr that need no GPU.
+
+* the shared library loads and exports every function include/librearr.h declares;
+* argument validation returns REARR_EINVAL before any CUDA call;
+* zero-size operations return REARR_OK and launch nothing;
+* the plan compiler's canonical form (collapsed extents, strides, folded cell)
+  describes the same permutation: a CPU interpretation of the collapsed plan
+  reproduces the oracle's bytes (the oracle itself never collapses axes).
+"""
+import ctypes
+import itertools
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_1011_3583_gb300 import build as rbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lr():
+    rbuild.build()
+    from paper_1011_3583_gb300 import librearr
+    librearr.load()
+    return librearr
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(rearr_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(lr):
+    names = declared_functions()
+    assert len(names) >= 19, names
+    L = ctypes.CDLL(lr.lib_path())
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lr):
+    assert [lr.status_str(i) for i in range(7)] == [
+        "REARR_OK", "REARR_EINVAL", "REARR_ENOMEM", "REARR_ECUDA", "REARR_ERANGE", "REARR_ETIMEDOUT", "REARR_EBUSY"]
+
+
+def test_selftest_host(lr):
+    lr.selftest_host()
+
+
+FAKE_DST = 0x7F0000000000
+FAKE_SRC = 0x7E0000000000
+
+
+@pytest.mark.parametrize("dims,perm,e", [
+    ([2, 3], [0, 0], 4),          # not a permutation
+    ([2, 3], [0, 2], 4),          # out of range
+    ([2, -1], [1, 0], 4),         # negative extent
+    ([1] * 9, list(range(9)), 4),  # rank > 8
+    ([2, 3], [1, 0], 0),          # elem_bytes == 0
+])
+def test_permute_rejects_invalid(lr, dims, perm, e):
+    with pytest.raises(lr.RearrError) as ex:
+        lr.permute(FAKE_DST, FAKE_SRC, e, dims, perm)
+    assert ex.value.status == 1
+
+
+def test_permute_rejects_null_and_overlap(lr):
+    with pytest.raises(lr.RearrError):
+        lr.permute(0, FAKE_SRC, 4, [4, 4], [1, 0])
+    with pytest.raises(lr.RearrError):
+        lr.permute(FAKE_SRC + 8, FAKE_SRC, 4, [4, 4], [1, 0])
+
+
+def test_rank_zero_rejected(lr):
+    with pytest.raises(lr.RearrError):
+        lr.permute(FAKE_DST, FAKE_SRC, 4, [], [])
+
+
+def test_zero_size_ops_are_noops(lr):
+    before = lr.launch_count()
+    lr.permute(0, 0, 4, [3, 0, 5], [2, 1, 0])
+    lr.reorder(0, 0, 0, 0, 4)
+    lr.interlace(0, [0, 0], 0, 4)
+    lr.deinterlace([0, 0, 0], 0, 0, 4)
+    assert lr.launch_count() == before
+
+
+def test_other_ops_reject_invalid(lr):
+    with pytest.raises(lr.RearrError):
+        lr.reorder(FAKE_DST, FAKE_SRC, 0, 16, 4)          # NULL idx
+    with pytest.raises(lr.RearrError):
+        lr.reorder(FAKE_DST, FAKE_SRC, FAKE_SRC + 3, 16, 4)  # misaligned idx (and overlap)
+    with pytest.raises(lr.RearrError):
+        lr.reorder(FAKE_DST, FAKE_DST + 4, 0x100000, 16, 4)  # dst overlaps src
+    with pytest.raises(lr.RearrError):
+        lr.interlace(FAKE_DST, [], 16, 4)                   # k = 0
+    with pytest.raises(lr.RearrError):
+        lr.interlace(FAKE_DST, [FAKE_SRC] * 257, 16, 4)     # k > 256
+    with pytest.raises(lr.RearrError):
+        lr.interlace(FAKE_DST, [FAKE_SRC, 0], 16, 4)        # NULL plane
+    with pytest.raises(lr.RearrError):
+        lr.interlace(FAKE_DST, [FAKE_DST + 16, FAKE_SRC], 16, 4)  # plane inside dst
+    with pytest.raises(lr.RearrError):
+        lr.deinterlace([FAKE_DST, FAKE_DST + 8], FAKE_SRC, 16, 4)  # destination planes overlap
+    with pytest.raises(lr.RearrError):
+        lr.interlace(FAKE_DST, [FAKE_SRC, FAKE_SRC + 4096], 16, 0)
+
+
+def test_plan_finalize_rules(lr):
+    p = lr.Plan()
+    p.add_permute(0, 0, 4, [0, 7], [1, 0])  # zero-size op is dropped
+    assert p.stats() == (0, 0)
+    with pytest.raises(lr.RearrError):
+        p.add_permute(FAKE_DST, FAKE_SRC, 4, [2, 2], [0, 0])
+    p.finalize()   # empty plan: nothing to upload, no CUDA call
+    with pytest.raises(lr.RearrError) as ex:
+        p.add_permute(FAKE_DST, FAKE_SRC, 4, [2, 2], [1, 0])
+    assert ex.value.status == 6
+    p.run()        # empty plan replays as a no-op
+    p.close()
+
+
+# --------------------------------------------------------------------------
+# Canonical form of the plan compiler.
+
+def test_describe_examples(lr):
+    # identity and extent-1 axes collapse to a copy
+    d = lr.describe_permute(4, [4, 1, 5, 6], [0, 1, 2, 3], FAKE_DST, FAKE_SRC)
+    assert d["kind"] == "copy"
+    d = lr.describe_permute(4, [4, 1, 5, 6], [1, 0, 2, 3], FAKE_DST, FAKE_SRC)
+    assert d["kind"] == "copy"
+    # 2-D transpose: a fast tile on the (A, B) plane
+    d = lr.describe_permute(4, [1024, 1024], [1, 0], FAKE_DST, FAKE_SRC)
+    assert d["kind"] == "tile" and d["dims"] == [1024, 1024] and d["in_strides"] == [1, 1024]
+    assert d["vec_in"] == 16 and d["vec_out"] == 16
+    # the survey's example: 64x128x256x64 with (0,1,3,2) is a batch of 8192 256x64 transposes
+    d = lr.describe_permute(4, [64, 128, 256, 64], [0, 1, 3, 2], FAKE_DST, FAKE_SRC)
+    assert d["kind"] == "tile" and d["dims"] == [8192, 64, 256] and d["plane_a"] == 1
+    # unmoved innermost axis folds into the cell
+    d = lr.describe_permute(4, [8, 16, 4], [1, 0, 2], FAKE_DST, FAKE_SRC)
+    assert d["cell_bytes"] == 16 and d["rank"] == 2 and d["kind"] == "tile"
+    # long unmoved runs are copied as runs
+    d = lr.describe_permute(4, [8, 16, 512], [1, 0, 2], FAKE_DST, FAKE_SRC)
+    assert d["kind"] == "runs" and d["cell_bytes"] == 2048
+    # element sizes that are not a power of two use multi-word cells
+    d = lr.describe_permute(12, [33, 65], [1, 0], FAKE_DST, FAKE_SRC)
+    assert d["kind"] == "tile_cells" and d["word_bytes"] == 4
+    # misaligned base pointers lower the access width
+    d = lr.describe_permute(4, [64, 64], [1, 0], FAKE_DST + 2, FAKE_SRC)
+    assert d["kind"] == "tile_cells" and d["word_bytes"] == 2
+    d = lr.describe_permute(4, [64, 64], [1, 0], FAKE_DST + 4, FAKE_SRC)
+    assert d["kind"] == "tile" and d["vec_out"] == 4 and d["vec_in"] == 16
+    # ragged extents lower the vector widths, never the correctness
+    d = lr.describe_permute(4, [37, 211], [1, 0], FAKE_DST, FAKE_SRC)
+    assert d["kind"] == "tile" and d["vec_in"] == 4 and d["vec_out"] == 4
+
+
+def interpret_plan(src_flat: np.ndarray, e: int, info: dict, total: int) -> np.ndarray:
+    """Evaluate a collapsed plan on the CPU: output axis i advances the input by
+    in_strides[i] cells of cell_bytes bytes; the output is row-major."""
+    cell = info["cell_bytes"]
+    if info["kind"] == "copy":
+        return src_flat.copy()
+    dims = info["dims"]
+    strides = [s * cell for s in info["in_strides"]]
+    view = np.lib.stride_tricks.as_strided(src_flat, shape=tuple(dims) + (cell,),
+                                           strides=tuple(strides) + (1,), writeable=False)
+    return np.ascontiguousarray(view).reshape(-1)
+
+
+def test_collapsed_plan_equivalence(lr):
+    orc = oracle.get()
+    g = synth.rng(77)
+    cases = []
+    for rank in range(1, 9):
+        for _ in range(12):
+            dims = [int(g.integers(1, 5)) for _ in range(rank)]
+            for _ in range(int(g.integers(0, rank))):
+                dims[int(g.integers(0, rank))] = 1
+            cases.append((dims, [int(v) for v in g.permutation(rank)]))
+    for dims in ([2, 3, 4], [3, 1, 4, 1], [2, 2, 2, 2]):
+        for perm in itertools.permutations(range(len(dims))):
+            cases.append((list(dims), list(perm)))
+    for ci, (dims, perm) in enumerate(cases):
+        e = (1, 2, 3, 4, 8, 12, 16, 40)[ci % 8]
+        n = int(np.prod(dims))
+        src = synth.random_elements(9000 + ci, n, e)
+        info = lr.describe_permute(e, dims, perm, FAKE_DST, FAKE_SRC)
+        got = interpret_plan(src, e, info, n)
+        want = orc.permute(src, e, dims, perm)
+        assert np.array_equal(got, want), (dims, perm, e, info)
+        # the canonical form never keeps an extent-1 axis and never an unmoved inner axis
+        if info["kind"] in ("tile", "tile_cells"):
+            assert all(d > 1 for d in info["dims"])
+            assert info["in_strides"][-1] != 1
