@@ -81,11 +81,12 @@ class Oracle:
         lib.oracle_permute_sample.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int, i64p, ip,
                                               i64p, ctypes.c_int64]
         lib.oracle_reorder.argtypes = [vp, vp, vp, ctypes.c_size_t, ctypes.c_size_t]
+        lib.oracle_reorder_sample.argtypes = [vp, vp, vp, ctypes.c_size_t, ctypes.c_size_t, i64p, ctypes.c_int64]
         lib.oracle_interlace.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t,
                                          ctypes.c_size_t]
         lib.oracle_deinterlace.argtypes = [ctypes.POINTER(vp), vp, ctypes.c_int, ctypes.c_size_t,
                                            ctypes.c_size_t]
-        for name in ("oracle_permute", "oracle_permute_sample", "oracle_reorder",
+        for name in ("oracle_permute", "oracle_permute_sample", "oracle_reorder", "oracle_reorder_sample",
                      "oracle_interlace", "oracle_deinterlace"):
             getattr(lib, name).restype = ctypes.c_int
         self.lib = lib
@@ -136,6 +137,21 @@ class Oracle:
             raise OracleError("oracle_reorder rejected its arguments")
         return out
 
+    def reorder_sample(self, src: np.ndarray, idx: np.ndarray, elem_bytes: int, pos: np.ndarray) -> np.ndarray:
+        """The reorder's output elements at positions pos (flat uint8)."""
+        sb = _bytes_view(src)
+        ix = np.ascontiguousarray(idx, dtype=np.uint32)
+        p = np.ascontiguousarray(pos, dtype=np.int64)
+        n = ix.size
+        if sb.size < n * elem_bytes:
+            raise OracleError("source buffer too small")
+        vals = np.empty(p.size * elem_bytes, dtype=np.uint8)
+        rc = self.lib.oracle_reorder_sample(_ptr(vals), _ptr(sb), _ptr(ix), n, elem_bytes,
+                                            p.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), p.size)
+        if rc != 0:
+            raise OracleError("oracle_reorder_sample rejected its arguments")
+        return vals
+
     # -- interlace / de-interlace ------------------------------------------------
     def interlace(self, planes: Sequence[np.ndarray], n: int, elem_bytes: int) -> np.ndarray:
         k = len(planes)
@@ -183,6 +199,10 @@ def permute_sample(*a, **k):
 
 def reorder(*a, **k):
     return get().reorder(*a, **k)
+
+
+def reorder_sample(*a, **k):
+    return get().reorder_sample(*a, **k)
 
 
 def interlace(*a, **k):

@@ -153,6 +153,24 @@ int oracle_reorder(void *dst, const void *src, const uint32_t *idx, size_t n,
     return 0;
 }
 
+int oracle_reorder_sample(void *vals, const void *src, const uint32_t *idx,
+                          size_t n, size_t elem_bytes, const int64_t *pos,
+                          int64_t count)
+{
+    if (elem_bytes == 0 || count < 0) return -1;
+    if (count == 0) return 0;
+    if (!vals || !src || !idx || !pos) return -1;
+    unsigned char *out = (unsigned char *)vals;
+    const unsigned char *in = (const unsigned char *)src;
+    for (int64_t t = 0; t < count; ++t) {
+        if (pos[t] < 0 || (size_t)pos[t] >= n) return -1;
+        const uint32_t j = idx[pos[t]];
+        if ((size_t)j >= n) return -1;
+        memcpy(out + (size_t)t * elem_bytes, in + (size_t)j * elem_bytes, elem_bytes);
+    }
+    return 0;
+}
+
 int oracle_interlace(void *dst, const void *const *srcs, int k, size_t n,
                      size_t elem_bytes)
 {

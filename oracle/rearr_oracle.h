@@ -34,6 +34,12 @@ int oracle_permute_sample(void *vals, const void *src, size_t elem_bytes,
 int oracle_reorder(void *dst, const void *src, const uint32_t *idx, size_t n,
                    size_t elem_bytes);
 
+/* The reorder definition evaluated only at the output positions pos[0..count):
+ * vals[t] = src[idx[pos[t]]], with src and idx of n entries each. */
+int oracle_reorder_sample(void *vals, const void *src, const uint32_t *idx,
+                          size_t n, size_t elem_bytes, const int64_t *pos,
+                          int64_t count);
+
 /* Interlace (Sec. III.C): dst[i*k + j] = srcs[j][i], i < n, j < k. */
 int oracle_interlace(void *dst, const void *const *srcs, int k, size_t n,
                      size_t elem_bytes);

@@ -245,6 +245,14 @@ def pin_reorder(orc) -> List[str]:
         inv[p] = np.arange(n, dtype=np.uint32)
         if not np.array_equal(orc.reorder(orc.reorder(src, p, e), inv, e), src):
             fails.append(f"reorder inverse n={n}")
+    # The pointwise evaluation agrees with numpy fancy indexing at sampled positions.
+    for t, (n, e) in enumerate([(1, 4), (999, 3), (4096, 8)]):
+        src = synth.random_elements(5300 + t, n, e)
+        idx = synth.random_indices(5400 + t, n, n)
+        pos = synth.random_indices(5500 + t, min(n, 257), n).astype(np.int64)
+        want = src.view(_void(e))[idx.astype(np.int64)[pos]]
+        if not np.array_equal(orc.reorder_sample(src, idx, e, pos).view(_void(e)), want):
+            fails.append(f"reorder sample n={n} e={e}")
     # A hand-worked example: src = [10 20 30 40], idx = [3 0 0 2] -> [40 10 10 30].
     got = orc.reorder(np.array([10, 20, 30, 40], np.uint32), np.array([3, 0, 0, 2], np.uint32), 4)
     if got.view(np.uint32).tolist() != [40, 10, 10, 30]:

@@ -110,7 +110,7 @@ def test_config_reorder_2p28(lr, orc, kind):
     g = synth.rng(31)
     lin = g.integers(0, n, size=N_SAMPLES, dtype=np.int64)
     lin[:2] = [0, n - 1]
-    want = orc.reorder(src_np, idx_np[lin], 4)
+    want = orc.reorder_sample(src_np, idx_np, 4, lin)
     sync()
     assert sampled_equal(out, 4, lin, want)
     # reorder by the inverse permutation restores the input everywhere

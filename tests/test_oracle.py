@@ -48,6 +48,8 @@ MUTANTS = [
     ("de-interlace reads planar order",
      "in + (i * (size_t)k + (size_t)j) * elem_bytes, elem_bytes);",
      "in + ((size_t)j * n + i) * elem_bytes, elem_bytes);"),
+    ("sampled reorder skips the index", "const uint32_t j = idx[pos[t]];",
+     "const uint32_t j = (uint32_t)pos[t];"),
     ("permutation check dropped", "if (seen[perm[i]]) return -1;", ""),
     ("reorder range check dropped", "if ((size_t)idx[i] >= n) return -1;", ""),
     ("last byte of each element dropped",
