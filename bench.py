@@ -98,7 +98,7 @@ class ClockSampler:
         self.lines = []
 
     def __enter__(self):
-        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50"]
         if self.gpu_id:
             cmd += ["-i", self.gpu_id]
         try:
@@ -333,6 +333,8 @@ def run_gpu(args):
     e2e = {"value": round(world * step_bytes * e2e_steps / t_e2e / 1e9, 1), "unit": "GB/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
 
+    batched = None if args.no_batched else run_batched(torch, rr, stream, device)
+
     result = None
     if rank == 0:
         cpu = None if (world > 1 or args.no_cpu_baseline) else cpu_baseline(wl)
@@ -348,12 +350,122 @@ def run_gpu(args):
             "frac_of_8tbs": round(value / world / 8000.0, 4),
             "roofline": roofline, "families": families, "per_op_gbs": per_op_gbs,
             "gpu_launches": int(launches), "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu,
+            "batched": batched,
             "source_digest": source_digest(),
         }
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     return result
+
+
+# ---------------------------------------------------------------------------
+# batched form: the uneven 4096-op mix, one graph replay vs one call per op
+
+def batch_buffers(torch, ops, device):
+    """Device buffers for every op of a mix, carved from one pool (256-byte
+    aligned).  Payload bytes are filled by torch's device RNG (contents are not
+    checked here; the parity tests check them); reorder indices are device
+    random permutations."""
+    def al(x):
+        return (x + 255) // 256 * 256
+    sizes = []
+    for o in ops:
+        e = o["elem_bytes"]
+        if o["kind"] == "permute":
+            n = int(np.prod(o["dims"]))
+            sizes.append([n * e, n * e])
+        elif o["kind"] == "reorder":
+            sizes.append([o["n"] * e, o["n"] * 4, o["n"] * e])
+        elif o["kind"] == "interlace":
+            sizes.append([o["n"] * e] * o["k"] + [o["n"] * o["k"] * e])
+        else:
+            sizes.append([o["n"] * o["k"] * e] + [o["n"] * e] * o["k"])
+    total = sum(al(x) for sz in sizes for x in sz)
+    pool = torch.empty(total, dtype=torch.uint8, device=device)
+    pool.random_()
+    base = pool.data_ptr()
+    off = 0
+    bufs = []
+    for o, sz in zip(ops, sizes):
+        ptrs = []
+        for x in sz:
+            ptrs.append(base + off)
+            off += al(x)
+        if o["kind"] == "reorder":
+            n = o["n"]
+            perm = torch.randperm(n, device=device, dtype=torch.int64).to(torch.int32)
+            start = ptrs[1] - base
+            pool[start:start + 4 * n].copy_(perm.view(torch.uint8))
+        bufs.append(ptrs)
+    return pool, bufs
+
+
+def issue_single(rr, o, p, stream):
+    e = o["elem_bytes"]
+    if o["kind"] == "permute":
+        rr.permute(p[1], p[0], e, o["dims"], o["perm"], stream)
+    elif o["kind"] == "reorder":
+        rr.reorder(p[2], p[0], p[1], o["n"], e, stream)
+    elif o["kind"] == "interlace":
+        rr.interlace(p[-1], p[:-1], o["n"], e, stream)
+    else:
+        rr.deinterlace(p[1:], p[0], o["n"], e, stream)
+
+
+def add_to_plan(plan, o, p):
+    e = o["elem_bytes"]
+    if o["kind"] == "permute":
+        plan.add_permute(p[1], p[0], e, o["dims"], o["perm"])
+    elif o["kind"] == "reorder":
+        plan.add_reorder(p[2], p[0], p[1], o["n"], e)
+    elif o["kind"] == "interlace":
+        plan.add_interlace(p[-1], p[:-1], o["n"], e)
+    else:
+        plan.add_deinterlace(p[1:], p[0], o["n"], e)
+
+
+def run_batched(torch, rr, stream, device, n_ops=4096, reps=5):
+    import synth
+    ops = synth.batch_mix(seed=1, n_ops=n_ops)
+    pool, bufs = batch_buffers(torch, ops, device)
+    total_bytes = sum(synth.op_bytes(o) for o in ops)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        for _ in range(reps):
+            fn()
+        e.record(stream)
+        e.synchronize()
+        return s.elapsed_time(e) / 1e3 / reps
+
+    def plain():
+        for o, p in zip(ops, bufs):
+            issue_single(rr, o, p, stream)
+
+    t_plain = timed(plain, reps)
+    l0 = rr.launch_count()
+    plan = rr.Plan()
+    t0 = time.perf_counter()
+    for o, p in zip(ops, bufs):
+        add_to_plan(plan, o, p)
+    plan.finalize(stream)
+    t_build = time.perf_counter() - t0
+    t_batch = timed(lambda: plan.run(stream), reps)
+    n_ops_plan, n_tiles = plan.stats()
+    plan.close()
+    del pool
+    return {"workload": f"{n_ops}-op uneven mix (seed 1): permute rank 2-5, reorder, interlace/de-interlace k 2-4; "
+                        "elem 1/2/4/8 B; extents log-uniform [1,512]; op totals in [2^8, 2^22] elements",
+            "bytes_per_batch": int(total_bytes), "tiles": int(n_tiles),
+            "batched_ms": round(t_batch * 1e3, 3), "plain_ms": round(t_plain * 1e3, 3),
+            "batched_ops_per_s": round(n_ops / t_batch, 1), "plain_ops_per_s": round(n_ops / t_plain, 1),
+            "batched_gbs": round(total_bytes / t_batch / 1e9, 1), "plain_gbs": round(total_bytes / t_plain / 1e9, 1),
+            "speedup": round(t_plain / t_batch, 3), "plan_build_s": round(t_build, 3),
+            "launches_per_replay": 1, "kernels_per_plain_pass": n_ops}
 
 
 def run_e2e(torch, rr, wl, ops, stream, args):
@@ -488,6 +600,7 @@ def main():
     ap.add_argument("--impl", default="librearr", choices=["librearr", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

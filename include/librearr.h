@@ -175,6 +175,8 @@ typedef struct {
     int64_t n_tiles;          /* work units (tiles, runs or copy blocks)         */
 } rearr_permute_info;
 
+/* dst_addr / src_addr only steer the alignment decisions (0: 256-byte aligned);
+ * nothing is read or written. */
 rearr_status rearr_permute_describe(size_t elem_bytes, int rank, const int64_t *dims,
                                     const int *perm, uintptr_t dst_addr, uintptr_t src_addr,
                                     rearr_permute_info *info);

@@ -99,6 +99,10 @@ rearr_status rearr_permute_describe(size_t elem_bytes, int rank, const int64_t *
                                     uintptr_t dst_addr, uintptr_t src_addr, rearr_permute_info *info)
 {
     if (!info) return fail(REARR_EINVAL, "rearr_permute_describe: info is NULL");
+    // Addresses only steer the alignment decisions; 0 stands for a 256-byte
+    // aligned buffer (two far-apart fake addresses, so no overlap is seen).
+    if (dst_addr == 0) dst_addr = uintptr_t(1) << 47;
+    if (src_addr == 0) src_addr = uintptr_t(1) << 46;
     PermPlan pl;
     std::string err;
     rearr_status st = plan_permute(reinterpret_cast<void *>(dst_addr), reinterpret_cast<const void *>(src_addr),

@@ -15,10 +15,11 @@
 #include <vector>
 
 #include "../../include/librearr.h"
-#include "batch.h"
+#include "tuning.h"
 #include "bodies.cuh"
 #include "launch.h"
 #include "plan.h"
+#include "variants.h"
 
 namespace rearr {
 
@@ -32,80 +33,123 @@ __device__ __forceinline__ char *const *planes_of(const InterlaceDesc &d)
     return d.k <= uint32_t(kInlineK) ? d.planes : d.planes_dev;
 }
 
-#define BT_CASE(E, VI, VO) \
-    case tile_variant(E, VI, VO): tile_fast_body<E, VI, VO>(d.tile, uint32_t(u), smem); return;
+// One non-inlined function per body variant, each running a range [u0, u1)
+// of one op's units.  Separate functions get separate register allocations
+// (a single function holding every inlined variant overflows the register
+// file), and the call overhead is paid once per range, not once per tile.
+template <int E, int VI, int VO, int RB>
+__device__ __noinline__ void tile_range(const TileDesc &d, uint32_t u0, uint32_t u1, unsigned char *smem)
+{
+    for (uint32_t u = u0; u < u1; ++u) tile_fast_body<E, VI, VO, RB>(d, u, smem);
+}
 
-__device__ __noinline__ void run_tile_fast(const OpDesc &d, uint64_t u, unsigned char *smem)
+template <int W>
+__device__ __noinline__ void cells_range(const TileDesc &d, uint32_t u0, uint32_t u1, unsigned char *smem)
+{
+    for (uint32_t u = u0; u < u1; ++u) tile_cells_body<W>(d, u, smem);
+}
+
+template <int W>
+__device__ __noinline__ void runs_range(const RunsDesc &d, uint64_t u0, uint64_t u1, unsigned char *smem)
+{
+    for (uint64_t u = u0; u < u1; ++u) runs_body<W>(d, u, smem);
+}
+
+template <int W>
+__device__ __noinline__ void copy_range(const CopyDesc &d, uint64_t u0, uint64_t u1)
+{
+    for (uint64_t u = u0; u < u1; ++u) copy_body<W>(d, u);
+}
+
+template <int W>
+__device__ __noinline__ void gather_range(const GatherDesc &d, uint64_t u0, uint64_t u1)
+{
+    for (uint64_t u = u0; u < u1; ++u) gather_body<W>(d, u);
+}
+
+template <int W>
+__device__ __noinline__ void igen_range(const InterlaceDesc &d, uint64_t u0, uint64_t u1, bool inter)
+{
+    for (uint64_t u = u0; u < u1; ++u) interlace_generic_body<W>(d, planes_of(d), u, inter);
+}
+
+template <int E, int K>
+__device__ __noinline__ void ifast_range(const InterlaceDesc &d, uint64_t u0, uint64_t u1, uint64_t n, bool inter)
+{
+    for (uint64_t u = u0; u < u1; ++u) {
+        if (inter) interlace_fast_body<E, K>(d, planes_of(d), u, n);
+        else deinterlace_fast_body<E, K>(d, planes_of(d), u, n);
+    }
+}
+
+#define BT_CASE(E, VI, VO, RB) \
+    case tile_variant(E, VI, VO, RB): tile_range<E, VI, VO, RB>(d.tile, uint32_t(u0), uint32_t(u1), smem); return;
+
+__device__ __forceinline__ void run_tile_fast(const OpDesc &d, uint64_t u0, uint64_t u1, unsigned char *smem)
 {
     switch (d.tile.variant) {
-        BT_CASE(1, 16, 4) BT_CASE(1, 4, 4) BT_CASE(1, 1, 4)
-        BT_CASE(1, 16, 1) BT_CASE(1, 4, 1) BT_CASE(1, 1, 1)
-        BT_CASE(2, 16, 8) BT_CASE(2, 4, 8) BT_CASE(2, 2, 8)
-        BT_CASE(2, 16, 4) BT_CASE(2, 4, 4) BT_CASE(2, 2, 4)
-        BT_CASE(2, 16, 2) BT_CASE(2, 4, 2) BT_CASE(2, 2, 2)
-        BT_CASE(4, 16, 16) BT_CASE(4, 4, 16) BT_CASE(4, 16, 4) BT_CASE(4, 4, 4)
-        BT_CASE(8, 16, 16) BT_CASE(8, 8, 16) BT_CASE(8, 16, 8) BT_CASE(8, 8, 8)
-        BT_CASE(16, 16, 16)
+        REARR_TILE_VARIANTS(BT_CASE)
         default: return;
     }
 }
 #undef BT_CASE
 
 template <int W>
-__device__ __noinline__ void run_word_class(const OpDesc &d, uint64_t u, unsigned char *smem)
+__device__ __forceinline__ void run_word_class(const OpDesc &d, uint64_t u0, uint64_t u1, unsigned char *smem)
 {
     switch (d.cls) {
-        case OC_TILE_CELLS: tile_cells_body<W>(d.tile, uint32_t(u), smem); return;
-        case OC_RUNS: runs_body<W>(d.runs, u); return;
-        case OC_COPY: copy_body<W>(d.copy, u); return;
-        case OC_GATHER: gather_body<W>(d.gather, u); return;
-        case OC_INTERLACE: interlace_generic_body<W>(d.inter, planes_of(d.inter), u, true); return;
-        case OC_DEINTERLACE: interlace_generic_body<W>(d.inter, planes_of(d.inter), u, false); return;
+        case OC_TILE_CELLS: cells_range<W>(d.tile, uint32_t(u0), uint32_t(u1), smem); return;
+        case OC_RUNS: runs_range<W>(d.runs, u0, u1, smem); return;
+        case OC_COPY: copy_range<W>(d.copy, u0, u1); return;
+        case OC_GATHER: gather_range<W>(d.gather, u0, u1); return;
+        case OC_INTERLACE: igen_range<W>(d.inter, u0, u1, true); return;
+        case OC_DEINTERLACE: igen_range<W>(d.inter, u0, u1, false); return;
         default: return;
     }
 }
 
 template <int E>
-__device__ __noinline__ void run_inter_fast(const OpDesc &d, uint64_t u)
+__device__ __forceinline__ void run_inter_fast(const OpDesc &d, uint64_t u0, uint64_t u1)
 {
-    char *const *pl = planes_of(d.inter);
     const bool inter = d.cls == OC_INTERLACE;
     switch (d.inter.k) {
-        case 1: inter ? interlace_fast_body<E, 1>(d.inter, pl, u, d.units) : deinterlace_fast_body<E, 1>(d.inter, pl, u, d.units); return;
-        case 2: inter ? interlace_fast_body<E, 2>(d.inter, pl, u, d.units) : deinterlace_fast_body<E, 2>(d.inter, pl, u, d.units); return;
-        case 3: inter ? interlace_fast_body<E, 3>(d.inter, pl, u, d.units) : deinterlace_fast_body<E, 3>(d.inter, pl, u, d.units); return;
-        case 4: inter ? interlace_fast_body<E, 4>(d.inter, pl, u, d.units) : deinterlace_fast_body<E, 4>(d.inter, pl, u, d.units); return;
+        case 1: ifast_range<E, 1>(d.inter, u0, u1, d.units, inter); return;
+        case 2: ifast_range<E, 2>(d.inter, u0, u1, d.units, inter); return;
+        case 3: ifast_range<E, 3>(d.inter, u0, u1, d.units, inter); return;
+        case 4: ifast_range<E, 4>(d.inter, u0, u1, d.units, inter); return;
         default: return;
     }
 }
 
-__device__ __forceinline__ void run_unit(const OpDesc &d, uint64_t u, unsigned char *smem)
+// Units [u0, u1) of one op.
+__device__ __forceinline__ void run_range(const OpDesc &d, uint64_t u0, uint64_t u1, unsigned char *smem)
 {
-    if (d.cls == OC_TILE) { run_tile_fast(d, u, smem); return; }
+    if (d.cls == OC_TILE) { run_tile_fast(d, u0, u1, smem); return; }
     if ((d.cls == OC_INTERLACE || d.cls == OC_DEINTERLACE) && d.inter.fast) {
         switch (d.inter.elem_bytes) {
-            case 1: run_inter_fast<1>(d, u); return;
-            case 2: run_inter_fast<2>(d, u); return;
-            case 4: run_inter_fast<4>(d, u); return;
-            case 8: run_inter_fast<8>(d, u); return;
-            case 16: run_inter_fast<16>(d, u); return;
+            case 1: run_inter_fast<1>(d, u0, u1); return;
+            case 2: run_inter_fast<2>(d, u0, u1); return;
+            case 4: run_inter_fast<4>(d, u0, u1); return;
+            case 8: run_inter_fast<8>(d, u0, u1); return;
+            case 16: run_inter_fast<16>(d, u0, u1); return;
             default: return;
         }
     }
     switch (d.word) {
-        case 1: run_word_class<1>(d, u, smem); return;
-        case 2: run_word_class<2>(d, u, smem); return;
-        case 4: run_word_class<4>(d, u, smem); return;
-        case 8: run_word_class<8>(d, u, smem); return;
-        case 16: run_word_class<16>(d, u, smem); return;
+        case 1: run_word_class<1>(d, u0, u1, smem); return;
+        case 2: run_word_class<2>(d, u0, u1, smem); return;
+        case 4: run_word_class<4>(d, u0, u1, smem); return;
+        case 8: run_word_class<8>(d, u0, u1, smem); return;
+        case 16: run_word_class<16>(d, u0, u1, smem); return;
         default: return;
     }
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads) k_batch(const OpDesc *__restrict__ ops, const uint64_t *__restrict__ prefix,
-                                                    int n_ops, unsigned long long *counter, uint32_t grab)
+__global__ void __launch_bounds__(kThreads, 4) k_batch(const OpDesc *__restrict__ ops,
+                                                       const uint64_t *__restrict__ prefix, int n_ops,
+                                                       unsigned long long *counter, uint32_t grab)
 {
     __shared__ __align__(16) unsigned char smem[kSmemBytes];
     __shared__ unsigned long long s_start;
@@ -124,10 +168,11 @@ __global__ void __launch_bounds__(kThreads) k_batch(const OpDesc *__restrict__ o
             if (prefix[mid] <= start) lo = mid;
             else hi = mid - 1;
         }
-        int op = lo;
-        for (uint64_t t = start; t < end; ++t) {
-            while (t >= prefix[op + 1]) ++op;
-            run_unit(ops[op], t - prefix[op], smem);
+        // the grabbed range, split at op boundaries
+        for (uint64_t t = start; t < end; ++lo) {
+            const uint64_t seg_end = min(end, prefix[lo + 1]);
+            run_range(ops[lo], t - prefix[lo], seg_end - prefix[lo], smem);
+            t = seg_end;
         }
     }
 }
@@ -154,12 +199,6 @@ struct rearr_plan {
     uint32_t grab = 1;
     int grid = 0;
 };
-
-namespace rearr {
-
-const BatchTuning &batch_tuning();
-
-}  // namespace rearr
 
 static rearr_status add_op(rearr_plan *p, const OpDesc &op, std::vector<char *> planes = {})
 {

@@ -18,13 +18,12 @@ namespace rearr {
 // memory, and written along B (contiguous in the output), so both global
 // sides are coalesced.  The remaining axes batch the plane.
 
-// Fast-tile shape per element size: 16 KB of payload, input rows of 128-256 B.
-template <int E> struct FastTile;
-template <> struct FastTile<1> { static constexpr int TA = 128, TB = 128; };
-template <> struct FastTile<2> { static constexpr int TA = 128, TB = 64; };
-template <> struct FastTile<4> { static constexpr int TA = 64, TB = 64; };
-template <> struct FastTile<8> { static constexpr int TA = 32, TB = 64; };
-template <> struct FastTile<16> { static constexpr int TA = 16, TB = 64; };
+// Fast tiles hold 16 KB of payload; the staged rows (along A) are ROWB = 128,
+// 256 or 512 bytes, so TB = 16384 / ROWB rows along B.
+template <int E, int ROWB> struct FastTile {
+    static constexpr int TA = ROWB / E;
+    static constexpr int TB = kTileBytes / ROWB;
+};
 
 // Origin of tile t: (a0, b0) in the plane and the byte offsets of its batch.
 __device__ __forceinline__ void tile_origin(const TileDesc &d, uint32_t t, uint32_t &a0,
@@ -96,11 +95,10 @@ __device__ __forceinline__ typename Word<E * VB>::T piece(const uint4 (&r)[VB], 
 // the tile row-major by B with 16-byte chunks XOR-swizzled by (row/VB)&7, so
 // the 16-byte row stores of the load phase and the 16-byte column-block loads
 // of the store phase are both free of bank conflicts.
-template <int E, int VIN, int VOUT>
+template <int E, int VIN, int VOUT, int ROWB>
 __device__ __forceinline__ void tile_fast_body(const TileDesc &d, uint32_t t, unsigned char *smem)
 {
-    constexpr int TA = FastTile<E>::TA, TB = FastTile<E>::TB;
-    constexpr int ROWB = TA * E;     // bytes per staged row
+    constexpr int TA = FastTile<E, ROWB>::TA, TB = FastTile<E, ROWB>::TB;
     constexpr int V = 16 / E;        // elements per 16-byte chunk
     constexpr int VB = VOUT / E;     // B-elements per output store
     constexpr int PPR = ROWB / VIN;  // load pieces per row
@@ -109,6 +107,7 @@ __device__ __forceinline__ void tile_fast_body(const TileDesc &d, uint32_t t, un
     static_assert(NP % kThreads == 0, "tile must split evenly over the CTA");
     static_assert(ROWB % 128 == 0, "swizzle works on groups of 8 chunks");
     static_assert(VB >= 1 && VB <= 4, "output block of 1..4 rows");
+    static_assert(TB / VB >= 8, "eight row groups per swizzle period");
 
     uint32_t a0, b0;
     int64_t ioff, ooff;
@@ -117,24 +116,31 @@ __device__ __forceinline__ void tile_fast_body(const TileDesc &d, uint32_t t, un
     const uint32_t nbv = min(uint32_t(TB), d.DB - b0);
     const char *in = d.src + ioff + int64_t(a0) * E + int64_t(b0) * d.sb_in;
     char *out = d.dst + ooff + int64_t(a0) * d.sa_out + int64_t(b0) * E;
-    const int tid = threadIdx.x;
+    const int tid = tid_x();
     const uint32_t row_valid_bytes = na * E;
 
-    typename Word<VIN>::T buf[PT];
+    // Loads are issued in batches of up to 8 per thread before their shared
+    // stores, which keeps narrow-width variants within the register budget.
+    constexpr int PB = PT < 8 ? PT : 8;
+    static_assert(PT % PB == 0, "load batches must divide the per-thread pieces");
 #pragma unroll
-    for (int k = 0; k < PT; ++k) {
-        const int f = k * kThreads + tid;
-        const int row = f / PPR, x = (f % PPR) * VIN;
-        if (uint32_t(row) < nbv && uint32_t(x) < row_valid_bytes)
-            buf[k] = ldg_stream<VIN>(in + int64_t(row) * d.sb_in + x);
-    }
+    for (int k0 = 0; k0 < PT; k0 += PB) {
+        typename Word<VIN>::T buf[PB];
 #pragma unroll
-    for (int k = 0; k < PT; ++k) {
-        const int f = k * kThreads + tid;
-        const int row = f / PPR, x = (f % PPR) * VIN;
-        if (uint32_t(row) < nbv && uint32_t(x) < row_valid_bytes) {
-            const int sw = (row / VB) & 7;
-            sts<VIN>(smem + row * ROWB + (((x >> 4) ^ sw) << 4) + (x & 15), buf[k]);
+        for (int k = 0; k < PB; ++k) {
+            const int f = (k0 + k) * kThreads + tid;
+            const int row = f / PPR, x = (f % PPR) * VIN;
+            if (uint32_t(row) < nbv && uint32_t(x) < row_valid_bytes)
+                buf[k] = ldg_stream<VIN>(in + int64_t(row) * d.sb_in + x);
+        }
+#pragma unroll
+        for (int k = 0; k < PB; ++k) {
+            const int f = (k0 + k) * kThreads + tid;
+            const int row = f / PPR, x = (f % PPR) * VIN;
+            if (uint32_t(row) < nbv && uint32_t(x) < row_valid_bytes) {
+                const int sw = (row / VB) & 7;
+                sts<VIN>(smem + row * ROWB + (((x >> 4) ^ sw) << 4) + (x & 15), buf[k]);
+            }
         }
     }
     __syncthreads();
@@ -179,7 +185,7 @@ __device__ __forceinline__ void tile_cells_body(const TileDesc &d, uint32_t t, u
     const uint32_t nbv = min(d.TB, d.DB - b0);
     const char *in = d.src + ioff + int64_t(a0) * c * W + int64_t(b0) * d.sb_in;
     char *out = d.dst + ooff + int64_t(a0) * d.sa_out + int64_t(b0) * c * W;
-    const int tid = threadIdx.x;
+    const int tid = tid_x();
     constexpr int U = 8;
 
     const uint32_t RW = d.rowwords_div.d;  // TA*c
@@ -222,43 +228,85 @@ __device__ __forceinline__ void tile_cells_body(const TileDesc &d, uint32_t t, u
 }
 
 // ---------------------------------------------------------------------------
-// Runs: permutes whose output is a sequence of long contiguous input runs
-// (an unmoved innermost axis of >= 256 bytes).  One warp per run.
-template <int W>
-__device__ __forceinline__ void runs_body(const RunsDesc &d, uint64_t unit)
+// Runs: permutes whose output is a sequence of contiguous input runs of at
+// least 128 bytes (an unmoved innermost axis, or large elements).  A unit is
+// runs_per_unit consecutive output runs: their input offsets are decoded
+// once into shared memory, then the CTA walks the unit's words with U loads
+// in flight per thread; consecutive threads take consecutive words, so both
+// sides are coalesced however short the runs are.
+__device__ __forceinline__ int64_t run_offset(const RunsDesc &d, uint32_t q)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int NW = kThreads / 32;
-    const uint64_t r0 = unit * d.runs_per_unit;
-    const uint64_t r1 = min(d.n_runs, r0 + d.runs_per_unit);
-    const uint64_t words = uint64_t(d.run_bytes) / W;
-    for (uint64_t r = r0 + warp; r < r1; r += NW) {
-        uint32_t q = uint32_t(r), dig;
-        int64_t off = 0;
+    int64_t off = 0;
 #pragma unroll
-        for (int i = kMaxRank - 1; i >= 0; --i) {
-            if (i < d.nd) {
-                fdivmod(q, d.div[i], q, dig);
-                off += int64_t(dig) * d.in_stride[i];
-            }
-        }
-        const char *s = d.src + off;
-        char *o = d.dst + int64_t(r) * d.run_bytes;
-        constexpr int U = 4;
-        for (uint64_t w0 = 0; w0 < words; w0 += 32 * U) {
-            typename Word<W>::T v[U];
-#pragma unroll
-            for (int k = 0; k < U; ++k) {
-                const uint64_t w = w0 + k * 32 + lane;
-                if (w < words) v[k] = ldg_stream<W>(s + w * W);
-            }
-#pragma unroll
-            for (int k = 0; k < U; ++k) {
-                const uint64_t w = w0 + k * 32 + lane;
-                if (w < words) stg<W>(o + w * W, v[k]);
-            }
+    for (int a = kMaxRank - 1; a >= 0; --a) {
+        if (a < d.nd) {
+            uint32_t dig;
+            fdivmod(q, d.div[a], q, dig);
+            off += int64_t(dig) * d.in_stride[a];
         }
     }
+    return off;
+}
+
+template <int W>
+__device__ __forceinline__ void copy_words(const char *src, char *dst, uint32_t w0, uint32_t w1)
+{
+    constexpr int U = 4;
+    for (uint32_t b = w0; b < w1; b += kThreads * U) {
+        typename Word<W>::T v[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const uint32_t w = b + k * kThreads + tid_x();
+            if (w < w1) v[k] = ldg_stream<W>(src + int64_t(w) * W);
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const uint32_t w = b + k * kThreads + tid_x();
+            if (w < w1) stg<W>(dst + int64_t(w) * W, v[k]);
+        }
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void runs_body(const RunsDesc &d, uint64_t unit, unsigned char *smem)
+{
+    if (d.cpr_div.d > 1) {
+        // Long runs: a unit is one chunk of chunk_words words of one run.
+        uint32_t run, ch;
+        fdivmod(uint32_t(unit), d.cpr_div, run, ch);
+        const uint32_t wpr = d.wpr_div.d;
+        const uint32_t w0 = ch * d.chunk_words;
+        const uint32_t w1 = min(wpr, w0 + d.chunk_words);
+        copy_words<W>(d.src + run_offset(d, run), d.dst + int64_t(run) * d.run_bytes, w0, w1);
+        return;
+    }
+    int64_t *base = reinterpret_cast<int64_t *>(smem);
+    const uint64_t r0 = unit * d.runs_per_unit;
+    const uint32_t nr = uint32_t(min(d.n_runs - r0, uint64_t(d.runs_per_unit)));
+    for (uint32_t i = tid_x(); i < nr; i += kThreads) base[i] = run_offset(d, uint32_t(r0 + i));
+    __syncthreads();
+    const uint32_t wpr = d.wpr_div.d;  // words per run
+    const uint32_t total = nr * wpr;
+    char *out = d.dst + int64_t(r0) * d.run_bytes;
+    constexpr int U = 4;
+    for (uint32_t f0 = 0; f0 < total; f0 += kThreads * U) {
+        typename Word<W>::T v[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const uint32_t f = f0 + k * kThreads + tid_x();
+            if (f < total) {
+                uint32_t r, w;
+                fdivmod(f, d.wpr_div, r, w);
+                v[k] = ldg_stream<W>(d.src + base[r] + int64_t(w) * W);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const uint32_t f = f0 + k * kThreads + tid_x();
+            if (f < total) stg<W>(out + int64_t(f) * W, v[k]);
+        }
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -272,12 +320,12 @@ __device__ __forceinline__ void copy_body(const CopyDesc &d, uint64_t unit)
     typename Word<W>::T v[U];
 #pragma unroll
     for (int k = 0; k < U; ++k) {
-        const uint64_t off = base + uint64_t(k * kThreads + threadIdx.x) * W;
+        const uint64_t off = base + uint64_t(k * kThreads + tid_x()) * W;
         if (off < d.bytes) v[k] = ldg_stream<W>(d.src + off);
     }
 #pragma unroll
     for (int k = 0; k < U; ++k) {
-        const uint64_t off = base + uint64_t(k * kThreads + threadIdx.x) * W;
+        const uint64_t off = base + uint64_t(k * kThreads + tid_x()) * W;
         if (off < d.bytes) stg<W>(d.dst + off, v[k]);
     }
 }
@@ -318,7 +366,7 @@ __device__ __forceinline__ void gather_body(const GatherDesc &d, uint64_t unit)
             bool full[G];
 #pragma unroll
             for (int k = 0; k < G; ++k) {
-                const uint64_t i = g0 + (uint64_t(k) * kThreads + threadIdx.x) * 4;
+                const uint64_t i = g0 + (uint64_t(k) * kThreads + tid_x()) * 4;
                 full[k] = i + 3 < e1;
                 if (full[k]) {
                     const uint4 ix = ldg_stream<16>(d.idx + i);
@@ -333,7 +381,7 @@ __device__ __forceinline__ void gather_body(const GatherDesc &d, uint64_t unit)
             }
 #pragma unroll
             for (int k = 0; k < G; ++k) {
-                const uint64_t i = g0 + (uint64_t(k) * kThreads + threadIdx.x) * 4;
+                const uint64_t i = g0 + (uint64_t(k) * kThreads + tid_x()) * 4;
                 if (full[k]) store4<W>(d.dst + i * W, v[k]);
             }
         }
@@ -345,12 +393,12 @@ __device__ __forceinline__ void gather_body(const GatherDesc &d, uint64_t unit)
             uint32_t src_i[U];
 #pragma unroll
             for (int k = 0; k < U; ++k) {
-                const uint64_t i = b0 + uint64_t(k) * kThreads + threadIdx.x;
+                const uint64_t i = b0 + uint64_t(k) * kThreads + tid_x();
                 src_i[k] = i < e1 ? ldg_stream<4>(d.idx + i) : 0u;
             }
 #pragma unroll
             for (int k = 0; k < U; ++k) {
-                const uint64_t i = b0 + uint64_t(k) * kThreads + threadIdx.x;
+                const uint64_t i = b0 + uint64_t(k) * kThreads + tid_x();
                 if (i < e1) {
                     const char *s = d.src + uint64_t(src_i[k]) * c * W;
                     char *o = d.dst + i * c * W;
@@ -425,7 +473,7 @@ __device__ __forceinline__ void interlace_tail(const InterlaceDesc &d, char *con
                                                bool inter)
 {
     const uint64_t cnt = (d.n - r0) * d.k;
-    for (uint64_t f = threadIdx.x; f < cnt; f += kThreads) {
+    for (uint64_t f = tid_x(); f < cnt; f += kThreads) {
         const uint64_t i = r0 + f / d.k;
         const uint32_t j = uint32_t(f % d.k);
         char *iv = d.inter + (i * d.k + j) * E;
@@ -442,7 +490,7 @@ __device__ __forceinline__ void interlace_fast_body(const InterlaceDesc &d, char
     const uint64_t groups = d.n * E / 16;
     const uint64_t g0 = unit * d.unit_groups;
     const uint64_t g1 = min(groups, g0 + d.unit_groups);
-    for (uint64_t g = g0 + threadIdx.x; g < g1; g += kThreads) {
+    for (uint64_t g = g0 + tid_x(); g < g1; g += kThreads) {
         uint32_t in[K][4], out[K * 4];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
@@ -465,7 +513,7 @@ __device__ __forceinline__ void deinterlace_fast_body(const InterlaceDesc &d, ch
     const uint64_t groups = d.n * E / 16;
     const uint64_t g0 = unit * d.unit_groups;
     const uint64_t g1 = min(groups, g0 + d.unit_groups);
-    for (uint64_t g = g0 + threadIdx.x; g < g1; g += kThreads) {
+    for (uint64_t g = g0 + tid_x(); g < g1; g += kThreads) {
         uint32_t in[K * 4], out[K][4];
         const char *s = d.inter + g * 16 * K;
 #pragma unroll
@@ -500,7 +548,7 @@ __device__ __forceinline__ void interlace_generic_body(const InterlaceDesc &d, c
         char *dstp[U];
 #pragma unroll
         for (int k = 0; k < U; ++k) {
-            const uint32_t f = base + k * kThreads + threadIdx.x;
+            const uint32_t f = base + k * kThreads + tid_x();
             dstp[k] = nullptr;
             if (f < total) {
                 uint32_t i, rem, j, w;

@@ -79,6 +79,17 @@ template <int N> __device__ __forceinline__ typename Word<N>::T lds(const void *
     return *reinterpret_cast<const typename Word<N>::T *>(p);
 }
 
+// Thread index read through a volatile move.  The persistent batched kernel
+// runs many inlined tile bodies inside one loop; with a plain threadIdx.x the
+// compiler hoists every body's thread-dependent offsets out of that loop and
+// keeps them all live, which overflows the register file.
+__device__ __forceinline__ int tid_x()
+{
+    int t;
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(t));
+    return t;
+}
+
 // Byte select of two words (PRMT): result byte i = byte sel_i of {b:a}.
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
 {

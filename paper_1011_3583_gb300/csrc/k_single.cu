@@ -6,16 +6,17 @@
 
 #include "bodies.cuh"
 #include "launch.h"
+#include "variants.h"
 
 namespace rearr {
 
 std::atomic<uint64_t> g_launches{0};
 
-template <int E, int VIN, int VOUT>
+template <int E, int VIN, int VOUT, int ROWB>
 __global__ void __launch_bounds__(kThreads) k_tile_fast(const __grid_constant__ TileDesc d, uint32_t n)
 {
     __shared__ __align__(16) unsigned char smem[kTileBytes];
-    for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) tile_fast_body<E, VIN, VOUT>(d, t, smem);
+    for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) tile_fast_body<E, VIN, VOUT, ROWB>(d, t, smem);
 }
 
 template <int W>
@@ -28,7 +29,8 @@ __global__ void __launch_bounds__(kThreads) k_tile_cells(const __grid_constant__
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_runs(const __grid_constant__ RunsDesc d, uint64_t n)
 {
-    for (uint64_t u = blockIdx.x; u < n; u += gridDim.x) runs_body<W>(d, u);
+    __shared__ __align__(16) unsigned char smem[kMaxRunsPerUnit * 8];
+    for (uint64_t u = blockIdx.x; u < n; u += gridDim.x) runs_body<W>(d, u, smem);
 }
 
 template <int W>
@@ -79,21 +81,14 @@ cudaError_t go(K kernel, uint64_t units, const P &param, N n, cudaStream_t s)
     return cudaGetLastError();
 }
 
-#define RT_CASE(E, VI, VO)                                                                    \
-    case tile_variant(E, VI, VO):                                                             \
-        return go(k_tile_fast<E, VI, VO>, op.units, op.tile, uint32_t(op.units), s);
+#define RT_CASE(E, VI, VO, RB)                                                                \
+    case tile_variant(E, VI, VO, RB):                                                             \
+        return go(k_tile_fast<E, VI, VO, RB>, op.units, op.tile, uint32_t(op.units), s);
 
 cudaError_t launch_tile_fast(const OpDesc &op, cudaStream_t s)
 {
     switch (op.tile.variant) {
-        RT_CASE(1, 16, 4) RT_CASE(1, 4, 4) RT_CASE(1, 1, 4)
-        RT_CASE(1, 16, 1) RT_CASE(1, 4, 1) RT_CASE(1, 1, 1)
-        RT_CASE(2, 16, 8) RT_CASE(2, 4, 8) RT_CASE(2, 2, 8)
-        RT_CASE(2, 16, 4) RT_CASE(2, 4, 4) RT_CASE(2, 2, 4)
-        RT_CASE(2, 16, 2) RT_CASE(2, 4, 2) RT_CASE(2, 2, 2)
-        RT_CASE(4, 16, 16) RT_CASE(4, 4, 16) RT_CASE(4, 16, 4) RT_CASE(4, 4, 4)
-        RT_CASE(8, 16, 16) RT_CASE(8, 8, 16) RT_CASE(8, 16, 8) RT_CASE(8, 8, 8)
-        RT_CASE(16, 16, 16)
+        REARR_TILE_VARIANTS(RT_CASE)
         default: return cudaErrorInvalidValue;
     }
 }

@@ -15,14 +15,20 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
+
+#include "tuning.h"
+#include "variants.h"
 
 namespace rearr {
 
 namespace {
 
 constexpr int64_t kMaxExtent = (int64_t(1) << 31) - 1;
+constexpr int64_t kRunMinBytes = 128;     // cells this large are copied as runs
+constexpr int64_t kRunUnitBytes = 32768;  // payload of one runs work unit
 constexpr uint64_t kMaxUnits = 0xFFFFFFFFull;
 
 bool mul_overflows(uint64_t a, uint64_t b, uint64_t &out)
@@ -49,6 +55,32 @@ int pow2_align(uint64_t a, uint64_t b, uint64_t c, uint64_t d)
 {
     const uint64_t v = a | b | c | d | 16;
     return int(v & (~v + 1));  // lowest set bit, at most 16
+}
+
+// Row length (bytes) of a fully vectorised fast tile: the one whose tiles are
+// filled best by the DA x DB plane (ragged last tiles waste bandwidth), ties
+// broken toward equal input-row and output-row bytes.  An autotuned table may
+// override the choice per (E, DA, DB) class.
+static int choose_rowb(int E, int64_t DA, int64_t DB)
+{
+    const int cands[3] = {128, 256, 512};
+    int best = default_rowb(E);
+    double best_util = -1.0, best_bal = 1e9;
+    for (int rowb : cands) {
+        if (E == 1 && rowb == 512) continue;
+        const int64_t TA = rowb / E, TB = kTileBytes / rowb;
+        const double ua = double(DA) / double(((DA + TA - 1) / TA) * TA);
+        const double ub = double(DB) / double(((DB + TB - 1) / TB) * TB);
+        const double util = ua * ub;
+        const double bal = std::fabs(std::log2(double(rowb)) - std::log2(double(TB * E)));
+        if (util > best_util + 0.01 || (util > best_util - 0.01 && bal < best_bal)) {
+            best = rowb;
+            best_util = std::max(best_util, util);
+            best_bal = bal;
+        }
+    }
+    const int o = tuned_rowb(E, DA, DB);
+    return o ? o : best;
 }
 
 static void fill_tile_common(TileDesc &t, const std::vector<Axis> &ax, int p, int64_t cell, int64_t DA,
@@ -184,8 +216,8 @@ rearr_status plan_permute(void *dst, const void *src, size_t elem_bytes, int ran
     for (int i = 0; i < R; ++i)
         if (ax[i].stride == 1) p = i;
 
-    // Long cells: one warp copies each cell as a contiguous run.
-    if (cell >= 256 || p < 0) {
+    // Cells of 128 bytes or more are copied as contiguous runs.
+    if (cell >= kRunMinBytes || p < 0) {
         const int W = pow2_align(da, sa, uint64_t(cell));
         uint64_t n_runs = 1;
         for (int i = 0; i < R; ++i) n_runs *= uint64_t(ax[i].extent);
@@ -205,9 +237,24 @@ rearr_status plan_permute(void *dst, const void *src, size_t elem_bytes, int ran
             r.div[i] = make_fastdiv(i < R ? uint32_t(ax[i].extent) : 1u);
         }
         r.n_runs = n_runs;
-        // about 16 KB per unit, at least one run per warp
-        r.runs_per_unit = uint32_t(std::max<int64_t>(kThreads / 32, 16384 / cell));
-        op.units = (n_runs + r.runs_per_unit - 1) / r.runs_per_unit;
+        const uint64_t wpr = uint64_t(cell) / W;
+        if (wpr > 0xFFFFFFFFull) { err = "a run has 2^32 or more words"; return REARR_EINVAL; }
+        r.wpr_div = make_fastdiv(uint32_t(wpr));
+        if (cell > kRunUnitBytes) {
+            // long runs: units are chunks of kRunUnitBytes
+            const uint64_t cw = kRunUnitBytes / W;
+            const uint64_t cpr = (wpr + cw - 1) / cw;
+            if (n_runs * cpr > kMaxUnits) { err = "too many run chunks"; return REARR_EINVAL; }
+            r.chunk_words = uint32_t(cw);
+            r.cpr_div = make_fastdiv(uint32_t(cpr));
+            r.runs_per_unit = 1;
+            op.units = n_runs * cpr;
+        } else {
+            r.chunk_words = uint32_t(wpr);
+            r.cpr_div = make_fastdiv(1);
+            r.runs_per_unit = uint32_t(std::min<int64_t>(kMaxRunsPerUnit, std::max<int64_t>(1, kRunUnitBytes / cell)));
+            op.units = (n_runs + r.runs_per_unit - 1) / r.runs_per_unit;
+        }
         info.n_tiles = int64_t(op.units);
         return REARR_OK;
     }
@@ -228,10 +275,7 @@ rearr_status plan_permute(void *dst, const void *src, size_t elem_bytes, int ran
     if (W == cell) {
         // Fast tile: one power-of-two element per cell.
         const int E = int(cell);
-        static const int TAs[17] = {0, 128, 128, 0, 64, 0, 0, 0, 32, 0, 0, 0, 0, 0, 0, 0, 16};
-        static const int TBs[17] = {0, 128, 64, 0, 64, 0, 0, 0, 64, 0, 0, 0, 0, 0, 0, 0, 64};
-        t.TA = uint32_t(TAs[E]);
-        t.TB = uint32_t(TBs[E]);
+
         // Widest legal global access on each side: every input row starts at a
         // multiple of DA*E bytes from src, every output row at a multiple of
         // DB*E bytes from dst.
@@ -244,10 +288,16 @@ rearr_status plan_permute(void *dst, const void *src, size_t elem_bytes, int ran
         for (int v : {vmax, 4}) {
             if (v > E && (uint64_t(DB) * E) % v == 0 && da % v == 0) { vout = v; break; }
         }
+        // Staged row length: the default for the element size, or for the fully
+        // vectorised widths the length that fills the tiles best.
+        int rowb = default_rowb(E);
+        if (vin == 16 && vout == std::min(16, 4 * E)) rowb = choose_rowb(E, DA, DB);
+        t.TA = uint32_t(rowb / E);
+        t.TB = uint32_t(kTileBytes / rowb);
         info.kind = REARR_KIND_TILE;
         info.vec_in = vin;
         info.vec_out = vout;
-        t.variant = tile_variant(E, vin, vout);
+        t.variant = tile_variant(E, vin, vout, rowb);
         t.c = 1;
         t.pitch = 0;
         op.cls = OC_TILE;

@@ -21,6 +21,7 @@ constexpr int kThreads = 256;  // threads per CTA of every tile kernel
 constexpr int kTileBytes = 16384;               // payload of one fast tile
 constexpr int kCellSmemBytes = 16384 + 4096;    // cells tile incl. padding
 constexpr int kSmemBytes = 20480;               // smem of any tile body
+constexpr int kMaxRunsPerUnit = 256;            // run offsets staged in smem
 
 // Unsigned 32-bit division by a run-time invariant divisor with one
 // multiply-high, a subtract, an add and two shifts (Granlund & Montgomery,
@@ -112,8 +113,11 @@ struct RunsDesc {
     int64_t in_stride[kMaxRank];  // bytes, per outer axis
     FastDiv div[kMaxRank];        // outer extents, innermost last
     int32_t nd;                   // number of outer axes
-    uint32_t runs_per_unit;       // runs handled per work unit
+    uint32_t runs_per_unit;       // runs handled per work unit (<= kMaxRunsPerUnit)
     uint64_t n_runs;
+    FastDiv wpr_div;              // words per run
+    FastDiv cpr_div;              // chunks per run (> 1: long runs, one chunk per unit)
+    uint32_t chunk_words;         // words per chunk of a long run
 };
 
 struct CopyDesc {
@@ -160,10 +164,10 @@ struct OpDesc {
     };
 };
 
-// Fast-tile variant ids: E in {1,2,4,8,16} x VIN x VOUT.
-constexpr RH_HD uint32_t tile_variant(int E, int vin, int vout)
+// Fast-tile variant ids: E in {1,2,4,8,16} x VIN x VOUT x staged row bytes.
+constexpr RH_HD uint32_t tile_variant(int E, int vin, int vout, int rowb)
 {
-    return uint32_t(E) | (uint32_t(vin) << 8) | (uint32_t(vout) << 16);
+    return uint32_t(E) | (uint32_t(vin) << 6) | (uint32_t(vout) << 12) | (uint32_t(rowb / 128) << 18);
 }
 
 }  // namespace rearr

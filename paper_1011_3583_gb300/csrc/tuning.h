@@ -1,4 +1,5 @@
-// batch.h -- tuning knobs of the batched persistent kernel.
+// tuning.h -- tuning knobs of librearr: the batched kernel's work grab and
+// the fast tile's staged row length per (element size, plane extents) class.
 #pragma once
 
 #include <stdint.h>
@@ -21,5 +22,12 @@ struct BatchTuning {
         return uint32_t(g);
     }
 };
+
+const BatchTuning &batch_tuning();
+
+// Staged row bytes (128, 256 or 512) the tuning table assigns to a fully
+// vectorised fast tile of element size E on a DA x DB plane; 0 if the table has
+// no entry for that class.
+int tuned_rowb(int E, int64_t DA, int64_t DB);
 
 }  // namespace rearr

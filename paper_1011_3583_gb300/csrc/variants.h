@@ -1,0 +1,26 @@
+// variants.h -- the fast-tile template instances compiled into librearr.
+// X(E, VIN, VOUT, ROWB): element bytes, global load width along A, global
+// store width along B, staged row bytes.  Every (E, VIN, VOUT) combination the
+// planner can pick exists at the element size's default row length; the
+// fully vectorised combination also exists at the other row lengths, which
+// the planner picks for narrow or short planes.
+#pragma once
+
+#define REARR_TILE_VARIANTS(X)                                                                   \
+    X(1, 16, 4, 128) X(1, 4, 4, 128) X(1, 1, 4, 128) X(1, 16, 1, 128) X(1, 4, 1, 128)             \
+    X(1, 1, 1, 128) X(1, 16, 4, 256)                                                              \
+    X(2, 16, 8, 256) X(2, 4, 8, 256) X(2, 2, 8, 256) X(2, 16, 4, 256) X(2, 4, 4, 256)             \
+    X(2, 2, 4, 256) X(2, 16, 2, 256) X(2, 4, 2, 256) X(2, 2, 2, 256) X(2, 16, 8, 128)             \
+    X(2, 16, 8, 512)                                                                              \
+    X(4, 16, 16, 256) X(4, 4, 16, 256) X(4, 16, 4, 256) X(4, 4, 4, 256) X(4, 16, 16, 128)         \
+    X(4, 16, 16, 512)                                                                             \
+    X(8, 16, 16, 256) X(8, 8, 16, 256) X(8, 16, 8, 256) X(8, 8, 8, 256) X(8, 16, 16, 128)         \
+    X(8, 16, 16, 512)                                                                             \
+    X(16, 16, 16, 256) X(16, 16, 16, 128) X(16, 16, 16, 512)
+
+namespace rearr {
+
+// Default staged row length of an element size (used by the fallback widths).
+constexpr int default_rowb(int E) { return E == 1 ? 128 : 256; }
+
+}  // namespace rearr
