@@ -142,6 +142,33 @@ rearr_status rearr_plan_finalize(rearr_plan *plan, rearr_stream_t stream);
 rearr_status rearr_batch(rearr_plan *plan, rearr_stream_t stream);
 void rearr_plan_destroy(rearr_plan *plan);
 
+/* ---------------------------------------------------------------------------
+ * rearr_batch_noalloc -- run a plan's ops with the batched kernel without any
+ * device allocation.  The paper has no counterpart; this is a service for
+ * callers that cannot call cudaMalloc, such as a serving process that has
+ * reserved the GPU's memory for its own pool and must not see a library grow
+ * device memory, or a latency-critical path that cannot take the device-wide
+ * synchronisation cudaMalloc / cudaFree may cause.
+ *
+ *   plan   : a plan built with rearr_plan_add_* (finalized or not; only its
+ *            host-side op list is read).  The caller still owns every input
+ *            and output buffer the ops name.
+ *   stream : the work list is copied and the kernel launched on this stream.
+ *
+ * The work list goes to a fixed 512 KiB device buffer compiled into the
+ * library (about 1400 ops; fewer when interlaces have more than 8 planes);
+ * every GPU that loads the library holds that buffer until the process exits.
+ * A plan that does not fit returns REARR_EINVAL and launches nothing.  The
+ * first call on a device looks up the buffer's address and the kernel's
+ * occupancy (cudaGetSymbolAddress and device queries) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the buffer and leave their contents in it: calls whose work overlaps on the
+ * GPU (several streams or host threads) race on it and must be ordered by the
+ * caller, e.g. by issuing them on one stream.  Results are the same as
+ * rearr_batch's.  Calls no cudaMalloc, cudaFree or other allocating routine.
+ * ------------------------------------------------------------------------- */
+rearr_status rearr_batch_noalloc(const rearr_plan *plan, rearr_stream_t stream);
+
 /* Number of ops and of work-list tiles in a plan (after finalize), host only. */
 rearr_status rearr_plan_stats(const rearr_plan *plan, int64_t *n_ops, int64_t *n_tiles);
 

@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -398,3 +399,113 @@ rearr_status rearr_plan_stats(const rearr_plan *plan, int64_t *n_ops, int64_t *n
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// rearr_batch_noalloc: the batched kernel run from a fixed, statically sized
+// work-list buffer instead of a buffer that rearr_plan_finalize allocates.
+//
+// Some callers cannot call cudaMalloc: a serving process that has reserved
+// the GPU's memory for its own pool up front must not have a library grow
+// device memory behind its back, and a latency-critical path cannot afford
+// the device-wide synchronisation cudaMalloc / cudaFree may imply.  For them
+// the work list (op descriptors, tile prefix sums, plane pointer arrays and
+// the work counter) lives in g_noalloc_worklist below, a file-scope device
+// array of kNoallocBytes that every GPU loading this library holds until the
+// process exits.  Every call shares it and leaves its contents behind; calls
+// whose kernels overlap on the GPU (different streams, or several host
+// threads) race on it, so callers must order them, e.g. on one stream.
+
+namespace {
+
+constexpr size_t kNoallocBytes = 512 * 1024;
+constexpr int kNoallocMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_worklist[kNoallocBytes];
+
+struct NoallocDevice {
+    bool ready = false;
+    unsigned char *addr = nullptr;  // device address of g_noalloc_worklist
+    int resident = 0;               // SMs x resident k_batch CTAs per SM
+};
+
+std::mutex g_noalloc_mu;
+NoallocDevice g_noalloc_dev[kNoallocMaxDevices];
+unsigned char g_noalloc_image[kNoallocBytes];  // host image, built under the mutex
+
+size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+extern "C" rearr_status rearr_batch_noalloc(const rearr_plan *plan, rearr_stream_t stream)
+{
+    if (!plan) return fail(REARR_EINVAL, "rearr_batch_noalloc: plan is NULL");
+    const size_t n = plan->ops.size();
+    if (n == 0) return REARR_OK;
+    size_t n_ptrs = 0;
+    for (auto &l : plan->plane_lists) n_ptrs += l.size();
+    const size_t off_prefix = round256(n * sizeof(OpDesc));
+    const size_t off_planes = off_prefix + round256((n + 1) * sizeof(uint64_t));
+    const size_t off_counter = off_planes + round256(n_ptrs * sizeof(char *));
+    const size_t need = off_counter + 256;
+    if (need > kNoallocBytes) {
+        return fail(REARR_EINVAL, "rearr_batch_noalloc: the plan's work list needs " + std::to_string(need) +
+                                      " bytes, more than the fixed " + std::to_string(kNoallocBytes) +
+                                      "-byte buffer (about 1400 ops); use rearr_plan_finalize + rearr_batch");
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "rearr_batch_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(REARR_EINVAL, "rearr_batch_noalloc: device id out of range");
+
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoallocDevice &nd = g_noalloc_dev[dev];
+    if (!nd.ready) {
+        // One-time set-up on this device, with the device current.
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_worklist);
+        if (e != cudaSuccess) return cuda_fail(e, "rearr_batch_noalloc: cudaGetSymbolAddress");
+        int sms = 0, per_sm = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kThreads, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "rearr_batch_noalloc: device query");
+        nd.addr = static_cast<unsigned char *>(p);
+        nd.resident = std::max(1, sms * std::max(per_sm, 1));
+        nd.ready = true;
+    }
+
+    // Host image: descriptors (plane arrays re-pointed into the buffer),
+    // prefix sums of the tile counts, plane pointers, and a zero work counter.
+    unsigned char *img = g_noalloc_image;
+    std::memset(img, 0, need);
+    OpDesc *ops = reinterpret_cast<OpDesc *>(img);
+    uint64_t *prefix = reinterpret_cast<uint64_t *>(img + off_prefix);
+    char **planes = reinterpret_cast<char **>(img + off_planes);
+    size_t pi = 0;
+    for (size_t i = 0; i < n; ++i) {
+        ops[i] = plan->ops[i];
+        prefix[i + 1] = prefix[i] + plan->ops[i].units;
+        const auto &l = plan->plane_lists[i];
+        if (!l.empty()) {
+            std::memcpy(planes + pi, l.data(), l.size() * sizeof(char *));
+            ops[i].inter.planes_dev = reinterpret_cast<char *const *>(nd.addr + off_planes + pi * sizeof(char *));
+            pi += l.size();
+        }
+    }
+    const uint64_t total = prefix[n];
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // From pageable host memory: the call returns once the image is staged,
+    // so the static host image may be rebuilt by the next call.
+    e = cudaMemcpyAsync(nd.addr, img, need, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "rearr_batch_noalloc: work-list upload");
+    const uint32_t grab = batch_tuning().grab_for(total, uint64_t(nd.resident));
+    uint64_t grid = uint64_t(nd.resident);
+    const uint64_t grabs = (total + grab - 1) / grab;
+    if (grid > grabs) grid = grabs;
+    k_batch<<<unsigned(std::max<uint64_t>(grid, 1)), kThreads, 0, s>>>(
+        reinterpret_cast<const OpDesc *>(nd.addr), reinterpret_cast<const uint64_t *>(nd.addr + off_prefix), int(n),
+        reinterpret_cast<unsigned long long *>(nd.addr + off_counter), grab);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "rearr_batch_noalloc: launch");
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return REARR_OK;
+}

@@ -77,6 +77,7 @@ def load() -> ctypes.CDLL:
         "rearr_plan_add_deinterlace": (st, [vp, ctypes.POINTER(vp), vp, ctypes.c_int, sz, sz]),
         "rearr_plan_finalize": (st, [vp, vp]),
         "rearr_batch": (st, [vp, vp]),
+        "rearr_batch_noalloc": (st, [vp, vp]),
         "rearr_plan_destroy": (None, [vp]),
         "rearr_plan_stats": (st, [vp, i64p, i64p]),
         "rearr_permute_describe": (st, [sz, ctypes.c_int, i64p, ip, ctypes.c_size_t, ctypes.c_size_t,
@@ -215,6 +216,11 @@ class Plan:
     def run(self, stream=None) -> None:
         _check(load().rearr_batch(self._h, _stream(stream)))
 
+    def run_noalloc(self, stream=None) -> None:
+        """rearr_batch_noalloc: run the plan from the library's fixed work-list
+        buffer, allocating nothing on the device."""
+        _check(load().rearr_batch_noalloc(self._h, _stream(stream)))
+
     def stats(self) -> tuple[int, int]:
         a, b = ctypes.c_int64(), ctypes.c_int64()
         _check(load().rearr_plan_stats(self._h, ctypes.byref(a), ctypes.byref(b)))
@@ -230,3 +236,9 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def batch_noalloc(plan: "Plan", stream=None) -> None:
+    """rearr_batch_noalloc: run a plan's ops from the library's fixed
+    work-list buffer, with no device allocation (see include/librearr.h)."""
+    _check(load().rearr_batch_noalloc(plan._h, _stream(stream)))
