@@ -592,6 +592,102 @@ def run_reference(args):
             "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def parse_case(spec: str):
+    """Single-op case spec: permute:E:d0,d1,..:p0,p1,.. | reorder:E:n:random|block4096 |
+    interlace:E:n:k | deinterlace:E:n:k."""
+    parts = spec.split(":")
+    kind, e = parts[0], int(parts[1])
+    if kind == "permute":
+        return dict(kind=kind, elem_bytes=e, dims=[int(x) for x in parts[2].split(",")],
+                    perm=[int(x) for x in parts[3].split(",")])
+    if kind == "reorder":
+        return dict(kind=kind, elem_bytes=e, n=int(parts[2]), idx=parts[3])
+    if kind in ("interlace", "deinterlace"):
+        return dict(kind=kind, elem_bytes=e, n=int(parts[2]), k=int(parts[3]))
+    raise SystemExit(f"unknown case kind {kind}")
+
+
+def run_case(args):
+    """Time one op (used for profiling captures and sweeps): W untimed and K
+    timed calls on one stream, CUDA events around each call."""
+    import torch
+    import synth
+    from paper_1011_3583_gb300 import build as rbuild
+    rbuild.build()
+    import paper_1011_3583_gb300 as rr
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    if args.case.startswith("batch:"):
+        return run_batch_case(torch, rr, stream, dev, int(args.case.split(":")[1]), args)
+    o = parse_case(args.case)
+    e = o["elem_bytes"]
+    if o["kind"] in ("permute", "reorder"):
+        n = int(np.prod(o["dims"])) if o["kind"] == "permute" else o["n"]
+        src = torch.empty(n * e, dtype=torch.uint8, device=dev).random_()
+        dst = torch.empty(n * e, dtype=torch.uint8, device=dev)
+        if o["kind"] == "reorder":
+            a = (synth.random_permutation(7, n) if o["idx"] == "random"
+                 else synth.block_shuffled_permutation(8, n, 4096))
+            idx = torch.from_numpy(a.view(np.uint8)).to(dev)
+            call = lambda: rr.reorder(dst, src, idx, n, e, stream)  # noqa: E731
+            nbytes = 2 * n * e + 4 * n
+        else:
+            call = lambda: rr.permute(dst, src, e, o["dims"], o["perm"], stream)  # noqa: E731
+            nbytes = 2 * n * e
+    else:
+        n, k = o["n"], o["k"]
+        planes = [torch.empty(n * e, dtype=torch.uint8, device=dev).random_() for _ in range(k)]
+        inter = torch.empty(n * k * e, dtype=torch.uint8, device=dev).random_()
+        if o["kind"] == "interlace":
+            call = lambda: rr.interlace(inter, planes, n, e, stream)  # noqa: E731
+        else:
+            call = lambda: rr.deinterlace(planes, inter, n, e, stream)  # noqa: E731
+        nbytes = 2 * n * k * e
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        call()
+        s1.record(stream)
+        s1.synchronize()
+        times.append(s0.elapsed_time(s1) / 1e3)
+    med = statistics.median(times)
+    plan = rr.describe_permute(e, o["dims"], o["perm"]) if o["kind"] == "permute" else None
+    return {"case": args.case, "bytes": nbytes, "median_ms": round(med * 1e3, 4),
+            "best_ms": round(min(times) * 1e3, 4), "gbs_median": round(nbytes / med / 1e9, 1),
+            "gbs_best": round(nbytes / min(times) / 1e9, 1), "plan": plan, "steps": args.steps}
+
+
+def run_batch_case(torch, rr, stream, dev, n_ops, args):
+    """batch:N -- the first N ops of the uneven mix as one plan, replayed."""
+    import synth
+    ops = synth.batch_mix(seed=1, n_ops=n_ops)
+    pool, bufs = batch_buffers(torch, ops, dev)
+    plan = rr.Plan()
+    for o, p in zip(ops, bufs):
+        add_to_plan(plan, o, p)
+    plan.finalize(stream)
+    nbytes = sum(synth.op_bytes(o) for o in ops)
+    for _ in range(args.warmup):
+        plan.run(stream)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        plan.run(stream)
+        s1.record(stream)
+        s1.synchronize()
+        times.append(s0.elapsed_time(s1) / 1e3)
+    plan.close()
+    med = statistics.median(times)
+    return {"case": args.case, "bytes": nbytes, "median_ms": round(med * 1e3, 4),
+            "gbs_median": round(nbytes / med / 1e9, 1), "ops_per_s": round(n_ops / med, 1), "steps": args.steps}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -601,7 +697,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--case", default=None, help="time one op instead of the workload (see parse_case)")
     args = ap.parse_args()
+    if args.case:
+        print(json.dumps(run_case(args)), flush=True)
+        return
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3
     res = run_reference(args) if args.impl == "reference" else run_gpu(args)
