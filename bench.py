@@ -319,7 +319,13 @@ def run_gpu(args):
                 "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "frac_of_memcpy": round(achieved / memcpy_gbs, 4),
                 "algorithmic_bytes_per_launch": int(fam_bytes[dom] / fam_launch[dom]),
-                "traffic": (traffic or {}).get("families", {}).get(dom)}
+                "traffic": None, "traffic_source": None}
+    fam_traffic = (traffic or {}).get("families", {}).get(dom)
+    if fam_traffic:
+        # DRAM bytes per launch from the committed ncu capture, scaled from the
+        # captured case to the mean launch of this family by algorithmic bytes
+        roofline["traffic"] = int(fam_traffic["ratio_to_algorithmic"] * roofline["algorithmic_bytes_per_launch"])
+        roofline["traffic_source"] = "profiles/traffic.json (" + fam_traffic["measured_case"] + ", scaled)"
     families = {f: {"gbs": round(fam_bytes[f] / fam_time[f] / 1e9, 1), "time_share": round(fam_time[f] / sum(fam_time.values()), 4),
                     "launches_per_step": fam_launch[f] // args.steps} for f in fam_time}
     per_op_gbs = [round(op_bytes(o) * args.steps / per_op[i] / 1e9, 1) for i, o in enumerate(ops)]
