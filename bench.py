@@ -340,6 +340,7 @@ def run_gpu(args):
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
 
     batched = None if args.no_batched else run_batched(torch, rr, stream, device)
+    serving = None if args.no_serving else run_serving(torch, rr, device)
 
     result = None
     if rank == 0:
@@ -356,7 +357,7 @@ def run_gpu(args):
             "frac_of_8tbs": round(value / world / 8000.0, 4),
             "roofline": roofline, "families": families, "per_op_gbs": per_op_gbs,
             "gpu_launches": int(launches), "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu,
-            "batched": batched,
+            "batched": batched, "serving": serving,
             "source_digest": source_digest(),
         }
     if world > 1:
@@ -472,6 +473,67 @@ def run_batched(torch, rr, stream, device, n_ops=4096, reps=5):
             "batched_gbs": round(total_bytes / t_batch / 1e9, 1), "plain_gbs": round(total_bytes / t_plain / 1e9, 1),
             "speedup": round(t_plain / t_batch, 3), "plan_build_s": round(t_build, 3),
             "launches_per_replay": 1, "kernels_per_plain_pass": n_ops}
+
+
+# ---------------------------------------------------------------------------
+# serving: Poisson arrivals into the request loop, batched vs plain
+
+def serving_trace(n_req, seed=2):
+    """95 % of requests from the uneven mix, 5 % large rank-3/4 fp32 permutes of
+    256 MB - 1 GB with random perms, in a seeded random order."""
+    import synth
+    g = synth.rng(seed)
+    mix = synth.batch_mix(seed=seed, n_ops=n_req)
+    ops = []
+    for i in range(n_req):
+        ops.append(synth.large_permute(g) if g.random() < 0.05 else mix[i])
+    return ops
+
+
+def pct(v, q):
+    return float(np.percentile(np.asarray(v), q))
+
+
+def run_serving(torch, rr, device, n_req=6000, budget=64 << 30):
+    import synth
+    ops = serving_trace(n_req)
+    templates, keep = [], []
+    for o in ops:
+        row = [None] * 4
+        if o["kind"] == "reorder":  # valid indices are part of a reorder request's payload
+            p = torch.randperm(o["n"], device=device, dtype=torch.int64).to(torch.int32)
+            keep.append(p)
+            row[1] = p
+        templates += row
+    total_bytes = sum(synth.op_bytes(o) for o in ops)
+
+    def run(batching, arrivals):
+        srv = rr.Server(budget_bytes=budget, n_streams=3, max_batch_ops=1024, batching=batching,
+                        poll_interval_us=10)
+        lat, wall = srv.run_trace(ops, arrivals, templates, timeout_us=600_000_000)
+        st = srv.stats()
+        srv.close()
+        lat_ms = [x * 1e3 for x in lat]
+        return {"p50_ms": round(pct(lat_ms, 50), 3), "p99_ms": round(pct(lat_ms, 99), 3),
+                "mean_ms": round(float(np.mean(lat_ms)), 3), "ops_per_s": round(n_req / wall, 1),
+                "gbs": round(total_bytes / wall / 1e9, 1), "launches": int(st["launches"]),
+                "slab_peak_gb": round(st["slab_peak"] / 1e9, 2)}
+
+    zero = np.zeros(n_req)
+    run(False, zero)  # warm-up (module load, first launches)
+    sat_plain = run(False, zero)
+    sat_batched = run(True, zero)
+    rates = []
+    for f in (0.5, 0.9, 1.5):
+        r = f * sat_plain["ops_per_s"]
+        arr = synth.poisson_arrivals(100 + int(10 * f), r, n_req)
+        rates.append({"offered_x_plain_saturated": f, "offered_ops_per_s": round(r, 1),
+                      "batched": run(True, arr), "plain": run(False, arr)})
+    del keep
+    return {"workload": f"{n_req} requests: 95 % uneven mix (seed 2), 5 % rank-3/4 fp32 permutes of 256 MB - 1 GB; "
+                        "Poisson arrivals; 64 GB device budget; 3 streams; batched = continuous batching into the "
+                        "persistent kernel, plain = one single-op launch per request",
+            "bytes": int(total_bytes), "saturated": {"plain": sat_plain, "batched": sat_batched}, "rates": rates}
 
 
 def run_e2e(torch, rr, wl, ops, stream, args):
@@ -703,6 +765,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--case", default=None, help="time one op instead of the workload (see parse_case)")
     args = ap.parse_args()
     if args.case:

@@ -21,6 +21,7 @@
 #include "launch.h"
 #include "plan.h"
 #include "variants.h"
+#include "worklist.h"
 
 namespace rearr {
 
@@ -509,3 +510,77 @@ extern "C" rearr_status rearr_batch_noalloc(const rearr_plan *plan, rearr_stream
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return REARR_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Work lists built and launched from host code (serving loop).
+
+namespace rearr {
+
+WorklistLayout worklist_layout(size_t n_ops, size_t n_ptrs)
+{
+    WorklistLayout l;
+    l.off_prefix = round256(n_ops * sizeof(OpDesc));
+    l.off_planes = l.off_prefix + round256((n_ops + 1) * sizeof(uint64_t));
+    l.off_counter = l.off_planes + round256(n_ptrs * sizeof(char *));
+    l.bytes = l.off_counter + 256;
+    return l;
+}
+
+uint64_t build_worklist(const OpDesc *ops, const std::vector<char *> *plane_lists, size_t n, unsigned char *img,
+                        uintptr_t dev_base, const WorklistLayout &layout)
+{
+    OpDesc *dops = reinterpret_cast<OpDesc *>(img);
+    uint64_t *prefix = reinterpret_cast<uint64_t *>(img + layout.off_prefix);
+    char **planes = reinterpret_cast<char **>(img + layout.off_planes);
+    prefix[0] = 0;
+    size_t pi = 0;
+    for (size_t i = 0; i < n; ++i) {
+        dops[i] = ops[i];
+        prefix[i + 1] = prefix[i] + ops[i].units;
+        const std::vector<char *> &l = plane_lists[i];
+        if (!l.empty()) {
+            std::memcpy(planes + pi, l.data(), l.size() * sizeof(char *));
+            dops[i].inter.planes_dev = reinterpret_cast<char *const *>(dev_base + layout.off_planes + pi * sizeof(char *));
+            pi += l.size();
+        }
+    }
+    std::memset(img + layout.off_counter, 0, 256);
+    return prefix[n];
+}
+
+static int resident_ctas_current_device()
+{
+    static std::mutex mu;
+    static int cached[kNoallocMaxDevices] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!cached[dev]) {
+        int sms = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kThreads, 0) != cudaSuccess) return 0;
+        cached[dev] = std::max(1, sms * std::max(per_sm, 1));
+    }
+    return cached[dev];
+}
+
+cudaError_t launch_worklist(uintptr_t dev_base, const WorklistLayout &layout, size_t n, uint64_t total_units,
+                            cudaStream_t s)
+{
+    if (n == 0 || total_units == 0) return cudaSuccess;
+    const int resident = resident_ctas_current_device();
+    if (resident == 0) return cudaErrorInvalidDevice;
+    const uint32_t grab = batch_tuning().grab_for(total_units, uint64_t(resident));
+    uint64_t grid = uint64_t(resident);
+    const uint64_t grabs = (total_units + grab - 1) / grab;
+    if (grid > grabs) grid = grabs;
+    const char *base = reinterpret_cast<const char *>(dev_base);
+    k_batch<<<unsigned(std::max<uint64_t>(grid, 1)), kThreads, 0, s>>>(
+        reinterpret_cast<const OpDesc *>(base), reinterpret_cast<const uint64_t *>(base + layout.off_prefix), int(n),
+        reinterpret_cast<unsigned long long *>(const_cast<char *>(base) + layout.off_counter), grab);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+    return e;
+}
+
+}  // namespace rearr

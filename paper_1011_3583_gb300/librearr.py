@@ -242,3 +242,196 @@ def batch_noalloc(plan: "Plan", stream=None) -> None:
     """rearr_batch_noalloc: run a plan's ops from the library's fixed
     work-list buffer, with no device allocation (see include/librearr.h)."""
     _check(load().rearr_batch_noalloc(plan._h, _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# Serving (include/librearr_serve.h)
+
+OP_PERMUTE, OP_REORDER, OP_INTERLACE, OP_DEINTERLACE = range(4)
+_OP_KINDS = {"permute": OP_PERMUTE, "reorder": OP_REORDER, "interlace": OP_INTERLACE,
+             "deinterlace": OP_DEINTERLACE}
+
+
+class OpSpec(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("rank", ctypes.c_int), ("k", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("elem_bytes", ctypes.c_size_t), ("n", ctypes.c_size_t), ("dims", ctypes.c_int64 * 8),
+                ("perm", ctypes.c_int * 8)]
+
+    @classmethod
+    def from_dict(cls, op: dict) -> "OpSpec":
+        s = cls()
+        s.kind = _OP_KINDS[op["kind"]]
+        s.elem_bytes = int(op["elem_bytes"])
+        if op["kind"] == "permute":
+            s.rank = len(op["dims"])
+            for i, (d, p) in enumerate(zip(op["dims"], op["perm"])):
+                s.dims[i] = int(d)
+                s.perm[i] = int(p)
+        else:
+            s.n = int(op["n"])
+            s.k = int(op.get("k", 0))
+        return s
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("n_streams", ctypes.c_int), ("max_batch_ops", ctypes.c_int),
+                ("batching", ctypes.c_int), ("poll_interval_us", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("released", ctypes.c_uint64),
+                ("launches", ctypes.c_uint64), ("slab_bytes", ctypes.c_size_t), ("slab_used", ctypes.c_size_t),
+                ("slab_peak", ctypes.c_size_t), ("busy_seconds", ctypes.c_double)]
+
+
+_serve_bound = False
+
+
+def _bind_serve():
+    global _serve_bound
+    if _serve_bound:
+        return load()
+    L = load()
+    vp, sz, st, u64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint64
+    up = ctypes.c_size_t  # uintptr_t
+    sigs = {
+        "rearr_arena_create": (st, [up, sz, ctypes.POINTER(vp)]),
+        "rearr_arena_alloc": (st, [vp, sz, ctypes.POINTER(up)]),
+        "rearr_arena_free": (st, [vp, up]),
+        "rearr_arena_stats": (st, [vp, ctypes.POINTER(sz), ctypes.POINTER(sz), ctypes.POINTER(sz), ctypes.POINTER(sz)]),
+        "rearr_arena_destroy": (None, [vp]),
+        "rearr_server_create": (st, [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]),
+        "rearr_server_reserve": (st, [vp, ctypes.POINTER(OpSpec), ctypes.c_int64, ctypes.POINTER(u64)]),
+        "rearr_server_buffers": (st, [vp, u64, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(vp),
+                                      ctypes.POINTER(ctypes.c_int)]),
+        "rearr_server_submit": (st, [vp, u64]),
+        "rearr_server_poll": (st, [vp, u64, ctypes.POINTER(ctypes.c_int)]),
+        "rearr_server_wait": (st, [vp, u64, ctypes.c_int64]),
+        "rearr_server_latency": (st, [vp, u64, ctypes.POINTER(ctypes.c_double)]),
+        "rearr_server_release": (st, [vp, u64]),
+        "rearr_server_stats_get": (st, [vp, ctypes.POINTER(ServerStats)]),
+        "rearr_server_inject_completion_delay": (st, [vp, ctypes.c_int64]),
+        "rearr_server_destroy": (st, [vp, ctypes.c_int64]),
+        "rearr_server_run_trace": (st, [vp, ctypes.POINTER(OpSpec), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(vp), sz, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.c_int64]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _serve_bound = True
+    return L
+
+
+class Arena:
+    """rearr_arena_*: first-fit allocator over an address range (host only)."""
+
+    def __init__(self, base: int, nbytes: int):
+        L = _bind_serve()
+        h = ctypes.c_void_p()
+        _check(L.rearr_arena_create(base, nbytes, ctypes.byref(h)))
+        self._h = h
+
+    def alloc(self, nbytes: int) -> int:
+        a = ctypes.c_size_t()
+        _check(_bind_serve().rearr_arena_alloc(self._h, nbytes, ctypes.byref(a)))
+        return a.value
+
+    def free(self, addr: int) -> None:
+        _check(_bind_serve().rearr_arena_free(self._h, addr))
+
+    def stats(self) -> dict:
+        u, f, lg, nb = (ctypes.c_size_t() for _ in range(4))
+        _check(_bind_serve().rearr_arena_stats(self._h, ctypes.byref(u), ctypes.byref(f), ctypes.byref(lg),
+                                               ctypes.byref(nb)))
+        return dict(used=u.value, free=f.value, largest_free=lg.value, blocks=nb.value)
+
+    def close(self) -> None:
+        if self._h.value:
+            _bind_serve().rearr_arena_destroy(self._h)
+        self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """rearr_server_*: the serving loop (continuous batching under a device budget)."""
+
+    def __init__(self, budget_bytes: int, n_streams: int = 3, max_batch_ops: int = 1024, batching: bool = True,
+                 poll_interval_us: int = 20):
+        L = _bind_serve()
+        cfg = ServerConfig(int(budget_bytes), int(n_streams), int(max_batch_ops), 1 if batching else 0,
+                           int(poll_interval_us))
+        h = ctypes.c_void_p()
+        _check(L.rearr_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def reserve(self, op: dict, timeout_us: int = -1) -> int:
+        spec = OpSpec.from_dict(op)
+        t = ctypes.c_uint64()
+        _check(_bind_serve().rearr_server_reserve(self._h, ctypes.byref(spec), int(timeout_us), ctypes.byref(t)))
+        return t.value
+
+    def buffers(self, ticket: int) -> tuple[list[int], list[int]]:
+        ins = (ctypes.c_void_p * MAX_K)()
+        outs = (ctypes.c_void_p * MAX_K)()
+        ni, no = ctypes.c_int(), ctypes.c_int()
+        _check(_bind_serve().rearr_server_buffers(self._h, ticket, ins, ctypes.byref(ni), outs, ctypes.byref(no)))
+        return [int(ins[i]) for i in range(ni.value)], [int(outs[i]) for i in range(no.value)]
+
+    def submit(self, ticket: int) -> None:
+        _check(_bind_serve().rearr_server_submit(self._h, ticket))
+
+    def poll(self, ticket: int) -> bool:
+        d = ctypes.c_int()
+        _check(_bind_serve().rearr_server_poll(self._h, ticket, ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket: int, timeout_us: int = -1) -> None:
+        _check(_bind_serve().rearr_server_wait(self._h, ticket, int(timeout_us)))
+
+    def latency(self, ticket: int) -> float:
+        s = ctypes.c_double()
+        _check(_bind_serve().rearr_server_latency(self._h, ticket, ctypes.byref(s)))
+        return s.value
+
+    def release(self, ticket: int) -> None:
+        _check(_bind_serve().rearr_server_release(self._h, ticket))
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(_bind_serve().rearr_server_stats_get(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_}
+
+    def inject_completion_delay(self, delay_us: int) -> None:
+        _check(_bind_serve().rearr_server_inject_completion_delay(self._h, int(delay_us)))
+
+    def run_trace(self, ops: Sequence[dict], arrival_s, templates=None, timeout_us: int = -1):
+        """Replay an arrival trace from native threads; returns (latencies, wall seconds)."""
+        n = len(ops)
+        specs = (OpSpec * max(n, 1))(*[OpSpec.from_dict(o) for o in ops])
+        arr = (ctypes.c_double * max(n, 1))(*[float(a) for a in arrival_s])
+        lat = (ctypes.c_double * max(n, 1))()
+        wall = ctypes.c_double()
+        tmpl = None
+        if templates is not None:
+            tmpl = (ctypes.c_void_p * (4 * max(n, 1)))(*[(_ptr(t) if t is not None else None) for t in templates])
+        _check(_bind_serve().rearr_server_run_trace(self._h, specs, arr, tmpl, n, lat, ctypes.byref(wall),
+                                                    int(timeout_us)))
+        return [lat[i] for i in range(n)], wall.value
+
+    def close(self, timeout_us: int = -1) -> None:
+        if self._h is not None and self._h.value:
+            _check(_bind_serve().rearr_server_destroy(self._h, int(timeout_us)))
+        self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close(timeout_us=10_000_000)
+        except Exception:
+            pass
