@@ -66,6 +66,8 @@ typedef struct {
 
 /* ---------------------------------------------------------------------------
  * Server.
+ * In batching mode, requests moving at least large_bytes (read + write) run as
+ * their own single-op launch in a stream slot; the others are grouped.
  *   budget_bytes     : size of the device slab holding every request buffer
  *                      (one cudaMalloc at create).
  *   n_streams        : batches in flight at once (1..8); each has its stream
@@ -83,6 +85,7 @@ typedef struct {
     int max_batch_ops;
     int batching;
     int poll_interval_us;
+    size_t large_bytes;     /* 0: default 64 MiB */
 } rearr_server_config;
 
 typedef struct rearr_server rearr_server;
@@ -104,6 +107,12 @@ rearr_status rearr_server_buffers(rearr_server *server, uint64_t ticket, void **
 
 /* Queue a reserved request for execution. */
 rearr_status rearr_server_submit(rearr_server *server, uint64_t ticket);
+
+/* Queue a reserved request whose inputs are first copied, on the server's own
+ * stream and in order before its kernel, from device sources: input j is
+ * filled from srcs[j] (NULL: left as the caller wrote it), j < n_srcs.  The
+ * sources must stay valid until the request completes. */
+rearr_status rearr_server_submit_from(rearr_server *server, uint64_t ticket, const void *const *srcs, int n_srcs);
 
 /* Completion: poll, or wait up to timeout_us (REARR_ETIMEDOUT when it runs
  * out; the request stays in flight and can be waited for again). */
@@ -136,12 +145,13 @@ rearr_status rearr_server_destroy(rearr_server *server, int64_t timeout_us);
 /* ---------------------------------------------------------------------------
  * Trace driver: replays an arrival trace against a server from native
  * threads.  Request i arrives at arrival_s[i] seconds after the call starts:
- * it is reserved (waiting for admission), the inputs that have a template
- * pointer in templates[i*4 + j] (device, NULL: leave as is) are copied into
- * its buffers, and it is submitted; a second thread waits for completions in
- * order, records latency_s[i] and releases.  At most 4 inputs carry templates.
- * Returns when every request has completed (or REARR_ETIMEDOUT after
- * timeout_us), with the wall time from the first arrival to the last
+ * it is reserved (waiting for admission) and submitted; inputs with a
+ * template pointer templates[i*4 + j] (device, NULL: left as is; templates
+ * may be NULL) are filled from it on the server's stream before the request's
+ * kernel (rearr_server_submit_from).  A second thread waits for completions
+ * in order, records latency_s[i] from the scheduled arrival time and releases
+ * the request.  Returns when every request has completed (or REARR_ETIMEDOUT
+ * after timeout_us), with the wall time from the first arrival to the last
  * completion in *wall_s.
  * ------------------------------------------------------------------------- */
 rearr_status rearr_server_run_trace(rearr_server *server, const rearr_op_spec *specs, const double *arrival_s,

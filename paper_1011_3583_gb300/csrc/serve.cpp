@@ -57,7 +57,21 @@ struct Req {
     double t_arrival = 0, t_done = 0;
     State state = RESERVED;
     cudaEvent_t ev = nullptr;  // plain mode: completion event of this request
+    std::vector<const void *> in_src;  // device sources copied into the inputs first
+    size_t bytes = 0;                  // read + write bytes of the op
 };
+
+// Copies a request's input sources into its inputs on stream s.
+cudaError_t copy_inputs(const Req &r, const std::vector<size_t> &in_sizes, cudaStream_t s)
+{
+    for (size_t j = 0; j < r.in_src.size() && j < r.ins.size(); ++j) {
+        if (!r.in_src[j]) continue;
+        cudaError_t e = cudaMemcpyAsync(reinterpret_cast<void *>(r.ins[j]), r.in_src[j], in_sizes[j],
+                                        cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
 
 // Byte sizes of a request's buffers (inputs, outputs), or false if invalid.
 bool buffer_sizes(const rearr_op_spec &s, std::vector<size_t> &in, std::vector<size_t> &out, std::string &err)
@@ -249,8 +263,29 @@ void Server::launch_batches(std::unique_lock<std::mutex> &)
         std::vector<std::vector<char *>> planes;
         std::vector<Req *> taken;
         size_t n_ptrs = 0;
+        // A large request runs alone as its single-op kernel.
+        if (ready.front()->bytes >= cfg.large_bytes) {
+            Req *r = ready.front();
+            ready.pop_front();
+            OpDesc op;
+            std::vector<char *> pl;
+            std::string err;
+            std::vector<size_t> in_sz, out_sz;
+            buffer_sizes(r->spec, in_sz, out_sz, err);
+            cudaError_t e = copy_inputs(*r, in_sz, s.stream);
+            if (e == cudaSuccess && plan_request(*r, op, pl, err) == REARR_OK) e = launch_single(op, pl.data(), s.stream);
+            if (e == cudaSuccess) e = cudaEventRecord(s.done, s.stream);
+            if (e != cudaSuccess) worker_error = std::string("launch failed: ") + cudaGetErrorString(e);
+            r->state = RUNNING;
+            s.reqs = {r};
+            s.busy = true;
+            s.t_launch = now_s();
+            ++st.launches;
+            continue;
+        }
         while (!ready.empty() && int(taken.size()) < cfg.max_batch_ops) {
             Req *r = ready.front();
+            if (r->bytes >= cfg.large_bytes) break;  // goes alone into the next free slot
             OpDesc op;
             std::vector<char *> pl;
             std::string err;
@@ -275,7 +310,14 @@ void Server::launch_batches(std::unique_lock<std::mutex> &)
         if (taken.empty()) return;
         const WorklistLayout lay = worklist_layout(ops.size(), n_ptrs);
         cudaError_t e = cudaSuccess;
-        if (!ops.empty()) {
+        for (Req *r : taken) {
+            if (r->in_src.empty() || e != cudaSuccess) continue;
+            std::vector<size_t> in_sz, out_sz;
+            std::string err;
+            buffer_sizes(r->spec, in_sz, out_sz, err);
+            e = copy_inputs(*r, in_sz, s.stream);
+        }
+        if (!ops.empty() && e == cudaSuccess) {
             const uint64_t total = build_worklist(ops.data(), planes.data(), ops.size(), s.host_wl,
                                                   reinterpret_cast<uintptr_t>(s.dev_wl), lay);
             e = cudaMemcpyAsync(s.dev_wl, s.host_wl, lay.bytes, cudaMemcpyHostToDevice, s.stream);
@@ -300,8 +342,12 @@ void Server::launch_plain(std::unique_lock<std::mutex> &)
         OpDesc op;
         std::vector<char *> pl;
         std::string err;
-        cudaError_t e = cudaSuccess;
-        if (plan_request(*r, op, pl, err) == REARR_OK) {
+        std::vector<size_t> in_sz, out_sz;
+        buffer_sizes(r->spec, in_sz, out_sz, err);
+        cudaError_t e = copy_inputs(*r, in_sz, s.stream);
+        if (e != cudaSuccess) {
+            worker_error = std::string("input copy failed: ") + cudaGetErrorString(e);
+        } else if (plan_request(*r, op, pl, err) == REARR_OK) {
             e = launch_single(op, pl.data(), s.stream);
         } else {
             worker_error = "plan failed in the server: " + err;
@@ -361,6 +407,7 @@ rearr_status rearr_server_create(const rearr_server_config *config, rearr_server
     if (c.max_batch_ops < 1 || c.max_batch_ops > 4096)
         return fail(REARR_EINVAL, "rearr_server_create: max_batch_ops must be 1..4096");
     if (c.poll_interval_us < 1) c.poll_interval_us = 1;
+    if (c.large_bytes == 0) c.large_bytes = size_t(64) << 20;
     if (!c.batching) c.n_streams = 1;
     auto *out = new (std::nothrow) rearr_server();
     if (!out) return fail(REARR_ENOMEM, "rearr_server_create: out of host memory");
@@ -424,6 +471,8 @@ rearr_status rearr_server_reserve(rearr_server *server, const rearr_op_spec *spe
     r->ticket = t;
     r->spec = *spec;
     r->t_arrival = t_arrival;
+    for (size_t b : in) r->bytes += b;
+    for (size_t b : out) r->bytes += b;
     auto try_admit = [&]() -> bool {
         if (S.admit_q.front() != t) return false;
         std::vector<uintptr_t> got;
@@ -503,6 +552,22 @@ rearr_status rearr_server_submit(rearr_server *server, uint64_t ticket)
     Req *r = find_req(S, ticket);
     if (!r) return fail(REARR_EINVAL, "rearr_server_submit: unknown ticket");
     if (r->state != RESERVED) return fail(REARR_EBUSY, "rearr_server_submit: request already submitted");
+    r->state = QUEUED;
+    S.ready.push_back(r);
+    S.cv.notify_all();
+    return REARR_OK;
+}
+
+rearr_status rearr_server_submit_from(rearr_server *server, uint64_t ticket, const void *const *srcs, int n_srcs)
+{
+    if (!server || (n_srcs > 0 && !srcs) || n_srcs < 0) return fail(REARR_EINVAL, "rearr_server_submit_from: bad argument");
+    Server &S = server->s;
+    std::lock_guard<std::mutex> lk(S.mu);
+    Req *r = find_req(S, ticket);
+    if (!r) return fail(REARR_EINVAL, "rearr_server_submit_from: unknown ticket");
+    if (r->state != RESERVED) return fail(REARR_EBUSY, "rearr_server_submit_from: request already submitted");
+    if (size_t(n_srcs) > r->ins.size()) return fail(REARR_EINVAL, "rearr_server_submit_from: more sources than inputs");
+    r->in_src.assign(srcs, srcs + n_srcs);
     r->state = QUEUED;
     S.ready.push_back(r);
     S.cv.notify_all();
@@ -630,8 +695,6 @@ rearr_status rearr_server_run_trace(rearr_server *server, const rearr_op_spec *s
 
     std::thread submitter([&] {
         cudaSetDevice(dev);
-        cudaStream_t cs;
-        cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
         for (size_t i = 0; i < n; ++i) {
             const double ta = t0 + arrival_s[i];
             for (;;) {  // sleep until the arrival time, spin for the last 50 us
@@ -643,23 +706,18 @@ rearr_status rearr_server_run_trace(rearr_server *server, const rearr_op_spec *s
             const int64_t left = int64_t((deadline - now_s()) * 1e6);
             rearr_status st = rearr_server_reserve(server, &specs[i], left > 0 ? left : 0, &tk);
             if (st != REARR_OK) { sub_status = st; sub_err = rearr_last_error(); break; }
-            if (templates) {
-                void *ins[kMaxK];
-                int n_in = 0;
-                rearr_server_buffers(server, tk, ins, &n_in, nullptr, nullptr);
-                bool copied = false;
-                for (int j = 0; j < n_in && j < 4; ++j) {
-                    const void *src = templates[i * 4 + size_t(j)];
-                    if (!src) continue;
-                    std::vector<size_t> in, out;
-                    std::string err;
-                    buffer_sizes(specs[i], in, out, err);
-                    cudaMemcpyAsync(ins[j], src, in[size_t(j)], cudaMemcpyDeviceToDevice, cs);
-                    copied = true;
-                }
-                if (copied) cudaStreamSynchronize(cs);
+            bool any = false;
+            if (templates)
+                for (int j = 0; j < 4; ++j) any = any || templates[i * 4 + size_t(j)] != nullptr;
+            if (any) {
+                std::vector<size_t> in, out;
+                std::string err;
+                buffer_sizes(specs[i], in, out, err);
+                const int n_src = int(std::min<size_t>(4, in.size()));
+                rearr_server_submit_from(server, tk, templates + i * 4, n_src);
+            } else {
+                rearr_server_submit(server, tk);
             }
-            rearr_server_submit(server, tk);
             {
                 std::lock_guard<std::mutex> g(tmu);
                 tickets[i] = tk;
@@ -667,7 +725,6 @@ rearr_status rearr_server_run_trace(rearr_server *server, const rearr_op_spec *s
             }
             tcv.notify_all();
         }
-        cudaStreamDestroy(cs);
         tcv.notify_all();
     });
 

@@ -275,7 +275,7 @@ class OpSpec(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_size_t), ("n_streams", ctypes.c_int), ("max_batch_ops", ctypes.c_int),
-                ("batching", ctypes.c_int), ("poll_interval_us", ctypes.c_int)]
+                ("batching", ctypes.c_int), ("poll_interval_us", ctypes.c_int), ("large_bytes", ctypes.c_size_t)]
 
 
 class ServerStats(ctypes.Structure):
@@ -305,6 +305,7 @@ def _bind_serve():
         "rearr_server_buffers": (st, [vp, u64, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(vp),
                                       ctypes.POINTER(ctypes.c_int)]),
         "rearr_server_submit": (st, [vp, u64]),
+        "rearr_server_submit_from": (st, [vp, u64, ctypes.POINTER(vp), ctypes.c_int]),
         "rearr_server_poll": (st, [vp, u64, ctypes.POINTER(ctypes.c_int)]),
         "rearr_server_wait": (st, [vp, u64, ctypes.c_int64]),
         "rearr_server_latency": (st, [vp, u64, ctypes.POINTER(ctypes.c_double)]),
@@ -363,10 +364,10 @@ class Server:
     """rearr_server_*: the serving loop (continuous batching under a device budget)."""
 
     def __init__(self, budget_bytes: int, n_streams: int = 3, max_batch_ops: int = 1024, batching: bool = True,
-                 poll_interval_us: int = 20):
+                 poll_interval_us: int = 20, large_bytes: int = 0):
         L = _bind_serve()
         cfg = ServerConfig(int(budget_bytes), int(n_streams), int(max_batch_ops), 1 if batching else 0,
-                           int(poll_interval_us))
+                           int(poll_interval_us), int(large_bytes))
         h = ctypes.c_void_p()
         _check(L.rearr_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h
@@ -386,6 +387,10 @@ class Server:
 
     def submit(self, ticket: int) -> None:
         _check(_bind_serve().rearr_server_submit(self._h, ticket))
+
+    def submit_from(self, ticket: int, srcs) -> None:
+        arr = _ptr_array(srcs)
+        _check(_bind_serve().rearr_server_submit_from(self._h, ticket, arr, len(srcs)))
 
     def poll(self, ticket: int) -> bool:
         d = ctypes.c_int()
