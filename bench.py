@@ -229,6 +229,22 @@ def measured_peak():
     return 6800.0, "fallback"
 
 
+def max_over_ranks(seconds: float, world: int, device) -> float:
+    """The slowest rank's time (every rank runs a full replica of the workload)."""
+    if world <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world: int, step_bytes: int, steps: int, seconds: float) -> float:
+    """Whole-job GB/s: every rank moved step_bytes per step, timed by the slowest."""
+    return world * step_bytes * steps / seconds / 1e9
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -290,18 +306,14 @@ def run_gpu(args):
         torch.cuda.synchronize()
     barrier()
     launches = rr.launch_count() - launches0
-    elapsed = evs[0].elapsed_time(evs[-1]) / 1e3
-    if world > 1:
-        t = torch.tensor([elapsed], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(evs[0].elapsed_time(evs[-1]) / 1e3, world, device)
     per_op = np.zeros(len(ops))
     k = 1
     for _ in range(args.steps):
         for i in range(len(ops)):
             per_op[i] += evs[k - 1].elapsed_time(evs[k]) / 1e3
             k += 1
-    value = world * step_bytes * args.steps / elapsed / 1e9
+    value = replica_value(world, step_bytes, args.steps, elapsed)
 
     # roofline of the dominant kernel family
     fam_time, fam_bytes, fam_launch = {}, {}, {}
@@ -332,11 +344,8 @@ def run_gpu(args):
 
     # end to end through the public API with pinned host buffers
     t_e2e, e2e_steps, h2d, d2h = run_e2e(torch, rr, wl, ops, stream, args)
-    if world > 1:
-        t = torch.tensor([t_e2e], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": round(world * step_bytes * e2e_steps / t_e2e / 1e9, 1), "unit": "GB/s",
+    t_e2e = max_over_ranks(t_e2e, world, device)
+    e2e = {"value": round(replica_value(world, step_bytes, e2e_steps, t_e2e), 1), "unit": "GB/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
 
     batched = None if args.no_batched else run_batched(torch, rr, stream, device)
