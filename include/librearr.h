@@ -209,6 +209,17 @@ rearr_status rearr_permute_describe(size_t elem_bytes, int rank, const int64_t *
                                     rearr_permute_info *info);
 
 /* ---------------------------------------------------------------------------
+ * Tuning table.  The paper chooses block and thread shapes per kernel by hand
+ * (Sec. III); here the fast tile's staged row length per (element size,
+ * plane-extent class) and the batched kernel's work grab come from a text
+ * table written by the project's autotuner.  rearr_tuning_load reads such a
+ * table (path NULL or "": built-in defaults) for plans compiled afterwards;
+ * REARR_EINVAL if the file cannot be read (the previous table stays).  The
+ * REARR_TUNE_TABLE environment variable names a table read on first use.
+ * ------------------------------------------------------------------------- */
+rearr_status rearr_tuning_load(const char *path);
+
+/* ---------------------------------------------------------------------------
  * Measurement helpers (not rearrangement operations).
  *   rearr_memcpy_d2d   : cudaMemcpyAsync(dst, src, bytes, DeviceToDevice, stream),
  *                        the roofline reference the paper measures against

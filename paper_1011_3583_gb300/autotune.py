@@ -1,0 +1,139 @@
+"""Autotuner of librearr's tuning table (run on the target GPU).
+
+    python -m paper_1011_3583_gb300.autotune --out paper_1011_3583_gb300/tuning/gb300.txt
+
+It measures, with CUDA events and the library's own kernels only:
+
+* for every fully vectorised fast-tile class -- element size E in
+  {1, 2, 4, 8, 16} x input-fastest extent DA x output-fastest extent DB, each
+  extent in one of five buckets -- the staged row length (128, 256 or 512
+  bytes, i.e. the tile shape) that moves a representative permute of that
+  class fastest.  The representative case is a [nb, DB, DA] tensor permuted
+  to [nb, DA, DB], nb chosen so that each call moves about 256 MiB;
+* the batched kernel's work grab (tiles taken per atomicAdd) on the first
+  1024 ops of the uneven mix.
+
+The result is a text table read by rearr_tuning_load (see tuning.cpp).
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import statistics
+import tempfile
+import time
+
+import numpy as np
+
+# (lo, hi, representative) extent buckets; representatives are multiples of 16
+BUCKETS = [(1, 48, 32), (49, 96, 64), (97, 192, 128), (193, 384, 256), (385, 2 ** 31 - 1, 1024)]
+ELEMS = (1, 2, 4, 8, 16)
+TARGET_BYTES = 256 << 20
+
+
+def _time(torch, fn, stream, reps=10, warmup=2):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b) / 1e3)
+    return statistics.median(ts)
+
+
+def _write(path, lines):
+    with open(path, "w") as f:
+        f.write("\n".join(lines) + "\n")
+
+
+def tune_rowb(rr, torch, stream, tmpdir, log):
+    rules = []
+    buf_a = torch.empty(TARGET_BYTES + (1 << 20), dtype=torch.uint8, device="cuda").random_()
+    buf_b = torch.empty_like(buf_a)
+    for E in ELEMS:
+        cands = (128, 256) if E == 1 else (128, 256, 512)
+        for (alo, ahi, DA) in BUCKETS:
+            for (blo, bhi, DB) in BUCKETS:
+                nb = max(1, TARGET_BYTES // (DA * DB * E))
+                dims, perm = [nb, DB, DA], [0, 2, 1]
+                best = None
+                for rowb in cands:
+                    table = os.path.join(tmpdir, "cand.txt")
+                    _write(table, [f"rowb {E} {alo} {ahi} {blo} {bhi} {rowb}"])
+                    rr.tuning_load(table)
+                    d = rr.describe_permute(E, dims, perm, buf_b.data_ptr(), buf_a.data_ptr())
+                    if d["kind"] != "tile" or d["tile_a"] * E != rowb:
+                        continue  # not a fully vectorised tile: the table does not apply
+                    t = _time(torch, lambda: rr.permute(buf_b, buf_a, E, dims, perm, stream), stream)
+                    gbs = 2 * nb * DA * DB * E / t / 1e9
+                    log(f"E={E:2d} DA={DA:5d} DB={DB:5d} rowb={rowb:3d}: {gbs:8.1f} GB/s")
+                    if best is None or gbs > best[1]:
+                        best = (rowb, gbs)
+                if best:
+                    rules.append(f"rowb {E} {alo} {ahi} {blo} {bhi} {best[0]}   # {best[1]:.0f} GB/s")
+    rr.tuning_load(None)
+    return rules
+
+
+def tune_grab(rr, torch, stream, tmpdir, log, n_ops=1024):
+    import bench  # the mix's buffers and plan helpers
+    import synth
+    ops = synth.batch_mix(seed=1, n_ops=n_ops)
+    pool, bufs = bench.batch_buffers(torch, ops, torch.device("cuda"))
+    nbytes = sum(synth.op_bytes(o) for o in ops)
+    best = None
+    for g in (1, 2, 4, 8, 16, 32):
+        table = os.path.join(tmpdir, "grab.txt")
+        _write(table, [f"min_grab {g}", f"max_grab {g}"])
+        rr.tuning_load(table)
+        plan = rr.Plan()
+        for o, p in zip(ops, bufs):
+            bench.add_to_plan(plan, o, p)
+        plan.finalize(stream)
+        t = _time(torch, lambda: plan.run(stream), stream)
+        plan.close()
+        log(f"grab={g:2d}: {nbytes / t / 1e9:8.1f} GB/s  {n_ops / t:10.0f} ops/s")
+        if best is None or t < best[1]:
+            best = (g, t)
+    rr.tuning_load(None)
+    del pool
+    return [f"min_grab {best[0]}", f"max_grab {best[0]}   # {nbytes / best[1] / 1e9:.0f} GB/s on the mix"]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", required=True)
+    args = ap.parse_args()
+    import torch
+    os.environ.pop("REARR_TUNE_TABLE", None)
+    from paper_1011_3583_gb300 import build
+    build.build()
+    import paper_1011_3583_gb300 as rr
+    rr.load()
+    rr.tuning_load(None)
+    stream = torch.cuda.Stream()
+    log_lines = []
+
+    def log(s):
+        print(s, flush=True)
+        log_lines.append("# " + s)
+
+    t0 = time.time()
+    with tempfile.TemporaryDirectory() as tmp:
+        rules = tune_rowb(rr, torch, stream, tmp, log)
+        grab = tune_grab(rr, torch, stream, tmp, log)
+    head = [f"# librearr tuning table for {torch.cuda.get_device_name()} "
+            f"(paper_1011_3583_gb300/autotune.py, {time.time() - t0:.0f} s)"]
+    os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
+    _write(args.out, head + grab + rules + log_lines)
+    print(f"wrote {args.out}: {len(rules)} tile rules")
+
+
+if __name__ == "__main__":
+    np.seterr(all="ignore")
+    main()

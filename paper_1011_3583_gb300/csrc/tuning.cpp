@@ -1,18 +1,24 @@
-// tuning.cpp -- tuning table of librearr.  The defaults can be replaced at
-// run time by a table written by the project's autotuner, named by the
-// REARR_TUNE_TABLE environment variable.  The file holds lines of
+// tuning.cpp -- tuning table of librearr.  The defaults can be replaced by a
+// table written by the project's autotuner (paper_1011_3583_gb300/autotune.py):
+// the file named by the REARR_TUNE_TABLE environment variable is read on first
+// use, and rearr_tuning_load swaps in another file at run time.  Lines:
 //   min_grab <v> | max_grab <v> | grabs_per_cta <v>
 //   rowb <E> <da_lo> <da_hi> <db_lo> <db_hi> <rowb>
-// ("#" starts a comment line).
+// ("#" starts a comment line).  Plans compiled after a load use the new table.
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <mutex>
+#include <string>
 #include <vector>
 
+#include "../../include/librearr.h"
 #include "tuning.h"
 
 namespace rearr {
+
+rearr_status fail(rearr_status st, const std::string &msg);
 
 namespace {
 
@@ -27,47 +33,71 @@ struct Table {
     std::vector<RowbRule> rowb;
 };
 
-const Table &table()
+std::shared_ptr<const Table> parse(const char *path)
 {
-    static Table t;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        const char *path = std::getenv("REARR_TUNE_TABLE");
-        if (!path || !*path) return;
-        FILE *f = std::fopen(path, "r");
-        if (!f) return;
-        char line[256];
-        while (std::fgets(line, sizeof line, f)) {
-            char key[32];
-            unsigned long v;
-            RowbRule r;
-            long long a, b, c, d;
-            if (line[0] == '#') continue;
-            if (std::sscanf(line, "rowb %d %lld %lld %lld %lld %d", &r.E, &a, &b, &c, &d, &r.rowb) == 6) {
-                r.da_lo = a; r.da_hi = b; r.db_lo = c; r.db_hi = d;
-                const bool ok_rowb = r.rowb == 128 || r.rowb == 256 || (r.rowb == 512 && r.E != 1);
-                if (ok_rowb) t.rowb.push_back(r);
-            } else if (std::sscanf(line, "%31s %lu", key, &v) == 2 && v >= 1) {
-                if (!std::strcmp(key, "min_grab")) t.batch.min_grab = uint32_t(v);
-                else if (!std::strcmp(key, "max_grab")) t.batch.max_grab = uint32_t(v);
-                else if (!std::strcmp(key, "grabs_per_cta")) t.batch.grabs_per_cta = uint32_t(v);
-            }
+    FILE *f = std::fopen(path, "r");
+    if (!f) return nullptr;
+    auto t = std::make_shared<Table>();
+    char line[256];
+    while (std::fgets(line, sizeof line, f)) {
+        char key[32];
+        unsigned long v;
+        RowbRule r;
+        long long a, b, c, d;
+        if (line[0] == '#') continue;
+        if (std::sscanf(line, "rowb %d %lld %lld %lld %lld %d", &r.E, &a, &b, &c, &d, &r.rowb) == 6) {
+            r.da_lo = a; r.da_hi = b; r.db_lo = c; r.db_hi = d;
+            const bool ok_rowb = r.rowb == 128 || r.rowb == 256 || (r.rowb == 512 && r.E != 1);
+            if (ok_rowb) t->rowb.push_back(r);
+        } else if (std::sscanf(line, "%31s %lu", key, &v) == 2 && v >= 1) {
+            if (!std::strcmp(key, "min_grab")) t->batch.min_grab = uint32_t(v);
+            else if (!std::strcmp(key, "max_grab")) t->batch.max_grab = uint32_t(v);
+            else if (!std::strcmp(key, "grabs_per_cta")) t->batch.grabs_per_cta = uint32_t(v);
         }
-        std::fclose(f);
-        if (t.batch.max_grab < t.batch.min_grab) t.batch.max_grab = t.batch.min_grab;
-    });
+    }
+    std::fclose(f);
+    if (t->batch.max_grab < t->batch.min_grab) t->batch.max_grab = t->batch.min_grab;
     return t;
+}
+
+std::mutex g_mu;
+std::shared_ptr<const Table> g_table;
+
+std::shared_ptr<const Table> current()
+{
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_table) {
+        const char *path = std::getenv("REARR_TUNE_TABLE");
+        if (path && *path) g_table = parse(path);
+        if (!g_table) g_table = std::make_shared<Table>();
+    }
+    return g_table;
 }
 
 }  // namespace
 
-const BatchTuning &batch_tuning() { return table().batch; }
+BatchTuning batch_tuning() { return current()->batch; }
 
 int tuned_rowb(int E, int64_t DA, int64_t DB)
 {
-    for (const RowbRule &r : table().rowb)
+    const std::shared_ptr<const Table> t = current();
+    for (const RowbRule &r : t->rowb)
         if (r.E == E && DA >= r.da_lo && DA <= r.da_hi && DB >= r.db_lo && DB <= r.db_hi) return r.rowb;
     return 0;
 }
 
 }  // namespace rearr
+
+extern "C" rearr_status rearr_tuning_load(const char *path)
+{
+    std::shared_ptr<const rearr::Table> t;
+    if (path && *path) {
+        t = rearr::parse(path);
+        if (!t) return rearr::fail(REARR_EINVAL, std::string("rearr_tuning_load: cannot read ") + path);
+    } else {
+        t = std::make_shared<rearr::Table>();
+    }
+    std::lock_guard<std::mutex> lock(rearr::g_mu);
+    rearr::g_table = t;
+    return REARR_OK;
+}

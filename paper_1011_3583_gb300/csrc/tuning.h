@@ -23,7 +23,7 @@ struct BatchTuning {
     }
 };
 
-const BatchTuning &batch_tuning();
+BatchTuning batch_tuning();
 
 // Staged row bytes (128, 256 or 512) the tuning table assigns to a fully
 // vectorised fast tile of element size E on a DA x DB plane; 0 if the table has

@@ -19,6 +19,7 @@ from .build import LIB
 
 MAX_RANK = 8
 MAX_K = 256
+DEFAULT_TUNE_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning", "gb300.txt")
 
 STATUS = {0: "REARR_OK", 1: "REARR_EINVAL", 2: "REARR_ENOMEM", 3: "REARR_ECUDA", 4: "REARR_ERANGE",
           5: "REARR_ETIMEDOUT", 6: "REARR_EBUSY"}
@@ -85,13 +86,22 @@ def load() -> ctypes.CDLL:
         "rearr_memcpy_d2d": (st, [vp, vp, sz, vp]),
         "rearr_launch_count": (ctypes.c_uint64, []),
         "rearr_selftest_host": (st, []),
+        "rearr_tuning_load": (st, [ctypes.c_char_p]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
         fn.restype = res
         fn.argtypes = args
     _lib = L
+    # the committed tuning table of this GPU, unless the caller named another
+    if not os.environ.get("REARR_TUNE_TABLE") and os.path.exists(DEFAULT_TUNE_TABLE):
+        L.rearr_tuning_load(DEFAULT_TUNE_TABLE.encode())
     return L
+
+
+def tuning_load(path: str | None) -> None:
+    """rearr_tuning_load: switch the tuning table (None: built-in defaults)."""
+    _check(load().rearr_tuning_load(path.encode() if path else None))
 
 
 def _ptr(x) -> int | None:
