@@ -77,8 +77,14 @@ rearr_status rearr_permute(void *dst, const void *src, size_t elem_bytes, int ra
  * of indices" pattern of arXiv:1011.3583 Sec. III.A:
  *       dst[i] = src[idx[i]],  0 <= i < n.
  *   src holds n elements of elem_bytes; idx holds n uint32 indices, each < n
- *   (repeats allowed).  An index >= n is undefined behaviour in this call (it
- *   is never written outside dst, but the value read is unspecified).
+ *   (repeats allowed).  An index >= n is undefined behaviour (the call would
+ *   read outside src).
+ *   When src is 128 MiB or more and elem_bytes is 4, 8 or 16, the call first
+ *   samples the locality of idx on the device; random indices then go through
+ *   L2-resident bucketed passes (partition by source and destination chunk,
+ *   gather, scatter) with (8 + elem_bytes) * n bytes of scratch from a
+ *   stream-ordered memory pool the library owns (kept for later calls), and
+ *   local indices through the direct gather.  Results are identical.
  * ------------------------------------------------------------------------- */
 rearr_status rearr_reorder(void *dst, const void *src, const uint32_t *idx, size_t n,
                            size_t elem_bytes, rearr_stream_t stream);

@@ -175,7 +175,9 @@ cudaError_t launch_single(const OpDesc &op, char *const *planes_all, cudaStream_
         case OC_TILE_CELLS: return by_word<RunCells>(int(op.word), op, s);
         case OC_RUNS: return by_word<RunRuns>(int(op.word), op, s);
         case OC_COPY: return by_word<RunCopy>(int(op.word), op, s);
-        case OC_GATHER: return by_word<RunGather>(int(op.word), op, s);
+        case OC_GATHER:
+            if (op.gather.l2) return launch_reorder_l2(op, s);
+            return by_word<RunGather>(int(op.word), op, s);
         case OC_INTERLACE:
         case OC_DEINTERLACE: {
             InterlaceParams p;

@@ -16,4 +16,7 @@ extern std::atomic<uint64_t> g_launches;
 // pointers of an interlace / de-interlace (ignored otherwise).
 cudaError_t launch_single(const OpDesc &op, char *const *planes_all, cudaStream_t s);
 
+// The L2-resident bucketed reorder (k_reorder_l2.cu) of a gather op with l2 set.
+cudaError_t launch_reorder_l2(const OpDesc &op, cudaStream_t s);
+
 }  // namespace rearr

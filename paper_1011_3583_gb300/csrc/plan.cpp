@@ -29,6 +29,7 @@ namespace {
 constexpr int64_t kMaxExtent = (int64_t(1) << 31) - 1;
 constexpr int64_t kRunMinBytes = 128;     // cells this large are copied as runs
 constexpr int64_t kRunUnitBytes = 32768;  // payload of one runs work unit
+constexpr uint64_t kReorderL2MinBytes = uint64_t(128) << 20;  // reorder sources this large use L2 passes
 constexpr uint64_t kMaxUnits = 0xFFFFFFFFull;
 
 bool mul_overflows(uint64_t a, uint64_t b, uint64_t &out)
@@ -372,6 +373,10 @@ rearr_status plan_reorder(void *dst, const void *src, const uint32_t *idx, size_
     g.vec = (g.c == 1 && ia % 16 == 0 && da % uint64_t(std::min(16, 4 * W)) == 0) ? 1u : 0u;
     g.unit_elems = g.vec ? uint32_t(kThreads) * 32 : uint32_t(kThreads) * 16;
     op.units = (uint64_t(n) + g.unit_elems - 1) / g.unit_elems;
+    // Sources much larger than the L2 go through the bucketed passes (which
+    // fall back to this direct gather on the device if the indices turn out
+    // to be local).
+    g.l2 = (g.vec && (W == 4 || W == 8 || W == 16) && bytes >= kReorderL2MinBytes && n <= 0xFFFFFFFFull) ? 1u : 0u;
     return REARR_OK;
 }
 

@@ -135,6 +135,7 @@ struct GatherDesc {
     uint32_t c;            // words per element
     uint32_t unit_elems;   // elements per work unit
     uint32_t vec;          // 1: aligned 4-element groups with vector stores
+    uint32_t l2;           // 1: single calls use the L2-resident bucketed passes
 };
 
 struct InterlaceDesc {

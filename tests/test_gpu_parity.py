@@ -333,3 +333,39 @@ def test_batch_many_planes(lr, orc):
     for g, w in zip(outputs_of(op2, b2), oracle_of(orc, op2, b2)):
         assert np.array_equal(g, w)
     plan.close()
+
+
+# ---------------------------------------------------------------------------
+# reorder of sources larger than the L2 (bucketed passes or direct gather,
+# chosen on the device from the index locality)
+
+def _l2_case(lr, orc, e, n, idx, seed):
+    import torch
+    src = synth.random_elements(seed, n, e)
+    s = torch.from_numpy(src).cuda()
+    ix = torch.from_numpy(idx.view(np.uint8)).cuda()
+    d = torch.empty_like(s).fill_(0x3C)
+    lr.reorder(d, s, ix, n, e)
+    sync()
+    got = d.cpu().numpy()
+    want = orc.reorder(src, idx, e)
+    assert np.array_equal(got, want), (e, n, seed)
+
+
+@pytest.mark.parametrize("e,kind", [(4, "perm"), (4, "repeat"), (4, "skewed"), (4, "reverse"), (4, "block"),
+                                    (8, "perm"), (16, "perm"), (16, "repeat")])
+def test_reorder_large_sources(lr, orc, e, kind):
+    n = (128 << 20) // e + 4099          # a little over 128 MiB, ragged last tile
+    if kind == "perm":
+        idx = synth.random_permutation(7 + e, n)
+    elif kind == "repeat":
+        idx = synth.random_indices(8 + e, n, n)
+    elif kind == "skewed":
+        idx = synth.random_indices(9, n, 1000)          # every index in one source chunk
+    elif kind == "reverse":
+        idx = np.arange(n - 1, -1, -1, dtype=np.uint32)
+    else:
+        m = n - n % 4096
+        idx = np.concatenate([synth.block_shuffled_permutation(10, m, 4096),
+                              np.arange(m, n, dtype=np.uint32)])
+    _l2_case(lr, orc, e, n, idx, seed=e * 100 + len(kind))
