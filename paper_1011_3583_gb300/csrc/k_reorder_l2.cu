@@ -3,7 +3,7 @@
 //
 // A direct gather from a source far larger than the L2 pays a whole DRAM
 // access (32-64 B) for every element it reads.  Here the source and the
-// destination are cut into chunks of about 32 MB (CS elements); element i
+// destination are cut into chunks of about 16 MB (CS elements); element i
 // belongs to bucket (c, d) with c = idx[i] / CS and d = i / CS.  The passes:
 //   K1 sample    : index locality on 4096 short runs of idx; if most
 //                  neighbours are close (|idx[j+1] - idx[j]| <= 16), the
@@ -16,9 +16,9 @@
 //                  memory and written as contiguous segments: s-array (source
 //                  index) and i-array (destination index), c-major.
 //   K5 gather    : v[k] = src[s[k]] walking k in order, so the CTAs in flight
-//                  read one ~32 MB source chunk at a time from L2.
+//                  read one ~16 MB source chunk at a time from L2.
 //   K6 scatter   : dst[i[k]] = v[k] walking the buckets d-major, so the CTAs
-//                  in flight complete one ~32 MB destination chunk in L2.
+//                  in flight complete one ~16 MB destination chunk in L2.
 //   K7 direct    : the plain gather (when K1 found locality).
 // Traffic: 2 (idx) + 2 (s, i written) + 2 (s, i read) + 1 (src) + 2 (v) + 1
 // (dst) = 10 n-word passes of streaming access instead of n random accesses.
@@ -50,6 +50,8 @@ struct L2Reorder {
     uint32_t cs_shift;             // chunk = 2^cs_shift elements
     uint32_t C, D;                 // source / destination chunks
     unsigned long long *near;      // K1: close neighbour pairs in the sample
+    unsigned int *ctr_gather;      // K5 / K6 work counters (units handed out in order)
+    unsigned int *ctr_scatter;
     uint32_t *hist;                // [C*D] bucket sizes, c-major (b = c*D + d)
     uint32_t *base;                // [C*D] bucket starts, c-major
     uint32_t *cursor;              // [C*D] partition write cursors
@@ -71,42 +73,85 @@ __device__ __forceinline__ bool bucketed(const L2Reorder &p)
     return *reinterpret_cast<volatile unsigned long long *>(p.near) < p.near_threshold;
 }
 
+// One warp per sampled run of 64 consecutive indices: each lane loads two
+// neighbouring entries and compares them with the next lane's.
 __global__ void __launch_bounds__(kThreads) k_l2_sample(const L2Reorder p)
 {
-    const uint32_t r = blockIdx.x * kThreads + threadIdx.x;  // one run per thread
+    const uint32_t r = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    const uint32_t lane = threadIdx.x & 31;
     uint32_t cnt = 0;
     if (r < kSampleRuns && p.n > kSampleLen) {
         const uint64_t start = uint64_t(r) * (p.n - kSampleLen) / kSampleRuns;
-        uint32_t prev = __ldg(p.idx + start);
-        for (int j = 1; j < kSampleLen; ++j) {
-            const uint32_t v = __ldg(p.idx + start + j);
-            const uint32_t dlt = v > prev ? v - prev : prev - v;
-            cnt += dlt <= kNear;
-            prev = v;
-        }
+        const uint32_t a = __ldg(p.idx + start + 2 * lane), b = __ldg(p.idx + start + 2 * lane + 1);
+        const uint32_t next_a = __shfl_down_sync(0xffffffffu, a, 1);
+        const uint32_t d1 = b > a ? b - a : a - b;
+        const uint32_t d2 = next_a > b ? next_a - b : b - next_a;
+        cnt = (d1 <= kNear) + (lane < 31 && d2 <= kNear);
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(p.near, (unsigned long long)cnt);
 }
 
-__global__ void __launch_bounds__(kThreads) k_l2_hist(const L2Reorder p)
+// Elements of a tile: warp w owns the contiguous slice [w*512, (w+1)*512);
+// lane l holds its elements j*32 + l, j < 16 (every load instruction of a warp
+// reads 128 contiguous bytes, all 16 are in flight together).
+constexpr int kWarps = kThreads / 32;
+constexpr int kPer = kTile / kThreads;  // 16
+
+__device__ __forceinline__ void load_tile(const L2Reorder &p, uint32_t i0, uint32_t m, uint32_t (&v)[kPer])
+{
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const uint32_t k = w * (kTile / kWarps) + j * 32 + lane;
+        v[j] = k < m ? __ldg(p.idx + i0 + k) : 0xFFFFFFFFu;
+    }
+}
+
+// Each CTA walks a contiguous range of tiles with per-warp shared counters
+// (the only contention is among the lanes of one warp) and flushes them to
+// the global histogram whenever the destination chunk changes.
+__global__ void __launch_bounds__(kThreads) k_l2_hist(const L2Reorder p, uint32_t tiles_per_cta)
 {
     if (!bucketed(p)) return;
-    __shared__ uint32_t sh[kMaxChunks];
+    __shared__ uint32_t sh[kWarps][kMaxChunks];
+    const uint32_t w = threadIdx.x >> 5;
     const uint32_t tiles = (p.n + kTile - 1) / kTile;
-    for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-        for (uint32_t c = threadIdx.x; c < p.C; c += kThreads) sh[c] = 0;
-        __syncthreads();
-        const uint32_t i0 = t * kTile;
-        const uint32_t cnt = min(uint32_t(kTile), p.n - i0);
-        for (uint32_t k = threadIdx.x; k < cnt; k += kThreads)
-            atomicAdd(&sh[chunk_of(p, __ldg(p.idx + i0 + k))], 1u);
-        __syncthreads();
-        const uint32_t d = i0 >> p.cs_shift;
-        for (uint32_t c = threadIdx.x; c < p.C; c += kThreads)
-            if (sh[c]) atomicAdd(&p.hist[c * p.D + d], sh[c]);
-        __syncthreads();
+    const uint32_t t0 = blockIdx.x * tiles_per_cta, t1 = min(tiles, t0 + tiles_per_cta);
+    for (uint32_t c = threadIdx.x; c < kWarps * kMaxChunks; c += kThreads) (&sh[0][0])[c] = 0;
+    __syncthreads();
+    uint32_t cur_d = t0 < t1 ? (t0 * kTile) >> p.cs_shift : 0;
+    uint32_t v[kPer];
+    if (t0 < t1) load_tile(p, t0 * kTile, min(uint32_t(kTile), p.n - t0 * kTile), v);
+    for (uint32_t t = t0; t < t1; ++t) {
+        uint32_t nxt[kPer];
+        if (t + 1 < t1) load_tile(p, (t + 1) * kTile, min(uint32_t(kTile), p.n - (t + 1) * kTile), nxt);
+        const uint32_t m = min(uint32_t(kTile), p.n - t * kTile);
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const uint32_t k = w * (kTile / kWarps) + j * 32 + (threadIdx.x & 31);
+            if (k < m) atomicAdd(&sh[w][chunk_of(p, v[j])], 1u);
+        }
+        const uint32_t next_d = t + 1 < t1 ? ((t + 1) * kTile) >> p.cs_shift : 0xFFFFFFFFu;
+        if (next_d != cur_d) {
+            __syncthreads();
+            for (uint32_t c = threadIdx.x; c < p.C; c += kThreads) {
+                uint32_t tot = 0;
+#pragma unroll
+                for (int x = 0; x < kWarps; ++x) {
+                    tot += sh[x][c];
+                    sh[x][c] = 0;
+                }
+                if (tot) atomicAdd(&p.hist[c * p.D + cur_d], tot);
+            }
+            __syncthreads();
+            cur_d = next_d;
+        }
+        if (t + 1 < t1) {
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) v[j] = nxt[j];
+        }
     }
 }
 
@@ -173,133 +218,271 @@ __global__ void __launch_bounds__(1024) k_l2_scan(const L2Reorder p)
     if (threadIdx.x == 0) p.uprefix[nb] = carry;
 }
 
-__global__ void __launch_bounds__(kThreads) k_l2_partition(const L2Reorder p)
+// Partition: per tile, every warp ranks its 512 elements by source chunk in
+// its own counters; warp offsets and chunk segment offsets are prefix sums
+// over those counters; the tile is then staged in shared memory grouped by
+// chunk and written out as contiguous segments at ranges reserved with one
+// global atomic per chunk.  The next tile's indices load while this one is
+// sorted.
+struct PartitionSmem {
+    uint32_t s_st[kTile], i_st[kTile];
+    uint16_t c_of[kTile];
+    uint32_t cnt[kWarps][kMaxChunks];   // per-warp counts, then per-warp offsets
+    uint32_t seg[kMaxChunks];           // segment start of each chunk in the tile
+    uint32_t gb[kMaxChunks];            // global start of each chunk's segment
+    uint32_t warp_sums[kWarps];
+};
+
+__global__ void __launch_bounds__(kThreads) k_l2_partition(const L2Reorder p, uint32_t tiles_per_cta)
 {
     if (!bucketed(p)) return;
-    constexpr int PER = kTile / kThreads;  // 16 elements per thread
-    __shared__ uint32_t s_st[kTile], i_st[kTile];
-    __shared__ uint16_t c_of[kTile];
-    __shared__ uint32_t cnt[kMaxChunks], off[kMaxChunks], gb[kMaxChunks];
-    __shared__ uint32_t warp_sums[32];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PartitionSmem &S = *reinterpret_cast<PartitionSmem *>(smem_raw);
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t tiles = (p.n + kTile - 1) / kTile;
-    for (uint32_t c = threadIdx.x; c < p.C; c += kThreads) cnt[c] = 0;
+    const uint32_t t0 = blockIdx.x * tiles_per_cta, t1 = min(tiles, t0 + tiles_per_cta);
+    for (uint32_t c = threadIdx.x; c < kWarps * kMaxChunks; c += kThreads) (&S.cnt[0][0])[c] = 0;
     __syncthreads();
-    for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    uint32_t v[kPer];
+    if (t0 < t1) load_tile(p, t0 * kTile, min(uint32_t(kTile), p.n - t0 * kTile), v);
+    for (uint32_t t = t0; t < t1; ++t) {
         const uint32_t i0 = t * kTile;
         const uint32_t m = min(uint32_t(kTile), p.n - i0);
         const uint32_t d = i0 >> p.cs_shift;
-        uint32_t v[PER], rk[PER];
+        uint32_t nxt[kPer];
+        if (t + 1 < t1) load_tile(p, (t + 1) * kTile, min(uint32_t(kTile), p.n - (t + 1) * kTile), nxt);
+        uint32_t rk[kPer];
 #pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const uint32_t k = j * kThreads + threadIdx.x;
-            v[j] = k < m ? __ldg(p.idx + i0 + k) : 0;
-        }
-#pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const uint32_t k = j * kThreads + threadIdx.x;
-            rk[j] = k < m ? atomicAdd(&cnt[chunk_of(p, v[j])], 1u) : 0;
+        for (int j = 0; j < kPer; ++j) {
+            const uint32_t k = w * (kTile / kWarps) + j * 32 + lane;
+            rk[j] = k < m ? atomicAdd(&S.cnt[w][chunk_of(p, v[j])], 1u) : 0u;
         }
         __syncthreads();
-        // segment offsets in the staging buffer (C <= 512: two entries per thread)
+        // per chunk: tile total, exclusive offsets of the warps (in place)
+        for (uint32_t c = threadIdx.x; c < p.C; c += kThreads) {
+            uint32_t run = 0;
+#pragma unroll
+            for (int x = 0; x < kWarps; ++x) {
+                const uint32_t q = S.cnt[x][c];
+                S.cnt[x][c] = run;
+                run += q;
+            }
+            S.seg[c] = run;  // tile count of chunk c, turned into a start below
+        }
+        __syncthreads();
+        // exclusive scan of the C chunk counts (C <= 512: two per thread)
         {
             const uint32_t c0 = 2 * threadIdx.x;
-            const uint32_t a = c0 < p.C ? cnt[c0] : 0, b = c0 + 1 < p.C ? cnt[c0 + 1] : 0;
-            // 256 threads: scan pairs with one warp-level pass per warp + warp sums
-            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            const uint32_t a = c0 < p.C ? S.seg[c0] : 0u, b = c0 + 1 < p.C ? S.seg[c0 + 1] : 0u;
             uint32_t x = a + b;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
                 if (lane >= o) x += y;
             }
-            if (lane == 31) warp_sums[warp] = x;
+            if (lane == 31) S.warp_sums[w] = x;
             __syncthreads();
             if (threadIdx.x == 0) {
-                uint32_t s = 0;
-                for (int w = 0; w < kThreads / 32; ++w) {
-                    const uint32_t q = warp_sums[w];
-                    warp_sums[w] = s;
-                    s += q;
+                uint32_t acc = 0;
+                for (int x2 = 0; x2 < kWarps; ++x2) {
+                    const uint32_t q = S.warp_sums[x2];
+                    S.warp_sums[x2] = acc;
+                    acc += q;
                 }
             }
             __syncthreads();
-            const uint32_t e = warp_sums[warp] + x - (a + b);
-            if (c0 < p.C) off[c0] = e;
-            if (c0 + 1 < p.C) off[c0 + 1] = e + a;
-            if (c0 < p.C && a) gb[c0] = atomicAdd(&p.cursor[c0 * p.D + d], a);
-            if (c0 + 1 < p.C && b) gb[c0 + 1] = atomicAdd(&p.cursor[(c0 + 1) * p.D + d], b);
+            const uint32_t e = S.warp_sums[w] + x - (a + b);
+            if (c0 < p.C) {
+                S.seg[c0] = e;
+                if (a) S.gb[c0] = atomicAdd(&p.cursor[c0 * p.D + d], a);
+            }
+            if (c0 + 1 < p.C) {
+                S.seg[c0 + 1] = e + a;
+                if (b) S.gb[c0 + 1] = atomicAdd(&p.cursor[(c0 + 1) * p.D + d], b);
+            }
         }
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const uint32_t k = j * kThreads + threadIdx.x;
+        for (int j = 0; j < kPer; ++j) {
+            const uint32_t k = w * (kTile / kWarps) + j * 32 + lane;
             if (k < m) {
                 const uint32_t c = chunk_of(p, v[j]);
-                const uint32_t pos = off[c] + rk[j];
-                s_st[pos] = v[j];
-                i_st[pos] = i0 + k;
-                c_of[pos] = uint16_t(c);
+                const uint32_t pos = S.seg[c] + S.cnt[w][c] + rk[j];
+                S.s_st[pos] = v[j];
+                S.i_st[pos] = i0 + k;
+                S.c_of[pos] = uint16_t(c);
             }
         }
         __syncthreads();
         for (uint32_t q = threadIdx.x; q < m; q += kThreads) {
-            const uint32_t c = c_of[q];
-            const uint32_t g = gb[c] + (q - off[c]);
-            p.sarr[g] = s_st[q];
-            p.iarr[g] = i_st[q];
+            const uint32_t c = S.c_of[q];
+            const uint32_t g = S.gb[c] + (q - S.seg[c]);
+            p.sarr[g] = S.s_st[q];
+            p.iarr[g] = S.i_st[q];
         }
-        for (uint32_t c = threadIdx.x; c < p.C; c += kThreads) cnt[c] = 0;
+        for (uint32_t c = threadIdx.x; c < kWarps * kMaxChunks; c += kThreads) (&S.cnt[0][0])[c] = 0;
         __syncthreads();
+        if (t + 1 < t1) {
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) v[j] = nxt[j];
+        }
     }
 }
 
-template <int W>
-__global__ void __launch_bounds__(kThreads) k_l2_gather(const L2Reorder p, const GatherDesc g, uint64_t units,
-                                                        int want_bucketed)
+// L2 eviction priorities: the streamed arrays (s, i, v) are marked to leave
+// the L2 first so that the resident source / destination chunk stays.
+__device__ __forceinline__ uint64_t policy_evict_first()
 {
-    if (bucketed(p) != bool(want_bucketed)) return;
-    for (uint64_t u = blockIdx.x; u < units; u += gridDim.x) gather_body<W>(g, u);
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
 
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+template <int W> __device__ __forceinline__ typename Word<W>::T ld_hint(const void *p, uint64_t pol);
+template <> __device__ __forceinline__ uint32_t ld_hint<4>(const void *p, uint64_t pol)
+{
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+template <> __device__ __forceinline__ uint2 ld_hint<8>(const void *p, uint64_t pol)
+{
+    uint2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+                 : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+template <> __device__ __forceinline__ uint4 ld_hint<16>(const void *p, uint64_t pol)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p), "l"(pol));
+    return v;
+}
+
+template <int W> __device__ __forceinline__ void st_hint(void *p, typename Word<W>::T v, uint64_t pol);
+template <> __device__ __forceinline__ void st_hint<4>(void *p, uint32_t v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
+}
+template <> __device__ __forceinline__ void st_hint<8>(void *p, uint2 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(v.x), "r"(v.y), "l"(pol) : "memory");
+}
+template <> __device__ __forceinline__ void st_hint<16>(void *p, uint4 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w), "l"(pol) : "memory");
+}
+
+// Next work unit for the whole CTA, handed out in increasing order so that the
+// units in flight stay a narrow window of the c-major (d-major) order.
+__device__ __forceinline__ uint32_t next_unit(unsigned int *ctr, uint32_t *slot)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) *slot = atomicAdd(ctr, 1u);
+    __syncthreads();
+    return *slot;
+}
+
+constexpr int kGatherUnit = 4096;  // elements per gather / scatter unit (16 per thread)
+
+// K5: v[k] = src[s[k]] in k order; the source chunk being read is L2-resident.
 template <int W>
-__global__ void __launch_bounds__(kThreads) k_l2_scatter(const L2Reorder p, uint32_t max_units)
+__global__ void __launch_bounds__(kThreads) k_l2_gather(const L2Reorder p)
 {
     if (!bucketed(p)) return;
+    __shared__ uint32_t slot;
     using T = typename Word<W>::T;
-    const uint32_t nb = p.C * p.D;
-    const uint32_t total = p.uprefix[nb];
-    for (uint32_t u = blockIdx.x; u < total && u < max_units; u += gridDim.x) {
-        // d-major segment s with uprefix[s] <= u < uprefix[s + 1]
-        uint32_t lo = 0, hi = nb - 1;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi + 1) >> 1;
-            if (p.uprefix[mid] <= u) lo = mid;
-            else hi = mid - 1;
+    const uint64_t first = policy_evict_first(), last = policy_evict_last();
+    const uint32_t units = (p.n + kGatherUnit - 1) / kGatherUnit;
+    for (;;) {
+        const uint32_t u = next_unit(p.ctr_gather, &slot);
+        if (u >= units) break;
+        const uint32_t k0 = u * kGatherUnit;
+        constexpr int PER = kGatherUnit / kThreads;
+        uint32_t sv[PER];
+        T val[PER];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const uint32_t k = k0 + j * kThreads + threadIdx.x;
+            sv[j] = k < p.n ? ld_hint<4>(p.sarr + k, first) : 0u;
         }
-        const uint32_t d = lo / p.C, c = lo - d * p.C;
-        const uint32_t b = c * p.D + d;
-        const uint32_t piece = u - p.uprefix[lo];
-        const uint32_t k0 = p.base[b] + piece * kTile;
-        const uint32_t k1 = p.base[b] + min(p.hist[b], (piece + 1) * uint32_t(kTile));
-        constexpr int U = 4;
-        for (uint32_t kb = k0; kb < k1; kb += kThreads * U) {
-            uint32_t di[U];
-            T val[U];
 #pragma unroll
-            for (int j = 0; j < U; ++j) {
-                const uint32_t k = kb + j * kThreads + threadIdx.x;
-                if (k < k1) {
-                    di[j] = __ldg(p.iarr + k);
-                    val[j] = ldg_stream<W>(p.varr + uint64_t(k) * W);
-                }
-            }
+        for (int j = 0; j < PER; ++j) {
+            const uint32_t k = k0 + j * kThreads + threadIdx.x;
+            if (k < p.n) val[j] = ld_hint<W>(p.src + uint64_t(sv[j]) * W, last);
+        }
 #pragma unroll
-            for (int j = 0; j < U; ++j) {
-                const uint32_t k = kb + j * kThreads + threadIdx.x;
-                if (k < k1) stg<W>(p.dst + uint64_t(di[j]) * W, val[j]);
-            }
+        for (int j = 0; j < PER; ++j) {
+            const uint32_t k = k0 + j * kThreads + threadIdx.x;
+            if (k < p.n) st_hint<W>(p.varr + uint64_t(k) * W, val[j], first);
         }
     }
+}
+
+// K6: dst[i[k]] = v[k] walking the buckets d-major; the destination chunk
+// being written is L2-resident, so its sectors are completed there.
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_l2_scatter(const L2Reorder p)
+{
+    if (!bucketed(p)) return;
+    __shared__ uint32_t slot, sk0, sk1;
+    using T = typename Word<W>::T;
+    const uint64_t first = policy_evict_first(), last = policy_evict_last();
+    const uint32_t nb = p.C * p.D;
+    const uint32_t total = p.uprefix[nb];
+    for (;;) {
+        const uint32_t u = next_unit(p.ctr_scatter, &slot);
+        if (u >= total) break;
+        if (threadIdx.x == 0) {
+            // d-major segment s with uprefix[s] <= u < uprefix[s + 1]
+            uint32_t lo = 0, hi = nb - 1;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                if (p.uprefix[mid] <= u) lo = mid;
+                else hi = mid - 1;
+            }
+            const uint32_t d = lo / p.C, c = lo - d * p.C;
+            const uint32_t b = c * p.D + d;
+            const uint32_t piece = u - p.uprefix[lo];
+            sk0 = p.base[b] + piece * kTile;
+            sk1 = p.base[b] + min(p.hist[b], (piece + 1) * uint32_t(kTile));
+        }
+        __syncthreads();
+        const uint32_t k0 = sk0, k1 = sk1;
+        constexpr int PER = kTile / kThreads;
+        uint32_t di[PER];
+        T val[PER];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const uint32_t k = k0 + j * kThreads + threadIdx.x;
+            if (k < k1) {
+                di[j] = ld_hint<4>(p.iarr + k, first);
+                val[j] = ld_hint<W>(p.varr + uint64_t(k) * W, first);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const uint32_t k = k0 + j * kThreads + threadIdx.x;
+            if (k < k1) st_hint<W>(p.dst + uint64_t(di[j]) * W, val[j], last);
+        }
+    }
+}
+
+// K7: the direct gather, when K1 found the indices local.
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_l2_direct(const L2Reorder p, const GatherDesc g, uint64_t units)
+{
+    if (bucketed(p)) return;
+    for (uint64_t u = blockIdx.x; u < units; u += gridDim.x) gather_body<W>(g, u);
 }
 
 std::mutex g_pool_mu;
@@ -336,9 +519,9 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
     p.dst = g.dst;
     p.idx = g.idx;
     p.n = uint32_t(g.n);
-    // ~32 MB chunks, at most kMaxChunks of them
+    // ~16 MB chunks, at most kMaxChunks of them
     uint32_t shift = 0;
-    while ((uint64_t(1) << shift) * W < (uint64_t(32) << 20)) ++shift;
+    while ((uint64_t(1) << shift) * W < (uint64_t(16) << 20)) ++shift;
     while (((uint64_t(g.n) + (uint64_t(1) << shift) - 1) >> shift) > kMaxChunks) ++shift;
     p.cs_shift = shift;
     p.C = p.D = uint32_t((uint64_t(g.n) + (uint64_t(1) << shift) - 1) >> shift);
@@ -354,6 +537,8 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
     e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&scratch), bytes, pool, s);
     if (e != cudaSuccess) return e;
     p.near = reinterpret_cast<unsigned long long *>(scratch);
+    p.ctr_gather = reinterpret_cast<unsigned int *>(scratch + 8);
+    p.ctr_scatter = reinterpret_cast<unsigned int *>(scratch + 16);
     p.hist = reinterpret_cast<uint32_t *>(scratch + off_hist);
     p.base = reinterpret_cast<uint32_t *>(scratch + off_base);
     p.cursor = reinterpret_cast<uint32_t *>(scratch + off_cur);
@@ -369,30 +554,27 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const uint32_t tiles = (p.n + kTile - 1) / kTile;
-    const unsigned pgrid = unsigned(std::min<uint32_t>(tiles, uint32_t(sms) * 4));
-    GatherDesc gb = g;  // K5: v[k] = src[s[k]]
-    gb.dst = p.varr;
-    gb.idx = p.sarr;
-    gb.vec = 1;
-    gb.c = 1;
-    gb.unit_elems = uint32_t(kThreads) * 32;
-    const uint64_t gunits = (g.n + gb.unit_elems - 1) / gb.unit_elems;
+    const uint32_t resident = uint32_t(sms) * 4;
+    const uint32_t tpc = (tiles + resident - 1) / resident;  // contiguous tiles per CTA
+    const unsigned pgrid = unsigned((tiles + tpc - 1) / tpc);
+    static bool smem_set[64] = {false};
+    if (dev >= 0 && dev < 64 && !smem_set[dev]) {
+        e = cudaFuncSetAttribute(k_l2_partition, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(PartitionSmem)));
+        smem_set[dev] = e == cudaSuccess;
+    }
+    const unsigned pers = unsigned(sms) * 8;  // persistent grids of the gated passes
     const uint64_t dunits = (g.n + g.unit_elems - 1) / g.unit_elems;
-    const uint32_t max_units = tiles + nb;
-    if (e == cudaSuccess) { k_l2_sample<<<kSampleRuns / kThreads, kThreads, 0, s>>>(p); e = cudaGetLastError(); }
-    if (e == cudaSuccess) { k_l2_hist<<<pgrid, kThreads, 0, s>>>(p); e = cudaGetLastError(); }
+    if (e == cudaSuccess) { k_l2_sample<<<kSampleRuns / (kThreads / 32), kThreads, 0, s>>>(p); e = cudaGetLastError(); }
+    if (e == cudaSuccess) { k_l2_hist<<<pgrid, kThreads, 0, s>>>(p, tpc); e = cudaGetLastError(); }
     if (e == cudaSuccess) { k_l2_scan<<<1, 1024, 0, s>>>(p); e = cudaGetLastError(); }
-    if (e == cudaSuccess) { k_l2_partition<<<pgrid, kThreads, 0, s>>>(p); e = cudaGetLastError(); }
     if (e == cudaSuccess) {
-        k_l2_gather<W><<<unsigned(std::min<uint64_t>(gunits, 0x7FFFFFFFull)), kThreads, 0, s>>>(p, gb, gunits, 1);
+        k_l2_partition<<<pgrid, kThreads, sizeof(PartitionSmem), s>>>(p, tpc);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess) { k_l2_gather<W><<<pers, kThreads, 0, s>>>(p); e = cudaGetLastError(); }
+    if (e == cudaSuccess) { k_l2_scatter<W><<<pers, kThreads, 0, s>>>(p); e = cudaGetLastError(); }
     if (e == cudaSuccess) {
-        k_l2_scatter<W><<<unsigned(std::min<uint32_t>(max_units, 0x7FFFFFFFu)), kThreads, 0, s>>>(p, max_units);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) {
-        k_l2_gather<W><<<unsigned(std::min<uint64_t>(dunits, 0x7FFFFFFFull)), kThreads, 0, s>>>(p, g, dunits, 0);
+        k_l2_direct<W><<<unsigned(std::min<uint64_t>(dunits, 0x7FFFFFFFull)), kThreads, 0, s>>>(p, g, dunits);
         e = cudaGetLastError();
     }
     g_launches.fetch_add(7, std::memory_order_relaxed);
