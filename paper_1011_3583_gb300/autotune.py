@@ -6,9 +6,9 @@ It measures, with CUDA events and the library's own kernels only:
 
 * for every fully vectorised fast-tile class -- element size E in
   {1, 2, 4, 8, 16} x input-fastest extent DA x output-fastest extent DB, each
-  extent in one of five buckets -- the staged row length (128, 256 or 512
-  bytes, i.e. the tile shape) that moves a representative permute of that
-  class fastest.  The representative case is a [nb, DB, DA] tensor permuted
+  extent in one of five buckets -- the tile shape (staged row length of 128,
+  256 or 512 bytes; 16 KB tiles, or 8 KB half tiles for 2- and 4-byte
+  elements) that moves a representative permute of that class fastest.  The representative case is a [nb, DB, DA] tensor permuted
   to [nb, DA, DB], nb chosen so that each call moves about 256 MiB;
 * the batched kernel's work grab (tiles taken per atomicAdd) on the first
   1024 ops of the uneven mix.
@@ -56,26 +56,30 @@ def tune_rowb(rr, torch, stream, tmpdir, log):
     buf_a = torch.empty(TARGET_BYTES + (1 << 20), dtype=torch.uint8, device="cuda").random_()
     buf_b = torch.empty_like(buf_a)
     for E in ELEMS:
-        cands = (128, 256) if E == 1 else (128, 256, 512)
+        # (staged row bytes, tile payload bytes); 2- and 4-byte elements also
+        # have an 8 KB half tile for planes too small to fill 16 KB
+        cands = [(128, 16384), (256, 16384)] + ([] if E == 1 else [(512, 16384)])
+        if E in (2, 4):
+            cands.append((128, 8192))
         for (alo, ahi, DA) in BUCKETS:
             for (blo, bhi, DB) in BUCKETS:
                 nb = max(1, TARGET_BYTES // (DA * DB * E))
                 dims, perm = [nb, DB, DA], [0, 2, 1]
                 best = None
-                for rowb in cands:
+                for rowb, tbytes in cands:
                     table = os.path.join(tmpdir, "cand.txt")
-                    _write(table, [f"rowb {E} {alo} {ahi} {blo} {bhi} {rowb}"])
+                    _write(table, [f"rowb {E} {alo} {ahi} {blo} {bhi} {rowb} {tbytes}"])
                     rr.tuning_load(table)
                     d = rr.describe_permute(E, dims, perm, buf_b.data_ptr(), buf_a.data_ptr())
-                    if d["kind"] != "tile" or d["tile_a"] * E != rowb:
+                    if d["kind"] != "tile" or d["tile_a"] * E != rowb or d["tile_a"] * d["tile_b"] * E != tbytes:
                         continue  # not a fully vectorised tile: the table does not apply
                     t = _time(torch, lambda: rr.permute(buf_b, buf_a, E, dims, perm, stream), stream)
                     gbs = 2 * nb * DA * DB * E / t / 1e9
-                    log(f"E={E:2d} DA={DA:5d} DB={DB:5d} rowb={rowb:3d}: {gbs:8.1f} GB/s")
-                    if best is None or gbs > best[1]:
-                        best = (rowb, gbs)
+                    log(f"E={E:2d} DA={DA:5d} DB={DB:5d} rowb={rowb:3d} tile={tbytes:5d}: {gbs:8.1f} GB/s")
+                    if best is None or gbs > best[2]:
+                        best = (rowb, tbytes, gbs)
                 if best:
-                    rules.append(f"rowb {E} {alo} {ahi} {blo} {bhi} {best[0]}   # {best[1]:.0f} GB/s")
+                    rules.append(f"rowb {E} {alo} {ahi} {blo} {bhi} {best[0]} {best[1]}   # {best[2]:.0f} GB/s")
     rr.tuning_load(None)
     return rules
 

@@ -39,10 +39,10 @@ __device__ __forceinline__ char *const *planes_of(const InterlaceDesc &d)
 // of one op's units.  Separate functions get separate register allocations
 // (a single function holding every inlined variant overflows the register
 // file), and the call overhead is paid once per range, not once per tile.
-template <int E, int VI, int VO, int RB>
+template <int E, int VI, int VO, int RB, int TBYTES = kTileBytes>
 __device__ __noinline__ void tile_range(const TileDesc &d, uint32_t u0, uint32_t u1, unsigned char *smem)
 {
-    for (uint32_t u = u0; u < u1; ++u) tile_fast_body<E, VI, VO, RB>(d, u, smem);
+    for (uint32_t u = u0; u < u1; ++u) tile_fast_body<E, VI, VO, RB, TBYTES>(d, u, smem);
 }
 
 template <int W>
@@ -87,14 +87,19 @@ __device__ __noinline__ void ifast_range(const InterlaceDesc &d, uint64_t u0, ui
 #define BT_CASE(E, VI, VO, RB) \
     case tile_variant(E, VI, VO, RB): tile_range<E, VI, VO, RB>(d.tile, uint32_t(u0), uint32_t(u1), smem); return;
 
+#define BT_HALF(E, VI, VO, RB) \
+    case tile_variant(E, VI, VO, RB, 8192): tile_range<E, VI, VO, RB, 8192>(d.tile, uint32_t(u0), uint32_t(u1), smem); return;
+
 __device__ __forceinline__ void run_tile_fast(const OpDesc &d, uint64_t u0, uint64_t u1, unsigned char *smem)
 {
     switch (d.tile.variant) {
         REARR_TILE_VARIANTS(BT_CASE)
+        REARR_TILE_HALF_VARIANTS(BT_HALF)
         default: return;
     }
 }
 #undef BT_CASE
+#undef BT_HALF
 
 template <int W>
 __device__ __forceinline__ void run_word_class(const OpDesc &d, uint64_t u0, uint64_t u1, unsigned char *smem)

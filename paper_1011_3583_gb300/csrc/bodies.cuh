@@ -18,11 +18,12 @@ namespace rearr {
 // memory, and written along B (contiguous in the output), so both global
 // sides are coalesced.  The remaining axes batch the plane.
 
-// Fast tiles hold 16 KB of payload; the staged rows (along A) are ROWB = 128,
-// 256 or 512 bytes, so TB = 16384 / ROWB rows along B.
-template <int E, int ROWB> struct FastTile {
+// Fast tiles hold TBYTES of payload (16 KB, or 8 KB for small planes); the
+// staged rows (along A) are ROWB = 128, 256 or 512 bytes, so TB = TBYTES / ROWB
+// rows along B.
+template <int E, int ROWB, int TBYTES = kTileBytes> struct FastTile {
     static constexpr int TA = ROWB / E;
-    static constexpr int TB = kTileBytes / ROWB;
+    static constexpr int TB = TBYTES / ROWB;
 };
 
 // Origin of tile t: (a0, b0) in the plane and the byte offsets of its batch.
@@ -95,10 +96,10 @@ __device__ __forceinline__ typename Word<E * VB>::T piece(const uint4 (&r)[VB], 
 // the tile row-major by B with 16-byte chunks XOR-swizzled by (row/VB)&7, so
 // the 16-byte row stores of the load phase and the 16-byte column-block loads
 // of the store phase are both free of bank conflicts.
-template <int E, int VIN, int VOUT, int ROWB>
+template <int E, int VIN, int VOUT, int ROWB, int TBYTES = kTileBytes>
 __device__ __forceinline__ void tile_fast_body(const TileDesc &d, uint32_t t, unsigned char *smem)
 {
-    constexpr int TA = FastTile<E, ROWB>::TA, TB = FastTile<E, ROWB>::TB;
+    constexpr int TA = FastTile<E, ROWB, TBYTES>::TA, TB = FastTile<E, ROWB, TBYTES>::TB;
     constexpr int V = 16 / E;        // elements per 16-byte chunk
     constexpr int VB = VOUT / E;     // B-elements per output store
     constexpr int PPR = ROWB / VIN;  // load pieces per row
@@ -251,7 +252,7 @@ __device__ __forceinline__ int64_t run_offset(const RunsDesc &d, uint32_t q)
 template <int W>
 __device__ __forceinline__ void copy_words(const char *src, char *dst, uint32_t w0, uint32_t w1)
 {
-    constexpr int U = 4;
+    constexpr int U = 8;
     for (uint32_t b = w0; b < w1; b += kThreads * U) {
         typename Word<W>::T v[U];
 #pragma unroll
@@ -288,7 +289,7 @@ __device__ __forceinline__ void runs_body(const RunsDesc &d, uint64_t unit, unsi
     const uint32_t wpr = d.wpr_div.d;  // words per run
     const uint32_t total = nr * wpr;
     char *out = d.dst + int64_t(r0) * d.run_bytes;
-    constexpr int U = 4;
+    constexpr int U = 8;
     for (uint32_t f0 = 0; f0 < total; f0 += kThreads * U) {
         typename Word<W>::T v[U];
 #pragma unroll

@@ -12,11 +12,11 @@ namespace rearr {
 
 std::atomic<uint64_t> g_launches{0};
 
-template <int E, int VIN, int VOUT, int ROWB>
+template <int E, int VIN, int VOUT, int ROWB, int TBYTES = kTileBytes>
 __global__ void __launch_bounds__(kThreads) k_tile_fast(const __grid_constant__ TileDesc d, uint32_t n)
 {
-    __shared__ __align__(16) unsigned char smem[kTileBytes];
-    for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) tile_fast_body<E, VIN, VOUT, ROWB>(d, t, smem);
+    __shared__ __align__(16) unsigned char smem[TBYTES];
+    for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) tile_fast_body<E, VIN, VOUT, ROWB, TBYTES>(d, t, smem);
 }
 
 template <int W>
@@ -85,14 +85,20 @@ cudaError_t go(K kernel, uint64_t units, const P &param, N n, cudaStream_t s)
     case tile_variant(E, VI, VO, RB):                                                             \
         return go(k_tile_fast<E, VI, VO, RB>, op.units, op.tile, uint32_t(op.units), s);
 
+#define RT_HALF(E, VI, VO, RB)                                                                \
+    case tile_variant(E, VI, VO, RB, 8192):                                                       \
+        return go(k_tile_fast<E, VI, VO, RB, 8192>, op.units, op.tile, uint32_t(op.units), s);
+
 cudaError_t launch_tile_fast(const OpDesc &op, cudaStream_t s)
 {
     switch (op.tile.variant) {
         REARR_TILE_VARIANTS(RT_CASE)
+        REARR_TILE_HALF_VARIANTS(RT_HALF)
         default: return cudaErrorInvalidValue;
     }
 }
 #undef RT_CASE
+#undef RT_HALF
 
 template <template <int> class Fn, typename... A>
 cudaError_t by_word(int W, A &&...a)

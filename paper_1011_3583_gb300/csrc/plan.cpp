@@ -58,30 +58,36 @@ int pow2_align(uint64_t a, uint64_t b, uint64_t c, uint64_t d)
     return int(v & (~v + 1));  // lowest set bit, at most 16
 }
 
-// Row length (bytes) of a fully vectorised fast tile: the one whose tiles are
-// filled best by the DA x DB plane (ragged last tiles waste bandwidth), ties
-// broken toward equal input-row and output-row bytes.  An autotuned table may
-// override the choice per (E, DA, DB) class.
-static int choose_rowb(int E, int64_t DA, int64_t DB)
+// Shape of a fully vectorised fast tile: staged row bytes (128/256/512) and
+// payload (16 KB, or the 8 KB half tile where an element size has one).  The
+// shape that fills the DA x DB plane best is chosen (ragged last tiles waste
+// bandwidth), ties broken toward full tiles and then toward equal input-row
+// and output-row bytes.  An autotuned table may override the choice per
+// (E, DA, DB) class.
+static TileShape choose_shape(int E, int64_t DA, int64_t DB)
 {
-    const int cands[3] = {128, 256, 512};
-    int best = default_rowb(E);
+    std::vector<TileShape> cands = {{128, kTileBytes}, {256, kTileBytes}};
+    if (E != 1) cands.push_back({512, kTileBytes});
+    if (half_tile_vout(E)) cands.push_back({128, kTileBytes / 2});
+    TileShape best{default_rowb(E), kTileBytes};
     double best_util = -1.0, best_bal = 1e9;
-    for (int rowb : cands) {
-        if (E == 1 && rowb == 512) continue;
-        const int64_t TA = rowb / E, TB = kTileBytes / rowb;
+    for (const TileShape &c : cands) {
+        const int64_t TA = c.rowb / E, TB = c.tbytes / c.rowb;
         const double ua = double(DA) / double(((DA + TA - 1) / TA) * TA);
         const double ub = double(DB) / double(((DB + TB - 1) / TB) * TB);
         const double util = ua * ub;
-        const double bal = std::fabs(std::log2(double(rowb)) - std::log2(double(TB * E)));
+        // a half tile must fill clearly better to be chosen
+        const double bal = std::fabs(std::log2(double(c.rowb)) - std::log2(double(TB * E))) +
+                           (c.tbytes < kTileBytes ? 8.0 : 0.0);
         if (util > best_util + 0.01 || (util > best_util - 0.01 && bal < best_bal)) {
-            best = rowb;
+            best = c;
             best_util = std::max(best_util, util);
             best_bal = bal;
         }
     }
-    const int o = tuned_rowb(E, DA, DB);
-    return o ? o : best;
+    TileShape tuned;
+    if (tuned_shape(E, DA, DB, tuned) && (tuned.tbytes == kTileBytes || half_tile_vout(E))) return tuned;
+    return best;
 }
 
 static void fill_tile_common(TileDesc &t, const std::vector<Axis> &ax, int p, int64_t cell, int64_t DA,
@@ -289,16 +295,19 @@ rearr_status plan_permute(void *dst, const void *src, size_t elem_bytes, int ran
         for (int v : {vmax, 4}) {
             if (v > E && (uint64_t(DB) * E) % v == 0 && da % v == 0) { vout = v; break; }
         }
-        // Staged row length: the default for the element size, or for the fully
-        // vectorised widths the length that fills the tiles best.
-        int rowb = default_rowb(E);
-        if (vin == 16 && vout == std::min(16, 4 * E)) rowb = choose_rowb(E, DA, DB);
-        t.TA = uint32_t(rowb / E);
-        t.TB = uint32_t(kTileBytes / rowb);
+        // Tile shape: the default for the element size, or for the fully
+        // vectorised widths the shape that fills the plane best.
+        TileShape shape{default_rowb(E), kTileBytes};
+        if (vin == 16 && vout == std::min(16, 4 * E)) {
+            shape = choose_shape(E, DA, DB);
+            if (shape.tbytes < kTileBytes) vout = half_tile_vout(E);
+        }
+        t.TA = uint32_t(shape.rowb / E);
+        t.TB = uint32_t(shape.tbytes / shape.rowb);
         info.kind = REARR_KIND_TILE;
         info.vec_in = vin;
         info.vec_out = vout;
-        t.variant = tile_variant(E, vin, vout, rowb);
+        t.variant = tile_variant(E, vin, vout, shape.rowb, shape.tbytes);
         t.c = 1;
         t.pitch = 0;
         op.cls = OC_TILE;

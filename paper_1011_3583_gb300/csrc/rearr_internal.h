@@ -165,10 +165,12 @@ struct OpDesc {
     };
 };
 
-// Fast-tile variant ids: E in {1,2,4,8,16} x VIN x VOUT x staged row bytes.
-constexpr RH_HD uint32_t tile_variant(int E, int vin, int vout, int rowb)
+// Fast-tile variant ids: E in {1,2,4,8,16} x VIN x VOUT x staged row bytes x
+// tile payload bytes.
+constexpr RH_HD uint32_t tile_variant(int E, int vin, int vout, int rowb, int tbytes = kTileBytes)
 {
-    return uint32_t(E) | (uint32_t(vin) << 6) | (uint32_t(vout) << 12) | (uint32_t(rowb / 128) << 18);
+    return uint32_t(E) | (uint32_t(vin) << 6) | (uint32_t(vout) << 12) | (uint32_t(rowb / 128) << 18) |
+           (uint32_t(tbytes / 8192) << 22);
 }
 
 }  // namespace rearr

@@ -3,7 +3,7 @@
 // the file named by the REARR_TUNE_TABLE environment variable is read on first
 // use, and rearr_tuning_load swaps in another file at run time.  Lines:
 //   min_grab <v> | max_grab <v> | grabs_per_cta <v>
-//   rowb <E> <da_lo> <da_hi> <db_lo> <db_hi> <rowb>
+//   rowb <E> <da_lo> <da_hi> <db_lo> <db_hi> <rowb> [<tile bytes>]
 // ("#" starts a comment line).  Plans compiled after a load use the new table.
 #include <cstdio>
 #include <cstdlib>
@@ -26,6 +26,7 @@ struct RowbRule {
     int E;
     int64_t da_lo, da_hi, db_lo, db_hi;
     int rowb;
+    int tbytes;
 };
 
 struct Table {
@@ -45,10 +46,14 @@ std::shared_ptr<const Table> parse(const char *path)
         RowbRule r;
         long long a, b, c, d;
         if (line[0] == '#') continue;
-        if (std::sscanf(line, "rowb %d %lld %lld %lld %lld %d", &r.E, &a, &b, &c, &d, &r.rowb) == 6) {
+        int tb = 16384;
+        const int got = std::sscanf(line, "rowb %d %lld %lld %lld %lld %d %d", &r.E, &a, &b, &c, &d, &r.rowb, &tb);
+        if (got >= 6) {
             r.da_lo = a; r.da_hi = b; r.db_lo = c; r.db_hi = d;
+            r.tbytes = got == 7 ? tb : 16384;
             const bool ok_rowb = r.rowb == 128 || r.rowb == 256 || (r.rowb == 512 && r.E != 1);
-            if (ok_rowb) t->rowb.push_back(r);
+            const bool ok_tb = r.tbytes == 16384 || (r.tbytes == 8192 && r.rowb == 128);
+            if (ok_rowb && ok_tb) t->rowb.push_back(r);
         } else if (std::sscanf(line, "%31s %lu", key, &v) == 2 && v >= 1) {
             if (!std::strcmp(key, "min_grab")) t->batch.min_grab = uint32_t(v);
             else if (!std::strcmp(key, "max_grab")) t->batch.max_grab = uint32_t(v);
@@ -78,12 +83,15 @@ std::shared_ptr<const Table> current()
 
 BatchTuning batch_tuning() { return current()->batch; }
 
-int tuned_rowb(int E, int64_t DA, int64_t DB)
+bool tuned_shape(int E, int64_t DA, int64_t DB, TileShape &shape)
 {
     const std::shared_ptr<const Table> t = current();
     for (const RowbRule &r : t->rowb)
-        if (r.E == E && DA >= r.da_lo && DA <= r.da_hi && DB >= r.db_lo && DB <= r.db_hi) return r.rowb;
-    return 0;
+        if (r.E == E && DA >= r.da_lo && DA <= r.da_hi && DB >= r.db_lo && DB <= r.db_hi) {
+            shape = {r.rowb, r.tbytes};
+            return true;
+        }
+    return false;
 }
 
 }  // namespace rearr

@@ -25,9 +25,15 @@ struct BatchTuning {
 
 BatchTuning batch_tuning();
 
-// Staged row bytes (128, 256 or 512) the tuning table assigns to a fully
-// vectorised fast tile of element size E on a DA x DB plane; 0 if the table has
-// no entry for that class.
-int tuned_rowb(int E, int64_t DA, int64_t DB);
+// Shape of a fast tile: staged row bytes (128, 256 or 512) and payload bytes
+// (16384, or 8192 for the half tile).
+struct TileShape {
+    int rowb;
+    int tbytes;
+};
+
+// The shape the tuning table assigns to a fully vectorised fast tile of
+// element size E on a DA x DB plane; false if the table has no entry.
+bool tuned_shape(int E, int64_t DA, int64_t DB, TileShape &shape);
 
 }  // namespace rearr

@@ -18,9 +18,16 @@
     X(8, 16, 16, 512)                                                                             \
     X(16, 16, 16, 256) X(16, 16, 16, 128) X(16, 16, 16, 512)
 
+// Half tiles (8 KB payload) for planes too small to fill 16 KB.
+// XH(E, VIN, VOUT, ROWB)
+#define REARR_TILE_HALF_VARIANTS(XH) XH(2, 16, 4, 128) XH(4, 16, 8, 128)
+
 namespace rearr {
 
 // Default staged row length of an element size (used by the fallback widths).
 constexpr int default_rowb(int E) { return E == 1 ? 128 : 256; }
+
+// Output width of the half-tile variant of an element size (0: none).
+constexpr int half_tile_vout(int E) { return E == 2 ? 4 : E == 4 ? 8 : 0; }
 
 }  // namespace rearr

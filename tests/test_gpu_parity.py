@@ -369,3 +369,26 @@ def test_reorder_large_sources(lr, orc, e, kind):
         idx = np.concatenate([synth.block_shuffled_permutation(10, m, 4096),
                               np.arange(m, n, dtype=np.uint32)])
     _l2_case(lr, orc, e, n, idx, seed=e * 100 + len(kind))
+
+
+def test_every_tile_shape(lr, orc, tmp_path):
+    """Each fast-tile shape (128/256/512-byte rows, 16 KB and 8 KB tiles),
+    forced through the tuning table, gives the oracle's bytes on planes with
+    ragged edges."""
+    shapes = {1: [(128, 16384), (256, 16384)], 2: [(128, 16384), (256, 16384), (512, 16384), (128, 8192)],
+              4: [(128, 16384), (256, 16384), (512, 16384), (128, 8192)], 8: [(128, 16384), (256, 16384), (512, 16384)],
+              16: [(128, 16384), (256, 16384), (512, 16384)]}
+    try:
+        for e, cands in shapes.items():
+            v = 16 // e
+            dims = [5, 7 * 16 * v // 4 + 3 * v, 9 * 16 * v // 4 + v]   # multiples of the vector width, ragged
+            for rowb, tb in cands:
+                t = tmp_path / f"t{e}_{rowb}_{tb}.txt"
+                t.write_text(f"rowb {e} 1 2147483647 1 2147483647 {rowb} {tb}\n")
+                lr.tuning_load(str(t))
+                d = lr.describe_permute(e, dims, [0, 2, 1])
+                assert d["kind"] == "tile" and d["tile_a"] * e == rowb and d["tile_a"] * d["tile_b"] * e == tb, d
+                check_permute(lr, orc, 31 * e + rowb + tb, e, dims, [0, 2, 1])
+    finally:
+        lr.tuning_load(None)
+        lr.tuning_load(lr.DEFAULT_TUNE_TABLE)
