@@ -81,12 +81,14 @@ class Oracle:
         lib.oracle_permute_sample.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int, i64p, ip,
                                               i64p, ctypes.c_int64]
         lib.oracle_reorder.argtypes = [vp, vp, vp, ctypes.c_size_t, ctypes.c_size_t]
+        lib.oracle_reorder_nm.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int, i64p, ctypes.c_int, ip, i64p, i64p]
         lib.oracle_reorder_sample.argtypes = [vp, vp, vp, ctypes.c_size_t, ctypes.c_size_t, i64p, ctypes.c_int64]
         lib.oracle_interlace.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t,
                                          ctypes.c_size_t]
         lib.oracle_deinterlace.argtypes = [ctypes.POINTER(vp), vp, ctypes.c_int, ctypes.c_size_t,
                                            ctypes.c_size_t]
         for name in ("oracle_permute", "oracle_permute_sample", "oracle_reorder", "oracle_reorder_sample",
+                     "oracle_reorder_nm",
                      "oracle_interlace", "oracle_deinterlace"):
             getattr(lib, name).restype = ctypes.c_int
         self.lib = lib
@@ -123,6 +125,26 @@ class Oracle:
         if rc != 0:
             raise OracleError("oracle_permute_sample rejected its arguments")
         return vals
+
+    # -- N-to-M reorder -----------------------------------------------------------
+    def reorder_nm(self, src: np.ndarray, elem_bytes: int, dims: Sequence[int], order: Sequence[int],
+                   base: Sequence[int], rng: Sequence[int]) -> np.ndarray:
+        """Sub-box of src (kept axes order[i] over [base, base + range), other
+        axes at base), output axes in the given order; flat uint8."""
+        rank_in, rank_out = len(dims), len(order)
+        sb = _bytes_view(src)
+        total = 1
+        for a in order:
+            total *= int(rng[a])
+        out = np.empty(max(total, 0) * elem_bytes, dtype=np.uint8)
+        d = (ctypes.c_int64 * max(rank_in, 1))(*[int(x) for x in dims])
+        o = (ctypes.c_int * max(rank_out, 1))(*[int(x) for x in order])
+        b = (ctypes.c_int64 * max(rank_in, 1))(*[int(x) for x in base])
+        r = (ctypes.c_int64 * max(rank_in, 1))(*[int(x) for x in rng])
+        rc = self.lib.oracle_reorder_nm(_ptr(out), _ptr(sb), elem_bytes, rank_in, d, rank_out, o, b, r)
+        if rc != 0:
+            raise OracleError("oracle_reorder_nm rejected its arguments")
+        return out
 
     # -- reorder ---------------------------------------------------------------
     def reorder(self, src: np.ndarray, idx: np.ndarray, elem_bytes: int) -> np.ndarray:
@@ -199,6 +221,10 @@ def permute_sample(*a, **k):
 
 def reorder(*a, **k):
     return get().reorder(*a, **k)
+
+
+def reorder_nm(*a, **k):
+    return get().reorder_nm(*a, **k)
 
 
 def reorder_sample(*a, **k):

@@ -138,6 +138,57 @@ int oracle_permute_sample(void *vals, const void *src, size_t elem_bytes,
     return 0;
 }
 
+int oracle_reorder_nm(void *dst, const void *src, size_t elem_bytes,
+                      int rank_in, const int64_t *dims, int rank_out,
+                      const int *order, const int64_t *base,
+                      const int64_t *range)
+{
+    if (elem_bytes == 0 || rank_in < 1 || rank_in > ORACLE_MAX_RANK || !dims ||
+        rank_out < 1 || rank_out > rank_in || !order || !base || !range)
+        return -1;
+    int kept[ORACLE_MAX_RANK] = {0};
+    for (int a = 0; a < rank_in; ++a)
+        if (dims[a] < 0) return -1;
+    for (int i = 0; i < rank_out; ++i) {
+        const int a = order[i];
+        if (a < 0 || a >= rank_in || kept[a]) return -1;
+        kept[a] = 1;
+    }
+    /* kept axes span [base, base + range); dropped axes sit at base */
+    int64_t total = 1;
+    for (int a = 0; a < rank_in; ++a) {
+        if (base[a] < 0) return -1;
+        if (kept[a]) {
+            if (range[a] < 0 || base[a] + range[a] > dims[a]) return -1;
+            total *= range[a];
+        } else if (base[a] >= dims[a]) {
+            return -1;
+        }
+    }
+    if (total == 0) return 0;
+    if (!dst || !src) return -1;
+
+    int64_t s[ORACLE_MAX_RANK], j[ORACLE_MAX_RANK], x[ORACLE_MAX_RANK];
+    row_major_strides(rank_in, dims, s);
+    for (int i = 0; i < rank_out; ++i) j[i] = 0;
+    unsigned char *out = (unsigned char *)dst;
+    const unsigned char *in = (const unsigned char *)src;
+    for (int64_t lin = 0; lin < total; ++lin) {
+        /* input multi-index of output multi-index j */
+        for (int a = 0; a < rank_in; ++a) x[a] = base[a];
+        for (int i = 0; i < rank_out; ++i) x[order[i]] += j[i];
+        int64_t off = 0;
+        for (int a = 0; a < rank_in; ++a) off += x[a] * s[a];
+        memcpy(out + (size_t)lin * elem_bytes, in + (size_t)off * elem_bytes,
+               elem_bytes);
+        for (int i = rank_out - 1; i >= 0; --i) {
+            if (++j[i] < range[order[i]]) break;
+            j[i] = 0;
+        }
+    }
+    return 0;
+}
+
 int oracle_reorder(void *dst, const void *src, const uint32_t *idx, size_t n,
                    size_t elem_bytes)
 {

@@ -29,6 +29,15 @@ int oracle_permute_sample(void *vals, const void *src, size_t elem_bytes,
                           int rank, const int64_t *dims, const int *perm,
                           const int64_t *out_lin, int64_t count);
 
+/* N-to-M reorder (Sec. III.B): the output has rank_out <= rank_in axes; output
+ * axis i is input axis order[i] and spans [base[a], base[a] + range[a]) of it
+ * (a = order[i]); every input axis not in order sits at index base[a]:
+ *   out[j] = in[x],  x[a] = base[a] + (j_i if a == order[i] else 0). */
+int oracle_reorder_nm(void *dst, const void *src, size_t elem_bytes,
+                      int rank_in, const int64_t *dims, int rank_out,
+                      const int *order, const int64_t *base,
+                      const int64_t *range);
+
 /* Reorder by an index sequence (Sec. III.A indexed access): dst[i] = src[idx[i]],
  * src holding n elements; an index >= n is rejected with -1. */
 int oracle_reorder(void *dst, const void *src, const uint32_t *idx, size_t n,

@@ -337,7 +337,82 @@ def pin_worked_examples(orc) -> List[str]:
     return fails
 
 
-ALL_PINS = [pin_worked_examples, pin_bruteforce_small, pin_numpy_transpose, pin_matrix_transpose,
+def random_box(g, rank_in, max_extent=6):
+    """A random N-to-M request: dims, order (kept axes in output order), base, range."""
+    dims = [int(g.integers(1, max_extent + 1)) for _ in range(rank_in)]
+    rank_out = int(g.integers(1, rank_in + 1))
+    order = [int(v) for v in g.permutation(rank_in)[:rank_out]]
+    base, rng = [], []
+    for a in range(rank_in):
+        if a in order:
+            b = int(g.integers(0, dims[a]))
+            base.append(b)
+            rng.append(int(g.integers(0 if dims[a] > 1 and g.random() < 0.05 else 1, dims[a] - b + 1)))
+        else:
+            base.append(int(g.integers(0, dims[a])))
+            rng.append(0)
+    return dims, order, base, rng
+
+
+def nm_numpy(src_flat, e, dims, order, base, rng):
+    """numpy slicing: ints for dropped axes, slices for kept ones, then the kept
+    axes (in input order) transposed into the requested output order."""
+    a = src_flat.view(_void(e)).reshape(dims)
+    key, kept = [], []
+    for ax in range(len(dims)):
+        if ax in order:
+            key.append(slice(base[ax], base[ax] + rng[ax]))
+            kept.append(ax)
+        else:
+            key.append(base[ax])
+    sub = a[tuple(key)]
+    return np.ascontiguousarray(sub.transpose([kept.index(ax) for ax in order])).reshape(-1)
+
+
+def pin_reorder_nm(orc) -> List[str]:
+    """N-to-M reorder (Sec. III.B) against numpy slicing + transpose, against a
+    scatter-side brute force, and its special cases: full box = permute, and a
+    rank-1 box = a contiguous range copy (the "specified range" access of
+    Sec. III.A)."""
+    fails = []
+    g = synth.rng(21)
+    for t in range(60):
+        rank_in = int(g.integers(1, 7))
+        dims, order, base, rng = random_box(g, rank_in)
+        e = ELEM_SIZES[t % len(ELEM_SIZES)]
+        n = int(np.prod(dims))
+        src = synth.random_elements(7000 + t, n, e)
+        got = orc.reorder_nm(src, e, dims, order, base, rng)
+        want = nm_numpy(src, e, dims, order, base, rng)
+        if not np.array_equal(got.view(_void(e)), want):
+            fails.append(f"nm numpy dims={dims} order={order} base={base} range={rng}")
+            continue
+        # scatter-side brute force: walk the input box, place each element
+        od = [rng[a] for a in order]
+        out = np.zeros(int(np.prod(od)) * e, dtype=np.uint8) if od else np.zeros(0, np.uint8)
+        boxes = [range(base[a], base[a] + rng[a]) if a in order else [base[a]] for a in range(rank_in)]
+        for x in itertools.product(*boxes):
+            pos = 0
+            for i, a in enumerate(order):
+                pos = pos * od[i] + (x[a] - base[a])
+            lin = int(np.ravel_multi_index(x, dims))
+            out[pos * e:(pos + 1) * e] = src[lin * e:(lin + 1) * e]
+        if not np.array_equal(got, out):
+            fails.append(f"nm brute force dims={dims} order={order}")
+    for t in range(10):  # full box with all axes kept is the permute
+        rank = int(g.integers(1, 6))
+        dims = [int(g.integers(1, 6)) for _ in range(rank)]
+        perm = [int(v) for v in g.permutation(rank)]
+        src = synth.random_elements(7500 + t, int(np.prod(dims)), 4)
+        if not np.array_equal(orc.reorder_nm(src, 4, dims, perm, [0] * rank, dims), orc.permute(src, 4, dims, perm)):
+            fails.append(f"nm full box != permute dims={dims} perm={perm}")
+    src = np.arange(100, dtype=np.uint32)
+    if orc.reorder_nm(src, 4, [100], [0], [17], [40]).view(np.uint32).tolist() != list(range(17, 57)):
+        fails.append("nm range copy")
+    return fails
+
+
+ALL_PINS = [pin_worked_examples, pin_reorder_nm, pin_bruteforce_small, pin_numpy_transpose, pin_matrix_transpose,
             pin_identity_is_memcpy, pin_inverse_roundtrip, pin_bijection,
             pin_paper_rank3_orders, pin_sample_matches_full, pin_reorder, pin_interlace,
             pin_rejects_invalid]

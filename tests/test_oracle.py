@@ -50,11 +50,15 @@ MUTANTS = [
      "in + ((size_t)j * n + i) * elem_bytes, elem_bytes);"),
     ("sampled reorder skips the index", "const uint32_t j = idx[pos[t]];",
      "const uint32_t j = (uint32_t)pos[t];"),
+    ("N-to-M dropped axes ignore their base", "for (int a = 0; a < rank_in; ++a) x[a] = base[a];",
+     "for (int a = 0; a < rank_in; ++a) x[a] = kept[a] ? base[a] : 0;"),
+    ("N-to-M odometer uses the input extents", "if (++j[i] < range[order[i]]) break;",
+     "if (++j[i] < dims[order[i]]) break;"),
     ("permutation check dropped", "if (seen[perm[i]]) return -1;", ""),
     ("reorder range check dropped", "if ((size_t)idx[i] >= n) return -1;", ""),
     ("last byte of each element dropped",
-     "memcpy(out + (size_t)lin * elem_bytes, in + (size_t)off * elem_bytes,\n               elem_bytes);",
-     "memcpy(out + (size_t)lin * elem_bytes, in + (size_t)off * elem_bytes,\n               elem_bytes > 1 ? elem_bytes - 1 : 1);"),
+     "int64_t off = input_offset(rank, perm, s, j);\n        memcpy(out + (size_t)lin * elem_bytes, in + (size_t)off * elem_bytes,\n               elem_bytes);",
+     "int64_t off = input_offset(rank, perm, s, j);\n        memcpy(out + (size_t)lin * elem_bytes, in + (size_t)off * elem_bytes,\n               elem_bytes > 1 ? elem_bytes - 1 : 1);"),
     ("interlace plane index swapped",
      "(const unsigned char *)srcs[j] + i * elem_bytes, elem_bytes);",
      "(const unsigned char *)srcs[(j + 1) % k] + i * elem_bytes, elem_bytes);"),
