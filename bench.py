@@ -671,7 +671,7 @@ def run_reference(args):
 
 def parse_case(spec: str):
     """Single-op case spec: permute:E:d0,d1,..:p0,p1,.. | reorder:E:n:random|block4096 |
-    interlace:E:n:k | deinterlace:E:n:k."""
+    interlace:E:n:k | deinterlace:E:n:k | nm:E:dims:order:base:range (comma lists)."""
     parts = spec.split(":")
     kind, e = parts[0], int(parts[1])
     if kind == "permute":
@@ -681,6 +681,9 @@ def parse_case(spec: str):
         return dict(kind=kind, elem_bytes=e, n=int(parts[2]), idx=parts[3])
     if kind in ("interlace", "deinterlace"):
         return dict(kind=kind, elem_bytes=e, n=int(parts[2]), k=int(parts[3]))
+    if kind == "nm":
+        ints = [[int(x) for x in q.split(",")] for q in parts[2:6]]
+        return dict(kind=kind, elem_bytes=e, dims=ints[0], order=ints[1], base=ints[2], range=ints[3])
     raise SystemExit(f"unknown case kind {kind}")
 
 
@@ -698,7 +701,14 @@ def run_case(args):
         return run_batch_case(torch, rr, stream, dev, int(args.case.split(":")[1]), args)
     o = parse_case(args.case)
     e = o["elem_bytes"]
-    if o["kind"] in ("permute", "reorder"):
+    if o["kind"] == "nm":
+        n = int(np.prod(o["dims"]))
+        total = int(np.prod([o["range"][a] for a in o["order"]]))
+        src = torch.empty(n * e, dtype=torch.uint8, device=dev).random_()
+        dst = torch.empty(total * e, dtype=torch.uint8, device=dev)
+        call = lambda: rr.reorder_nm(dst, src, e, o["dims"], o["order"], o["base"], o["range"], stream)  # noqa: E731
+        nbytes = 2 * total * e
+    elif o["kind"] in ("permute", "reorder"):
         n = int(np.prod(o["dims"])) if o["kind"] == "permute" else o["n"]
         src = torch.empty(n * e, dtype=torch.uint8, device=dev).random_()
         dst = torch.empty(n * e, dtype=torch.uint8, device=dev)

@@ -73,6 +73,28 @@ rearr_status rearr_permute(void *dst, const void *src, size_t elem_bytes, int ra
                            const int64_t *dims, const int *perm, rearr_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * rearr_reorder_nm -- N-to-M reorder (arXiv:1011.3583 Sec. III.B: "N-to-M"
+ * reorder with a base index and a range per dimension): a sub-box of the
+ * input, with some axes dropped, in a chosen axis order.
+ *
+ *   src      : rank_in-dimensional row-major array of extents dims.
+ *   order    : rank_out distinct input axes; output axis i is input axis
+ *              order[i] (1 <= rank_out <= rank_in).
+ *   base     : per input axis, the start index (dropped axes sit there).
+ *   range    : per input axis, the extent taken from base (kept axes only;
+ *              base + range <= dims); ignored for dropped axes.
+ *   dst      : row-major over extents range[order[i]]:
+ *       dst[j] = src[x],  x[a] = base[a] + (j_i if a == order[i] else 0).
+ *   With rank_out == rank_in, base 0 and range dims it is rearr_permute; a
+ *   rank-1 box is the "specified range" access of Sec. III.A.  When the box
+ *   keeps no input-contiguous axis, reads cannot be coalesced (the paper notes
+ *   the same) and the op runs as a gather of short runs.
+ * ------------------------------------------------------------------------- */
+rearr_status rearr_reorder_nm(void *dst, const void *src, size_t elem_bytes, int rank_in,
+                              const int64_t *dims, int rank_out, const int *order,
+                              const int64_t *base, const int64_t *range, rearr_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * rearr_reorder -- reorder by an index sequence, the "accessing specified set
  * of indices" pattern of arXiv:1011.3583 Sec. III.A:
  *       dst[i] = src[idx[i]],  0 <= i < n.
@@ -140,6 +162,9 @@ rearr_status rearr_plan_add_permute(rearr_plan *plan, void *dst, const void *src
                                     const int *perm);
 rearr_status rearr_plan_add_reorder(rearr_plan *plan, void *dst, const void *src,
                                     const uint32_t *idx, size_t n, size_t elem_bytes);
+rearr_status rearr_plan_add_reorder_nm(rearr_plan *plan, void *dst, const void *src, size_t elem_bytes,
+                                       int rank_in, const int64_t *dims, int rank_out, const int *order,
+                                       const int64_t *base, const int64_t *range);
 rearr_status rearr_plan_add_interlace(rearr_plan *plan, void *dst, const void *const *srcs,
                                       int k, size_t n, size_t elem_bytes);
 rearr_status rearr_plan_add_deinterlace(rearr_plan *plan, void *const *dsts, const void *src,

@@ -57,6 +57,19 @@ rearr_status rearr_permute(void *dst, const void *src, size_t elem_bytes, int ra
     return REARR_OK;
 }
 
+rearr_status rearr_reorder_nm(void *dst, const void *src, size_t elem_bytes, int rank_in, const int64_t *dims,
+                              int rank_out, const int *order, const int64_t *base, const int64_t *range,
+                              rearr_stream_t stream)
+{
+    PermPlan pl;
+    std::string err;
+    rearr_status st = plan_reorder_nm(dst, src, elem_bytes, rank_in, dims, rank_out, order, base, range, pl, err);
+    if (st != REARR_OK) return fail(st, "rearr_reorder_nm: " + err);
+    cudaError_t e = launch_single(pl.op, nullptr, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "rearr_reorder_nm launch");
+    return REARR_OK;
+}
+
 rearr_status rearr_reorder(void *dst, const void *src, const uint32_t *idx, size_t n, size_t elem_bytes,
                            rearr_stream_t stream)
 {

@@ -237,6 +237,19 @@ rearr_status rearr_plan_add_permute(rearr_plan *plan, void *dst, const void *src
     return add_op(plan, pl.op);
 }
 
+rearr_status rearr_plan_add_reorder_nm(rearr_plan *plan, void *dst, const void *src, size_t elem_bytes,
+                                       int rank_in, const int64_t *dims, int rank_out, const int *order,
+                                       const int64_t *base, const int64_t *range)
+{
+    if (!plan) return fail(REARR_EINVAL, "rearr_plan_add_reorder_nm: plan is NULL");
+    if (plan->finalized) return fail(REARR_EBUSY, "rearr_plan_add_reorder_nm: plan is finalized");
+    PermPlan pl;
+    std::string err;
+    rearr_status st = plan_reorder_nm(dst, src, elem_bytes, rank_in, dims, rank_out, order, base, range, pl, err);
+    if (st != REARR_OK) return fail(st, "rearr_plan_add_reorder_nm: " + err);
+    return add_op(plan, pl.op);
+}
+
 rearr_status rearr_plan_add_reorder(rearr_plan *plan, void *dst, const void *src, const uint32_t *idx, size_t n,
                                     size_t elem_bytes)
 {

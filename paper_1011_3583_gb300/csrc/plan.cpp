@@ -47,7 +47,7 @@ bool ranges_overlap(uintptr_t a, uint64_t na, uintptr_t b, uint64_t nb)
 
 struct Axis {
     int64_t extent;
-    int64_t stride;  // input stride in cells
+    int64_t stride;  // input stride in bytes
 };
 
 }  // namespace
@@ -100,14 +100,14 @@ static void fill_tile_common(TileDesc &t, const std::vector<Axis> &ax, int p, in
     for (int i = R - 2; i >= 0; --i) os[i] = os[i + 1] * ax[i + 1].extent;
     t.dst = dst;
     t.src = src;
-    t.sb_in = ax[R - 1].stride * cell;
+    t.sb_in = ax[R - 1].stride;
     t.sa_out = os[p] * cell;
     t.DA = uint32_t(DA);
     t.DB = uint32_t(DB);
     int nb = 0;
     for (int i = 0; i < R; ++i) {
         if (i == p || i == R - 1) continue;
-        t.bin[nb] = ax[i].stride * cell;
+        t.bin[nb] = ax[i].stride;
         t.bout[nb] = os[i] * cell;
         t.bdiv[nb] = make_fastdiv(uint32_t(ax[i].extent));
         ++nb;
@@ -120,54 +120,18 @@ static void fill_tile_common(TileDesc &t, const std::vector<Axis> &ax, int p, in
     t.nb = nb;
 }
 
-rearr_status plan_permute(void *dst, const void *src, size_t elem_bytes, int rank, const int64_t *dims,
-                          const int *perm, PermPlan &pl, std::string &err)
+// Plans a gather of `total` elements of elem_bytes whose output axes are
+// given in order (slowest first) with their input byte strides; src already
+// points at the element of output index 0.  The output is contiguous.
+static rearr_status plan_axes(void *dst, const char *src, size_t elem_bytes, const std::vector<Axis> &in_axes,
+                              uint64_t total, PermPlan &pl, std::string &err)
 {
-    std::memset(&pl, 0, sizeof(pl));
     rearr_permute_info &info = pl.info;
-    info.plane_a = -1;
-    if (elem_bytes == 0) { err = "elem_bytes must be >= 1"; return REARR_EINVAL; }
-    if (rank < 1 || rank > kMaxRank) { err = "rank must be in [1, 8]"; return REARR_EINVAL; }
-    if (!dims || !perm) { err = "dims and perm must not be NULL"; return REARR_EINVAL; }
-    bool seen[kMaxRank] = {false};
-    for (int i = 0; i < rank; ++i) {
-        if (dims[i] < 0) { err = "dims must be >= 0"; return REARR_EINVAL; }
-        if (perm[i] < 0 || perm[i] >= rank || seen[perm[i]]) {
-            err = "perm is not a permutation of 0..rank-1";
-            return REARR_EINVAL;
-        }
-        seen[perm[i]] = true;
-    }
-    uint64_t total = 1;
-    for (int i = 0; i < rank; ++i)
-        if (mul_overflows(total, uint64_t(dims[i]), total)) { err = "element count overflows"; return REARR_EINVAL; }
-    uint64_t bytes;
-    if (mul_overflows(total, elem_bytes, bytes) || bytes > (uint64_t(1) << 62)) {
-        err = "byte count overflows";
-        return REARR_EINVAL;
-    }
-    if (total == 0) {
-        info.kind = REARR_KIND_NOOP;
-        pl.op.units = 0;
-        return REARR_OK;
-    }
-    if (!dst || !src) { err = "dst and src must not be NULL"; return REARR_EINVAL; }
-    if (ranges_overlap(uintptr_t(dst), bytes, uintptr_t(src), bytes)) {
-        err = "dst overlaps src (in-place permute is not supported)";
-        return REARR_EINVAL;
-    }
-
-    // Row-major input strides, in elements.
-    int64_t s[kMaxRank];
-    s[rank - 1] = 1;
-    for (int i = rank - 2; i >= 0; --i) s[i] = s[i + 1] * dims[i + 1];
-
-    // Output axes with extent > 1, merged where adjacent and in order.
+    const uint64_t bytes = total * elem_bytes;
+    // Axes with extent > 1, merged where adjacent and in order.
     std::vector<Axis> ax;
-    for (int i = 0; i < rank; ++i) {
-        const int a = perm[i];
-        if (dims[a] == 1) continue;
-        Axis cur{dims[a], s[a]};
+    for (const Axis &cur : in_axes) {
+        if (cur.extent == 1) continue;
         if (!ax.empty() && ax.back().stride == cur.stride * cur.extent) {
             ax.back().extent *= cur.extent;
             ax.back().stride = cur.stride;
@@ -190,45 +154,48 @@ rearr_status plan_permute(void *dst, const void *src, size_t elem_bytes, int ran
         op.cls = OC_COPY;
         op.word = uint32_t(W);
         op.copy.dst = static_cast<char *>(dst);
-        op.copy.src = static_cast<const char *>(src);
+        op.copy.src = src;
         op.copy.bytes = bytes;
         op.copy.unit_bytes = uint64_t(kThreads) * 4 * W;
         op.units = (bytes + op.copy.unit_bytes - 1) / op.copy.unit_bytes;
         info.n_tiles = int64_t(op.units);
     };
 
-    if (ax.size() <= 1) {  // identity after dropping / merging
+    if (ax.empty() || (ax.size() == 1 && ax[0].stride == cell)) {  // one contiguous range
         set_copy();
         return REARR_OK;
     }
-    // Fold an unmoved innermost axis into the cell.
-    if (ax.back().stride == 1) {
-        const int64_t inner = ax.back().extent;
-        cell *= inner;
+    // Fold an unmoved (input-contiguous) innermost axis into the cell.
+    if (ax.back().stride == cell) {
+        cell *= ax.back().extent;
         ax.pop_back();
-        for (Axis &a : ax) a.stride /= inner;  // every other stride is a multiple of inner
-        if (ax.size() == 1 && ax[0].stride == 1) {
+        if (ax.empty() || (ax.size() == 1 && ax[0].stride == cell)) {
             set_copy();
             return REARR_OK;
         }
     }
     const int R = int(ax.size());
+    uint64_t strides_or = 0;
     info.rank = R;
     for (int i = 0; i < R; ++i) {
         info.dims[i] = ax[i].extent;
-        info.in_strides[i] = ax[i].stride;
+        info.in_strides[i] = ax[i].stride / cell;
+        strides_or |= uint64_t(ax[i].stride);
     }
     info.cell_bytes = cell;
-    int p = -1;
+    int p = -1;  // output axis along which input cells are contiguous
     for (int i = 0; i < R; ++i)
-        if (ax[i].stride == 1) p = i;
+        if (ax[i].stride == cell) p = i;
 
-    // Cells of 128 bytes or more are copied as contiguous runs.
+    // Cells of 128 bytes or more are copied as runs, and so are boxes with no
+    // input-contiguous axis (there both sides cannot be coalesced).
     if (cell >= kRunMinBytes || p < 0) {
-        const int W = pow2_align(da, sa, uint64_t(cell));
+        const int W = pow2_align(da, sa, uint64_t(cell), strides_or);
         uint64_t n_runs = 1;
         for (int i = 0; i < R; ++i) n_runs *= uint64_t(ax[i].extent);
         if (n_runs > kMaxUnits) { err = "too many runs"; return REARR_EINVAL; }
+        for (int i = 0; i < R; ++i)
+            if (ax[i].extent > int64_t(kMaxUnits)) { err = "a collapsed axis has 2^32 or more elements"; return REARR_EINVAL; }
         info.kind = REARR_KIND_RUNS;
         info.word_bytes = W;
         OpDesc &op = pl.op;
@@ -236,11 +203,11 @@ rearr_status plan_permute(void *dst, const void *src, size_t elem_bytes, int ran
         op.word = uint32_t(W);
         RunsDesc &r = op.runs;
         r.dst = static_cast<char *>(dst);
-        r.src = static_cast<const char *>(src);
+        r.src = src;
         r.run_bytes = cell;
         r.nd = R;
         for (int i = 0; i < kMaxRank; ++i) {
-            r.in_stride[i] = i < R ? ax[i].stride * cell : 0;
+            r.in_stride[i] = i < R ? ax[i].stride : 0;
             r.div[i] = make_fastdiv(i < R ? uint32_t(ax[i].extent) : 1u);
         }
         r.n_runs = n_runs;
@@ -273,8 +240,8 @@ rearr_status plan_permute(void *dst, const void *src, size_t elem_bytes, int ran
 
     OpDesc &op = pl.op;
     TileDesc &t = op.tile;
-    fill_tile_common(t, ax, p, cell, DA, DB, static_cast<char *>(dst), static_cast<const char *>(src));
-    const int W = pow2_align(da, sa, uint64_t(cell));
+    fill_tile_common(t, ax, p, cell, DA, DB, static_cast<char *>(dst), src);
+    const int W = pow2_align(da, sa, uint64_t(cell), strides_or);
     info.word_bytes = W;
     uint64_t batch = 1;
     for (int i = 0; i < t.nb; ++i) batch *= t.bdiv[i].d;
@@ -282,13 +249,14 @@ rearr_status plan_permute(void *dst, const void *src, size_t elem_bytes, int ran
     if (W == cell) {
         // Fast tile: one power-of-two element per cell.
         const int E = int(cell);
-
-        // Widest legal global access on each side: every input row starts at a
-        // multiple of DA*E bytes from src, every output row at a multiple of
-        // DB*E bytes from dst.
+        // Widest legal global access on each side.  Input rows start at src
+        // plus sums of the (non-A) input strides; output rows start at
+        // multiples of DB*E bytes from dst.
+        uint64_t in_or = uint64_t(t.sb_in);
+        for (int i = 0; i < t.nb; ++i) in_or |= uint64_t(t.bin[i]);
         int vin = E;
         for (int v : {16, 4}) {
-            if (v > E && (uint64_t(DA) * E) % v == 0 && sa % v == 0) { vin = v; break; }
+            if (v > E && (uint64_t(DA) * E) % v == 0 && sa % v == 0 && in_or % v == 0) { vin = v; break; }
         }
         int vout = E;
         const int vmax = std::min(16, 4 * E);
@@ -349,6 +317,105 @@ rearr_status plan_permute(void *dst, const void *src, size_t elem_bytes, int ran
     op.units = units;
     info.n_tiles = int64_t(units);
     return REARR_OK;
+}
+
+rearr_status plan_permute(void *dst, const void *src, size_t elem_bytes, int rank, const int64_t *dims,
+                          const int *perm, PermPlan &pl, std::string &err)
+{
+    std::memset(&pl, 0, sizeof(pl));
+    rearr_permute_info &info = pl.info;
+    info.plane_a = -1;
+    if (elem_bytes == 0) { err = "elem_bytes must be >= 1"; return REARR_EINVAL; }
+    if (rank < 1 || rank > kMaxRank) { err = "rank must be in [1, 8]"; return REARR_EINVAL; }
+    if (!dims || !perm) { err = "dims and perm must not be NULL"; return REARR_EINVAL; }
+    bool seen[kMaxRank] = {false};
+    for (int i = 0; i < rank; ++i) {
+        if (dims[i] < 0) { err = "dims must be >= 0"; return REARR_EINVAL; }
+        if (perm[i] < 0 || perm[i] >= rank || seen[perm[i]]) {
+            err = "perm is not a permutation of 0..rank-1";
+            return REARR_EINVAL;
+        }
+        seen[perm[i]] = true;
+    }
+    uint64_t total = 1;
+    for (int i = 0; i < rank; ++i)
+        if (mul_overflows(total, uint64_t(dims[i]), total)) { err = "element count overflows"; return REARR_EINVAL; }
+    uint64_t bytes;
+    if (mul_overflows(total, elem_bytes, bytes) || bytes > (uint64_t(1) << 62)) {
+        err = "byte count overflows";
+        return REARR_EINVAL;
+    }
+    if (total == 0) {
+        info.kind = REARR_KIND_NOOP;
+        pl.op.units = 0;
+        return REARR_OK;
+    }
+    if (!dst || !src) { err = "dst and src must not be NULL"; return REARR_EINVAL; }
+    if (ranges_overlap(uintptr_t(dst), bytes, uintptr_t(src), bytes)) {
+        err = "dst overlaps src (in-place permute is not supported)";
+        return REARR_EINVAL;
+    }
+    // Row-major input strides in bytes; output axis i is input axis perm[i].
+    int64_t s[kMaxRank];
+    s[rank - 1] = int64_t(elem_bytes);
+    for (int i = rank - 2; i >= 0; --i) s[i] = s[i + 1] * dims[i + 1];
+    std::vector<Axis> ax;
+    for (int i = 0; i < rank; ++i) ax.push_back(Axis{dims[perm[i]], s[perm[i]]});
+    return plan_axes(dst, static_cast<const char *>(src), elem_bytes, ax, total, pl, err);
+}
+
+rearr_status plan_reorder_nm(void *dst, const void *src, size_t elem_bytes, int rank_in, const int64_t *dims,
+                             int rank_out, const int *order, const int64_t *base, const int64_t *range,
+                             PermPlan &pl, std::string &err)
+{
+    std::memset(&pl, 0, sizeof(pl));
+    pl.info.plane_a = -1;
+    if (elem_bytes == 0) { err = "elem_bytes must be >= 1"; return REARR_EINVAL; }
+    if (rank_in < 1 || rank_in > kMaxRank) { err = "rank_in must be in [1, 8]"; return REARR_EINVAL; }
+    if (rank_out < 1 || rank_out > rank_in) { err = "rank_out must be in [1, rank_in]"; return REARR_EINVAL; }
+    if (!dims || !order || !base || !range) { err = "dims, order, base and range must not be NULL"; return REARR_EINVAL; }
+    bool kept[kMaxRank] = {false};
+    for (int i = 0; i < rank_out; ++i) {
+        const int a = order[i];
+        if (a < 0 || a >= rank_in || kept[a]) { err = "order must list distinct input axes"; return REARR_EINVAL; }
+        kept[a] = true;
+    }
+    uint64_t total = 1, in_total = 1;
+    for (int a = 0; a < rank_in; ++a) {
+        if (dims[a] < 0 || base[a] < 0) { err = "dims and base must be >= 0"; return REARR_EINVAL; }
+        if (kept[a]) {
+            if (range[a] < 0 || base[a] + range[a] > dims[a]) { err = "a kept axis range leaves the input"; return REARR_EINVAL; }
+            if (mul_overflows(total, uint64_t(range[a]), total)) { err = "element count overflows"; return REARR_EINVAL; }
+        } else if (base[a] >= dims[a]) {
+            err = "a dropped axis base index is out of range";
+            return REARR_EINVAL;
+        }
+        if (mul_overflows(in_total, uint64_t(dims[a]), in_total)) { err = "element count overflows"; return REARR_EINVAL; }
+    }
+    uint64_t bytes, in_bytes;
+    if (mul_overflows(total, elem_bytes, bytes) || mul_overflows(in_total, elem_bytes, in_bytes) ||
+        in_bytes > (uint64_t(1) << 62)) {
+        err = "byte count overflows";
+        return REARR_EINVAL;
+    }
+    if (total == 0) {
+        pl.info.kind = REARR_KIND_NOOP;
+        pl.op.units = 0;
+        return REARR_OK;
+    }
+    if (!dst || !src) { err = "dst and src must not be NULL"; return REARR_EINVAL; }
+    if (ranges_overlap(uintptr_t(dst), bytes, uintptr_t(src), in_bytes)) {
+        err = "dst overlaps src";
+        return REARR_EINVAL;
+    }
+    int64_t s[kMaxRank];
+    s[rank_in - 1] = int64_t(elem_bytes);
+    for (int a = rank_in - 2; a >= 0; --a) s[a] = s[a + 1] * dims[a + 1];
+    int64_t off = 0;
+    for (int a = 0; a < rank_in; ++a) off += base[a] * s[a];
+    std::vector<Axis> ax;
+    for (int i = 0; i < rank_out; ++i) ax.push_back(Axis{range[order[i]], s[order[i]]});
+    return plan_axes(dst, static_cast<const char *>(src) + off, elem_bytes, ax, total, pl, err);
 }
 
 rearr_status plan_reorder(void *dst, const void *src, const uint32_t *idx, size_t n, size_t elem_bytes,

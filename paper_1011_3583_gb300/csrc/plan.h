@@ -26,6 +26,9 @@ struct InterlacePlan {
 // op.units == 0 is a no-op.
 rearr_status plan_permute(void *dst, const void *src, size_t elem_bytes, int rank,
                           const int64_t *dims, const int *perm, PermPlan &pl, std::string &err);
+rearr_status plan_reorder_nm(void *dst, const void *src, size_t elem_bytes, int rank_in, const int64_t *dims,
+                             int rank_out, const int *order, const int64_t *base, const int64_t *range,
+                             PermPlan &pl, std::string &err);
 rearr_status plan_reorder(void *dst, const void *src, const uint32_t *idx, size_t n,
                           size_t elem_bytes, OpDesc &op, std::string &err);
 rearr_status plan_interlace(bool inter, char *interlaced, char *const *planes, int k, size_t n,

@@ -69,6 +69,8 @@ def load() -> ctypes.CDLL:
         "rearr_last_error": (ctypes.c_char_p, []),
         "rearr_permute": (st, [vp, vp, sz, ctypes.c_int, i64p, ip, vp]),
         "rearr_reorder": (st, [vp, vp, vp, sz, sz, vp]),
+        "rearr_reorder_nm": (st, [vp, vp, sz, ctypes.c_int, i64p, ctypes.c_int, ip, i64p, i64p, vp]),
+        "rearr_plan_add_reorder_nm": (st, [vp, vp, vp, sz, ctypes.c_int, i64p, ctypes.c_int, ip, i64p, i64p]),
         "rearr_interlace": (st, [vp, ctypes.POINTER(vp), ctypes.c_int, sz, sz, vp]),
         "rearr_deinterlace": (st, [ctypes.POINTER(vp), vp, ctypes.c_int, sz, sz, vp]),
         "rearr_plan_create": (st, [ctypes.POINTER(vp)]),
@@ -152,6 +154,23 @@ def permute(dst, src, elem_bytes: int, dims: Sequence[int], perm: Sequence[int],
     _check(load().rearr_permute(_ptr(dst), _ptr(src), int(elem_bytes), rank, d, p, _stream(stream)))
 
 
+def _nm_args(dims, order, base, rng):
+    rank_in, rank_out = len(dims), len(order)
+    d = (ctypes.c_int64 * max(rank_in, 1))(*[int(v) for v in dims])
+    o = (ctypes.c_int * max(rank_out, 1))(*[int(v) for v in order])
+    b = (ctypes.c_int64 * max(rank_in, 1))(*[int(v) for v in base])
+    r = (ctypes.c_int64 * max(rank_in, 1))(*[int(v) for v in rng])
+    return rank_in, d, rank_out, o, b, r
+
+
+def reorder_nm(dst, src, elem_bytes: int, dims: Sequence[int], order: Sequence[int], base: Sequence[int],
+               rng: Sequence[int], stream=None) -> None:
+    """rearr_reorder_nm: sub-box of src (kept axes `order` over [base, base+range), other axes at base)."""
+    rank_in, d, rank_out, o, b, r = _nm_args(dims, order, base, rng)
+    _check(load().rearr_reorder_nm(_ptr(dst), _ptr(src), int(elem_bytes), rank_in, d, rank_out, o, b, r,
+                                   _stream(stream)))
+
+
 def reorder(dst, src, idx, n: int, elem_bytes: int, stream=None) -> None:
     """rearr_reorder: dst[i] = src[idx[i]]."""
     _check(load().rearr_reorder(_ptr(dst), _ptr(src), _ptr(idx), int(n), int(elem_bytes), _stream(stream)))
@@ -211,6 +230,11 @@ class Plan:
 
     def add_reorder(self, dst, src, idx, n: int, elem_bytes: int) -> None:
         _check(load().rearr_plan_add_reorder(self._h, _ptr(dst), _ptr(src), _ptr(idx), int(n), int(elem_bytes)))
+
+    def add_reorder_nm(self, dst, src, elem_bytes: int, dims, order, base, rng) -> None:
+        rank_in, d, rank_out, o, b, r = _nm_args(dims, order, base, rng)
+        _check(load().rearr_plan_add_reorder_nm(self._h, _ptr(dst), _ptr(src), int(elem_bytes), rank_in, d,
+                                                rank_out, o, b, r))
 
     def add_interlace(self, dst, srcs, n: int, elem_bytes: int) -> None:
         arr = _ptr_array(srcs)
