@@ -81,6 +81,7 @@ class Oracle:
         lib.oracle_permute_sample.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int, i64p, ip,
                                               i64p, ctypes.c_int64]
         lib.oracle_reorder.argtypes = [vp, vp, vp, ctypes.c_size_t, ctypes.c_size_t]
+        lib.oracle_indexed.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_size_t]
         lib.oracle_reorder_nm.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int, i64p, ctypes.c_int, ip, i64p, i64p]
         lib.oracle_reorder_sample.argtypes = [vp, vp, vp, ctypes.c_size_t, ctypes.c_size_t, i64p, ctypes.c_int64]
         lib.oracle_interlace.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t,
@@ -88,7 +89,7 @@ class Oracle:
         lib.oracle_deinterlace.argtypes = [ctypes.POINTER(vp), vp, ctypes.c_int, ctypes.c_size_t,
                                            ctypes.c_size_t]
         for name in ("oracle_permute", "oracle_permute_sample", "oracle_reorder", "oracle_reorder_sample",
-                     "oracle_reorder_nm",
+                     "oracle_reorder_nm", "oracle_indexed",
                      "oracle_interlace", "oracle_deinterlace"):
             getattr(lib, name).restype = ctypes.c_int
         self.lib = lib
@@ -125,6 +126,25 @@ class Oracle:
         if rc != 0:
             raise OracleError("oracle_permute_sample rejected its arguments")
         return vals
+
+    # -- indexed (gather / scatter, 32- or 64-bit indices) ------------------------
+    def indexed(self, src: np.ndarray, idx: np.ndarray, elem_bytes: int, scatter: bool,
+                dst_init: np.ndarray | None = None) -> np.ndarray:
+        """Gather (dst[i] = src[idx[i]]) or scatter (dst[idx[i]] = src[i]) with
+        uint32 or uint64 indices; a scatter starts from dst_init (zeros if None)."""
+        sb = _bytes_view(src)
+        ix = np.ascontiguousarray(idx)
+        if ix.dtype not in (np.uint32, np.uint64):
+            raise OracleError("indices must be uint32 or uint64")
+        n = ix.size
+        if sb.size < n * elem_bytes:
+            raise OracleError("source buffer too small")
+        out = np.zeros(n * elem_bytes, np.uint8) if dst_init is None else _bytes_view(dst_init).copy()
+        rc = self.lib.oracle_indexed(_ptr(out), _ptr(sb), _ptr(ix), ix.dtype.itemsize, 1 if scatter else 0, n,
+                                     elem_bytes)
+        if rc != 0:
+            raise OracleError("oracle_indexed rejected its arguments")
+        return out
 
     # -- N-to-M reorder -----------------------------------------------------------
     def reorder_nm(self, src: np.ndarray, elem_bytes: int, dims: Sequence[int], order: Sequence[int],

@@ -222,6 +222,26 @@ int oracle_reorder_sample(void *vals, const void *src, const uint32_t *idx,
     return 0;
 }
 
+int oracle_indexed(void *dst, const void *src, const void *idx, int idx_bytes,
+                   int scatter, size_t n, size_t elem_bytes)
+{
+    if (elem_bytes == 0 || (idx_bytes != 4 && idx_bytes != 8)) return -1;
+    if (n == 0) return 0;
+    if (!dst || !src || !idx) return -1;
+    unsigned char *out = (unsigned char *)dst;
+    const unsigned char *in = (const unsigned char *)src;
+    for (size_t i = 0; i < n; ++i) {
+        const uint64_t j = idx_bytes == 4 ? (uint64_t)((const uint32_t *)idx)[i]
+                                          : ((const uint64_t *)idx)[i];
+        if (j >= (uint64_t)n) return -1;
+        if (scatter) /* dst[idx[i]] = src[i]; a repeated index keeps the last write */
+            memcpy(out + (size_t)j * elem_bytes, in + i * elem_bytes, elem_bytes);
+        else         /* dst[i] = src[idx[i]] */
+            memcpy(out + i * elem_bytes, in + (size_t)j * elem_bytes, elem_bytes);
+    }
+    return 0;
+}
+
 int oracle_interlace(void *dst, const void *const *srcs, int k, size_t n,
                      size_t elem_bytes)
 {

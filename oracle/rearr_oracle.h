@@ -49,6 +49,13 @@ int oracle_reorder_sample(void *vals, const void *src, const uint32_t *idx,
                           size_t n, size_t elem_bytes, const int64_t *pos,
                           int64_t count);
 
+/* Reorder by an index sequence with 4- or 8-byte indices, as a gather
+ * (scatter == 0: dst[i] = src[idx[i]]) or a scatter (scatter != 0:
+ * dst[idx[i]] = src[i], a repeated index keeping the last write); src, dst and
+ * idx hold n entries and every index must be < n. */
+int oracle_indexed(void *dst, const void *src, const void *idx, int idx_bytes,
+                   int scatter, size_t n, size_t elem_bytes);
+
 /* Interlace (Sec. III.C): dst[i*k + j] = srcs[j][i], i < n, j < k. */
 int oracle_interlace(void *dst, const void *const *srcs, int k, size_t n,
                      size_t elem_bytes);

@@ -412,7 +412,37 @@ def pin_reorder_nm(orc) -> List[str]:
     return fails
 
 
-ALL_PINS = [pin_worked_examples, pin_reorder_nm, pin_bruteforce_small, pin_numpy_transpose, pin_matrix_transpose,
+def pin_indexed(orc) -> List[str]:
+    """Scatter and 64-bit indices: a scatter by p equals a gather by p^-1;
+    numpy fancy assignment out[p] = src (unique indices); 64-bit indices give
+    the 32-bit results; the gather form equals oracle_reorder; a hand-worked
+    scatter."""
+    fails = []
+    for t, (n, e) in enumerate([(1, 4), (9, 1), (1000, 3), (4097, 8), (700, 16)]):
+        src = synth.random_elements(8000 + t, n, e)
+        p = synth.random_permutation(8100 + t, n)
+        inv = np.empty_like(p)
+        inv[p] = np.arange(n, dtype=np.uint32)
+        sc = orc.indexed(src, p, e, scatter=True)
+        if not np.array_equal(sc, orc.indexed(src, inv, e, scatter=False)):
+            fails.append(f"scatter != gather by inverse n={n}")
+        want = np.zeros(n, _void(e))
+        want[p.astype(np.int64)] = src.view(_void(e))
+        if not np.array_equal(sc.view(_void(e)), want):
+            fails.append(f"scatter vs numpy n={n}")
+        if not np.array_equal(orc.indexed(src, p.astype(np.uint64), e, scatter=True), sc):
+            fails.append(f"scatter64 != scatter32 n={n}")
+        g32 = orc.indexed(src, p, e, scatter=False)
+        if not np.array_equal(orc.indexed(src, p.astype(np.uint64), e, scatter=False), g32) or \
+                not np.array_equal(g32, orc.reorder(src, p, e)):
+            fails.append(f"gather64 / gather32 / reorder disagree n={n}")
+    got = orc.indexed(np.array([10, 20, 30], np.uint32), np.array([2, 0, 1], np.uint32), 4, scatter=True)
+    if got.view(np.uint32).tolist() != [20, 30, 10]:
+        fails.append("hand-worked scatter")
+    return fails
+
+
+ALL_PINS = [pin_worked_examples, pin_reorder_nm, pin_indexed, pin_bruteforce_small, pin_numpy_transpose, pin_matrix_transpose,
             pin_identity_is_memcpy, pin_inverse_roundtrip, pin_bijection,
             pin_paper_rank3_orders, pin_sample_matches_full, pin_reorder, pin_interlace,
             pin_rejects_invalid]

@@ -54,6 +54,10 @@ MUTANTS = [
      "for (int a = 0; a < rank_in; ++a) x[a] = kept[a] ? base[a] : 0;"),
     ("N-to-M odometer uses the input extents", "if (++j[i] < range[order[i]]) break;",
      "if (++j[i] < dims[order[i]]) break;"),
+    ("indexed scatter writes the gather way", "if (scatter) /* dst[idx[i]] = src[i]; a repeated index keeps the last write */",
+     "if (0)"),
+    ("64-bit indices read as 32-bit", "                                          : ((const uint64_t *)idx)[i];",
+     "                                          : (uint64_t)((const uint32_t *)idx)[i];"),
     ("permutation check dropped", "if (seen[perm[i]]) return -1;", ""),
     ("reorder range check dropped", "if ((size_t)idx[i] >= n) return -1;", ""),
     ("last byte of each element dropped",
