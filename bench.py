@@ -677,7 +677,7 @@ def parse_case(spec: str):
     if kind == "permute":
         return dict(kind=kind, elem_bytes=e, dims=[int(x) for x in parts[2].split(",")],
                     perm=[int(x) for x in parts[3].split(",")])
-    if kind == "reorder":
+    if kind in ("reorder", "scatter", "reorder64", "scatter64"):
         return dict(kind=kind, elem_bytes=e, n=int(parts[2]), idx=parts[3])
     if kind in ("interlace", "deinterlace"):
         return dict(kind=kind, elem_bytes=e, n=int(parts[2]), k=int(parts[3]))
@@ -708,16 +708,21 @@ def run_case(args):
         dst = torch.empty(total * e, dtype=torch.uint8, device=dev)
         call = lambda: rr.reorder_nm(dst, src, e, o["dims"], o["order"], o["base"], o["range"], stream)  # noqa: E731
         nbytes = 2 * total * e
-    elif o["kind"] in ("permute", "reorder"):
+    elif o["kind"] in ("permute", "reorder", "scatter", "reorder64", "scatter64"):
         n = int(np.prod(o["dims"])) if o["kind"] == "permute" else o["n"]
         src = torch.empty(n * e, dtype=torch.uint8, device=dev).random_()
         dst = torch.empty(n * e, dtype=torch.uint8, device=dev)
-        if o["kind"] == "reorder":
+        if o["kind"] != "permute":
             a = (synth.random_permutation(7, n) if o["idx"] == "random"
                  else synth.block_shuffled_permutation(8, n, 4096))
+            wide = o["kind"].endswith("64")
+            if wide:
+                a = a.astype(np.uint64)
             idx = torch.from_numpy(a.view(np.uint8)).to(dev)
-            call = lambda: rr.reorder(dst, src, idx, n, e, stream)  # noqa: E731
-            nbytes = 2 * n * e + 4 * n
+            fn = {"reorder": rr.reorder, "scatter": rr.scatter, "reorder64": rr.reorder64,
+                  "scatter64": rr.scatter64}[o["kind"]]
+            call = lambda: fn(dst, src, idx, n, e, stream)  # noqa: E731
+            nbytes = 2 * n * e + (8 if wide else 4) * n
         else:
             call = lambda: rr.permute(dst, src, e, o["dims"], o["perm"], stream)  # noqa: E731
             nbytes = 2 * n * e

@@ -112,6 +112,25 @@ rearr_status rearr_reorder(void *dst, const void *src, const uint32_t *idx, size
                            size_t elem_bytes, rearr_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Other index-sequence forms (the scatter direction and 64-bit indices of the
+ * reorder; Sec. III.A accesses "a specified set of indices"):
+ *   rearr_scatter   : dst[idx[i]] = src[i], uint32 indices.
+ *   rearr_reorder64 : dst[i] = src[idx[i]], uint64 indices (n may exceed 2^32).
+ *   rearr_scatter64 : dst[idx[i]] = src[i], uint64 indices.
+ *   src, dst and idx hold n entries; every index must be < n (an index >= n
+ *   is undefined behaviour).  For a scatter whose indices repeat, a
+ *   destination element receives one of the colliding source elements, which
+ *   one is unspecified; with a permutation the result is unique.  idx must be
+ *   aligned to its index size.
+ * ------------------------------------------------------------------------- */
+rearr_status rearr_scatter(void *dst, const void *src, const uint32_t *idx, size_t n,
+                           size_t elem_bytes, rearr_stream_t stream);
+rearr_status rearr_reorder64(void *dst, const void *src, const uint64_t *idx, size_t n,
+                             size_t elem_bytes, rearr_stream_t stream);
+rearr_status rearr_scatter64(void *dst, const void *src, const uint64_t *idx, size_t n,
+                             size_t elem_bytes, rearr_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * rearr_interlace -- join k arrays into one interlaced array
  * (arXiv:1011.3583 Sec. III.C, Table 3):
  *       dst[i*k + j] = srcs[j][i],  0 <= i < n, 0 <= j < k.
@@ -161,6 +180,8 @@ rearr_status rearr_plan_add_permute(rearr_plan *plan, void *dst, const void *src
                                     size_t elem_bytes, int rank, const int64_t *dims,
                                     const int *perm);
 rearr_status rearr_plan_add_reorder(rearr_plan *plan, void *dst, const void *src,
+                                    const uint32_t *idx, size_t n, size_t elem_bytes);
+rearr_status rearr_plan_add_scatter(rearr_plan *plan, void *dst, const void *src,
                                     const uint32_t *idx, size_t n, size_t elem_bytes);
 rearr_status rearr_plan_add_reorder_nm(rearr_plan *plan, void *dst, const void *src, size_t elem_bytes,
                                        int rank_in, const int64_t *dims, int rank_out, const int *order,

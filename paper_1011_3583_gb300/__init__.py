@@ -4,5 +4,6 @@ de-interlace), behind a C ABI (include/librearr.h) with this thin binding."""
 from .librearr import (  # noqa: F401
     EINVAL, Arena, OpSpec, Server, batch_noalloc, tuning_load,
     MAX_K, MAX_RANK, Plan, PermuteInfo, RearrError, deinterlace, describe_permute, interlace, launch_count,
-    lib_path, load, memcpy_d2d, permute, reorder, reorder_nm, selftest_host, status_str,
+    lib_path, load, memcpy_d2d, permute, reorder, reorder64, reorder_nm, scatter, scatter64, selftest_host,
+    status_str,
 )

@@ -82,6 +82,37 @@ rearr_status rearr_reorder(void *dst, const void *src, const uint32_t *idx, size
     return REARR_OK;
 }
 
+static rearr_status indexed_call(const char *who, void *dst, const void *src, const void *idx, size_t n,
+                                 size_t elem_bytes, int idx_bytes, bool scatter, rearr_stream_t stream)
+{
+    OpDesc op;
+    std::string err;
+    rearr_status st = plan_reorder(dst, src, static_cast<const uint32_t *>(idx), n, elem_bytes, op, err, idx_bytes,
+                                   scatter);
+    if (st != REARR_OK) return fail(st, std::string(who) + ": " + err);
+    cudaError_t e = launch_single(op, nullptr, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    return REARR_OK;
+}
+
+rearr_status rearr_scatter(void *dst, const void *src, const uint32_t *idx, size_t n, size_t elem_bytes,
+                           rearr_stream_t stream)
+{
+    return indexed_call("rearr_scatter", dst, src, idx, n, elem_bytes, 4, true, stream);
+}
+
+rearr_status rearr_reorder64(void *dst, const void *src, const uint64_t *idx, size_t n, size_t elem_bytes,
+                             rearr_stream_t stream)
+{
+    return indexed_call("rearr_reorder64", dst, src, idx, n, elem_bytes, 8, false, stream);
+}
+
+rearr_status rearr_scatter64(void *dst, const void *src, const uint64_t *idx, size_t n, size_t elem_bytes,
+                             rearr_stream_t stream)
+{
+    return indexed_call("rearr_scatter64", dst, src, idx, n, elem_bytes, 8, true, stream);
+}
+
 rearr_status rearr_interlace(void *dst, const void *const *srcs, int k, size_t n, size_t elem_bytes,
                              rearr_stream_t stream)
 {

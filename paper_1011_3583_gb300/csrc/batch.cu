@@ -237,6 +237,18 @@ rearr_status rearr_plan_add_permute(rearr_plan *plan, void *dst, const void *src
     return add_op(plan, pl.op);
 }
 
+rearr_status rearr_plan_add_scatter(rearr_plan *plan, void *dst, const void *src, const uint32_t *idx, size_t n,
+                                    size_t elem_bytes)
+{
+    if (!plan) return fail(REARR_EINVAL, "rearr_plan_add_scatter: plan is NULL");
+    if (plan->finalized) return fail(REARR_EBUSY, "rearr_plan_add_scatter: plan is finalized");
+    OpDesc op;
+    std::string err;
+    rearr_status st = plan_reorder(dst, src, idx, n, elem_bytes, op, err, 4, true);
+    if (st != REARR_OK) return fail(st, "rearr_plan_add_scatter: " + err);
+    return add_op(plan, op);
+}
+
 rearr_status rearr_plan_add_reorder_nm(rearr_plan *plan, void *dst, const void *src, size_t elem_bytes,
                                        int rank_in, const int64_t *dims, int rank_out, const int *order,
                                        const int64_t *base, const int64_t *range)

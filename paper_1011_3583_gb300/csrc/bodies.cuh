@@ -352,13 +352,57 @@ __device__ __forceinline__ void store4(char *p, const typename Word<W>::T (&v)[4
     }
 }
 
+// Four consecutive W-byte words from an address aligned to min(16, 4W).
+template <int W>
+__device__ __forceinline__ void load4(const char *p, typename Word<W>::T (&v)[4])
+{
+    if constexpr (W == 1) {
+        const uint32_t x = ldg_stream<4>(p);
+        v[0] = uint8_t(x); v[1] = uint8_t(x >> 8); v[2] = uint8_t(x >> 16); v[3] = uint8_t(x >> 24);
+    } else if constexpr (W == 2) {
+        const uint2 x = ldg_stream<8>(p);
+        v[0] = uint16_t(x.x); v[1] = uint16_t(x.x >> 16); v[2] = uint16_t(x.y); v[3] = uint16_t(x.y >> 16);
+    } else if constexpr (W == 4) {
+        const uint4 x = ldg_stream<16>(p);
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    } else if constexpr (W == 8) {
+        const uint4 a = ldg_stream<16>(p), b = ldg_stream<16>(p + 16);
+        v[0] = make_uint2(a.x, a.y); v[1] = make_uint2(a.z, a.w); v[2] = make_uint2(b.x, b.y); v[3] = make_uint2(b.z, b.w);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = ldg_stream<16>(p + 16 * k);
+    }
+}
+
 template <int W>
 __device__ __forceinline__ void gather_body(const GatherDesc &d, uint64_t unit)
 {
     using T = typename Word<W>::T;
     const uint64_t e0 = unit * d.unit_elems;
     const uint64_t e1 = min(d.n, e0 + d.unit_elems);
-    if (d.vec) {
+    if (d.vec && d.scatter) {
+        // Scatter, groups of 4 consecutive elements per thread: one 16-byte
+        // index load, one 4*W-byte source load, four independent stores.
+        constexpr int G = 2;
+        for (uint64_t g0 = e0; g0 < e1; g0 += uint64_t(kThreads) * 4 * G) {
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                const uint64_t i = g0 + (uint64_t(k) * kThreads + tid_x()) * 4;
+                if (i + 3 < e1) {
+                    const uint4 ix = ldg_stream<16>(d.idx + i);
+                    T v[4];
+                    load4<W>(d.src + i * W, v);
+                    stg<W>(d.dst + uint64_t(ix.x) * W, v[0]);
+                    stg<W>(d.dst + uint64_t(ix.y) * W, v[1]);
+                    stg<W>(d.dst + uint64_t(ix.z) * W, v[2]);
+                    stg<W>(d.dst + uint64_t(ix.w) * W, v[3]);
+                } else {
+                    for (uint64_t q = i; q < e1 && q < i + 4; ++q)
+                        stg<W>(d.dst + uint64_t(d.idx[q]) * W, ldg_any<W>(d.src + q * W));
+                }
+            }
+        }
+    } else if (d.vec) {
         // Groups of 4 consecutive elements per thread: one 16-byte index load,
         // four independent source loads, one store of 4*W bytes.
         constexpr int G = 2;  // groups per thread in flight
@@ -387,22 +431,25 @@ __device__ __forceinline__ void gather_body(const GatherDesc &d, uint64_t unit)
             }
         }
     } else {
-        // Any element size: c words per element, U elements per thread in flight.
+        // Any element size, 32- or 64-bit indices, gather or scatter: c words
+        // per element, U elements per thread in flight.
         constexpr int U = 4;
         const uint32_t c = d.c;
+        const uint64_t *idx64 = reinterpret_cast<const uint64_t *>(d.idx);
         for (uint64_t b0 = e0; b0 < e1; b0 += uint64_t(kThreads) * U) {
-            uint32_t src_i[U];
+            uint64_t j[U];
 #pragma unroll
             for (int k = 0; k < U; ++k) {
                 const uint64_t i = b0 + uint64_t(k) * kThreads + tid_x();
-                src_i[k] = i < e1 ? ldg_stream<4>(d.idx + i) : 0u;
+                j[k] = i < e1 ? (d.idx64 ? __ldg(idx64 + i) : uint64_t(ldg_stream<4>(d.idx + i))) : 0u;
             }
 #pragma unroll
             for (int k = 0; k < U; ++k) {
                 const uint64_t i = b0 + uint64_t(k) * kThreads + tid_x();
                 if (i < e1) {
-                    const char *s = d.src + uint64_t(src_i[k]) * c * W;
-                    char *o = d.dst + i * c * W;
+                    const uint64_t from = d.scatter ? i : j[k], to = d.scatter ? j[k] : i;
+                    const char *s = d.src + from * c * W;
+                    char *o = d.dst + to * c * W;
                     for (uint32_t w = 0; w < c; ++w) stg<W>(o + w * W, ldg_any<W>(s + w * W));
                 }
             }

@@ -419,7 +419,7 @@ rearr_status plan_reorder_nm(void *dst, const void *src, size_t elem_bytes, int 
 }
 
 rearr_status plan_reorder(void *dst, const void *src, const uint32_t *idx, size_t n, size_t elem_bytes,
-                          OpDesc &op, std::string &err)
+                          OpDesc &op, std::string &err, int idx_bytes, bool scatter)
 {
     std::memset(&op, 0, sizeof(op));
     if (elem_bytes == 0) { err = "elem_bytes must be >= 1"; return REARR_EINVAL; }
@@ -428,15 +428,15 @@ rearr_status plan_reorder(void *dst, const void *src, const uint32_t *idx, size_
         err = "byte count overflows";
         return REARR_EINVAL;
     }
-    if (n > 0xFFFFFFFFull + 1) { err = "n exceeds the uint32 index range"; return REARR_EINVAL; }
+    if (idx_bytes == 4 && n > 0xFFFFFFFFull + 1) { err = "n exceeds the uint32 index range"; return REARR_EINVAL; }
     if (n == 0) { op.units = 0; return REARR_OK; }
     if (!dst || !src || !idx) { err = "dst, src and idx must not be NULL"; return REARR_EINVAL; }
     const uintptr_t da = uintptr_t(dst), sa = uintptr_t(src), ia = uintptr_t(idx);
-    if (ranges_overlap(da, bytes, sa, bytes) || ranges_overlap(da, bytes, ia, uint64_t(n) * 4)) {
+    if (ranges_overlap(da, bytes, sa, bytes) || ranges_overlap(da, bytes, ia, uint64_t(n) * idx_bytes)) {
         err = "dst overlaps src or idx";
         return REARR_EINVAL;
     }
-    if (ia % 4 != 0) { err = "idx must be 4-byte aligned"; return REARR_EINVAL; }
+    if (ia % uintptr_t(idx_bytes) != 0) { err = "idx must be aligned to its index size"; return REARR_EINVAL; }
     const int W = pow2_align(da, sa, elem_bytes);
     op.cls = OC_GATHER;
     op.word = uint32_t(W);
@@ -446,13 +446,18 @@ rearr_status plan_reorder(void *dst, const void *src, const uint32_t *idx, size_
     g.idx = idx;
     g.n = n;
     g.c = uint32_t(elem_bytes / W);
-    g.vec = (g.c == 1 && ia % 16 == 0 && da % uint64_t(std::min(16, 4 * W)) == 0) ? 1u : 0u;
+    g.idx64 = idx_bytes == 8 ? 1u : 0u;
+    g.scatter = scatter ? 1u : 0u;
+    // the contiguous side (dst of a gather, src of a scatter) in groups of 4
+    const uintptr_t contiguous = scatter ? sa : da;
+    g.vec = (g.c == 1 && idx_bytes == 4 && ia % 16 == 0 && contiguous % uint64_t(std::min(16, 4 * W)) == 0) ? 1u : 0u;
     g.unit_elems = g.vec ? uint32_t(kThreads) * 32 : uint32_t(kThreads) * 16;
     op.units = (uint64_t(n) + g.unit_elems - 1) / g.unit_elems;
     // Sources much larger than the L2 go through the bucketed passes (which
     // fall back to this direct gather on the device if the indices turn out
     // to be local).
-    g.l2 = (g.vec && (W == 4 || W == 8 || W == 16) && bytes >= kReorderL2MinBytes && n <= 0xFFFFFFFFull) ? 1u : 0u;
+    g.l2 = (g.vec && !scatter && (W == 4 || W == 8 || W == 16) && bytes >= kReorderL2MinBytes &&
+            n <= 0xFFFFFFFFull) ? 1u : 0u;
     return REARR_OK;
 }
 

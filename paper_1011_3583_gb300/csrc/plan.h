@@ -29,8 +29,11 @@ rearr_status plan_permute(void *dst, const void *src, size_t elem_bytes, int ran
 rearr_status plan_reorder_nm(void *dst, const void *src, size_t elem_bytes, int rank_in, const int64_t *dims,
                              int rank_out, const int *order, const int64_t *base, const int64_t *range,
                              PermPlan &pl, std::string &err);
+// Gather dst[i] = src[idx[i]] (or, with scatter, dst[idx[i]] = src[i]) with
+// idx_bytes-byte (4 or 8) indices.
 rearr_status plan_reorder(void *dst, const void *src, const uint32_t *idx, size_t n,
-                          size_t elem_bytes, OpDesc &op, std::string &err);
+                          size_t elem_bytes, OpDesc &op, std::string &err, int idx_bytes = 4,
+                          bool scatter = false);
 rearr_status plan_interlace(bool inter, char *interlaced, char *const *planes, int k, size_t n,
                             size_t elem_bytes, InterlacePlan &pl, std::string &err);
 

@@ -136,6 +136,8 @@ struct GatherDesc {
     uint32_t unit_elems;   // elements per work unit
     uint32_t vec;          // 1: aligned 4-element groups with vector stores
     uint32_t l2;           // 1: single calls use the L2-resident bucketed passes
+    uint32_t idx64;        // 1: idx points at uint64 indices
+    uint32_t scatter;      // 1: dst[idx[i]] = src[i] instead of dst[i] = src[idx[i]]
 };
 
 struct InterlaceDesc {

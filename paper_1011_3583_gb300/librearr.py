@@ -69,6 +69,10 @@ def load() -> ctypes.CDLL:
         "rearr_last_error": (ctypes.c_char_p, []),
         "rearr_permute": (st, [vp, vp, sz, ctypes.c_int, i64p, ip, vp]),
         "rearr_reorder": (st, [vp, vp, vp, sz, sz, vp]),
+        "rearr_scatter": (st, [vp, vp, vp, sz, sz, vp]),
+        "rearr_reorder64": (st, [vp, vp, vp, sz, sz, vp]),
+        "rearr_scatter64": (st, [vp, vp, vp, sz, sz, vp]),
+        "rearr_plan_add_scatter": (st, [vp, vp, vp, vp, sz, sz]),
         "rearr_reorder_nm": (st, [vp, vp, sz, ctypes.c_int, i64p, ctypes.c_int, ip, i64p, i64p, vp]),
         "rearr_plan_add_reorder_nm": (st, [vp, vp, vp, sz, ctypes.c_int, i64p, ctypes.c_int, ip, i64p, i64p]),
         "rearr_interlace": (st, [vp, ctypes.POINTER(vp), ctypes.c_int, sz, sz, vp]),
@@ -176,6 +180,21 @@ def reorder(dst, src, idx, n: int, elem_bytes: int, stream=None) -> None:
     _check(load().rearr_reorder(_ptr(dst), _ptr(src), _ptr(idx), int(n), int(elem_bytes), _stream(stream)))
 
 
+def scatter(dst, src, idx, n: int, elem_bytes: int, stream=None) -> None:
+    """rearr_scatter: dst[idx[i]] = src[i] (uint32 indices)."""
+    _check(load().rearr_scatter(_ptr(dst), _ptr(src), _ptr(idx), int(n), int(elem_bytes), _stream(stream)))
+
+
+def reorder64(dst, src, idx, n: int, elem_bytes: int, stream=None) -> None:
+    """rearr_reorder64: dst[i] = src[idx[i]] (uint64 indices)."""
+    _check(load().rearr_reorder64(_ptr(dst), _ptr(src), _ptr(idx), int(n), int(elem_bytes), _stream(stream)))
+
+
+def scatter64(dst, src, idx, n: int, elem_bytes: int, stream=None) -> None:
+    """rearr_scatter64: dst[idx[i]] = src[i] (uint64 indices)."""
+    _check(load().rearr_scatter64(_ptr(dst), _ptr(src), _ptr(idx), int(n), int(elem_bytes), _stream(stream)))
+
+
 def interlace(dst, srcs: Sequence, n: int, elem_bytes: int, stream=None) -> None:
     """rearr_interlace: dst[i*k + j] = srcs[j][i]."""
     arr = _ptr_array(srcs)
@@ -230,6 +249,9 @@ class Plan:
 
     def add_reorder(self, dst, src, idx, n: int, elem_bytes: int) -> None:
         _check(load().rearr_plan_add_reorder(self._h, _ptr(dst), _ptr(src), _ptr(idx), int(n), int(elem_bytes)))
+
+    def add_scatter(self, dst, src, idx, n: int, elem_bytes: int) -> None:
+        _check(load().rearr_plan_add_scatter(self._h, _ptr(dst), _ptr(src), _ptr(idx), int(n), int(elem_bytes)))
 
     def add_reorder_nm(self, dst, src, elem_bytes: int, dims, order, base, rng) -> None:
         rank_in, d, rank_out, o, b, r = _nm_args(dims, order, base, rng)

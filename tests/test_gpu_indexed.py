@@ -1,0 +1,96 @@
+"""Scatter reorder and 64-bit index sequences on the GPU against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import DevBuf, sync, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lr():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1011_3583_gb300 import build, librearr
+    build.build()
+    librearr.load()
+    return librearr
+
+
+@pytest.fixture(scope="module")
+def orc():
+    return oracle.get()
+
+
+def run(lr, fn, src, idx, e, n, fill, offs=(0, 0, 0)):
+    s, ix = to_dev(src, offs[0]), to_dev(idx, offs[2])
+    d = DevBuf(n * e, offs[1], fill=fill)
+    fn(d.ptr, s.ptr, ix.ptr, n, e)
+    sync()
+    return d.download()
+
+
+@pytest.mark.parametrize("e", [1, 2, 3, 4, 8, 12, 16])
+def test_scatter_permutation(lr, orc, e):
+    for t, n in enumerate([1, 5, 1000, 65539, (1 << 18) + 7]):
+        src = synth.random_elements(40 + t, n, e)
+        p = synth.random_permutation(50 + t, n)
+        got = run(lr, lr.scatter, src, p, e, n, fill=0)
+        assert np.array_equal(got, orc.indexed(src, p, e, scatter=True)), (n, e)
+        p64 = p.astype(np.uint64)
+        got = run(lr, lr.scatter64, src, p64, e, n, fill=0)
+        assert np.array_equal(got, orc.indexed(src, p64, e, scatter=True)), (n, e, "64")
+        got = run(lr, lr.reorder64, src, p64, e, n, fill=0)
+        assert np.array_equal(got, orc.indexed(src, p64, e, scatter=False)), (n, e, "gather64")
+
+
+def test_scatter_unaligned(lr, orc):
+    n = 5003
+    for e, so, do, io in [(4, 4, 0, 4), (4, 0, 8, 0), (8, 8, 4, 8), (2, 2, 6, 12), (1, 1, 3, 4)]:
+        src = synth.random_elements(e + so, n, e)
+        p = synth.random_permutation(e + io, n)
+        got = run(lr, lr.scatter, src, p, e, n, fill=0, offs=(so, do, io))
+        assert np.array_equal(got, orc.indexed(src, p, e, scatter=True)), (e, so, do, io)
+
+
+def test_scatter_repeats_are_valid(lr):
+    """With repeated indices the written value is one of the colliding
+    sources (which one is unspecified) and untouched positions keep theirs."""
+    n, e = 70001, 4
+    src = np.arange(n, dtype=np.uint32).view(np.uint8)     # tag = source position
+    idx = synth.random_indices(9, n, n // 3)               # many collisions, a third targeted
+    got = run(lr, lr.scatter, src, idx, e, n, fill=0xFF).view(np.uint32)
+    targeted = np.zeros(n, bool)
+    targeted[idx] = True
+    assert np.all(got[~targeted] == 0xFFFFFFFF)
+    # every targeted destination holds the tag of some i with idx[i] == destination
+    ok = idx[got[targeted]] == np.flatnonzero(targeted)
+    assert np.all(ok)
+
+
+def test_gather64_with_repeats(lr, orc):
+    for e in (1, 4, 8, 12):
+        n = 33333
+        src = synth.random_elements(60 + e, n, e)
+        idx = synth.random_indices(61 + e, n, n).astype(np.uint64)
+        got = run(lr, lr.reorder64, src, idx, e, n, fill=0)
+        assert np.array_equal(got, orc.indexed(src, idx, e, scatter=False)), e
+
+
+def test_scatter_in_a_batch(lr, orc):
+    plan = lr.Plan()
+    cases = []
+    for t, (n, e) in enumerate([(1000, 4), (4099, 1), (77777, 8), (5, 16)]):
+        src = synth.random_elements(70 + t, n, e)
+        p = synth.random_permutation(80 + t, n)
+        s, ix, d = to_dev(src), to_dev(p), DevBuf(n * e, fill=0)
+        plan.add_scatter(d.ptr, s.ptr, ix.ptr, n, e)
+        cases.append((src, p, e, s, ix, d))
+    plan.finalize()
+    plan.run()
+    sync()
+    for src, p, e, s, ix, d in cases:
+        assert np.array_equal(d.download(), orc.indexed(src, p, e, scatter=True))
+    plan.close()
