@@ -22,6 +22,10 @@
 //   K7 direct    : the plain gather (when K1 found locality).
 // Traffic: 2 (idx) + 2 (s, i written) + 2 (s, i read) + 1 (src) + 2 (v) + 1
 // (dst) = 10 n-word passes of streaming access instead of n random accesses.
+// A scatter (dst[idx[i]] = src[i]) uses one destination dimension only
+// (D = 1, buckets by the chunk of idx[i]): the partition's source positions
+// are read back in order to gather v (reads local to each tile), and a linear
+// pass writes dst[s[k]] = v[k] with the destination chunk L2-resident.
 // Scratch ((8 + E) n bytes) comes from a stream-ordered pool owned by the
 // library; the kernels are ordered on the caller's stream and none waits on
 // another.
@@ -66,6 +70,13 @@ struct L2Reorder {
 __device__ __forceinline__ uint32_t chunk_of(const L2Reorder &p, uint32_t v)
 {
     return min(v >> p.cs_shift, p.C - 1);
+}
+
+// Second bucket coordinate of element i: its destination chunk for a gather;
+// a scatter has one (D = 1).
+__device__ __forceinline__ uint32_t dest_chunk(const L2Reorder &p, uint32_t i)
+{
+    return p.D == 1 ? 0u : i >> p.cs_shift;
 }
 
 __device__ __forceinline__ bool bucketed(const L2Reorder &p)
@@ -121,7 +132,7 @@ __global__ void __launch_bounds__(kThreads) k_l2_hist(const L2Reorder p, uint32_
     const uint32_t t0 = blockIdx.x * tiles_per_cta, t1 = min(tiles, t0 + tiles_per_cta);
     for (uint32_t c = threadIdx.x; c < kWarps * kMaxChunks; c += kThreads) (&sh[0][0])[c] = 0;
     __syncthreads();
-    uint32_t cur_d = t0 < t1 ? (t0 * kTile) >> p.cs_shift : 0;
+    uint32_t cur_d = t0 < t1 ? dest_chunk(p, t0 * kTile) : 0;
     uint32_t v[kPer];
     if (t0 < t1) load_tile(p, t0 * kTile, min(uint32_t(kTile), p.n - t0 * kTile), v);
     for (uint32_t t = t0; t < t1; ++t) {
@@ -133,7 +144,7 @@ __global__ void __launch_bounds__(kThreads) k_l2_hist(const L2Reorder p, uint32_
             const uint32_t k = w * (kTile / kWarps) + j * 32 + (threadIdx.x & 31);
             if (k < m) atomicAdd(&sh[w][chunk_of(p, v[j])], 1u);
         }
-        const uint32_t next_d = t + 1 < t1 ? ((t + 1) * kTile) >> p.cs_shift : 0xFFFFFFFFu;
+        const uint32_t next_d = t + 1 < t1 ? dest_chunk(p, (t + 1) * kTile) : 0xFFFFFFFFu;
         if (next_d != cur_d) {
             __syncthreads();
             for (uint32_t c = threadIdx.x; c < p.C; c += kThreads) {
@@ -248,7 +259,7 @@ __global__ void __launch_bounds__(kThreads) k_l2_partition(const L2Reorder p, ui
     for (uint32_t t = t0; t < t1; ++t) {
         const uint32_t i0 = t * kTile;
         const uint32_t m = min(uint32_t(kTile), p.n - i0);
-        const uint32_t d = i0 >> p.cs_shift;
+        const uint32_t d = dest_chunk(p, i0);
         uint32_t nxt[kPer];
         if (t + 1 < t1) load_tile(p, (t + 1) * kTile, min(uint32_t(kTile), p.n - (t + 1) * kTile), nxt);
         uint32_t rk[kPer];
@@ -477,6 +488,39 @@ __global__ void __launch_bounds__(kThreads) k_l2_scatter(const L2Reorder p)
     }
 }
 
+// Scatter form, last pass: dst[s[k]] = v[k] in k order (c-major: one
+// destination chunk at a time, L2-resident while its sectors are completed).
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_l2_scatter_linear(const L2Reorder p)
+{
+    if (!bucketed(p)) return;
+    __shared__ uint32_t slot;
+    using T = typename Word<W>::T;
+    const uint64_t first = policy_evict_first(), last = policy_evict_last();
+    const uint32_t units = (p.n + kGatherUnit - 1) / kGatherUnit;
+    for (;;) {
+        const uint32_t u = next_unit(p.ctr_scatter, &slot);
+        if (u >= units) break;
+        const uint32_t k0 = u * kGatherUnit;
+        constexpr int PER = kGatherUnit / kThreads;
+        uint32_t di[PER];
+        T val[PER];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const uint32_t k = k0 + j * kThreads + threadIdx.x;
+            if (k < p.n) {
+                di[j] = ld_hint<4>(p.sarr + k, first);
+                val[j] = ld_hint<W>(p.varr + uint64_t(k) * W, first);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const uint32_t k = k0 + j * kThreads + threadIdx.x;
+            if (k < p.n) st_hint<W>(p.dst + uint64_t(di[j]) * W, val[j], last);
+        }
+    }
+}
+
 // K7: the direct gather, when K1 found the indices local.
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_l2_direct(const L2Reorder p, const GatherDesc g, uint64_t units)
@@ -525,6 +569,7 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
     while (((uint64_t(g.n) + (uint64_t(1) << shift) - 1) >> shift) > kMaxChunks) ++shift;
     p.cs_shift = shift;
     p.C = p.D = uint32_t((uint64_t(g.n) + (uint64_t(1) << shift) - 1) >> shift);
+    if (g.scatter) p.D = 1;  // buckets by destination chunk only
     const uint32_t nb = p.C * p.D;
     auto al = [](size_t x) { return (x + 255) / 256 * 256; };
     const size_t off_hist = 256, off_base = off_hist + al(nb * 4), off_cur = off_base + al(nb * 4),
@@ -571,8 +616,15 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
         k_l2_partition<<<pgrid, kThreads, sizeof(PartitionSmem), s>>>(p, tpc);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) { k_l2_gather<W><<<pers, kThreads, 0, s>>>(p); e = cudaGetLastError(); }
-    if (e == cudaSuccess) { k_l2_scatter<W><<<pers, kThreads, 0, s>>>(p); e = cudaGetLastError(); }
+    if (!g.scatter) {
+        if (e == cudaSuccess) { k_l2_gather<W><<<pers, kThreads, 0, s>>>(p); e = cudaGetLastError(); }
+        if (e == cudaSuccess) { k_l2_scatter<W><<<pers, kThreads, 0, s>>>(p); e = cudaGetLastError(); }
+    } else {
+        L2Reorder q = p;  // v[k] = src[i[k]]: gather by the source positions
+        q.sarr = p.iarr;
+        if (e == cudaSuccess) { k_l2_gather<W><<<pers, kThreads, 0, s>>>(q); e = cudaGetLastError(); }
+        if (e == cudaSuccess) { k_l2_scatter_linear<W><<<pers, kThreads, 0, s>>>(p); e = cudaGetLastError(); }
+    }
     if (e == cudaSuccess) {
         k_l2_direct<W><<<unsigned(std::min<uint64_t>(dunits, 0x7FFFFFFFull)), kThreads, 0, s>>>(p, g, dunits);
         e = cudaGetLastError();

@@ -456,8 +456,7 @@ rearr_status plan_reorder(void *dst, const void *src, const uint32_t *idx, size_
     // Sources much larger than the L2 go through the bucketed passes (which
     // fall back to this direct gather on the device if the indices turn out
     // to be local).
-    g.l2 = (g.vec && !scatter && (W == 4 || W == 8 || W == 16) && bytes >= kReorderL2MinBytes &&
-            n <= 0xFFFFFFFFull) ? 1u : 0u;
+    g.l2 = (g.vec && (W == 4 || W == 8 || W == 16) && bytes >= kReorderL2MinBytes && n <= 0xFFFFFFFFull) ? 1u : 0u;
     return REARR_OK;
 }
 

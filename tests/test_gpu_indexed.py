@@ -94,3 +94,31 @@ def test_scatter_in_a_batch(lr, orc):
     for src, p, e, s, ix, d in cases:
         assert np.array_equal(d.download(), orc.indexed(src, p, e, scatter=True))
     plan.close()
+
+
+@pytest.mark.parametrize("e,kind", [(4, "perm"), (4, "block"), (4, "reverse"), (8, "perm"), (16, "perm")])
+def test_scatter_large_sources(lr, orc, e, kind):
+    """Scatters of 128 MiB or more (L2-resident passes, or the direct scatter
+    when the indices are local)."""
+    n = (128 << 20) // e + 4099
+    if kind == "perm":
+        idx = synth.random_permutation(17 + e, n)
+    elif kind == "reverse":
+        idx = np.arange(n - 1, -1, -1, dtype=np.uint32)
+    else:
+        m = n - n % 4096
+        idx = np.concatenate([synth.block_shuffled_permutation(18, m, 4096), np.arange(m, n, dtype=np.uint32)])
+    src = synth.random_elements(19 + e, n, e)
+    got = run(lr, lr.scatter, src, idx, e, n, fill=0)
+    assert np.array_equal(got, orc.indexed(src, idx, e, scatter=True)), (e, kind)
+
+
+def test_scatter_large_repeats_are_valid(lr):
+    n, e = (128 << 20) // 4 + 17, 4
+    src = np.arange(n, dtype=np.uint32).view(np.uint8)
+    idx = synth.random_indices(23, n, n // 2)
+    got = run(lr, lr.scatter, src, idx, e, n, fill=0xFF).view(np.uint32)
+    targeted = np.zeros(n, bool)
+    targeted[idx] = True
+    assert np.all(got[~targeted] == 0xFFFFFFFF)
+    assert np.all(idx[got[targeted]] == np.flatnonzero(targeted))
