@@ -81,6 +81,8 @@ class Oracle:
         lib.oracle_permute_sample.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int, i64p, ip,
                                               i64p, ctypes.c_int64]
         lib.oracle_reorder.argtypes = [vp, vp, vp, ctypes.c_size_t, ctypes.c_size_t]
+        lib.oracle_stencil2d.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ip, ip,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int]
         lib.oracle_indexed.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_size_t]
         lib.oracle_reorder_nm.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int, i64p, ctypes.c_int, ip, i64p, i64p]
         lib.oracle_reorder_sample.argtypes = [vp, vp, vp, ctypes.c_size_t, ctypes.c_size_t, i64p, ctypes.c_int64]
@@ -89,7 +91,7 @@ class Oracle:
         lib.oracle_deinterlace.argtypes = [ctypes.POINTER(vp), vp, ctypes.c_int, ctypes.c_size_t,
                                            ctypes.c_size_t]
         for name in ("oracle_permute", "oracle_permute_sample", "oracle_reorder", "oracle_reorder_sample",
-                     "oracle_reorder_nm", "oracle_indexed",
+                     "oracle_reorder_nm", "oracle_indexed", "oracle_stencil2d",
                      "oracle_interlace", "oracle_deinterlace"):
             getattr(lib, name).restype = ctypes.c_int
         self.lib = lib
@@ -126,6 +128,21 @@ class Oracle:
         if rc != 0:
             raise OracleError("oracle_permute_sample rejected its arguments")
         return vals
+
+    # -- 2-D stencil ----------------------------------------------------------------
+    def stencil2d(self, src: np.ndarray, taps, boundary: int) -> np.ndarray:
+        """taps: list of (dy, dx, w).  src: 2-D float32 array.  Returns float64."""
+        a = np.ascontiguousarray(src, dtype=np.float32)
+        ny, nx = a.shape
+        k = len(taps)
+        dy = (ctypes.c_int * max(k, 1))(*[int(t[0]) for t in taps])
+        dx = (ctypes.c_int * max(k, 1))(*[int(t[1]) for t in taps])
+        w = (ctypes.c_double * max(k, 1))(*[float(t[2]) for t in taps])
+        out = np.empty((ny, nx), dtype=np.float64)
+        rc = self.lib.oracle_stencil2d(_ptr(out), _ptr(a), ny, nx, k, dy, dx, w, int(boundary))
+        if rc != 0:
+            raise OracleError("oracle_stencil2d rejected its arguments")
+        return out
 
     # -- indexed (gather / scatter, 32- or 64-bit indices) ------------------------
     def indexed(self, src: np.ndarray, idx: np.ndarray, elem_bytes: int, scatter: bool,

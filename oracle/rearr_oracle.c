@@ -273,3 +273,38 @@ int oracle_deinterlace(void *const *dsts, const void *src, int k, size_t n,
                    in + (i * (size_t)k + (size_t)j) * elem_bytes, elem_bytes);
     return 0;
 }
+
+/* 2-D stencil (Sec. III.D): out[y][x] = sum_k w[k] * in[y + dy[k]][x + dx[k]],
+ * accumulated in double in tap order.  Points outside the grid read 0
+ * (boundary 0) or the nearest grid point (boundary 1).  The result is
+ * returned in double, one value per grid point. */
+int oracle_stencil2d(double *dst, const float *src, int64_t ny, int64_t nx,
+                     int ntaps, const int *dy, const int *dx, const double *w,
+                     int boundary)
+{
+    if (ny < 0 || nx < 0 || ntaps < 1 || !dy || !dx || !w) return -1;
+    if (boundary != 0 && boundary != 1) return -1;
+    if (ny == 0 || nx == 0) return 0;
+    if (!dst || !src) return -1;
+    for (int64_t y = 0; y < ny; ++y) {
+        for (int64_t x = 0; x < nx; ++x) {
+            double acc = 0.0;
+            for (int k = 0; k < ntaps; ++k) {
+                int64_t yy = y + dy[k], xx = x + dx[k];
+                double v;
+                if (yy >= 0 && yy < ny && xx >= 0 && xx < nx) {
+                    v = (double)src[yy * nx + xx];
+                } else if (boundary == 0) {
+                    v = 0.0;
+                } else {
+                    yy = yy < 0 ? 0 : (yy >= ny ? ny - 1 : yy);
+                    xx = xx < 0 ? 0 : (xx >= nx ? nx - 1 : xx);
+                    v = (double)src[yy * nx + xx];
+                }
+                acc += w[k] * v;
+            }
+            dst[y * nx + x] = acc;
+        }
+    }
+    return 0;
+}

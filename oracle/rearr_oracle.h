@@ -64,6 +64,13 @@ int oracle_interlace(void *dst, const void *const *srcs, int k, size_t n,
 int oracle_deinterlace(void *const *dsts, const void *src, int k, size_t n,
                        size_t elem_bytes);
 
+/* 2-D stencil (Sec. III.D): out[y][x] = sum_k w[k] * in[y + dy[k]][x + dx[k]]
+ * in double, taps in order; boundary 0 reads zeros outside the grid, 1 the
+ * nearest grid point. */
+int oracle_stencil2d(double *dst, const float *src, int64_t ny, int64_t nx,
+                     int ntaps, const int *dy, const int *dx, const double *w,
+                     int boundary);
+
 #ifdef __cplusplus
 }
 #endif

@@ -442,7 +442,65 @@ def pin_indexed(orc) -> List[str]:
     return fails
 
 
-ALL_PINS = [pin_worked_examples, pin_reorder_nm, pin_indexed, pin_bruteforce_small, pin_numpy_transpose, pin_matrix_transpose,
+def pin_stencil2d(orc) -> List[str]:
+    """2-D stencil (Sec. III.D) against scipy.ndimage.correlate (a library
+    routine, both boundary modes), exactness of the finite-difference
+    Laplacians on low-degree polynomials, single-tap shifts and linearity."""
+    from scipy import ndimage
+    from synth.stencils import fd_laplacian
+    fails = []
+    g = synth.rng(31)
+    for t in range(12):
+        ny, nx = int(g.integers(1, 40)), int(g.integers(1, 50))
+        R = int(g.integers(0, 5))
+        k = int(g.integers(1, 12))
+        taps = [(int(g.integers(-R, R + 1)), int(g.integers(-R, R + 1)), float(g.normal())) for _ in range(k)]
+        src = g.normal(size=(ny, nx)).astype(np.float32)
+        ker = np.zeros((2 * R + 1, 2 * R + 1))
+        for dy, dx, w in taps:
+            ker[dy + R, dx + R] += w
+        for boundary, mode in ((0, "constant"), (1, "nearest")):
+            got = orc.stencil2d(src, taps, boundary)
+            want = ndimage.correlate(src.astype(np.float64), ker, mode=mode, cval=0.0)
+            if not np.allclose(got, want, rtol=1e-12, atol=1e-12):
+                fails.append(f"stencil vs scipy {ny}x{nx} R={R} boundary={boundary}")
+    yy, xx = np.mgrid[0:24, 0:24].astype(np.float64)
+    for order in (1, 2, 3, 4):
+        taps = fd_laplacian(order)
+        # Laplacian of x^4 + y^2 is 12 x^2 + 2: exact for accuracy >= 4; order
+        # 1 (accuracy 2) is exact on degree 3: use x^3 + y^2 (6 x + 2) there.
+        f = (xx ** 3 + yy ** 2) if order == 1 else (xx ** 4 + yy ** 2)
+        lap = (6 * xx + 2) if order == 1 else (12 * xx ** 2 + 2)
+        got = orc.stencil2d(f.astype(np.float32), taps, 0)
+        r = order
+        inner = (slice(r, 24 - r), slice(r, 24 - r))
+        if not np.allclose(got[inner], lap[inner], rtol=0, atol=1e-7):
+            fails.append(f"FD Laplacian order {order} not exact on its polynomial")
+    src = g.normal(size=(17, 23)).astype(np.float32)
+    for dy, dx in ((0, 0), (2, -3), (-1, 4)):
+        for boundary in (0, 1):
+            got = orc.stencil2d(src, [(dy, dx, 1.0)], boundary)
+            want = np.zeros((17, 23))
+            for y in range(17):
+                for x in range(23):
+                    yy2, xx2 = y + dy, x + dx
+                    if 0 <= yy2 < 17 and 0 <= xx2 < 23:
+                        want[y, x] = src[yy2, xx2]
+                    elif boundary == 1:
+                        want[y, x] = src[min(max(yy2, 0), 16), min(max(xx2, 0), 22)]
+            if not np.array_equal(got, want):
+                fails.append(f"shift ({dy},{dx}) boundary {boundary}")
+    a = g.normal(size=(15, 19)).astype(np.float32)
+    b = g.normal(size=(15, 19)).astype(np.float32)
+    taps = fd_laplacian(2)
+    lhs = orc.stencil2d((2 * a + b).astype(np.float32), taps, 1)
+    rhs = 2 * orc.stencil2d(a, taps, 1) + orc.stencil2d(b, taps, 1)
+    if not np.allclose(lhs, rhs, rtol=1e-5, atol=1e-5):
+        fails.append("stencil linearity")
+    return fails
+
+
+ALL_PINS = [pin_worked_examples, pin_reorder_nm, pin_indexed, pin_stencil2d, pin_bruteforce_small, pin_numpy_transpose, pin_matrix_transpose,
             pin_identity_is_memcpy, pin_inverse_roundtrip, pin_bijection,
             pin_paper_rank3_orders, pin_sample_matches_full, pin_reorder, pin_interlace,
             pin_rejects_invalid]

@@ -58,6 +58,11 @@ MUTANTS = [
      "if (0)"),
     ("64-bit indices read as 32-bit", "                                          : ((const uint64_t *)idx)[i];",
      "                                          : (uint64_t)((const uint32_t *)idx)[i];"),
+    ("stencil clamp reads zeros", "                } else if (boundary == 0) {\n                    v = 0.0;",
+     "                } else if (boundary >= 0) {\n                    v = 0.0;"),
+    ("stencil offsets applied with the wrong sign", "int64_t yy = y + dy[k], xx = x + dx[k];",
+     "int64_t yy = y - dy[k], xx = x - dx[k];"),
+    ("stencil dx and dy swapped", "int64_t yy = y + dy[k], xx = x + dx[k];", "int64_t yy = y + dx[k], xx = x + dy[k];"),
     ("permutation check dropped", "if (seen[perm[i]]) return -1;", ""),
     ("reorder range check dropped", "if ((size_t)idx[i] >= n) return -1;", ""),
     ("last byte of each element dropped",
