@@ -671,7 +671,8 @@ def run_reference(args):
 
 def parse_case(spec: str):
     """Single-op case spec: permute:E:d0,d1,..:p0,p1,.. | reorder:E:n:random|block4096 |
-    interlace:E:n:k | deinterlace:E:n:k | nm:E:dims:order:base:range (comma lists)."""
+    interlace:E:n:k | deinterlace:E:n:k | nm:E:dims:order:base:range (comma lists);
+    batch:N and stencil:TAPS:NY:NX[:BOUNDARY] are handled by their own runners."""
     parts = spec.split(":")
     kind, e = parts[0], int(parts[1])
     if kind == "permute":
@@ -687,6 +688,64 @@ def parse_case(spec: str):
     raise SystemExit(f"unknown case kind {kind}")
 
 
+def stencil_taps(name: str):
+    """fdN: order-N finite-difference Laplacian; boxN: (2N+1)^2 mean filter;
+    crossN: seeded random weights on the full cross of radius N; genK: K
+    seeded random taps within radius 4."""
+    from synth.stencils import fd_laplacian
+    g = np.random.default_rng(17)
+    if name.startswith("fd"):
+        return fd_laplacian(int(name[2:]))
+    r = int(name[3:]) if name[:3] in ("box", "gen") else int(name[5:])
+    if name.startswith("box"):
+        return [(dy, dx, 1.0 / (2 * r + 1) ** 2) for dy in range(-r, r + 1) for dx in range(-r, r + 1)]
+    if name.startswith("cross"):
+        return [(d, 0, float(g.normal())) for d in range(-r, r + 1)] + \
+               [(0, d, float(g.normal())) for d in range(-r, r + 1) if d]
+    return [(int(g.integers(-4, 5)), int(g.integers(-4, 5)), float(g.normal())) for _ in range(r)]
+
+
+def run_stencil_case(torch, rr, stream, dev, spec, args):
+    """stencil:TAPS:NY:NX[:BOUNDARY] -- the 2-D stencil on a float grid (Table 4
+    uses fd1 on 4096 x 4096).  L2 is flushed before every timed call (the
+    4096^2 grid fits in L2), and a device copy of the same bytes is timed the
+    same way as the bandwidth reference."""
+    parts = spec.split(":")
+    taps = stencil_taps(parts[1])
+    ny, nx = int(parts[2]), int(parts[3])
+    boundary = int(parts[4]) if len(parts) > 4 else 0
+    gen = torch.Generator(device=dev).manual_seed(5)
+    src = torch.randn((ny, nx), device=dev, generator=gen, dtype=torch.float32)
+    dst = torch.empty_like(src)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    nbytes = 2 * ny * nx * 4
+
+    def timed(call):
+        for _ in range(args.warmup):
+            call()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            call()
+            s1.record(stream)
+            s1.synchronize()
+            ts.append(s0.elapsed_time(s1) / 1e3)
+        return ts
+
+    t = timed(lambda: rr.stencil2d(dst, src, ny, nx, taps, boundary, stream))
+    c = timed(lambda: rr.memcpy_d2d(dst, src, ny * nx * 4, stream))
+    med, cmed = statistics.median(t), statistics.median(c)
+    return {"case": spec, "bytes": nbytes, "median_ms": round(med * 1e3, 4), "best_ms": round(min(t) * 1e3, 4),
+            "gbs_median": round(nbytes / med / 1e9, 1), "gbs_best": round(nbytes / min(t) / 1e9, 1),
+            "copy_gbs_median": round(nbytes / cmed / 1e9, 1), "l2": "flushed before each call",
+            "plan": rr.describe_stencil(ny, nx, taps, boundary, dst.data_ptr(), src.data_ptr()),
+            "steps": args.steps}
+
+
 def run_case(args):
     """Time one op (used for profiling captures and sweeps): W untimed and K
     timed calls on one stream, CUDA events around each call."""
@@ -699,6 +758,8 @@ def run_case(args):
     stream = torch.cuda.Stream(dev)
     if args.case.startswith("batch:"):
         return run_batch_case(torch, rr, stream, dev, int(args.case.split(":")[1]), args)
+    if args.case.startswith("stencil:"):
+        return run_stencil_case(torch, rr, stream, dev, args.case, args)
     o = parse_case(args.case)
     e = o["elem_bytes"]
     if o["kind"] == "nm":

@@ -153,6 +153,69 @@ rearr_status rearr_deinterlace(void *const *dsts, const void *src, int k, size_t
                                size_t elem_bytes, rearr_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * rearr_stencil2d_f32 -- generic 2-D stencil on a float grid (arXiv:1011.3583
+ * Sec. III.D, "Generic 2D Stencil Calculation Kernel"; Fig. 2, Table 4):
+ *       dst[y][x] = sum_k w[k] * src[y + dy[k]][x + dx[k]],
+ *   0 <= y < ny, 0 <= x < nx.
+ *   src, dst : ny x nx row-major float32 grids (device, caller-owned); they
+ *              must not overlap.
+ *   dy, dx, w: ntaps host entries (1 <= ntaps <= REARR_STENCIL_MAX_TAPS),
+ *              |dy[k]|, |dx[k]| <= REARR_STENCIL_MAX_RADIUS.  The paper's
+ *              functor holding a single-threaded stencil function becomes this
+ *              weighted tap list (a C caller cannot pass a template functor).
+ *              Offsets may repeat; each tap is one term of the sum.
+ *   boundary : REARR_STENCIL_ZERO -- points outside the grid read 0;
+ *              REARR_STENCIL_CLAMP -- they read the nearest grid point.
+ *   Arithmetic is fp32 fused multiply-add in the kernel's order, so each
+ *   result is within (ntaps + 1) * 2^-24 * sum_k |w[k]| |src[y+dy[k]][x+dx[k]]|
+ *   of the exact sum (NaN and infinities propagate as in that sum).
+ *   The tap set selects the kernel: a full cross of radius r (the order-r
+ *   finite-difference Laplacian of the paper's experiments) or a full box of
+ *   radius 1 or 2 (smoothing filters), with distinct offsets, run
+ *   register-blocked bodies; any other set runs the generic body (one
+ *   shared-memory read per tap and point).
+ *   Grids whose rows are 16-byte aligned (src and dst 16-byte aligned, nx a
+ *   multiple of 4) are staged by TMA tensor copies, others by plain loads;
+ *   the results are the same.
+ * ------------------------------------------------------------------------- */
+#define REARR_STENCIL_MAX_RADIUS 8
+#define REARR_STENCIL_MAX_TAPS 64
+
+typedef enum { REARR_STENCIL_ZERO = 0, REARR_STENCIL_CLAMP = 1 } rearr_stencil_boundary;
+
+rearr_status rearr_stencil2d_f32(float *dst, const float *src, int64_t ny, int64_t nx, int ntaps,
+                                 const int *dy, const int *dx, const float *w, int boundary,
+                                 rearr_stream_t stream);
+
+typedef enum {
+    REARR_STENCIL_GENERIC = 0,  /* any tap set                               */
+    REARR_STENCIL_CROSS = 1,    /* every offset with dy == 0 or dx == 0, |.| <= r */
+    REARR_STENCIL_BOX = 2       /* every offset with |dy|, |dx| <= r (r <= 2)  */
+} rearr_stencil_shape;
+
+typedef struct {
+    int shape;           /* rearr_stencil_shape of the tap set                */
+    int radius;          /* largest |dy| or |dx| of the taps                  */
+    int n_unique;        /* distinct tap offsets                              */
+    int tma;             /* 1: staged by TMA tensor copies; 0: plain loads    */
+    int tile_y, tile_x;  /* outputs per CTA                                   */
+    int64_t n_tiles;     /* CTAs launched                                     */
+    int64_t smem_bytes;  /* shared memory per CTA                             */
+} rearr_stencil_info;
+
+/* The kernel choice of rearr_stencil2d_f32 for these arguments (host only;
+ * nothing is read or written; dst_addr / src_addr steer the alignment test,
+ * 0 meaning 256-byte aligned).  Same validation as the call. */
+rearr_status rearr_stencil2d_describe(int64_t ny, int64_t nx, int ntaps, const int *dy, const int *dx,
+                                      const float *w, int boundary, uintptr_t dst_addr,
+                                      uintptr_t src_addr, rearr_stencil_info *info);
+
+/* Number of bounded device-side waits (a TMA copy's completion barrier) that
+ * ran out of time since the library was loaded, on the current device; such
+ * a CTA skips its outputs.  0 in normal operation.  Synchronises the device. */
+rearr_status rearr_wait_timeouts(uint64_t *count);
+
+/* ---------------------------------------------------------------------------
  * Batched execution.  The paper has no batching; these calls run many of the
  * operations above in one persistent kernel launch driven by a device-side
  * tile work list, captured once in a CUDA graph and replayed.

@@ -7,6 +7,7 @@
 #include "../../include/librearr.h"
 #include "launch.h"
 #include "plan.h"
+#include "stencil.h"
 
 namespace rearr {
 
@@ -136,6 +137,48 @@ rearr_status rearr_deinterlace(void *const *dsts, const void *src, int k, size_t
     if (st != REARR_OK) return fail(st, "rearr_deinterlace: " + err);
     cudaError_t e = launch_single(pl.op, pl.planes.data(), reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "rearr_deinterlace launch");
+    return REARR_OK;
+}
+
+rearr_status rearr_stencil2d_f32(float *dst, const float *src, int64_t ny, int64_t nx, int ntaps, const int *dy,
+                                 const int *dx, const float *w, int boundary, rearr_stream_t stream)
+{
+    StencilPlan pl;
+    std::string err;
+    rearr_status st = plan_stencil2d(dst, src, ny, nx, ntaps, dy, dx, w, boundary, pl, err);
+    if (st != REARR_OK) return fail(st, "rearr_stencil2d_f32: " + err);
+    cudaError_t e = launch_stencil2d(pl, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "rearr_stencil2d_f32 launch");
+    return REARR_OK;
+}
+
+rearr_status rearr_stencil2d_describe(int64_t ny, int64_t nx, int ntaps, const int *dy, const int *dx, const float *w,
+                                      int boundary, uintptr_t dst_addr, uintptr_t src_addr, rearr_stencil_info *info)
+{
+    if (!info) return fail(REARR_EINVAL, "rearr_stencil2d_describe: info is NULL");
+    if (dst_addr == 0) dst_addr = uintptr_t(1) << 47;
+    if (src_addr == 0) src_addr = uintptr_t(1) << 46;
+    StencilPlan pl;
+    std::string err;
+    rearr_status st = plan_stencil2d(reinterpret_cast<float *>(dst_addr), reinterpret_cast<const float *>(src_addr),
+                                     ny, nx, ntaps, dy, dx, w, boundary, pl, err);
+    if (st != REARR_OK) return fail(st, "rearr_stencil2d_describe: " + err);
+    info->shape = pl.shape;
+    info->radius = pl.a.r;
+    info->n_unique = pl.n_unique;
+    info->tma = pl.a.tma;
+    info->tile_y = kStencilTileY;
+    info->tile_x = kStencilTileX;
+    info->n_tiles = pl.n_tiles;
+    info->smem_bytes = int64_t(pl.smem_bytes);
+    return REARR_OK;
+}
+
+rearr_status rearr_wait_timeouts(uint64_t *count)
+{
+    if (!count) return fail(REARR_EINVAL, "rearr_wait_timeouts: count is NULL");
+    cudaError_t e = read_wait_timeouts(count);
+    if (e != cudaSuccess) return cuda_fail(e, "rearr_wait_timeouts");
     return REARR_OK;
 }
 

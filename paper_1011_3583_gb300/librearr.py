@@ -47,6 +47,20 @@ class PermuteInfo(ctypes.Structure):
                     tile_b=self.tile_b, n_tiles=self.n_tiles)
 
 
+class StencilInfo(ctypes.Structure):
+    _fields_ = [("shape", ctypes.c_int), ("radius", ctypes.c_int), ("n_unique", ctypes.c_int), ("tma", ctypes.c_int),
+                ("tile_y", ctypes.c_int), ("tile_x", ctypes.c_int), ("n_tiles", ctypes.c_int64),
+                ("smem_bytes", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return dict(shape=STENCIL_SHAPES.get(self.shape, self.shape), radius=self.radius, n_unique=self.n_unique,
+                    tma=self.tma, tile_y=self.tile_y, tile_x=self.tile_x, n_tiles=self.n_tiles,
+                    smem_bytes=self.smem_bytes)
+
+
+STENCIL_SHAPES = {0: "generic", 1: "cross", 2: "box"}
+STENCIL_ZERO, STENCIL_CLAMP = 0, 1
+
 _lib = None
 
 
@@ -93,6 +107,12 @@ def load() -> ctypes.CDLL:
         "rearr_launch_count": (ctypes.c_uint64, []),
         "rearr_selftest_host": (st, []),
         "rearr_tuning_load": (st, [ctypes.c_char_p]),
+        "rearr_stencil2d_f32": (st, [vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ip, ip,
+                                     ctypes.POINTER(ctypes.c_float), ctypes.c_int, vp]),
+        "rearr_stencil2d_describe": (st, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ip, ip,
+                                          ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.c_size_t,
+                                          ctypes.c_size_t, ctypes.POINTER(StencilInfo)]),
+        "rearr_wait_timeouts": (st, [ctypes.POINTER(ctypes.c_uint64)]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -173,6 +193,38 @@ def reorder_nm(dst, src, elem_bytes: int, dims: Sequence[int], order: Sequence[i
     rank_in, d, rank_out, o, b, r = _nm_args(dims, order, base, rng)
     _check(load().rearr_reorder_nm(_ptr(dst), _ptr(src), int(elem_bytes), rank_in, d, rank_out, o, b, r,
                                    _stream(stream)))
+
+
+def _taps(taps):
+    k = len(taps)
+    dy = (ctypes.c_int * max(k, 1))(*[int(t[0]) for t in taps])
+    dx = (ctypes.c_int * max(k, 1))(*[int(t[1]) for t in taps])
+    w = (ctypes.c_float * max(k, 1))(*[float(t[2]) for t in taps])
+    return k, dy, dx, w
+
+
+def stencil2d(dst, src, ny: int, nx: int, taps, boundary: int = STENCIL_ZERO, stream=None) -> None:
+    """rearr_stencil2d_f32: dst[y][x] = sum over taps (dy, dx, w) of w * src[y+dy][x+dx] (float32 grids)."""
+    k, dy, dx, w = _taps(taps)
+    _check(load().rearr_stencil2d_f32(_ptr(dst), _ptr(src), int(ny), int(nx), k, dy, dx, w, int(boundary),
+                                      _stream(stream)))
+
+
+def describe_stencil(ny: int, nx: int, taps, boundary: int = STENCIL_ZERO, dst_addr: int = 0,
+                     src_addr: int = 0) -> dict:
+    """rearr_stencil2d_describe: the kernel choice of a stencil call (host only)."""
+    k, dy, dx, w = _taps(taps)
+    info = StencilInfo()
+    _check(load().rearr_stencil2d_describe(int(ny), int(nx), k, dy, dx, w, int(boundary), int(dst_addr),
+                                           int(src_addr), ctypes.byref(info)))
+    return info.as_dict()
+
+
+def wait_timeouts() -> int:
+    """rearr_wait_timeouts: device waits that ran out of time (0 in normal operation)."""
+    v = ctypes.c_uint64()
+    _check(load().rearr_wait_timeouts(ctypes.byref(v)))
+    return int(v.value)
 
 
 def reorder(dst, src, idx, n: int, elem_bytes: int, stream=None) -> None:
