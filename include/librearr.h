@@ -195,6 +195,9 @@ typedef enum {
 
 typedef struct {
     int shape;           /* rearr_stencil_shape of the tap set                */
+    int body;            /* kernel body: 1 cross, 2 box; generic lists run 3
+                            (one shared read per tap, <= 24 taps) or 0
+                            (input columns held in registers)                */
     int radius;          /* largest |dy| or |dx| of the taps                  */
     int n_unique;        /* distinct tap offsets                              */
     int tma;             /* 1: staged by TMA tensor copies; 0: plain loads    */

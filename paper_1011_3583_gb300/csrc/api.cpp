@@ -164,6 +164,7 @@ rearr_status rearr_stencil2d_describe(int64_t ny, int64_t nx, int ntaps, const i
                                      ny, nx, ntaps, dy, dx, w, boundary, pl, err);
     if (st != REARR_OK) return fail(st, "rearr_stencil2d_describe: " + err);
     info->shape = pl.shape;
+    info->body = pl.body;
     info->radius = pl.a.r;
     info->n_unique = pl.n_unique;
     info->tma = pl.a.tma;

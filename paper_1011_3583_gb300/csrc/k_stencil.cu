@@ -1,25 +1,36 @@
 // k_stencil.cu -- generic 2-D stencil kernels (Sec. III.D) for sm_103a.
 //
-// A CTA of 256 threads computes a 128 x 64 tile of outputs.  Its input box --
-// the tile, r halo rows above and below and 8 staged columns left and right --
-// is copied to shared memory (the "user managed cache" of Sec. III.D) by ONE
-// TMA tensor copy when the grid's rows are 16-byte aligned: the copy engine
-// zero-fills cells outside the grid, so the halo needs no per-thread
-// boundary logic and no uncoalesced apron loads (the cost Sec. III.D
-// attributes to designated halo threads).  Other grids are staged by plain
-// coalesced loads.  With the clamped boundary, edge tiles then overwrite their
-// out-of-grid cells with the nearest in-grid cell.
+// Every CTA of 256 threads computes 128 x 64 tiles of outputs from an input
+// box in shared memory (the "user managed cache" of Sec. III.D): the tile, r
+// halo rows above and below and 8 staged columns left and right.
 //
-// Compute bodies reading that box:
+// Staging.  When the grid's rows are 16-byte aligned the box arrives by ONE
+// TMA tensor copy (cp.async.bulk.tensor.2d) whose out-of-grid cells the copy
+// engine fills with zeros, so the halo needs neither designated halo threads
+// nor uncoalesced apron loads (the costs Sec. III.D names).  Other grids are
+// staged by plain coalesced loads.  With the clamped boundary, edge tiles then
+// overwrite their out-of-grid cells with the nearest in-grid cell.  One tile
+// per CTA and four CTAs per SM: while some CTAs compute, the others' copies
+// are in flight.  (A persistent variant with two boxes per CTA, copying tile
+// i + 1 while computing tile i, fits only two CTAs per SM and measured
+// slower: 5.4 against 7.0 TB/s on a 16384^2 grid.)
+//
+// Compute bodies reading a box:
 //   cross<r> / box<r>: each thread owns 8 rows x 4 columns of outputs and
 //     streams the input rows it needs through registers (16-byte shared
-//     loads); every staged value is read once per thread and used by all the
+//     loads); every staged value is read once per thread and feeds all the
 //     taps that touch it.  Weights are compile-time-indexed kernel parameters.
-//   generic: each thread owns 32 rows of one column and loops over the tap
-//     list: one shared-memory read and one FMA per tap and output.
+//   generic, long tap lists (more than 24 taps): each thread owns 32 rows of
+//     one column, computed as two halves of 16.  Per distinct dx of the tap
+//     list it loads that input column (16 + 2r values) into registers and
+//     applies the column's taps from there (a switch on dy selects the
+//     compile-time register offset).
+//   generic, short tap lists: each thread owns 32 rows of one column and
+//     reads one staged value per tap and output (fewer instructions per tap;
+//     measured faster up to about two dozen taps).
 // The paper's diagonal block order (partition camping) has no counterpart on
-// this memory system: tiles run in row-major order, so horizontally adjacent
-// CTAs share halo columns in L2.
+// this memory system: tiles run in row-major order, so neighbouring CTAs
+// share halo cells in L2.
 #include <cuda.h>
 
 #include <mutex>
@@ -35,9 +46,10 @@ namespace {
 
 constexpr int TY = kStencilTileY;
 constexpr int PITCH = kStencilPitch;
+constexpr int MAXR = kStencilMaxRadius;
+constexpr int WARPS = kStencilThreads / 32;
 static_assert(kStencilPitch * 4 % 16 == 0, "staged rows must stay 16-byte aligned");
-static_assert((kStencilTileY + 2 * kStencilMaxRadius) * kStencilPitch * 4 <= 48 * 1024,
-              "box must fit the default dynamic shared memory limit");
+static_assert(PITCH <= 3 * 32, "a warp stages a row in three passes");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -73,72 +85,70 @@ __device__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
 
 __device__ __forceinline__ int64_t clamp64(int64_t v, int64_t n) { return v < 0 ? 0 : (v >= n ? n - 1 : v); }
 
-// Stages rows y0 - r .. y0 + TY + r - 1 and columns x0 - 8 .. x0 + 71 of the
-// source into box (row pitch PITCH floats).  Returns false when the TMA copy
-// did not complete in time (the CTA then computes nothing).
-__device__ bool stage_box(const StencilArgs &a, const CUtensorMap *tmap, float *box, uint64_t *bar, int64_t y0,
-                          int64_t x0)
+// One thread: copy the box whose cell (0, 0) is grid point (by, bx) into box,
+// completing on the mbarrier at bar.  bx is a multiple of 4 floats (tile
+// columns start at multiples of 64, the halo is 8 columns), the TMA rule for
+// the innermost coordinate.
+__device__ __forceinline__ void tma_issue(const CUtensorMap *tmap, float *box, uint32_t bar, int64_t by, int64_t bx,
+                                          uint32_t bytes)
 {
-    const int rows = TY + 2 * a.r;
-    const int tid = threadIdx.x;
-    const int64_t by = y0 - a.r, bx = x0 - kStencilHaloX;  // grid position of box cell (0, 0)
-    if (a.tma) {
-        const uint32_t b = smem_u32(bar);
-        if (tid == 0) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b),
-                         "r"(rows * PITCH * 4)
+    // Order this CTA's earlier generic-proxy accesses of the buffer (reads of
+    // the previous tile, clamp rewrites) before the copy's async-proxy writes.
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(box)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(int(bx)), "r"(int(by)), "r"(bar)
+        : "memory");
+}
+
+// Clamped boundary: every out-of-grid cell of the box takes the nearest
+// in-grid cell, which the box also holds (it overlaps the grid).  In-grid
+// cells are only read, so the rewrite has no read/write conflict.  A warp
+// per box row.
+__device__ void clamp_fixup(const StencilArgs &a, float *box, int64_t by, int64_t bx, int rows)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c0 = int(bx < 0 ? -bx : 0), c1 = int(a.nx - bx < PITCH ? a.nx - bx : PITCH);
+    const int r0 = int(by < 0 ? -by : 0), r1 = int(a.ny - by < rows ? a.ny - by : rows);
+    for (int rr = warp; rr < rows; rr += WARPS) {
+        const int sr = rr < r0 ? r0 : (rr >= r1 ? r1 - 1 : rr);
+        for (int cc = lane; cc < PITCH; cc += 32) {
+            const int sc = cc < c0 ? c0 : (cc >= c1 ? c1 - 1 : cc);
+            if (sr != rr || sc != cc) box[rr * PITCH + cc] = box[sr * PITCH + sc];
+        }
+    }
+}
+
+// Plain staging of the box (any alignment), boundary applied: a warp per
+// box row, 32 consecutive columns per instruction, as 4-byte cp.async copies
+// (all of a thread's copies in flight at once; a copy of 0 source bytes
+// zero-fills its cell).  The caller waits with cp.async.wait_all.
+__device__ void plain_stage(const StencilArgs &a, float *box, int64_t by, int64_t bx, int rows)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool clamp = a.boundary == REARR_STENCIL_CLAMP;
+    for (int rr = warp; rr < rows; rr += WARPS) {
+        const int64_t gy = by + rr;
+        const bool row_in = gy >= 0 && gy < a.ny;
+        const float *src_row = a.src + clamp64(gy, a.ny) * a.nx;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int cc = lane + 32 * q;
+            if (cc >= PITCH) break;
+            const int64_t gx = bx + cc;
+            const uint32_t n = (clamp || (row_in && gx >= 0 && gx < a.nx)) ? 4 : 0;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(box + rr * PITCH + cc)),
+                         "l"(src_row + clamp64(gx, a.nx)), "r"(n)
                          : "memory");
-            // x = bx is a multiple of 4 floats (16 bytes): x0 is a multiple of
-            // 64 and the halo is 8 columns.  Cells outside the grid read 0.
-            asm volatile(
-                "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(box)),
-                "l"(reinterpret_cast<uint64_t>(tmap)), "r"(int(bx)), "r"(int(by)), "r"(b)
-                : "memory");
         }
-        __syncthreads();  // the barrier is initialised before anyone polls it
-        const bool ok = mbar_wait_bounded(b, 0);
-        if (!__syncthreads_and(ok)) {
-            if (tid == 0) atomicAdd(&g_stencil_wait_timeouts, 1ull);
-            mbar_wait_bounded(b, 0);  // let a late copy land before the CTA exits
-            return false;
-        }
-        const bool edge = by < 0 || bx < 0 || by + rows > a.ny || bx + PITCH > a.nx;
-        if (a.boundary == REARR_STENCIL_CLAMP && edge) {
-            // Out-of-grid cells take the nearest in-grid cell, which lies in
-            // the box too (the box overlaps the grid); in-grid cells are only
-            // read here, so the rewrite has no read/write conflict.
-            for (int i = tid; i < rows * PITCH; i += kStencilThreads) {
-                const int rr = i / PITCH, cc = i - rr * PITCH;
-                const int64_t gy = by + rr, gx = bx + cc;
-                if (gy >= 0 && gy < a.ny && gx >= 0 && gx < a.nx) continue;
-                box[i] = box[(clamp64(gy, a.ny) - by) * PITCH + (clamp64(gx, a.nx) - bx)];
-            }
-            __syncthreads();
-        }
-        return true;
     }
-    for (int i = tid; i < rows * PITCH; i += kStencilThreads) {
-        const int rr = i / PITCH, cc = i - rr * PITCH;
-        int64_t gy = by + rr, gx = bx + cc;
-        float v = 0.f;
-        const bool in = gy >= 0 && gy < a.ny && gx >= 0 && gx < a.nx;
-        if (in || a.boundary == REARR_STENCIL_CLAMP) {
-            gy = clamp64(gy, a.ny);
-            gx = clamp64(gx, a.nx);
-            v = __ldg(a.src + gy * a.nx + gx);
-        }
-        box[i] = v;
-    }
-    __syncthreads();
-    return true;
 }
 
 // Cross / box bodies: thread (cx, cy) owns tile rows cy*8 .. cy*8+7 and
 // columns 4cx .. 4cx+3.
-template <int R, int SHAPE>
+template <int R, int BODY>
 __device__ __forceinline__ void compute_blocked(const StencilArgs &a, const float *box, int64_t y0, int64_t x0)
 {
     constexpr int BY = 8;
@@ -161,7 +171,7 @@ __device__ __forceinline__ void compute_blocked(const StencilArgs &a, const floa
         const float *row = base + j * PITCH;
         // Only taps with dy == 0 reach sideways in a cross: input row j feeds
         // them for output row v = j - R.
-        const bool side = SHAPE == REARR_STENCIL_BOX || (j >= R && j < R + BY);
+        const bool side = BODY == kBodyBox || (j >= R && j < R + BY);
         float seg[4 + 2 * R4];
         {
             const float4 m = *reinterpret_cast<const float4 *>(row);
@@ -183,7 +193,7 @@ __device__ __forceinline__ void compute_blocked(const StencilArgs &a, const floa
             if (dy < -R || dy > R) continue;
 #pragma unroll
             for (int dx = -R; dx <= R; ++dx) {
-                if (SHAPE == REARR_STENCIL_CROSS && dy != 0 && dx != 0) continue;
+                if (BODY == kBodyCross && dy != 0 && dx != 0) continue;
                 const float wt = a.w[(dy + R) * NW + dx + R];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[v][c] = fmaf(wt, seg[R4 + c + dx], acc[v][c]);
@@ -208,21 +218,90 @@ __device__ __forceinline__ void compute_blocked(const StencilArgs &a, const floa
     }
 }
 
-// Generic body: thread (tx, ty) owns tile column tx, rows ty*32 .. ty*32+31.
+constexpr int RPT = TY / (kStencilThreads / kStencilTileX);  // generic body: rows per thread
+constexpr int HALF = RPT / 2;                                 // rows per pass
+constexpr int NCOL = HALF + 2 * MAXR;                         // registers of one input column
+
+// acc[v] += w * col[v + DY + MAXR]: one tap of the generic body.
+template <int DY>
+__device__ __forceinline__ void tap_column(float (&acc)[HALF], const float (&col)[NCOL], float w)
+{
+#pragma unroll
+    for (int v = 0; v < HALF; ++v) acc[v] = fmaf(w, col[v + DY + MAXR], acc[v]);
+}
+
+// Generic body: thread (tx, ty) owns tile column tx, rows ty*RPT .. +RPT-1,
+// in two passes of HALF rows.
 __device__ __forceinline__ void compute_generic(const StencilArgs &a, const float *box, int64_t y0, int64_t x0)
 {
-    constexpr int RPT = TY / 4;
-    static_assert(kStencilThreads == 4 * kStencilTileX, "thread grid must cover the tile");
-    const int tx = threadIdx.x & (kStencilTileX - 1), ty = threadIdx.x / kStencilTileX;
+    static_assert(kStencilThreads % kStencilTileX == 0 && RPT * (kStencilThreads / kStencilTileX) == TY,
+                  "thread grid must cover the tile");
+    const int tx = threadIdx.x % kStencilTileX, ty = threadIdx.x / kStencilTileX;
+    const int64_t gx = x0 + tx;
+    const int ilo = MAXR - a.r, ihi = HALF + MAXR + a.r;
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        float acc[HALF];
+#pragma unroll
+        for (int v = 0; v < HALF; ++v) acc[v] = 0.f;
+        // col[i] holds tile row ty*RPT + h*HALF + i - MAXR, i.e. box row
+        // row0 + i; only i in [MAXR - r, HALF + MAXR + r) is read (|dy| <= r).
+        const int row0 = ty * RPT + h * HALF + a.r - MAXR;
+        int k = 0;
+        for (int g = 0; g < a.ngroups; ++g) {
+            const int c = kStencilHaloX + tx + a.gdx[g];
+            float col[NCOL];
+#pragma unroll
+            for (int i = 0; i < NCOL; ++i)
+                if (i >= ilo && i < ihi) col[i] = box[(row0 + i) * PITCH + c];
+            for (const int kend = a.gend[g]; k < kend; ++k) {
+                const float w = a.tw[k];
+                switch (a.tdy[k]) {
+                    case -8: tap_column<-8>(acc, col, w); break;
+                    case -7: tap_column<-7>(acc, col, w); break;
+                    case -6: tap_column<-6>(acc, col, w); break;
+                    case -5: tap_column<-5>(acc, col, w); break;
+                    case -4: tap_column<-4>(acc, col, w); break;
+                    case -3: tap_column<-3>(acc, col, w); break;
+                    case -2: tap_column<-2>(acc, col, w); break;
+                    case -1: tap_column<-1>(acc, col, w); break;
+                    case 0: tap_column<0>(acc, col, w); break;
+                    case 1: tap_column<1>(acc, col, w); break;
+                    case 2: tap_column<2>(acc, col, w); break;
+                    case 3: tap_column<3>(acc, col, w); break;
+                    case 4: tap_column<4>(acc, col, w); break;
+                    case 5: tap_column<5>(acc, col, w); break;
+                    case 6: tap_column<6>(acc, col, w); break;
+                    case 7: tap_column<7>(acc, col, w); break;
+                    default: tap_column<8>(acc, col, w); break;  // |dy| <= 8 is checked on the host
+                }
+            }
+        }
+        if (gx < a.nx) {
+#pragma unroll
+            for (int v = 0; v < HALF; ++v) {
+                const int64_t gy = y0 + ty * RPT + h * HALF + v;
+                if (gy >= a.ny) break;
+                a.dst[gy * a.nx + gx] = acc[v];
+            }
+        }
+    }
+}
+
+// Generic body for short tap lists: thread (tx, ty) owns tile column tx,
+// rows ty*RPT .. +RPT-1, and reads one staged value per tap and output.
+__device__ __forceinline__ void compute_generic_taps(const StencilArgs &a, const float *box, int64_t y0, int64_t x0)
+{
+    const int tx = threadIdx.x % kStencilTileX, ty = threadIdx.x / kStencilTileX;
     float acc[RPT];
 #pragma unroll
     for (int v = 0; v < RPT; ++v) acc[v] = 0.f;
     const float *base = box + (ty * RPT + a.r) * PITCH + kStencilHaloX + tx;
     for (int k = 0; k < a.ntaps; ++k) {
-        const float wt = a.tw[k];
+        const float w = a.tw[k];
         const float *p = base + a.tdy[k] * PITCH + a.tdx[k];
 #pragma unroll
-        for (int v = 0; v < RPT; ++v) acc[v] = fmaf(wt, p[v * PITCH], acc[v]);
+        for (int v = 0; v < RPT; ++v) acc[v] = fmaf(w, p[v * PITCH], acc[v]);
     }
     const int64_t gx = x0 + tx;
     if (gx >= a.nx) return;
@@ -234,25 +313,75 @@ __device__ __forceinline__ void compute_generic(const StencilArgs &a, const floa
     }
 }
 
-template <int R, int SHAPE>
-__global__ void __launch_bounds__(kStencilThreads, 4)
-    k_stencil(const __grid_constant__ StencilArgs a, const __grid_constant__ CUtensorMap tmap)
+template <int R, int BODY>
+__device__ __forceinline__ void compute(const StencilArgs &a, const float *box, int64_t y0, int64_t x0)
 {
-    extern __shared__ __align__(128) float box[];
-    __shared__ __align__(8) uint64_t bar;
-    const int64_t t = blockIdx.x;
-    const int64_t ty = t / a.tiles_x, tx = t - ty * a.tiles_x;
-    const int64_t y0 = ty * TY, x0 = tx * kStencilTileX;
-    if (!stage_box(a, &tmap, box, &bar, y0, x0)) return;
-    if constexpr (SHAPE == REARR_STENCIL_GENERIC) compute_generic(a, box, y0, x0);
-    else compute_blocked<R, SHAPE>(a, box, y0, x0);
+    if constexpr (BODY == kBodyGenericColumns) compute_generic(a, box, y0, x0);
+    else if constexpr (BODY == kBodyGenericTaps) compute_generic_taps(a, box, y0, x0);
+    else compute_blocked<R, BODY>(a, box, y0, x0);
 }
 
-template <int R, int SHAPE>
-cudaError_t launch_one(const StencilPlan &pl, const CUtensorMap &m, cudaStream_t s)
+// Tile of CTA blockIdx.x: row-major, rotated by one row of tiles so that the
+// bottom edge (whose clamped boundary costs a rewrite) runs first instead of
+// forming the kernel's tail.
+__device__ __forceinline__ void tile_origin(const StencilArgs &a, int64_t &y0, int64_t &x0)
 {
-    k_stencil<R, SHAPE><<<unsigned(pl.n_tiles), kStencilThreads, pl.smem_bytes, s>>>(pl.a, m);
-    return cudaGetLastError();
+    const int64_t n = gridDim.x;
+    int64_t t = int64_t(blockIdx.x) + (n - a.tiles_x);
+    if (t >= n) t -= n;
+    const int64_t ty = t / a.tiles_x;
+    y0 = ty * TY;
+    x0 = (t - ty * a.tiles_x) * kStencilTileX;
+}
+
+__device__ __forceinline__ bool edge_box(const StencilArgs &a, int64_t by, int64_t bx, int rows)
+{
+    return by < 0 || bx < 0 || by + rows > a.ny || bx + PITCH > a.nx;
+}
+
+// One tile per CTA, staged by a TMA tensor copy.
+template <int R, int BODY>
+__global__ void __launch_bounds__(kStencilThreads, 4)
+    k_stencil_tma(const __grid_constant__ StencilArgs a, const __grid_constant__ CUtensorMap tmap)
+{
+    extern __shared__ __align__(128) float smem[];
+    __shared__ __align__(8) uint64_t bar_storage;
+    const int rows = TY + 2 * a.r;
+    int64_t y0, x0;
+    tile_origin(a, y0, x0);
+    const int64_t by = y0 - a.r, bx = x0 - kStencilHaloX;
+    const uint32_t bar = smem_u32(&bar_storage);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tma_issue(&tmap, smem, bar, by, bx, uint32_t(rows) * PITCH * 4);
+    }
+    __syncthreads();  // the barrier is initialised before anyone polls it
+    const bool ok = mbar_wait_bounded(bar, 0);
+    if (!__syncthreads_and(ok)) {
+        if (threadIdx.x == 0) atomicAdd(&g_stencil_wait_timeouts, 1ull);
+        mbar_wait_bounded(bar, 0);  // let a late copy land before the CTA exits
+        return;
+    }
+    if (a.boundary == REARR_STENCIL_CLAMP && edge_box(a, by, bx, rows)) {
+        clamp_fixup(a, smem, by, bx, rows);
+        __syncthreads();
+    }
+    compute<R, BODY>(a, smem, y0, x0);
+}
+
+// One tile per CTA, plain staging (rows not 16-byte aligned).
+template <int R, int BODY>
+__global__ void __launch_bounds__(kStencilThreads, 4) k_stencil_plain(const __grid_constant__ StencilArgs a)
+{
+    extern __shared__ __align__(128) float smem[];
+    const int rows = TY + 2 * a.r;
+    int64_t y0, x0;
+    tile_origin(a, y0, x0);
+    plain_stage(a, smem, y0 - a.r, x0 - kStencilHaloX, rows);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    compute<R, BODY>(a, smem, y0, x0);
 }
 
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -273,6 +402,14 @@ EncodeTiled encode_tiled()
             fn = reinterpret_cast<EncodeTiled>(p);
     });
     return fn;
+}
+
+template <int R, int BODY>
+cudaError_t launch_one(const StencilPlan &pl, const CUtensorMap &m, cudaStream_t s)
+{
+    if (pl.a.tma) k_stencil_tma<R, BODY><<<unsigned(pl.n_tiles), kStencilThreads, pl.smem_bytes, s>>>(pl.a, m);
+    else k_stencil_plain<R, BODY><<<unsigned(pl.n_tiles), kStencilThreads, pl.smem_bytes, s>>>(pl.a);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -296,23 +433,25 @@ cudaError_t launch_stencil2d(const StencilPlan &pl, cudaStream_t s)
     }
     cudaError_t e = cudaErrorInvalidValue;
     const int r = pl.a.r;
-    if (pl.shape == REARR_STENCIL_CROSS) {
+    if (pl.body == kBodyCross) {
         switch (r) {
-            case 1: e = launch_one<1, REARR_STENCIL_CROSS>(pl, m, s); break;
-            case 2: e = launch_one<2, REARR_STENCIL_CROSS>(pl, m, s); break;
-            case 3: e = launch_one<3, REARR_STENCIL_CROSS>(pl, m, s); break;
-            case 4: e = launch_one<4, REARR_STENCIL_CROSS>(pl, m, s); break;
-            case 5: e = launch_one<5, REARR_STENCIL_CROSS>(pl, m, s); break;
-            case 6: e = launch_one<6, REARR_STENCIL_CROSS>(pl, m, s); break;
-            case 7: e = launch_one<7, REARR_STENCIL_CROSS>(pl, m, s); break;
-            case 8: e = launch_one<8, REARR_STENCIL_CROSS>(pl, m, s); break;
+            case 1: e = launch_one<1, kBodyCross>(pl, m, s); break;
+            case 2: e = launch_one<2, kBodyCross>(pl, m, s); break;
+            case 3: e = launch_one<3, kBodyCross>(pl, m, s); break;
+            case 4: e = launch_one<4, kBodyCross>(pl, m, s); break;
+            case 5: e = launch_one<5, kBodyCross>(pl, m, s); break;
+            case 6: e = launch_one<6, kBodyCross>(pl, m, s); break;
+            case 7: e = launch_one<7, kBodyCross>(pl, m, s); break;
+            case 8: e = launch_one<8, kBodyCross>(pl, m, s); break;
             default: break;
         }
-    } else if (pl.shape == REARR_STENCIL_BOX) {
-        if (r == 1) e = launch_one<1, REARR_STENCIL_BOX>(pl, m, s);
-        else if (r == 2) e = launch_one<2, REARR_STENCIL_BOX>(pl, m, s);
+    } else if (pl.body == kBodyBox) {
+        if (r == 1) e = launch_one<1, kBodyBox>(pl, m, s);
+        else if (r == 2) e = launch_one<2, kBodyBox>(pl, m, s);
+    } else if (pl.body == kBodyGenericTaps) {
+        e = launch_one<0, kBodyGenericTaps>(pl, m, s);
     } else {
-        e = launch_one<0, REARR_STENCIL_GENERIC>(pl, m, s);
+        e = launch_one<0, kBodyGenericColumns>(pl, m, s);
     }
     if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
     return e;

@@ -22,6 +22,14 @@ constexpr int kStencilHaloX = 8;
 constexpr int kStencilPitch = kStencilTileX + 2 * kStencilHaloX;  // floats per staged row
 constexpr int kStencilDense = 2 * kStencilMaxRadius + 1;
 
+// Compute bodies (kernel template argument).  Cross and box equal their
+// rearr_stencil_shape values.
+constexpr int kBodyGenericColumns = 0;  // generic, input columns held in registers
+constexpr int kBodyCross = REARR_STENCIL_CROSS;
+constexpr int kBodyBox = REARR_STENCIL_BOX;
+constexpr int kBodyGenericTaps = 3;     // generic, one shared read per tap and output
+constexpr int kGenericTapsMax = 24;     // longest list for kBodyGenericTaps
+
 // Kernel parameters (passed by value; about 1.6 KB).
 struct StencilArgs {
     const float *src;
@@ -31,9 +39,13 @@ struct StencilArgs {
     int r;            // halo rows above and below a tile: largest |dy|, |dx|
     int boundary;     // REARR_STENCIL_ZERO / REARR_STENCIL_CLAMP
     int tma;          // 1: box staged by a TMA tensor copy, 16-byte stores
-    int ntaps;        // taps as given (generic body)
+    int ntaps;        // taps (generic body), grouped by dx in ascending dx,
+                      // each group in the caller's order
+    int ngroups;      // distinct dx values
     int8_t tdy[kStencilMaxTaps], tdx[kStencilMaxTaps];
     float tw[kStencilMaxTaps];
+    int8_t gdx[kStencilDense];   // dx of group g
+    uint8_t gend[kStencilDense]; // one past the last tap of group g
     // Dense weights of the cross / box bodies: w[(dy + r) * (2r + 1) + dx + r].
     float w[kStencilDense * kStencilDense];
 };
@@ -41,6 +53,7 @@ struct StencilArgs {
 struct StencilPlan {
     StencilArgs a;
     int shape;           // rearr_stencil_shape
+    int body;            // kBody*
     int n_unique;        // distinct tap offsets
     int64_t n_tiles;     // 0: nothing to launch
     size_t smem_bytes;   // dynamic shared memory per CTA

@@ -51,17 +51,35 @@ rearr_status plan_stencil2d(float *dst, const float *src, int64_t ny, int64_t nx
     a.ntaps = ntaps;
     bool on_axes = true;
     for (int k = 0; k < ntaps; ++k) {
-        a.tdy[k] = int8_t(dy[k]);
-        a.tdx[k] = int8_t(dx[k]);
-        a.tw[k] = w[k];
         a.w[(dy[k] + r) * (2 * r + 1) + dx[k] + r] = w[k];
         on_axes &= dy[k] == 0 || dx[k] == 0;
+    }
+    // The generic body loads one input column per distinct dx and applies
+    // every tap of that column from registers: group the taps by dx.
+    int k_out = 0;
+    for (int gx = -kStencilMaxRadius; gx <= kStencilMaxRadius; ++gx) {
+        const int k0 = k_out;
+        for (int k = 0; k < ntaps; ++k) {
+            if (dx[k] != gx) continue;
+            a.tdy[k_out] = int8_t(dy[k]);
+            a.tdx[k_out] = int8_t(dx[k]);
+            a.tw[k_out] = w[k];
+            ++k_out;
+        }
+        if (k_out > k0) {
+            a.gdx[a.ngroups] = int8_t(gx);
+            a.gend[a.ngroups] = uint8_t(k_out);
+            ++a.ngroups;
+        }
     }
     // With distinct offsets, a count of 4r + 1 on the axes is the full cross
     // and (2r + 1)^2 the full box.
     pl.shape = REARR_STENCIL_GENERIC;
     if (!repeats && r >= 1 && on_axes && ntaps == 4 * r + 1) pl.shape = REARR_STENCIL_CROSS;
     if (!repeats && r >= 1 && r <= 2 && ntaps == (2 * r + 1) * (2 * r + 1)) pl.shape = REARR_STENCIL_BOX;
+    pl.body = pl.shape != REARR_STENCIL_GENERIC ? pl.shape
+              : ntaps <= kGenericTapsMax        ? kBodyGenericTaps
+                                                : kBodyGenericColumns;
     pl.n_unique = n_unique;
     pl.smem_bytes = size_t(kStencilTileY + 2 * r) * kStencilPitch * sizeof(float);
 

@@ -48,17 +48,20 @@ class PermuteInfo(ctypes.Structure):
 
 
 class StencilInfo(ctypes.Structure):
-    _fields_ = [("shape", ctypes.c_int), ("radius", ctypes.c_int), ("n_unique", ctypes.c_int), ("tma", ctypes.c_int),
+    _fields_ = [("shape", ctypes.c_int), ("body", ctypes.c_int), ("radius", ctypes.c_int), ("n_unique", ctypes.c_int),
+                ("tma", ctypes.c_int),
                 ("tile_y", ctypes.c_int), ("tile_x", ctypes.c_int), ("n_tiles", ctypes.c_int64),
                 ("smem_bytes", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
-        return dict(shape=STENCIL_SHAPES.get(self.shape, self.shape), radius=self.radius, n_unique=self.n_unique,
+        return dict(shape=STENCIL_SHAPES.get(self.shape, self.shape), body=STENCIL_BODIES.get(self.body, self.body),
+                    radius=self.radius, n_unique=self.n_unique,
                     tma=self.tma, tile_y=self.tile_y, tile_x=self.tile_x, n_tiles=self.n_tiles,
                     smem_bytes=self.smem_bytes)
 
 
 STENCIL_SHAPES = {0: "generic", 1: "cross", 2: "box"}
+STENCIL_BODIES = {0: "generic_columns", 1: "cross", 2: "box", 3: "generic_taps"}
 STENCIL_ZERO, STENCIL_CLAMP = 0, 1
 
 _lib = None

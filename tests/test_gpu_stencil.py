@@ -130,6 +130,17 @@ def test_generic_tap_sets(lr, orc):
         check(lr, orc, grid(t, ny, nx), taps, t % 2)
 
 
+@pytest.mark.parametrize("r", range(0, 9))
+def test_both_generic_bodies_every_radius(lr, orc, r):
+    for k, body in ((11, "generic_taps"), (40, "generic_columns")):
+        taps = random_taps(50 + r + k, k, r)
+        taps[0] = (r, -r, 0.5)  # reach the radius
+        assert lr.describe_stencil(259, 200, f32_taps(taps))["body"] == body
+        for boundary in (0, 1):
+            check(lr, orc, grid(r + k, 259, 200), taps, boundary)
+            check(lr, orc, grid(r + k, 131, 77), taps, boundary)
+
+
 def test_max_taps_and_radius(lr, orc):
     taps = random_taps(77, 64, 8) + []
     taps[0] = (8, -8, 0.25)

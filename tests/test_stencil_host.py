@@ -65,6 +65,15 @@ def test_repeated_offsets_run_generic(lr):
     assert d["shape"] == "generic" and d["n_unique"] == 9 and d["radius"] == 2
 
 
+def test_generic_body_by_tap_count(lr):
+    taps = [(dy, dx, 1.0) for dy in range(-2, 3) for dx in range(-2, 3)]  # a 5x5 box minus a tap
+    assert lr.describe_stencil(64, 64, taps[:24])["body"] == "generic_taps"
+    d = lr.describe_stencil(64, 64, taps[:24] + [(3, 3, 1.0)])
+    assert d["shape"] == "generic" and d["body"] == "generic_columns"
+    assert lr.describe_stencil(64, 64, fd_laplacian(3))["body"] == "cross"
+    assert lr.describe_stencil(64, 64, box(2))["body"] == "box"
+
+
 def test_tma_rule(lr):
     taps = fd_laplacian(1)
     assert lr.describe_stencil(64, 64, taps)["tma"] == 1
