@@ -218,6 +218,14 @@ rearr_status rearr_stencil2d_describe(int64_t ny, int64_t nx, int ntaps, const i
  * a CTA skips its outputs.  0 in normal operation.  Synchronises the device. */
 rearr_status rearr_wait_timeouts(uint64_t *count);
 
+/* Fault injection for tests of those waits: the next n_launches TMA-staged
+ * stencil launches of this process expect 16 bytes more than their copy
+ * delivers, so each CTA's barrier never completes, its bounded waits run out
+ * (about 2 s each, twice), it counts a timeout and skips its outputs.  No
+ * copy is left in flight and the context stays usable.  n_launches < 0 is
+ * REARR_EINVAL; 0 cancels. */
+rearr_status rearr_inject_wait_timeout(int n_launches);
+
 /* ---------------------------------------------------------------------------
  * Batched execution.  The paper has no batching; these calls run many of the
  * operations above in one persistent kernel launch driven by a device-side

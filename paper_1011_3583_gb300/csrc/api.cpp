@@ -183,6 +183,13 @@ rearr_status rearr_wait_timeouts(uint64_t *count)
     return REARR_OK;
 }
 
+rearr_status rearr_inject_wait_timeout(int n_launches)
+{
+    if (n_launches < 0) return fail(REARR_EINVAL, "rearr_inject_wait_timeout: negative count");
+    inject_wait_timeout(n_launches);
+    return REARR_OK;
+}
+
 rearr_status rearr_permute_describe(size_t elem_bytes, int rank, const int64_t *dims, const int *perm,
                                     uintptr_t dst_addr, uintptr_t src_addr, rearr_permute_info *info)
 {

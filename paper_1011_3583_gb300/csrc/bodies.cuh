@@ -252,7 +252,7 @@ __device__ __forceinline__ int64_t run_offset(const RunsDesc &d, uint32_t q)
 template <int W>
 __device__ __forceinline__ void copy_words(const char *src, char *dst, uint32_t w0, uint32_t w1)
 {
-    constexpr int U = 8;
+    constexpr int U = W >= 16 ? 4 : 8;  // 64 bytes in flight per thread for 16-byte words (80 registers at U = 8)
     for (uint32_t b = w0; b < w1; b += kThreads * U) {
         typename Word<W>::T v[U];
 #pragma unroll
@@ -289,7 +289,7 @@ __device__ __forceinline__ void runs_body(const RunsDesc &d, uint64_t unit, unsi
     const uint32_t wpr = d.wpr_div.d;  // words per run
     const uint32_t total = nr * wpr;
     char *out = d.dst + int64_t(r0) * d.run_bytes;
-    constexpr int U = 8;
+    constexpr int U = W >= 16 ? 4 : 8;  // 64 bytes in flight per thread for 16-byte words (80 registers at U = 8)
     for (uint32_t f0 = 0; f0 < total; f0 += kThreads * U) {
         typename Word<W>::T v[U];
 #pragma unroll

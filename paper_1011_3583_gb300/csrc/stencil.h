@@ -39,6 +39,7 @@ struct StencilArgs {
     int r;            // halo rows above and below a tile: largest |dy|, |dx|
     int boundary;     // REARR_STENCIL_ZERO / REARR_STENCIL_CLAMP
     int tma;          // 1: box staged by a TMA tensor copy, 16-byte stores
+    uint32_t extra_tx;  // bytes expected beyond the copy (0; > 0 only to inject a timeout)
     int ntaps;        // taps (generic body), grouped by dx in ascending dx,
                       // each group in the caller's order
     int ngroups;      // distinct dx values
@@ -67,5 +68,8 @@ cudaError_t launch_stencil2d(const StencilPlan &pl, cudaStream_t s);
 
 // Reads the device's count of timed-out waits (synchronous).
 cudaError_t read_wait_timeouts(uint64_t *count);
+
+// Makes the next n TMA-staged launches wait for bytes that never arrive.
+void inject_wait_timeout(int n);
 
 }  // namespace rearr

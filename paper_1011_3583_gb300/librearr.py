@@ -116,6 +116,7 @@ def load() -> ctypes.CDLL:
                                           ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.c_size_t,
                                           ctypes.c_size_t, ctypes.POINTER(StencilInfo)]),
         "rearr_wait_timeouts": (st, [ctypes.POINTER(ctypes.c_uint64)]),
+        "rearr_inject_wait_timeout": (st, [ctypes.c_int]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -228,6 +229,11 @@ def wait_timeouts() -> int:
     v = ctypes.c_uint64()
     _check(load().rearr_wait_timeouts(ctypes.byref(v)))
     return int(v.value)
+
+
+def inject_wait_timeout(n_launches: int) -> None:
+    """rearr_inject_wait_timeout: the next n TMA-staged stencil launches time out (test hook)."""
+    _check(load().rearr_inject_wait_timeout(int(n_launches)))
 
 
 def reorder(dst, src, idx, n: int, elem_bytes: int, stream=None) -> None:

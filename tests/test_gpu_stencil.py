@@ -251,3 +251,19 @@ def test_large_grid_sampled_rows(lr, orc, order):
         want, tol = band_oracle(orc, src, taps, boundary, rows)
         got = d[rows].cpu().numpy()
         assert_close(got, want, tol, ("16384", order, boundary))
+
+
+def test_injected_wait_timeout_is_reported(lr, orc):
+    """A TMA barrier that never completes (16 bytes more expected than the
+    copy delivers): the bounded waits run out, the CTA counts a timeout and
+    skips its outputs, and the context stays usable for the next call."""
+    src = grid(2, 64, 64)
+    d = lr.describe_stencil(64, 64, f32_taps(fd_laplacian(1)))
+    assert d["n_tiles"] == 1 and d["tma"] == 1
+    before = lr.wait_timeouts()
+    lr.inject_wait_timeout(1)
+    got = run(lr, src, f32_taps(fd_laplacian(1)), 0)
+    assert lr.wait_timeouts() == before + 1
+    assert np.all(got.view(np.uint32) == 0x7F7F7F7F)  # outputs skipped
+    check(lr, orc, src, fd_laplacian(1), 0)            # the next launch is normal
+    assert lr.wait_timeouts() == before + 1

@@ -117,3 +117,9 @@ def test_empty_grid_launches_nothing(lr):
     lr.stencil2d(None, None, 0, 100, fd_laplacian(1))
     lr.stencil2d(None, None, 100, 0, fd_laplacian(1))
     assert lr.launch_count() == n0
+
+
+def test_inject_wait_timeout_validation(lr):
+    with pytest.raises(lr.RearrError):
+        lr.inject_wait_timeout(-1)
+    lr.inject_wait_timeout(0)
