@@ -552,40 +552,39 @@ def run_serving(torch, rr, device, n_req=6000, budget=64 << 30):
 
 
 def run_e2e(torch, rr, wl, ops, stream, args):
-    """Same step through the public API, inputs copied from pinned host memory
-    and outputs copied back inside the timed region."""
+    """Same step through the public host-buffer API (rearr_pipeline_*): every
+    op's inputs are copied from pinned host memory and its output back inside
+    the timed region, with the upload of op i+1, the kernel of op i and the
+    download of op i-1 overlapped on the pipeline's three streams."""
     max_in = wl.dst.numel()
     h_src = torch.empty(max_in, dtype=torch.uint8, pin_memory=True)
     h_src.copy_(torch.from_numpy(wl.src_np.view(np.uint8)))
     h_dst = torch.empty(max_in, dtype=torch.uint8, pin_memory=True)
     h_idx = {k: torch.from_numpy(v.view(np.uint8)).pin_memory() for k, v in wl.idx_np.items()}
-    d_src = torch.empty(max_in, dtype=torch.uint8, device=wl.src.device)
-    d_idx = {k: torch.empty_like(v) for k, v in wl.idx.items()}
     h2d = sum(op_in_bytes(o) for o in ops)
     d2h = sum(op_out_bytes(o) for o in ops)
+    slot = max(op_in_bytes(o) + op_out_bytes(o) for o in ops) + (4 << 10)
+    pipe = rr.Pipeline(slot_bytes=slot, slots=3)
 
     def step():
-        with torch.cuda.stream(stream):
-            for o in ops:
-                nin = (int(np.prod(o["dims"])) if o["kind"] == "permute" else o["n"]) * o["elem_bytes"]
-                d_src[:nin].copy_(h_src[:nin], non_blocking=True)
-                if o["kind"] == "reorder":
-                    d_idx[o["idx"]].copy_(h_idx[o["idx"]], non_blocking=True)
-                    rr.reorder(wl.dst, d_src, d_idx[o["idx"]], o["n"], o["elem_bytes"], stream)
-                else:
-                    rr.permute(wl.dst, d_src, o["elem_bytes"], o["dims"], o["perm"], stream)
-                h_dst[:op_out_bytes(o)].copy_(wl.dst[:op_out_bytes(o)], non_blocking=True)
+        for o in ops:
+            if o["kind"] == "reorder":
+                pipe.reorder(h_dst, h_src, h_idx[o["idx"]], o["n"], o["elem_bytes"])
+            else:
+                pipe.permute(h_dst, h_src, o["elem_bytes"], o["dims"], o["perm"])
 
     steps = max(1, min(args.steps, args.e2e_steps))
     step()
+    pipe.sync()
     torch.cuda.synchronize()
-    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s.record(stream)
+    t0 = time.perf_counter()
     for _ in range(steps):
         step()
-    e.record(stream)
-    e.synchronize()
-    t = s.elapsed_time(e) / 1e3
+    pipe.sync()
+    t = time.perf_counter() - t0
+    st = pipe.stats()
+    pipe.close()
+    assert st["h2d_bytes"] == (steps + 1) * h2d and st["d2h_bytes"] == (steps + 1) * d2h
     return t, steps, int(h2d), int(d2h)
 
 

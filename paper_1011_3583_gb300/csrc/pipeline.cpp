@@ -1,0 +1,292 @@
+// pipeline.cpp -- host-buffer pipeline of librearr (include/librearr_pipeline.h).
+//
+// Three streams per pipeline (uploads, kernels, downloads) and a ring of
+// device staging slots.  For the op in slot s:
+//   upload stream   : wait for slot s's previous download; copy inputs in;
+//                     record in_ready[s]
+//   kernel stream   : wait in_ready[s]; launch the op's kernel on the slot;
+//                     record computed[s]
+//   download stream : wait computed[s]; copy outputs out; record out_done[s]
+// so consecutive ops overlap their uploads, kernels and downloads, and a slot
+// is never overwritten while its previous op is still being read.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/librearr_pipeline.h"
+#include "launch.h"
+#include "plan.h"
+#include "stencil.h"
+
+namespace rearr {
+rearr_status fail(rearr_status st, const std::string &msg);
+rearr_status cuda_fail(cudaError_t e, const char *what);
+}  // namespace rearr
+
+using namespace rearr;
+
+struct rearr_pipeline {
+    char *dev = nullptr;
+    size_t slot_bytes = 0;
+    int slots = 0;
+    int next = 0;
+    cudaStream_t up = nullptr, comp = nullptr, down = nullptr;
+    std::vector<cudaEvent_t> in_ready, computed, out_done;
+    std::vector<bool> used;
+    cudaError_t broken = cudaSuccess;
+    uint64_t ops = 0, h2d = 0, d2h = 0;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t round_up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
+
+struct HostRange {
+    const void *host;
+    size_t bytes;
+};
+struct HostOut {
+    void *host;
+    size_t bytes;
+};
+
+// Device addresses of an op's inputs and outputs inside one slot.
+struct SlotLayout {
+    std::vector<char *> in, out;
+};
+
+rearr_status layout(rearr_pipeline *p, int slot, const std::vector<HostRange> &ins,
+                    const std::vector<HostOut> &outs, SlotLayout &lay, const char *who)
+{
+    size_t need = 0;
+    for (const HostRange &r : ins) need += round_up(r.bytes);
+    for (const HostOut &r : outs) need += round_up(r.bytes);
+    if (need > p->slot_bytes)
+        return fail(REARR_EINVAL, std::string(who) + ": op needs " + std::to_string(need) +
+                                      " bytes of staging, a slot holds " + std::to_string(p->slot_bytes));
+    char *at = p->dev + size_t(slot) * p->slot_bytes;
+    for (const HostRange &r : ins) {
+        lay.in.push_back(at);
+        at += round_up(r.bytes);
+    }
+    for (const HostOut &r : outs) {
+        lay.out.push_back(at);
+        at += round_up(r.bytes);
+    }
+    return REARR_OK;
+}
+
+template <class Launch>
+rearr_status run_op(rearr_pipeline *p, const char *who, const std::vector<HostRange> &ins,
+                    const std::vector<HostOut> &outs, Launch &&launch)
+{
+    if (!p) return fail(REARR_EINVAL, std::string(who) + ": pipeline is NULL");
+    if (p->broken != cudaSuccess) return cuda_fail(p->broken, who);
+    for (const HostRange &r : ins)
+        if (r.bytes && !r.host) return fail(REARR_EINVAL, std::string(who) + ": NULL host input");
+    for (const HostOut &r : outs)
+        if (r.bytes && !r.host) return fail(REARR_EINVAL, std::string(who) + ": NULL host output");
+    const int s = p->next;
+    SlotLayout lay;
+    rearr_status st = layout(p, s, ins, outs, lay, who);
+    if (st != REARR_OK) return st;
+    // The op is planned (and validated) on the slot's device addresses before
+    // anything is enqueued.
+    std::string err;
+    std::function<cudaError_t(cudaStream_t)> go;
+    st = launch(lay, go, err);
+    if (st != REARR_OK) return fail(st, std::string(who) + ": " + err);
+
+    cudaError_t e = cudaSuccess;
+    if (p->used[s]) e = cudaStreamWaitEvent(p->up, p->out_done[s], 0);
+    for (size_t i = 0; i < ins.size() && e == cudaSuccess; ++i)
+        if (ins[i].bytes) e = cudaMemcpyAsync(lay.in[i], ins[i].host, ins[i].bytes, cudaMemcpyHostToDevice, p->up);
+    if (e == cudaSuccess) e = cudaEventRecord(p->in_ready[s], p->up);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->comp, p->in_ready[s], 0);
+    if (e == cudaSuccess) e = go(p->comp);
+    if (e == cudaSuccess) e = cudaEventRecord(p->computed[s], p->comp);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->down, p->computed[s], 0);
+    for (size_t i = 0; i < outs.size() && e == cudaSuccess; ++i)
+        if (outs[i].bytes)
+            e = cudaMemcpyAsync(outs[i].host, lay.out[i], outs[i].bytes, cudaMemcpyDeviceToHost, p->down);
+    if (e == cudaSuccess) e = cudaEventRecord(p->out_done[s], p->down);
+    if (e != cudaSuccess) {
+        p->broken = e;
+        return cuda_fail(e, who);
+    }
+    p->used[s] = true;
+    p->next = (s + 1) % p->slots;
+    p->ops += 1;
+    for (const HostRange &r : ins) p->h2d += r.bytes;
+    for (const HostOut &r : outs) p->d2h += r.bytes;
+    return REARR_OK;
+}
+
+size_t product(int rank, const int64_t *dims)
+{
+    size_t n = 1;
+    for (int i = 0; i < rank; ++i) n *= dims[i] < 0 ? 0 : size_t(dims[i]);
+    return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+rearr_status rearr_pipeline_create(size_t slot_bytes, int slots, rearr_pipeline **pipe)
+{
+    if (!pipe) return fail(REARR_EINVAL, "rearr_pipeline_create: pipe is NULL");
+    *pipe = nullptr;
+    if (slots < 1 || slots > 8) return fail(REARR_EINVAL, "rearr_pipeline_create: slots must be 1..8");
+    if (slot_bytes == 0) return fail(REARR_EINVAL, "rearr_pipeline_create: slot_bytes is 0");
+    auto *p = new rearr_pipeline;
+    p->slot_bytes = round_up(slot_bytes);
+    p->slots = slots;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&p->dev), p->slot_bytes * size_t(slots));
+    if (e != cudaSuccess) {
+        delete p;
+        cudaGetLastError();
+        return fail(REARR_ENOMEM, std::string("rearr_pipeline_create: cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    for (cudaStream_t *s : {&p->up, &p->comp, &p->down})
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(s, cudaStreamNonBlocking);
+    p->in_ready.assign(slots, nullptr);
+    p->computed.assign(slots, nullptr);
+    p->out_done.assign(slots, nullptr);
+    p->used.assign(slots, false);
+    for (int i = 0; i < slots && e == cudaSuccess; ++i)
+        for (cudaEvent_t *ev : {&p->in_ready[i], &p->computed[i], &p->out_done[i]})
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        rearr_pipeline_destroy(p);
+        return cuda_fail(e, "rearr_pipeline_create");
+    }
+    *pipe = p;
+    return REARR_OK;
+}
+
+rearr_status rearr_pipeline_permute(rearr_pipeline *pipe, void *dst, const void *src, size_t elem_bytes, int rank,
+                                    const int64_t *dims, const int *perm)
+{
+    const size_t bytes = (rank >= 1 && rank <= REARR_MAX_RANK && dims) ? product(rank, dims) * elem_bytes : 0;
+    return run_op(pipe, "rearr_pipeline_permute", {{src, bytes}}, {{dst, bytes}},
+                  [&](const SlotLayout &l, std::function<cudaError_t(cudaStream_t)> &go, std::string &err) {
+                      auto pl = std::make_shared<PermPlan>();
+                      rearr_status st = plan_permute(l.out[0], l.in[0], elem_bytes, rank, dims, perm, *pl, err);
+                      go = [pl](cudaStream_t s) { return launch_single(pl->op, nullptr, s); };
+                      return st;
+                  });
+}
+
+rearr_status rearr_pipeline_reorder(rearr_pipeline *pipe, void *dst, const void *src, const uint32_t *idx, size_t n,
+                                    size_t elem_bytes)
+{
+    return run_op(pipe, "rearr_pipeline_reorder", {{src, n * elem_bytes}, {idx, n * sizeof(uint32_t)}},
+                  {{dst, n * elem_bytes}},
+                  [&](const SlotLayout &l, std::function<cudaError_t(cudaStream_t)> &go, std::string &err) {
+                      auto op = std::make_shared<OpDesc>();
+                      rearr_status st = plan_reorder(l.out[0], l.in[0], reinterpret_cast<const uint32_t *>(l.in[1]),
+                                                     n, elem_bytes, *op, err);
+                      go = [op](cudaStream_t s) { return launch_single(*op, nullptr, s); };
+                      return st;
+                  });
+}
+
+rearr_status rearr_pipeline_interlace(rearr_pipeline *pipe, void *dst, const void *const *srcs, int k, size_t n,
+                                      size_t elem_bytes)
+{
+    std::vector<HostRange> ins;
+    if (srcs && k >= 1 && k <= REARR_MAX_K)
+        for (int j = 0; j < k; ++j) ins.push_back({srcs[j], n * elem_bytes});
+    const size_t out = ins.empty() ? 0 : n * elem_bytes * size_t(k);
+    return run_op(pipe, "rearr_pipeline_interlace", ins, {{dst, out}},
+                  [&](const SlotLayout &l, std::function<cudaError_t(cudaStream_t)> &go, std::string &err) {
+                      auto pl = std::make_shared<InterlacePlan>();
+                      std::vector<char *> planes(l.in.begin(), l.in.end());
+                      rearr_status st = plan_interlace(true, l.out.empty() ? nullptr : l.out[0],
+                                                       planes.empty() ? nullptr : planes.data(), k, n, elem_bytes,
+                                                       *pl, err);
+                      go = [pl](cudaStream_t s) { return launch_single(pl->op, pl->planes.data(), s); };
+                      return st;
+                  });
+}
+
+rearr_status rearr_pipeline_deinterlace(rearr_pipeline *pipe, void *const *dsts, const void *src, int k, size_t n,
+                                        size_t elem_bytes)
+{
+    std::vector<HostOut> outs;
+    if (dsts && k >= 1 && k <= REARR_MAX_K)
+        for (int j = 0; j < k; ++j) outs.push_back({dsts[j], n * elem_bytes});
+    const size_t in = outs.empty() ? 0 : n * elem_bytes * size_t(k);
+    return run_op(pipe, "rearr_pipeline_deinterlace", {{src, in}}, outs,
+                  [&](const SlotLayout &l, std::function<cudaError_t(cudaStream_t)> &go, std::string &err) {
+                      auto pl = std::make_shared<InterlacePlan>();
+                      std::vector<char *> planes(l.out.begin(), l.out.end());
+                      rearr_status st = plan_interlace(false, l.in[0], planes.empty() ? nullptr : planes.data(), k,
+                                                       n, elem_bytes, *pl, err);
+                      go = [pl](cudaStream_t s) { return launch_single(pl->op, pl->planes.data(), s); };
+                      return st;
+                  });
+}
+
+rearr_status rearr_pipeline_stencil2d_f32(rearr_pipeline *pipe, float *dst, const float *src, int64_t ny, int64_t nx,
+                                          int ntaps, const int *dy, const int *dx, const float *w, int boundary)
+{
+    const size_t bytes = (ny > 0 && nx > 0) ? size_t(ny) * size_t(nx) * sizeof(float) : 0;
+    return run_op(pipe, "rearr_pipeline_stencil2d_f32", {{src, bytes}}, {{dst, bytes}},
+                  [&](const SlotLayout &l, std::function<cudaError_t(cudaStream_t)> &go, std::string &err) {
+                      auto pl = std::make_shared<StencilPlan>();
+                      rearr_status st = plan_stencil2d(reinterpret_cast<float *>(l.out[0]),
+                                                       reinterpret_cast<const float *>(l.in[0]), ny, nx, ntaps, dy,
+                                                       dx, w, boundary, *pl, err);
+                      go = [pl](cudaStream_t s) { return launch_stencil2d(*pl, s); };
+                      return st;
+                  });
+}
+
+rearr_status rearr_pipeline_sync(rearr_pipeline *pipe)
+{
+    if (!pipe) return fail(REARR_EINVAL, "rearr_pipeline_sync: pipeline is NULL");
+    cudaError_t e = cudaSuccess;
+    for (cudaStream_t s : {pipe->up, pipe->comp, pipe->down}) {
+        cudaError_t es = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = es;
+    }
+    if (e != cudaSuccess) {
+        pipe->broken = e;
+        return cuda_fail(e, "rearr_pipeline_sync");
+    }
+    if (pipe->broken != cudaSuccess) return cuda_fail(pipe->broken, "rearr_pipeline_sync");
+    return REARR_OK;
+}
+
+rearr_status rearr_pipeline_stats(const rearr_pipeline *pipe, uint64_t *ops, uint64_t *h2d_bytes, uint64_t *d2h_bytes)
+{
+    if (!pipe) return fail(REARR_EINVAL, "rearr_pipeline_stats: pipeline is NULL");
+    if (ops) *ops = pipe->ops;
+    if (h2d_bytes) *h2d_bytes = pipe->h2d;
+    if (d2h_bytes) *d2h_bytes = pipe->d2h;
+    return REARR_OK;
+}
+
+void rearr_pipeline_destroy(rearr_pipeline *pipe)
+{
+    if (!pipe) return;
+    for (cudaStream_t s : {pipe->up, pipe->comp, pipe->down})
+        if (s) cudaStreamSynchronize(s);
+    for (auto *v : {&pipe->in_ready, &pipe->computed, &pipe->out_done})
+        for (cudaEvent_t ev : *v)
+            if (ev) cudaEventDestroy(ev);
+    for (cudaStream_t s : {pipe->up, pipe->comp, pipe->down})
+        if (s) cudaStreamDestroy(s);
+    if (pipe->dev) cudaFree(pipe->dev);
+    delete pipe;
+}
+
+}  // extern "C"

@@ -15,6 +15,8 @@ import ctypes
 import os
 from typing import Sequence
 
+import numpy as np
+
 from .build import LIB
 
 MAX_RANK = 8
@@ -555,5 +557,118 @@ class Server:
     def __del__(self):
         try:
             self.close(timeout_us=10_000_000)
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# Host-buffer pipeline (include/librearr_pipeline.h)
+
+_pipe_bound = False
+
+
+def _bind_pipeline():
+    global _pipe_bound
+    L = load()
+    if _pipe_bound:
+        return L
+    vp, sz, st, ip, i64p = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_int), \
+        ctypes.POINTER(ctypes.c_int64)
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    sigs = {
+        "rearr_pipeline_create": (st, [sz, ctypes.c_int, ctypes.POINTER(vp)]),
+        "rearr_pipeline_permute": (st, [vp, vp, vp, sz, ctypes.c_int, i64p, ip]),
+        "rearr_pipeline_reorder": (st, [vp, vp, vp, vp, sz, sz]),
+        "rearr_pipeline_interlace": (st, [vp, vp, ctypes.POINTER(vp), ctypes.c_int, sz, sz]),
+        "rearr_pipeline_deinterlace": (st, [vp, ctypes.POINTER(vp), vp, ctypes.c_int, sz, sz]),
+        "rearr_pipeline_stencil2d_f32": (st, [vp, vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ip, ip,
+                                              ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
+        "rearr_pipeline_sync": (st, [vp]),
+        "rearr_pipeline_stats": (st, [vp, u64p, u64p, u64p]),
+        "rearr_pipeline_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _pipe_bound = True
+    return L
+
+
+def _hptr(x) -> int | None:
+    """Host address of a numpy array, a CPU torch tensor or an int."""
+    if x is None or isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous")
+        return int(x.ctypes.data)
+    if hasattr(x, "data_ptr"):
+        if getattr(x, "is_cuda", False):
+            raise TypeError("pipeline ops take host buffers; got a CUDA tensor")
+        return int(x.data_ptr())
+    raise TypeError(f"cannot take a host pointer from {type(x).__name__}")
+
+
+class Pipeline:
+    """rearr_pipeline_*: ops on HOST buffers, staged through device slots with
+    uploads, kernels and downloads overlapped on three streams."""
+
+    def __init__(self, slot_bytes: int, slots: int = 3):
+        L = _bind_pipeline()
+        h = ctypes.c_void_p()
+        _check(L.rearr_pipeline_create(int(slot_bytes), int(slots), ctypes.byref(h)))
+        self._h = h
+        self._keep = []  # host arrays referenced by queued ops, released at sync
+
+    def permute(self, dst, src, elem_bytes: int, dims: Sequence[int], perm: Sequence[int]) -> None:
+        rank, d, p = _dims_perm(dims, perm)
+        self._keep.append((dst, src))
+        _check(load().rearr_pipeline_permute(self._h, _hptr(dst), _hptr(src), int(elem_bytes), rank, d, p))
+
+    def reorder(self, dst, src, idx, n: int, elem_bytes: int) -> None:
+        self._keep.append((dst, src, idx))
+        _check(load().rearr_pipeline_reorder(self._h, _hptr(dst), _hptr(src), _hptr(idx), int(n), int(elem_bytes)))
+
+    def interlace(self, dst, srcs, n: int, elem_bytes: int) -> None:
+        arr = (ctypes.c_void_p * max(len(srcs), 1))(*[_hptr(x) for x in srcs])
+        self._keep.append((dst, list(srcs)))
+        _check(load().rearr_pipeline_interlace(self._h, _hptr(dst), arr, len(srcs), int(n), int(elem_bytes)))
+
+    def deinterlace(self, dsts, src, n: int, elem_bytes: int) -> None:
+        arr = (ctypes.c_void_p * max(len(dsts), 1))(*[_hptr(x) for x in dsts])
+        self._keep.append((list(dsts), src))
+        _check(load().rearr_pipeline_deinterlace(self._h, arr, _hptr(src), len(dsts), int(n), int(elem_bytes)))
+
+    def stencil2d(self, dst, src, ny: int, nx: int, taps, boundary: int = STENCIL_ZERO) -> None:
+        k, dy, dx, w = _taps(taps)
+        self._keep.append((dst, src))
+        _check(load().rearr_pipeline_stencil2d_f32(self._h, _hptr(dst), _hptr(src), int(ny), int(nx), k, dy, dx, w,
+                                                   int(boundary)))
+
+    def sync(self) -> None:
+        _check(load().rearr_pipeline_sync(self._h))
+        self._keep.clear()
+
+    def stats(self) -> dict:
+        ops, h2d, d2h = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().rearr_pipeline_stats(self._h, ctypes.byref(ops), ctypes.byref(h2d), ctypes.byref(d2h)))
+        return dict(ops=ops.value, h2d_bytes=h2d.value, d2h_bytes=d2h.value)
+
+    def close(self) -> None:
+        if self._h:
+            load().rearr_pipeline_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass

@@ -1,0 +1,132 @@
+"""Host-buffer pipeline (include/librearr_pipeline.h) on the GPU against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth.stencils import fd_laplacian
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lr():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1011_3583_gb300 import build, librearr
+    build.build()
+    librearr.load()
+    return librearr
+
+
+@pytest.fixture(scope="module")
+def orc():
+    return oracle.get()
+
+
+def pinned(nbytes):
+    import torch
+    return torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+
+
+@pytest.mark.parametrize("host", ["pageable", "pinned"])
+def test_mixed_ops_more_ops_than_slots(lr, orc, host):
+    """Ten ops of different kinds and sizes through three slots: every output
+    lands intact (slot reuse waits for the previous download)."""
+    ops = []
+    g = np.random.default_rng(3)
+    for i in range(10):
+        kind = ["permute", "reorder", "interlace", "deinterlace", "stencil"][i % 5]
+        ops.append((kind, i, g))
+    with lr.Pipeline(slot_bytes=8 << 20, slots=3) as pipe:
+        checks = []
+        for kind, i, _ in ops:
+            seed = 100 + i
+            if kind == "permute":
+                dims, perm, e = [37, 64, 29], [2, 0, 1], 4
+                src = synth.random_elements(seed, int(np.prod(dims)), e)
+                dst = np.zeros(src.size, dtype=np.uint8)
+                if host == "pinned":
+                    s_t, d_t = pinned(src.size), pinned(dst.size)
+                    s_t.numpy()[:] = src
+                    pipe.permute(d_t, s_t, e, dims, perm)
+                    checks.append((lambda d_t=d_t: d_t.numpy().copy(), orc.permute(src, e, dims, perm)))
+                else:
+                    pipe.permute(dst, src, e, dims, perm)
+                    checks.append((lambda dst=dst: dst, orc.permute(src, e, dims, perm)))
+            elif kind == "reorder":
+                n, e = 100003, 8
+                src = synth.random_elements(seed, n, e)
+                idx = synth.random_indices(seed, n, n)
+                dst = np.zeros(n * e, dtype=np.uint8)
+                pipe.reorder(dst, src, idx, n, e)
+                checks.append((lambda dst=dst: dst, orc.reorder(src, idx, e)))
+            elif kind == "interlace":
+                n, k, e = 50001, 3, 2
+                planes = [synth.random_elements(seed + j, n, e) for j in range(k)]
+                dst = np.zeros(n * k * e, dtype=np.uint8)
+                pipe.interlace(dst, planes, n, e)
+                checks.append((lambda dst=dst: dst, orc.interlace(planes, n, e)))
+            elif kind == "deinterlace":
+                n, k, e = 40000, 4, 4
+                src = synth.random_elements(seed, n * k, e)
+                outs = [np.zeros(n * e, dtype=np.uint8) for _ in range(k)]
+                pipe.deinterlace(outs, src, n, e)
+                want = orc.deinterlace(src, k, n, e)
+                checks.append((lambda outs=outs: np.concatenate(outs), np.concatenate(want)))
+            else:
+                ny, nx = 300, 260
+                grid = np.random.default_rng(seed).normal(size=(ny, nx)).astype(np.float32)
+                taps = [(dy, dx, float(np.float32(w))) for dy, dx, w in fd_laplacian(2)]
+                out = np.zeros((ny, nx), dtype=np.float32)
+                pipe.stencil2d(out, grid, ny, nx, taps, 1)
+                want = orc.stencil2d(grid, taps, 1)
+                s = orc.stencil2d(np.abs(grid), [(a, b, abs(w)) for a, b, w in taps], 1)
+                tol = (len(taps) + 1) * 2.0 ** -24 * s
+                checks.append((lambda out=out, want=want, tol=tol: np.abs(out.astype(np.float64) - want) <= tol,
+                               np.ones((ny, nx), dtype=bool)))
+        pipe.sync()
+        for i, (got, want) in enumerate(checks):
+            assert np.array_equal(got(), want), ops[i][0]
+        st = pipe.stats()
+        assert st["ops"] == 10 and st["h2d_bytes"] > 0 and st["d2h_bytes"] > 0
+
+
+def test_op_larger_than_a_slot_is_rejected(lr, orc):
+    with lr.Pipeline(slot_bytes=1 << 20, slots=3) as pipe:
+        big = np.zeros(1 << 20, dtype=np.uint8)
+        out = np.zeros_like(big)
+        with pytest.raises(lr.RearrError) as ex:
+            pipe.permute(out, big, 1, [1024, 1024], [1, 0])  # 2 MiB of staging
+        assert ex.value.status == lr.EINVAL
+        # invalid arguments are rejected before anything is enqueued, and the
+        # pipeline stays usable
+        with pytest.raises(lr.RearrError):
+            pipe.permute(out, big, 4, [16, 16], [0, 0])
+        src = synth.random_elements(9, 256 * 128, 4)
+        dst = np.zeros(src.size, dtype=np.uint8)
+        pipe.permute(dst, src, 4, [256, 128], [1, 0])
+        pipe.sync()
+        assert np.array_equal(dst, orc.permute(src, 4, [256, 128], [1, 0]))
+        assert pipe.stats()["ops"] == 1
+
+
+def test_large_ops_stream_through(lr, orc):
+    """Ops of 256 MiB each through three slots (the bench's e2e scale)."""
+    import torch
+    n = 1 << 26
+    e = 4
+    with lr.Pipeline(slot_bytes=2 * n * e + (1 << 20), slots=3) as pipe:
+        src = pinned(n * e)
+        src.numpy()[:] = synth.random_elements(1, n, e)
+        dsts = [pinned(n * e) for _ in range(4)]
+        dims, perms = [512, 256, 512], [[2, 1, 0], [1, 2, 0], [0, 2, 1], [2, 0, 1]]
+        for d, p in zip(dsts, perms):
+            pipe.permute(d, src, e, dims, p)
+        pipe.sync()
+        for d, p in zip(dsts, perms):
+            lin = np.random.default_rng(sum(p)).integers(0, n, size=4096)
+            want = orc.permute_sample(src.numpy(), e, dims, p, lin)
+            got = d.numpy().view(np.uint32)[lin].view(np.uint8)
+            assert np.array_equal(got, want), p
+    del torch

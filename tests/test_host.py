@@ -50,6 +50,14 @@ def test_exports_every_declared_symbol(lr):
     assert not missing, missing
 
 
+def test_pipeline_rejects_invalid_before_cuda(lr):
+    from paper_1011_3583_gb300 import librearr
+    for slot_bytes, slots in ((1 << 20, 0), (1 << 20, 9), (0, 3)):
+        with pytest.raises(librearr.RearrError) as ex:
+            librearr.Pipeline(slot_bytes, slots)
+        assert ex.value.status == librearr.EINVAL
+
+
 def test_status_strings(lr):
     assert [lr.status_str(i) for i in range(7)] == [
         "REARR_OK", "REARR_EINVAL", "REARR_ENOMEM", "REARR_ECUDA", "REARR_ERANGE", "REARR_ETIMEDOUT", "REARR_EBUSY"]
