@@ -819,6 +819,80 @@ def run_case(args):
             "gbs_best": round(nbytes / min(times) / 1e9, 1), "plan": plan, "steps": args.steps}
 
 
+def _time_calls(torch, stream, call, steps, warmup, flush=None):
+    """Per-call CUDA-event times on `stream`; `flush` (untimed) runs before each."""
+    for _ in range(warmup):
+        call()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        if flush is not None:
+            flush()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        call()
+        s1.record(stream)
+        s1.synchronize()
+        ts.append(s0.elapsed_time(s1) / 1e3)
+    return statistics.median(ts), min(ts)
+
+
+def run_configs(args):
+    """The single-op configs beside the bench step: the 1024^2 fp32 transpose
+    (warm and L2-flushed) and every interlace / de-interlace case of the
+    interlace config, each against a device copy of the same bytes timed the
+    same way.  GB/s counts bytes read + bytes written."""
+    import torch
+    from paper_1011_3583_gb300 import build as rbuild
+    rbuild.build()
+    import paper_1011_3583_gb300 as rr
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def flush():
+        with torch.cuda.stream(stream):
+            flush_buf.fill_(1)
+
+    out = []
+
+    def record(name, nbytes_moved, call, copy_bytes, flushed):
+        fl = flush if flushed else None
+        med, best = _time_calls(torch, stream, call, args.steps, args.warmup, fl)
+        a = torch.empty(copy_bytes, dtype=torch.uint8, device=dev)
+        b = torch.empty_like(a)
+        cmed, _ = _time_calls(torch, stream, lambda: rr.memcpy_d2d(b, a, copy_bytes, stream), args.steps,
+                              args.warmup, fl)
+        del a, b
+        out.append({"config": name, "l2": "flushed" if flushed else "warm", "bytes": nbytes_moved,
+                    "median_us": round(med * 1e6, 2), "best_us": round(best * 1e6, 2),
+                    "gbs": round(nbytes_moved / med / 1e9, 1), "memcpy_gbs": round(2 * copy_bytes / cmed / 1e9, 1),
+                    "frac_of_memcpy": round((nbytes_moved / med) / (2 * copy_bytes / cmed), 3)})
+
+    # config 1: one 1024 x 1024 fp32 transpose
+    n = 1024 * 1024 * 4
+    src = torch.empty(n, dtype=torch.uint8, device=dev).random_()
+    dst = torch.empty_like(src)
+    for flushed in (False, True):
+        record("transpose 1024x1024 fp32", 2 * n, lambda: rr.permute(dst, src, 4, [1024, 1024], [1, 0], stream), n,
+               flushed)
+    del src, dst
+    # interlace config: complex split, image planes, AoS/SoA
+    cases = [("complex64 2^28 <-> 2 fp32 planes", 4, 1 << 28, 2)] + \
+            [(f"4096^2 uint8 x {k} planes", 1, 4096 * 4096, k) for k in (3, 4)] + \
+            [(f"AoS/SoA 2^26 records x {k} fp32", 4, 1 << 26, k) for k in (2, 3, 4, 8)]
+    for name, e, n, k in cases:
+        planes = [torch.empty(n * e, dtype=torch.uint8, device=dev).random_() for _ in range(k)]
+        inter = torch.empty(n * k * e, dtype=torch.uint8, device=dev).random_()
+        flushed = n * k * e < (256 << 20)  # comparable to L2: flush
+        record(name + " interlace", 2 * n * k * e, lambda: rr.interlace(inter, planes, n, e, stream), n * k * e,
+               flushed)
+        record(name + " de-interlace", 2 * n * k * e, lambda: rr.deinterlace(planes, inter, n, e, stream),
+               n * k * e, flushed)
+        del planes, inter
+    return {"configs": out, "steps": args.steps, "warmup": args.warmup, "timing": "CUDA events per call"}
+
+
 def run_batch_case(torch, rr, stream, dev, n_ops, args):
     """batch:N -- the first N ops of the uneven mix as one plan, replayed."""
     import synth
@@ -857,9 +931,13 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--case", default=None, help="time one op instead of the workload (see parse_case)")
+    ap.add_argument("--configs", action="store_true", help="time the single-op configs (transpose, interlace)")
     args = ap.parse_args()
     if args.case:
         print(json.dumps(run_case(args)), flush=True)
+        return
+    if args.configs:
+        print(json.dumps(run_configs(args)), flush=True)
         return
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

@@ -133,6 +133,23 @@ rearr_status rearr_scatter64(void *dst, const void *src, const uint64_t *idx, si
                              size_t elem_bytes, rearr_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Checked index sequences.  The reorders above leave an out-of-range index
+ * undefined (the fast path does not test it).  The checked forms test every
+ * index on the device first:
+ *   rearr_check_indices   : *n_bad = number of the n entries of idx (idx_bytes
+ *                           4 or 8, aligned to it) that are >= bound.  Waits for
+ *                           its kernel on `stream` (synchronous).
+ *   rearr_reorder_checked : rearr_reorder after that check; REARR_ERANGE, with
+ *                           dst untouched and nothing launched after the check,
+ *                           if any idx[i] >= n.  Waits for the check only; the
+ *                           reorder itself is asynchronous as usual.
+ * ------------------------------------------------------------------------- */
+rearr_status rearr_check_indices(const void *idx, size_t n, int idx_bytes, uint64_t bound, uint64_t *n_bad,
+                                 rearr_stream_t stream);
+rearr_status rearr_reorder_checked(void *dst, const void *src, const uint32_t *idx, size_t n,
+                                   size_t elem_bytes, rearr_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * rearr_interlace -- join k arrays into one interlaced array
  * (arXiv:1011.3583 Sec. III.C, Table 3):
  *       dst[i*k + j] = srcs[j][i],  0 <= i < n, 0 <= j < k.

@@ -7,5 +7,5 @@ from .librearr import (  # noqa: F401
     MAX_K, MAX_RANK, Plan, PermuteInfo, RearrError, deinterlace, describe_permute, interlace, launch_count,
     lib_path, load, memcpy_d2d, permute, reorder, reorder64, reorder_nm, scatter, scatter64, selftest_host,
     status_str, STENCIL_CLAMP, STENCIL_ZERO, describe_stencil, stencil2d, wait_timeouts, inject_wait_timeout,
-    Pipeline,
+    Pipeline, check_indices, reorder_checked, ERANGE,
 )

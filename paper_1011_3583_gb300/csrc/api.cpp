@@ -114,6 +114,39 @@ rearr_status rearr_scatter64(void *dst, const void *src, const uint64_t *idx, si
     return indexed_call("rearr_scatter64", dst, src, idx, n, elem_bytes, 8, true, stream);
 }
 
+rearr_status rearr_check_indices(const void *idx, size_t n, int idx_bytes, uint64_t bound, uint64_t *n_bad,
+                                 rearr_stream_t stream)
+{
+    if (!n_bad) return fail(REARR_EINVAL, "rearr_check_indices: n_bad is NULL");
+    *n_bad = 0;
+    if (idx_bytes != 4 && idx_bytes != 8) return fail(REARR_EINVAL, "rearr_check_indices: idx_bytes must be 4 or 8");
+    if (n == 0) return REARR_OK;
+    if (!idx) return fail(REARR_EINVAL, "rearr_check_indices: idx is NULL");
+    if (reinterpret_cast<uintptr_t>(idx) % uintptr_t(idx_bytes) != 0)
+        return fail(REARR_EINVAL, "rearr_check_indices: idx not aligned to its index size");
+    cudaError_t e = count_bad_indices(idx, n, idx_bytes, bound, n_bad, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "rearr_check_indices");
+    return REARR_OK;
+}
+
+rearr_status rearr_reorder_checked(void *dst, const void *src, const uint32_t *idx, size_t n, size_t elem_bytes,
+                                   rearr_stream_t stream)
+{
+    OpDesc op;
+    std::string err;
+    rearr_status st = plan_reorder(dst, src, idx, n, elem_bytes, op, err);
+    if (st != REARR_OK) return fail(st, "rearr_reorder_checked: " + err);
+    if (op.units == 0) return REARR_OK;
+    uint64_t bad = 0;
+    cudaError_t e = count_bad_indices(idx, n, 4, n, &bad, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "rearr_reorder_checked: index check");
+    if (bad) return fail(REARR_ERANGE, "rearr_reorder_checked: " + std::to_string(bad) + " of " + std::to_string(n) +
+                                           " indices are >= n");
+    e = launch_single(op, nullptr, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "rearr_reorder_checked launch");
+    return REARR_OK;
+}
+
 rearr_status rearr_interlace(void *dst, const void *const *srcs, int k, size_t n, size_t elem_bytes,
                              rearr_stream_t stream)
 {

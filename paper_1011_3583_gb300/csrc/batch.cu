@@ -76,11 +76,12 @@ __device__ __noinline__ void igen_range(const InterlaceDesc &d, uint64_t u0, uin
 }
 
 template <int E, int K>
-__device__ __noinline__ void ifast_range(const InterlaceDesc &d, uint64_t u0, uint64_t u1, uint64_t n, bool inter)
+__device__ __noinline__ void ifast_range(const InterlaceDesc &d, uint64_t u0, uint64_t u1, uint64_t n, bool inter,
+                                         unsigned char *smem)
 {
     for (uint64_t u = u0; u < u1; ++u) {
-        if (inter) interlace_fast_body<E, K>(d, planes_of(d), u, n);
-        else deinterlace_fast_body<E, K>(d, planes_of(d), u, n);
+        if (inter) interlace_fast_body<E, K>(d, planes_of(d), u, n, smem);
+        else deinterlace_fast_body<E, K>(d, planes_of(d), u, n, smem);
     }
 }
 
@@ -116,14 +117,14 @@ __device__ __forceinline__ void run_word_class(const OpDesc &d, uint64_t u0, uin
 }
 
 template <int E>
-__device__ __forceinline__ void run_inter_fast(const OpDesc &d, uint64_t u0, uint64_t u1)
+__device__ __forceinline__ void run_inter_fast(const OpDesc &d, uint64_t u0, uint64_t u1, unsigned char *smem)
 {
     const bool inter = d.cls == OC_INTERLACE;
     switch (d.inter.k) {
-        case 1: ifast_range<E, 1>(d.inter, u0, u1, d.units, inter); return;
-        case 2: ifast_range<E, 2>(d.inter, u0, u1, d.units, inter); return;
-        case 3: ifast_range<E, 3>(d.inter, u0, u1, d.units, inter); return;
-        case 4: ifast_range<E, 4>(d.inter, u0, u1, d.units, inter); return;
+        case 1: ifast_range<E, 1>(d.inter, u0, u1, d.units, inter, smem); return;
+        case 2: ifast_range<E, 2>(d.inter, u0, u1, d.units, inter, smem); return;
+        case 3: ifast_range<E, 3>(d.inter, u0, u1, d.units, inter, smem); return;
+        case 4: ifast_range<E, 4>(d.inter, u0, u1, d.units, inter, smem); return;
         default: return;
     }
 }
@@ -134,11 +135,11 @@ __device__ __forceinline__ void run_range(const OpDesc &d, uint64_t u0, uint64_t
     if (d.cls == OC_TILE) { run_tile_fast(d, u0, u1, smem); return; }
     if ((d.cls == OC_INTERLACE || d.cls == OC_DEINTERLACE) && d.inter.fast) {
         switch (d.inter.elem_bytes) {
-            case 1: run_inter_fast<1>(d, u0, u1); return;
-            case 2: run_inter_fast<2>(d, u0, u1); return;
-            case 4: run_inter_fast<4>(d, u0, u1); return;
-            case 8: run_inter_fast<8>(d, u0, u1); return;
-            case 16: run_inter_fast<16>(d, u0, u1); return;
+            case 1: run_inter_fast<1>(d, u0, u1, smem); return;
+            case 2: run_inter_fast<2>(d, u0, u1, smem); return;
+            case 4: run_inter_fast<4>(d, u0, u1, smem); return;
+            case 8: run_inter_fast<8>(d, u0, u1, smem); return;
+            case 16: run_inter_fast<16>(d, u0, u1, smem); return;
             default: return;
         }
     }
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch(const OpDesc *__restrict_
                                                        const uint64_t *__restrict__ prefix, int n_ops,
                                                        unsigned long long *counter, uint32_t grab)
 {
-    __shared__ __align__(16) unsigned char smem[kSmemBytes];
+    __shared__ __align__(16) unsigned char smem[kSmemBytes > kInterStageBytes ? kSmemBytes : kInterStageBytes];
     __shared__ unsigned long long s_start;
     const uint64_t total = prefix[n_ops];
     for (;;) {

@@ -531,49 +531,106 @@ __device__ __forceinline__ void interlace_tail(const InterlaceDesc &d, char *con
     }
 }
 
+// Fast interlace / de-interlace.  A warp handles 32 consecutive 16-byte groups
+// per step, one per lane, reading (interlace) or writing (de-interlace) one
+// 16-byte vector per plane per lane -- 512 contiguous bytes per instruction on
+// every plane.  The interlaced side of those 32 groups is K * 512 contiguous
+// bytes; it goes through a per-warp staging area in shared memory, so that it
+// too is moved 512 contiguous bytes per instruction (a lane's own K chunks
+// are K * 16 bytes apart from its neighbours', which would touch 32 lines per
+// instruction).  Chunk x of lane l sits at stage_pos<K>(l, x): a bijection on
+// the K * 32 chunks, skewed so that neither the lane-major nor the
+// chunk-major access has a shared-memory bank conflict (K = 6: the
+// chunk-major side keeps a few two-way conflicts).
+template <int K>
+__device__ __forceinline__ int stage_pos(int l, int x)
+{
+    if constexpr (K > 1 && (K & (K - 1)) == 0) return l * K + (x ^ ((l / (8 / K)) & (K - 1)));
+    else if constexpr (K == 6) return l * K + (x + ((l >> 2) & 1)) % K;
+    else return l * K + x;
+}
+
 template <int E, int K>
 __device__ __forceinline__ void interlace_fast_body(const InterlaceDesc &d, char *const *planes, uint64_t unit,
-                                                    uint64_t n_units)
+                                                    uint64_t n_units, unsigned char *smem)
 {
     const uint64_t groups = d.n * E / 16;
     const uint64_t g0 = unit * d.unit_groups;
     const uint64_t g1 = min(groups, g0 + d.unit_groups);
-    for (uint64_t g = g0 + tid_x(); g < g1; g += kThreads) {
-        uint32_t in[K][4], out[K * 4];
+    const int tid = tid_x(), lane = tid & 31, warp = tid >> 5;
+    uint4 *stage = reinterpret_cast<uint4 *>(smem) + warp * K * 32;
+    for (uint64_t gw = g0 + uint64_t(warp) * 32; gw < g1; gw += kThreads) {
+        const uint64_t g = gw + lane;
+        if (g < g1) {
+            uint32_t in[K][4], out[K * 4];
 #pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const uint4 v = ldg_stream<16>(planes[j] + g * 16);
-            in[j][0] = v.x; in[j][1] = v.y; in[j][2] = v.z; in[j][3] = v.w;
+            for (int j = 0; j < K; ++j) {
+                const uint4 v = ldg_stream<16>(planes[j] + g * 16);
+                in[j][0] = v.x; in[j][1] = v.y; in[j][2] = v.z; in[j][3] = v.w;
+            }
+            interleave_regs<E, K>(in, out);
+#pragma unroll
+            for (int x = 0; x < K; ++x)
+                stage[stage_pos<K>(lane, x)] = make_uint4(out[4 * x], out[4 * x + 1], out[4 * x + 2], out[4 * x + 3]);
         }
-        interleave_regs<E, K>(in, out);
-        char *o = d.inter + g * 16 * K;
+        __syncwarp();
+        const uint32_t nq = uint32_t(min(uint64_t(32), g1 - gw)) * K;  // chunks of this warp's groups
+        char *o = d.inter + gw * 16 * K;
 #pragma unroll
-        for (int x = 0; x < K; ++x)
-            stg<16>(o + 16 * x, make_uint4(out[4 * x], out[4 * x + 1], out[4 * x + 2], out[4 * x + 3]));
+        for (int sidx = 0; sidx < K; ++sidx) {
+            const uint32_t q = uint32_t(sidx) * 32 + lane;
+            const uint32_t t = q / K, x = q - t * K;
+            if (q < nq) stg<16>(o + uint64_t(q) * 16, stage[stage_pos<K>(int(t), int(x))]);
+        }
+        __syncwarp();
     }
+    // Every warp is done with its staging before the CTA's next body (in the
+    // batched kernel another op's body) writes shared memory.
+    __syncthreads();
     if (unit == n_units - 1 && groups * 16 / E < d.n) interlace_tail<E>(d, planes, groups * 16 / E, true);
 }
 
 template <int E, int K>
 __device__ __forceinline__ void deinterlace_fast_body(const InterlaceDesc &d, char *const *planes, uint64_t unit,
-                                                      uint64_t n_units)
+                                                      uint64_t n_units, unsigned char *smem)
 {
     const uint64_t groups = d.n * E / 16;
     const uint64_t g0 = unit * d.unit_groups;
     const uint64_t g1 = min(groups, g0 + d.unit_groups);
-    for (uint64_t g = g0 + tid_x(); g < g1; g += kThreads) {
-        uint32_t in[K * 4], out[K][4];
-        const char *s = d.inter + g * 16 * K;
+    const int tid = tid_x(), lane = tid & 31, warp = tid >> 5;
+    uint4 *stage = reinterpret_cast<uint4 *>(smem) + warp * K * 32;
+    for (uint64_t gw = g0 + uint64_t(warp) * 32; gw < g1; gw += kThreads) {
+        const uint32_t nq = uint32_t(min(uint64_t(32), g1 - gw)) * K;
+        const char *src = d.inter + gw * 16 * K;
+        uint4 v[K];
 #pragma unroll
-        for (int x = 0; x < K; ++x) {
-            const uint4 v = ldg_stream<16>(s + 16 * x);
-            in[4 * x] = v.x; in[4 * x + 1] = v.y; in[4 * x + 2] = v.z; in[4 * x + 3] = v.w;
+        for (int sidx = 0; sidx < K; ++sidx) {
+            const uint32_t q = uint32_t(sidx) * 32 + lane;
+            if (q < nq) v[sidx] = ldg_stream<16>(src + uint64_t(q) * 16);
         }
-        deinterleave_regs<E, K>(in, out);
 #pragma unroll
-        for (int j = 0; j < K; ++j)
-            stg<16>(planes[j] + g * 16, make_uint4(out[j][0], out[j][1], out[j][2], out[j][3]));
+        for (int sidx = 0; sidx < K; ++sidx) {
+            const uint32_t q = uint32_t(sidx) * 32 + lane;
+            const uint32_t t = q / K, x = q - t * K;
+            if (q < nq) stage[stage_pos<K>(int(t), int(x))] = v[sidx];
+        }
+        __syncwarp();
+        const uint64_t g = gw + lane;
+        if (g < g1) {
+            uint32_t in[K * 4], out[K][4];
+#pragma unroll
+            for (int x = 0; x < K; ++x) {
+                const uint4 w = stage[stage_pos<K>(lane, x)];
+                in[4 * x] = w.x; in[4 * x + 1] = w.y; in[4 * x + 2] = w.z; in[4 * x + 3] = w.w;
+            }
+            deinterleave_regs<E, K>(in, out);
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                stg<16>(planes[j] + g * 16, make_uint4(out[j][0], out[j][1], out[j][2], out[j][3]));
+        }
+        __syncwarp();
     }
+    __syncthreads();  // staging free for the CTA's next body
     if (unit == n_units - 1 && groups * 16 / E < d.n) interlace_tail<E>(d, planes, groups * 16 / E, false);
 }
 

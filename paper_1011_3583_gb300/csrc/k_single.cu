@@ -54,9 +54,10 @@ struct InterlaceParams {
 template <int E, int K, bool INTER>
 __global__ void __launch_bounds__(kThreads) k_inter_fast(const __grid_constant__ InterlaceParams p, uint64_t n)
 {
+    __shared__ __align__(16) unsigned char smem[kThreads / 32 * K * 32 * 16];
     for (uint64_t u = blockIdx.x; u < n; u += gridDim.x) {
-        if constexpr (INTER) interlace_fast_body<E, K>(p.d, p.planes, u, n);
-        else deinterlace_fast_body<E, K>(p.d, p.planes, u, n);
+        if constexpr (INTER) interlace_fast_body<E, K>(p.d, p.planes, u, n, smem);
+        else deinterlace_fast_body<E, K>(p.d, p.planes, u, n, smem);
     }
 }
 

@@ -19,4 +19,9 @@ cudaError_t launch_single(const OpDesc &op, char *const *planes_all, cudaStream_
 // The L2-resident bucketed reorder (k_reorder_l2.cu) of a gather op with l2 set.
 cudaError_t launch_reorder_l2(const OpDesc &op, cudaStream_t s);
 
+// Number of the n indices (idx_bytes 4 or 8) that are >= bound, counted on the
+// device; waits for the count on stream s (k_check.cu).
+cudaError_t count_bad_indices(const void *idx, size_t n, int idx_bytes, uint64_t bound, uint64_t *n_bad,
+                              cudaStream_t s);
+
 }  // namespace rearr

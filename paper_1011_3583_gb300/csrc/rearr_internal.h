@@ -21,6 +21,7 @@ constexpr int kThreads = 256;  // threads per CTA of every tile kernel
 constexpr int kTileBytes = 16384;               // payload of one fast tile
 constexpr int kCellSmemBytes = 16384 + 4096;    // cells tile incl. padding
 constexpr int kSmemBytes = 20480;               // smem of any tile body
+constexpr int kInterStageBytes = kThreads / 32 * 8 * 32 * 16;  // interlace staging: K <= 8 chunks x 32 lanes per warp
 constexpr int kMaxRunsPerUnit = 256;            // run offsets staged in smem
 
 // Unsigned 32-bit division by a run-time invariant divisor with one

@@ -119,6 +119,8 @@ def load() -> ctypes.CDLL:
                                           ctypes.c_size_t, ctypes.POINTER(StencilInfo)]),
         "rearr_wait_timeouts": (st, [ctypes.POINTER(ctypes.c_uint64)]),
         "rearr_inject_wait_timeout": (st, [ctypes.c_int]),
+        "rearr_check_indices": (st, [vp, sz, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), vp]),
+        "rearr_reorder_checked": (st, [vp, vp, vp, sz, sz, vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -241,6 +243,18 @@ def inject_wait_timeout(n_launches: int) -> None:
 def reorder(dst, src, idx, n: int, elem_bytes: int, stream=None) -> None:
     """rearr_reorder: dst[i] = src[idx[i]]."""
     _check(load().rearr_reorder(_ptr(dst), _ptr(src), _ptr(idx), int(n), int(elem_bytes), _stream(stream)))
+
+
+def check_indices(idx, n: int, idx_bytes: int, bound: int, stream=None) -> int:
+    """rearr_check_indices: how many of the n indices are >= bound (synchronous)."""
+    v = ctypes.c_uint64()
+    _check(load().rearr_check_indices(_ptr(idx), int(n), int(idx_bytes), int(bound), ctypes.byref(v), _stream(stream)))
+    return int(v.value)
+
+
+def reorder_checked(dst, src, idx, n: int, elem_bytes: int, stream=None) -> None:
+    """rearr_reorder_checked: rearr_reorder after a device check of every index (REARR_ERANGE if any >= n)."""
+    _check(load().rearr_reorder_checked(_ptr(dst), _ptr(src), _ptr(idx), int(n), int(elem_bytes), _stream(stream)))
 
 
 def scatter(dst, src, idx, n: int, elem_bytes: int, stream=None) -> None:

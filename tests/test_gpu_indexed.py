@@ -122,3 +122,47 @@ def test_scatter_large_repeats_are_valid(lr):
     targeted[idx] = True
     assert np.all(got[~targeted] == 0xFFFFFFFF)
     assert np.all(idx[got[targeted]] == np.flatnonzero(targeted))
+
+
+@pytest.mark.parametrize("idx_bytes", [4, 8])
+@pytest.mark.parametrize("off", [0, 4, 8])
+def test_check_indices_counts_exactly(lr, idx_bytes, off):
+    if idx_bytes == 8 and off % 8:
+        pytest.skip("8-byte indices must be 8-byte aligned")
+    g = np.random.default_rng(idx_bytes + off)
+    for n in (1, 3, 1000, 65537, (1 << 20) + 5):
+        bound = n
+        dt = np.uint32 if idx_bytes == 4 else np.uint64
+        idx = g.integers(0, n, size=n).astype(dt)
+        k = int(g.integers(0, min(n, 50) + 1))
+        pos = g.choice(n, size=k, replace=False) if k else np.array([], dtype=np.int64)
+        big = (2 ** 32 + 7) if idx_bytes == 8 else (2 ** 32 - 1)
+        idx[pos] = g.integers(n, big, size=k).astype(dt) if k else idx[pos]
+        ix = to_dev(idx, off)
+        assert lr.check_indices(ix.ptr, n, idx_bytes, bound) == int((idx.astype(np.uint64) >= bound).sum())
+
+
+def test_reorder_checked(lr, orc):
+    n, e = 100003, 4
+    src = synth.random_elements(7, n, e)
+    idx = synth.random_indices(8, n, n)
+    got = run(lr, lr.reorder_checked, src, idx, e, n, fill=0x5A)
+    assert np.array_equal(got, orc.reorder(src, idx, e))
+    bad = idx.copy()
+    bad[[0, 777, n - 1]] = [n, n + 5, 2 ** 32 - 1]
+    with pytest.raises(lr.RearrError) as ex:
+        run(lr, lr.reorder_checked, src, bad, e, n, fill=0x5A)
+    assert ex.value.status == lr.ERANGE and "3 of" in str(ex.value)
+
+
+def test_reorder_checked_leaves_dst_untouched(lr):
+    n, e = 4096, 8
+    src = synth.random_elements(9, n, e)
+    idx = synth.random_indices(10, n, n)
+    idx[100] = n
+    s, ix = to_dev(src), to_dev(idx)
+    d = DevBuf(n * e, 0, fill=0x33)
+    with pytest.raises(lr.RearrError):
+        lr.reorder_checked(d.ptr, s.ptr, ix.ptr, n, e)
+    sync()
+    assert np.all(d.download() == 0x33)

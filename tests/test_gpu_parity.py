@@ -319,6 +319,33 @@ def test_batch_equals_single_calls(lr, orc):
     plan.close()
 
 
+def test_batch_interlace_next_to_shared_memory_bodies(lr, orc):
+    """Staged interlaces (k <= 4, 16-byte groups) alternating with runs and
+    tile permutes: in one grab a CTA runs a staged interlace and then a body
+    that fills shared memory (run offsets, tiles).  Every output must match."""
+    ops = []
+    for i in range(240):
+        if i % 3 == 0:
+            ops.append(dict(kind="interlace" if i % 2 else "deinterlace", elem_bytes=4, k=2 + i % 3,
+                            n=1024 + 4 * (i % 7), data_seed=i))
+        elif i % 3 == 1:
+            ops.append(dict(kind="permute", elem_bytes=4, dims=[3 + i % 5, 9, 64], perm=[1, 0, 2], data_seed=i))
+        else:
+            ops.append(dict(kind="permute", elem_bytes=4, dims=[40, 33 + i % 4], perm=[1, 0], data_seed=i))
+    bufs = [make_op_buffers(op) for op in ops]
+    plan = lr.Plan()
+    for op, b in zip(ops, bufs):
+        add_to_plan(plan, op, b)
+    plan.finalize()
+    for rep in range(3):
+        plan.run()
+        sync()
+        for i, (op, b) in enumerate(zip(ops, bufs)):
+            for w, g in zip(oracle_of(orc, op, b), outputs_of(op, b)):
+                assert np.array_equal(g, w), (rep, i, op)
+    plan.close()
+
+
 def test_batch_many_planes(lr, orc):
     op = dict(kind="interlace", elem_bytes=4, k=12, n=333, data_seed=3)
     op2 = dict(kind="deinterlace", elem_bytes=2, k=9, n=1001, data_seed=4)

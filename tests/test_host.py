@@ -58,6 +58,15 @@ def test_pipeline_rejects_invalid_before_cuda(lr):
         assert ex.value.status == librearr.EINVAL
 
 
+def test_check_indices_validation(lr):
+    from paper_1011_3583_gb300 import librearr
+    for args in ((FAKE_SRC, 16, 3, 16), (None, 16, 4, 16), (FAKE_SRC + 4, 16, 8, 16)):
+        with pytest.raises(librearr.RearrError) as ex:
+            librearr.check_indices(*args)
+        assert ex.value.status == librearr.EINVAL
+    assert librearr.check_indices(None, 0, 4, 0) == 0
+
+
 def test_status_strings(lr):
     assert [lr.status_str(i) for i in range(7)] == [
         "REARR_OK", "REARR_EINVAL", "REARR_ENOMEM", "REARR_ECUDA", "REARR_ERANGE", "REARR_ETIMEDOUT", "REARR_EBUSY"]
