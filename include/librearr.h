@@ -331,7 +331,11 @@ typedef enum {
     REARR_KIND_COPY = 1,        /* contiguous copy (identity after collapsing)  */
     REARR_KIND_TILE = 2,        /* shared-memory tiled transpose, 1 word/cell   */
     REARR_KIND_TILE_CELLS = 3,  /* tiled transpose of multi-word cells          */
-    REARR_KIND_RUNS = 4         /* copy of long contiguous runs                 */
+    REARR_KIND_RUNS = 4,        /* copy of long contiguous runs                 */
+    REARR_KIND_STRIDED = 5      /* element-wise strided copy: a transpose plane
+                                   too small to fill tiles (by default under
+                                   1 KB of payload, or for ops up to 32 MiB
+                                   under 1024 cells, per tile on average)    */
 } rearr_kind;
 
 typedef struct {
@@ -356,8 +360,9 @@ rearr_status rearr_permute_describe(size_t elem_bytes, int rank, const int64_t *
 /* ---------------------------------------------------------------------------
  * Tuning table.  The paper chooses block and thread shapes per kernel by hand
  * (Sec. III); here the fast tile's staged row length per (element size,
- * plane-extent class) and the batched kernel's work grab come from a text
- * table written by the project's autotuner.  rearr_tuning_load reads such a
+ * plane-extent class), the batched kernel's work grab and the thin-plane
+ * thresholds of the strided copy come from a text table written by the
+ * project's autotuner.  rearr_tuning_load reads such a
  * table (path NULL or "": built-in defaults) for plans compiled afterwards;
  * REARR_EINVAL if the file cannot be read (the previous table stays).  The
  * REARR_TUNE_TABLE environment variable names a table read on first use.

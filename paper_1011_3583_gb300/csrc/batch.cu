@@ -64,6 +64,12 @@ __device__ __noinline__ void copy_range(const CopyDesc &d, uint64_t u0, uint64_t
 }
 
 template <int W>
+__device__ __noinline__ void strided_range(const StridedDesc &d, uint64_t u0, uint64_t u1)
+{
+    for (uint64_t u = u0; u < u1; ++u) strided_body<W>(d, u);
+}
+
+template <int W>
 __device__ __noinline__ void gather_range(const GatherDesc &d, uint64_t u0, uint64_t u1)
 {
     for (uint64_t u = u0; u < u1; ++u) gather_body<W>(d, u);
@@ -109,6 +115,7 @@ __device__ __forceinline__ void run_word_class(const OpDesc &d, uint64_t u0, uin
         case OC_TILE_CELLS: cells_range<W>(d.tile, uint32_t(u0), uint32_t(u1), smem); return;
         case OC_RUNS: runs_range<W>(d.runs, u0, u1, smem); return;
         case OC_COPY: copy_range<W>(d.copy, u0, u1); return;
+        case OC_STRIDED: strided_range<W>(d.strided, u0, u1); return;
         case OC_GATHER: gather_range<W>(d.gather, u0, u1); return;
         case OC_INTERLACE: igen_range<W>(d.inter, u0, u1, true); return;
         case OC_DEINTERLACE: igen_range<W>(d.inter, u0, u1, false); return;
@@ -208,9 +215,11 @@ struct rearr_plan {
     int grid = 0;
 };
 
-static rearr_status add_op(rearr_plan *p, const OpDesc &op, std::vector<char *> planes = {})
+static rearr_status add_op(rearr_plan *p, const OpDesc &op_in, std::vector<char *> planes = {})
 {
-    if (op.units == 0) return REARR_OK;
+    if (op_in.units == 0) return REARR_OK;
+    OpDesc op = op_in;
+    batch_form(op);
     p->ops.push_back(op);
     p->plane_lists.push_back(std::move(planes));
     return REARR_OK;
@@ -285,20 +294,6 @@ static rearr_status plan_add_inter(rearr_plan *plan, bool inter, char *iv, char 
     rearr_status st = plan_interlace(inter, iv, planes, k, n, elem_bytes, pl, err);
     if (st != REARR_OK) return fail(st, std::string(who) + ": " + err);
     if (pl.op.units == 0) return REARR_OK;
-    // The batched kernel instantiates the 16-byte group bodies for k <= 4 only.
-    if (pl.op.inter.fast && pl.op.inter.k > 4) {
-        const uint64_t al = 16;
-        const int W = pow2_align(al, elem_bytes);
-        InterlaceDesc &d = pl.op.inter;
-        d.fast = 0;
-        pl.op.word = uint32_t(W);
-        d.c = uint32_t(elem_bytes / W);
-        const uint64_t kc = uint64_t(k) * d.c;
-        d.unit_groups = std::max<uint64_t>(1, 8192 / kc);
-        d.kc_div = make_fastdiv(uint32_t(kc));
-        d.c_div = make_fastdiv(d.c);
-        pl.op.units = (uint64_t(n) + d.unit_groups - 1) / d.unit_groups;
-    }
     std::vector<char *> lst;
     if (k > kInlineK) lst = pl.planes;
     return add_op(plan, pl.op, std::move(lst));
@@ -546,6 +541,31 @@ extern "C" rearr_status rearr_batch_noalloc(const rearr_plan *plan, rearr_stream
 // Work lists built and launched from host code (serving loop).
 
 namespace rearr {
+
+void batch_form(OpDesc &op)
+{
+    if ((op.cls == OC_INTERLACE || op.cls == OC_DEINTERLACE) && op.inter.fast && op.inter.k > 4) {
+        // The batched kernel instantiates the 16-byte group bodies for k <= 4
+        // only: larger k runs the generic body (the fast path implies a
+        // power-of-two element of at most 16 bytes on 16-byte aligned planes).
+        InterlaceDesc &d = op.inter;
+        const int W = pow2_align(16, d.elem_bytes);
+        d.fast = 0;
+        op.word = uint32_t(W);
+        d.c = d.elem_bytes / uint32_t(W);
+        const uint64_t kc = uint64_t(d.k) * d.c;
+        d.unit_groups = std::max<uint64_t>(1, 8192 / kc);
+        d.kc_div = make_fastdiv(uint32_t(kc));
+        d.c_div = make_fastdiv(d.c);
+        op.units = (d.n + d.unit_groups - 1) / d.unit_groups;
+    }
+    if (op.cls == OC_GATHER && op.units > 0) {
+        // one iteration of gather_body per unit: 4 elements x 2 groups per
+        // thread (vector path) or 4 elements per thread
+        op.gather.unit_elems = op.gather.vec ? uint32_t(kThreads) * 8 : uint32_t(kThreads) * 4;
+        op.units = (op.gather.n + op.gather.unit_elems - 1) / op.gather.unit_elems;
+    }
+}
 
 WorklistLayout worklist_layout(size_t n_ops, size_t n_ptrs)
 {

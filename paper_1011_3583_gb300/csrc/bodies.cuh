@@ -352,6 +352,26 @@ __device__ __forceinline__ void store4(char *p, const typename Word<W>::T (&v)[4
     }
 }
 
+// store4 with an L2 policy on every store.
+template <int W>
+__device__ __forceinline__ void store4_hint(char *p, const typename Word<W>::T (&v)[4], uint64_t pol)
+{
+    if constexpr (W == 1) {
+        stg_hint<4>(p, uint32_t(v[0]) | (uint32_t(v[1]) << 8) | (uint32_t(v[2]) << 16) | (uint32_t(v[3]) << 24), pol);
+    } else if constexpr (W == 2) {
+        stg_hint<8>(p, make_uint2(uint32_t(v[0]) | (uint32_t(v[1]) << 16), uint32_t(v[2]) | (uint32_t(v[3]) << 16)),
+                    pol);
+    } else if constexpr (W == 4) {
+        stg_hint<16>(p, make_uint4(v[0], v[1], v[2], v[3]), pol);
+    } else if constexpr (W == 8) {
+        stg_hint<16>(p, make_uint4(v[0].x, v[0].y, v[1].x, v[1].y), pol);
+        stg_hint<16>(p + 16, make_uint4(v[2].x, v[2].y, v[3].x, v[3].y), pol);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) stg_hint<16>(p + 16 * k, v[k], pol);
+    }
+}
+
 // Four consecutive W-byte words from an address aligned to min(16, 4W).
 template <int W>
 __device__ __forceinline__ void load4(const char *p, typename Word<W>::T (&v)[4])
@@ -404,8 +424,12 @@ __device__ __forceinline__ void gather_body(const GatherDesc &d, uint64_t unit)
         }
     } else if (d.vec) {
         // Groups of 4 consecutive elements per thread: one 16-byte index load,
-        // four independent source loads, one store of 4*W bytes.
+        // four independent source loads, one store of 4*W bytes.  The index
+        // and destination streams are marked to leave the L2 first, so that
+        // the randomly read source stays resident (many ops are in flight in
+        // the batched kernel).
         constexpr int G = 2;  // groups per thread in flight
+        const uint64_t stream_pol = l2_evict_first();
         for (uint64_t g0 = e0; g0 < e1; g0 += uint64_t(kThreads) * 4 * G) {
             T v[G][4];
             bool full[G];
@@ -414,7 +438,7 @@ __device__ __forceinline__ void gather_body(const GatherDesc &d, uint64_t unit)
                 const uint64_t i = g0 + (uint64_t(k) * kThreads + tid_x()) * 4;
                 full[k] = i + 3 < e1;
                 if (full[k]) {
-                    const uint4 ix = ldg_stream<16>(d.idx + i);
+                    const uint4 ix = ldg_hint<16>(d.idx + i, stream_pol);
                     v[k][0] = ldg_any<W>(d.src + uint64_t(ix.x) * W);
                     v[k][1] = ldg_any<W>(d.src + uint64_t(ix.y) * W);
                     v[k][2] = ldg_any<W>(d.src + uint64_t(ix.z) * W);
@@ -427,7 +451,7 @@ __device__ __forceinline__ void gather_body(const GatherDesc &d, uint64_t unit)
 #pragma unroll
             for (int k = 0; k < G; ++k) {
                 const uint64_t i = g0 + (uint64_t(k) * kThreads + tid_x()) * 4;
-                if (full[k]) store4<W>(d.dst + i * W, v[k]);
+                if (full[k]) store4_hint<W>(d.dst + i * W, v[k], stream_pol);
             }
         }
     } else {
@@ -528,6 +552,59 @@ __device__ __forceinline__ void interlace_tail(const InterlaceDesc &d, char *con
         char *pl = planes[j] + i * E;
         if (inter) stg<E>(iv, lds<E>(pl));  // plain (coherent) loads: tail is tiny
         else stg<E>(pl, lds<E>(iv));
+    }
+}
+
+// Element-wise strided copy (OC_STRIDED): permutes whose transpose plane is
+// too small to fill a tile (a tile per tiny plane would move a few dozen
+// bytes per pass).  Each output cell's input offset is decomposed directly
+// from its index; the writes are coalesced (consecutive cells per thread,
+// 16-byte stores when aligned) and the reads hit the L1 / L2 wherever
+// neighbouring cells share sectors.
+__device__ __forceinline__ int64_t strided_offset(const StridedDesc &d, uint32_t q)
+{
+    int64_t off = 0;
+#pragma unroll
+    for (int i = kMaxRank - 1; i >= 0; --i) {
+        if (i < d.nd) {
+            uint32_t r;
+            fdivmod(q, d.div[i], q, r);
+            off += int64_t(r) * d.in_stride[i];
+        }
+    }
+    return off;
+}
+
+template <int W>
+__device__ __forceinline__ void strided_body(const StridedDesc &d, uint64_t unit)
+{
+    constexpr int V = 16 / W;  // cells per 16-byte store
+    using T = typename Word<W>::T;
+    const uint64_t per_unit = uint64_t(kThreads) * V * kStridedSteps;
+    const uint64_t c0 = unit * per_unit;
+    const uint64_t c1 = min(d.n_cells, c0 + per_unit);
+    const int tid = tid_x();
+    if (d.vec) {
+        for (uint64_t base = c0 + uint64_t(tid) * V; base < c1; base += uint64_t(kThreads) * V) {
+            union {
+                uint4 u;
+                T e[V];
+            } v;
+            v.u = make_uint4(0, 0, 0, 0);
+#pragma unroll
+            for (int k = 0; k < V; ++k)
+                if (base + k < c1) v.e[k] = ldg_any<W>(d.src + strided_offset(d, uint32_t(base + k)));
+            if (base + V <= c1) {
+                stg<16>(d.dst + base * W, v.u);
+            } else {
+#pragma unroll
+                for (int k = 0; k < V; ++k)
+                    if (base + k < c1) stg<W>(d.dst + (base + k) * W, v.e[k]);
+            }
+        }
+    } else {
+        for (uint64_t q = c0 + tid; q < c1; q += kThreads)
+            stg<W>(d.dst + q * W, ldg_any<W>(d.src + strided_offset(d, uint32_t(q))));
     }
 }
 

@@ -79,6 +79,62 @@ template <int N> __device__ __forceinline__ typename Word<N>::T lds(const void *
     return *reinterpret_cast<const typename Word<N>::T *>(p);
 }
 
+// L2 eviction priorities (createpolicy): data read or written once is marked
+// to leave the L2 first, data that is reused to stay.
+__device__ __forceinline__ uint64_t l2_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t l2_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// Loads (non-coherent, no L1 allocation) and stores with an L2 policy.
+template <int N> __device__ __forceinline__ typename Word<N>::T ldg_hint(const void *p, uint64_t pol);
+template <> __device__ __forceinline__ uint32_t ldg_hint<4>(const void *p, uint64_t pol)
+{
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+template <> __device__ __forceinline__ uint2 ldg_hint<8>(const void *p, uint64_t pol)
+{
+    uint2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+                 : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+template <> __device__ __forceinline__ uint4 ldg_hint<16>(const void *p, uint64_t pol)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p), "l"(pol));
+    return v;
+}
+
+template <int N> __device__ __forceinline__ void stg_hint(void *p, typename Word<N>::T v, uint64_t pol);
+template <> __device__ __forceinline__ void stg_hint<4>(void *p, uint32_t v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
+}
+template <> __device__ __forceinline__ void stg_hint<8>(void *p, uint2 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(v.x), "r"(v.y), "l"(pol)
+                 : "memory");
+}
+template <> __device__ __forceinline__ void stg_hint<16>(void *p, uint4 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w), "l"(pol)
+                 : "memory");
+}
+
 // Thread index read through a volatile move.  The persistent batched kernel
 // runs many inlined tile bodies inside one loop; with a plain threadIdx.x the
 // compiler hoists every body's thread-dependent offsets out of that loop and

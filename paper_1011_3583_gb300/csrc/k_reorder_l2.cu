@@ -340,58 +340,9 @@ __global__ void __launch_bounds__(kThreads) k_l2_partition(const L2Reorder p, ui
     }
 }
 
-// L2 eviction priorities: the streamed arrays (s, i, v) are marked to leave
-// the L2 first so that the resident source / destination chunk stays.
-__device__ __forceinline__ uint64_t policy_evict_first()
-{
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-__device__ __forceinline__ uint64_t policy_evict_last()
-{
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-template <int W> __device__ __forceinline__ typename Word<W>::T ld_hint(const void *p, uint64_t pol);
-template <> __device__ __forceinline__ uint32_t ld_hint<4>(const void *p, uint64_t pol)
-{
-    uint32_t v;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
-    return v;
-}
-template <> __device__ __forceinline__ uint2 ld_hint<8>(const void *p, uint64_t pol)
-{
-    uint2 v;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
-                 : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
-    return v;
-}
-template <> __device__ __forceinline__ uint4 ld_hint<16>(const void *p, uint64_t pol)
-{
-    uint4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p), "l"(pol));
-    return v;
-}
-
-template <int W> __device__ __forceinline__ void st_hint(void *p, typename Word<W>::T v, uint64_t pol);
-template <> __device__ __forceinline__ void st_hint<4>(void *p, uint32_t v, uint64_t pol)
-{
-    asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
-}
-template <> __device__ __forceinline__ void st_hint<8>(void *p, uint2 v, uint64_t pol)
-{
-    asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(v.x), "r"(v.y), "l"(pol) : "memory");
-}
-template <> __device__ __forceinline__ void st_hint<16>(void *p, uint4 v, uint64_t pol)
-{
-    asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
-                 "r"(v.w), "l"(pol) : "memory");
-}
+// The streamed arrays (s, i, v) are marked to leave the L2 first
+// (l2_evict_first) so that the resident source / destination chunk
+// (l2_evict_last) stays.
 
 // Next work unit for the whole CTA, handed out in increasing order so that the
 // units in flight stay a narrow window of the c-major (d-major) order.
@@ -412,7 +363,7 @@ __global__ void __launch_bounds__(kThreads) k_l2_gather(const L2Reorder p)
     if (!bucketed(p)) return;
     __shared__ uint32_t slot;
     using T = typename Word<W>::T;
-    const uint64_t first = policy_evict_first(), last = policy_evict_last();
+    const uint64_t first = l2_evict_first(), last = l2_evict_last();
     const uint32_t units = (p.n + kGatherUnit - 1) / kGatherUnit;
     for (;;) {
         const uint32_t u = next_unit(p.ctr_gather, &slot);
@@ -424,17 +375,17 @@ __global__ void __launch_bounds__(kThreads) k_l2_gather(const L2Reorder p)
 #pragma unroll
         for (int j = 0; j < PER; ++j) {
             const uint32_t k = k0 + j * kThreads + threadIdx.x;
-            sv[j] = k < p.n ? ld_hint<4>(p.sarr + k, first) : 0u;
+            sv[j] = k < p.n ? ldg_hint<4>(p.sarr + k, first) : 0u;
         }
 #pragma unroll
         for (int j = 0; j < PER; ++j) {
             const uint32_t k = k0 + j * kThreads + threadIdx.x;
-            if (k < p.n) val[j] = ld_hint<W>(p.src + uint64_t(sv[j]) * W, last);
+            if (k < p.n) val[j] = ldg_hint<W>(p.src + uint64_t(sv[j]) * W, last);
         }
 #pragma unroll
         for (int j = 0; j < PER; ++j) {
             const uint32_t k = k0 + j * kThreads + threadIdx.x;
-            if (k < p.n) st_hint<W>(p.varr + uint64_t(k) * W, val[j], first);
+            if (k < p.n) stg_hint<W>(p.varr + uint64_t(k) * W, val[j], first);
         }
     }
 }
@@ -447,7 +398,7 @@ __global__ void __launch_bounds__(kThreads) k_l2_scatter(const L2Reorder p)
     if (!bucketed(p)) return;
     __shared__ uint32_t slot, sk0, sk1;
     using T = typename Word<W>::T;
-    const uint64_t first = policy_evict_first(), last = policy_evict_last();
+    const uint64_t first = l2_evict_first(), last = l2_evict_last();
     const uint32_t nb = p.C * p.D;
     const uint32_t total = p.uprefix[nb];
     for (;;) {
@@ -476,14 +427,14 @@ __global__ void __launch_bounds__(kThreads) k_l2_scatter(const L2Reorder p)
         for (int j = 0; j < PER; ++j) {
             const uint32_t k = k0 + j * kThreads + threadIdx.x;
             if (k < k1) {
-                di[j] = ld_hint<4>(p.iarr + k, first);
-                val[j] = ld_hint<W>(p.varr + uint64_t(k) * W, first);
+                di[j] = ldg_hint<4>(p.iarr + k, first);
+                val[j] = ldg_hint<W>(p.varr + uint64_t(k) * W, first);
             }
         }
 #pragma unroll
         for (int j = 0; j < PER; ++j) {
             const uint32_t k = k0 + j * kThreads + threadIdx.x;
-            if (k < k1) st_hint<W>(p.dst + uint64_t(di[j]) * W, val[j], last);
+            if (k < k1) stg_hint<W>(p.dst + uint64_t(di[j]) * W, val[j], last);
         }
     }
 }
@@ -496,7 +447,7 @@ __global__ void __launch_bounds__(kThreads) k_l2_scatter_linear(const L2Reorder 
     if (!bucketed(p)) return;
     __shared__ uint32_t slot;
     using T = typename Word<W>::T;
-    const uint64_t first = policy_evict_first(), last = policy_evict_last();
+    const uint64_t first = l2_evict_first(), last = l2_evict_last();
     const uint32_t units = (p.n + kGatherUnit - 1) / kGatherUnit;
     for (;;) {
         const uint32_t u = next_unit(p.ctr_scatter, &slot);
@@ -509,14 +460,14 @@ __global__ void __launch_bounds__(kThreads) k_l2_scatter_linear(const L2Reorder 
         for (int j = 0; j < PER; ++j) {
             const uint32_t k = k0 + j * kThreads + threadIdx.x;
             if (k < p.n) {
-                di[j] = ld_hint<4>(p.sarr + k, first);
-                val[j] = ld_hint<W>(p.varr + uint64_t(k) * W, first);
+                di[j] = ldg_hint<4>(p.sarr + k, first);
+                val[j] = ldg_hint<W>(p.varr + uint64_t(k) * W, first);
             }
         }
 #pragma unroll
         for (int j = 0; j < PER; ++j) {
             const uint32_t k = k0 + j * kThreads + threadIdx.x;
-            if (k < p.n) st_hint<W>(p.dst + uint64_t(di[j]) * W, val[j], last);
+            if (k < p.n) stg_hint<W>(p.dst + uint64_t(di[j]) * W, val[j], last);
         }
     }
 }

@@ -45,6 +45,12 @@ __global__ void __launch_bounds__(kThreads) k_gather(const __grid_constant__ Gat
     for (uint64_t u = blockIdx.x; u < n; u += gridDim.x) gather_body<W>(d, u);
 }
 
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_strided(const __grid_constant__ StridedDesc d, uint64_t n)
+{
+    for (uint64_t u = blockIdx.x; u < n; u += gridDim.x) strided_body<W>(d, u);
+}
+
 // Interlace kernels take every plane pointer by value.
 struct InterlaceParams {
     InterlaceDesc d;
@@ -126,6 +132,12 @@ template <int W> struct RunRuns {
 template <int W> struct RunCopy {
     static cudaError_t run(const OpDesc &op, cudaStream_t s) { return go(k_copy<W>, op.units, op.copy, op.units, s); }
 };
+template <int W> struct RunStrided {
+    static cudaError_t run(const OpDesc &op, cudaStream_t s)
+    {
+        return go(k_strided<W>, op.units, op.strided, op.units, s);
+    }
+};
 template <int W> struct RunGather {
     static cudaError_t run(const OpDesc &op, cudaStream_t s)
     {
@@ -182,6 +194,7 @@ cudaError_t launch_single(const OpDesc &op, char *const *planes_all, cudaStream_
         case OC_TILE_CELLS: return by_word<RunCells>(int(op.word), op, s);
         case OC_RUNS: return by_word<RunRuns>(int(op.word), op, s);
         case OC_COPY: return by_word<RunCopy>(int(op.word), op, s);
+        case OC_STRIDED: return by_word<RunStrided>(int(op.word), op, s);
         case OC_GATHER:
             if (op.gather.l2) return launch_reorder_l2(op, s);
             return by_word<RunGather>(int(op.word), op, s);

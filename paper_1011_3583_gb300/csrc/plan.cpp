@@ -316,6 +316,38 @@ static rearr_status plan_axes(void *dst, const char *src, size_t elem_bytes, con
     op.word = uint32_t(W);
     op.units = units;
     info.n_tiles = int64_t(units);
+
+    // Thin planes (DA x DB far below a tile): every output cell copied on its
+    // own (one cell is one W-byte word) when the tiles would carry little
+    // payload on average -- a tile costs a whole load / store round trip
+    // whatever its fill.  Decided after the tile plan so that the tile count
+    // is the one the tile kernel would run; the thresholds are tuning knobs.
+    const uint64_t n_cells = bytes / uint64_t(cell);
+    const ThinTuning thin = thin_tuning();
+    const bool thin_plane =
+        bytes < units * thin.tile_bytes || (bytes <= thin.l2_bytes && n_cells < units * thin.tile_cells);
+    if (W == cell && thin_plane && n_cells < kMaxUnits) {
+        StridedDesc sd;
+        std::memset(&sd, 0, sizeof(sd));
+        sd.dst = static_cast<char *>(dst);
+        sd.src = src;
+        sd.nd = R;
+        for (int i = 0; i < kMaxRank; ++i) {
+            sd.in_stride[i] = i < R ? ax[i].stride : 0;
+            sd.div[i] = make_fastdiv(i < R ? uint32_t(ax[i].extent) : 1u);
+        }
+        sd.n_cells = n_cells;
+        sd.vec = (da % 16 == 0) ? 1u : 0u;
+        const uint64_t per_unit = uint64_t(kThreads) * (16 / W) * kStridedSteps;
+        op.cls = OC_STRIDED;
+        op.strided = sd;
+        op.units = (n_cells + per_unit - 1) / per_unit;
+        info.kind = REARR_KIND_STRIDED;
+        info.tile_a = info.tile_b = 0;
+        info.vec_in = W;
+        info.vec_out = sd.vec ? 16 : W;
+        info.n_tiles = int64_t(op.units);
+    }
     return REARR_OK;
 }
 

@@ -23,6 +23,7 @@ constexpr int kCellSmemBytes = 16384 + 4096;    // cells tile incl. padding
 constexpr int kSmemBytes = 20480;               // smem of any tile body
 constexpr int kInterStageBytes = kThreads / 32 * 8 * 32 * 16;  // interlace staging: K <= 8 chunks x 32 lanes per warp
 constexpr int kMaxRunsPerUnit = 256;            // run offsets staged in smem
+constexpr int kStridedSteps = 4;                // strided copy: thread steps per work unit
 
 // Unsigned 32-bit division by a run-time invariant divisor with one
 // multiply-high, a subtract, an add and two shifts (Granlund & Montgomery,
@@ -80,7 +81,8 @@ enum OpClass : uint32_t {
     OC_GATHER = 4,       // dst[i] = src[idx[i]]
     OC_INTERLACE = 5,    // dst[i*k+j] = src_j[i]
     OC_DEINTERLACE = 6,  // dst_j[i] = src[i*k+j]
-    OC_COUNT = 7
+    OC_STRIDED = 7,      // element-wise strided copy (permutes of thin planes)
+    OC_COUNT = 8
 };
 
 // Plane of a tiled transpose: A = input-innermost axis (input stride one
@@ -141,6 +143,20 @@ struct GatherDesc {
     uint32_t scatter;      // 1: dst[idx[i]] = src[i] instead of dst[i] = src[idx[i]]
 };
 
+// Element-wise strided copy: output cell q (row-major over the collapsed
+// output axes, innermost last) comes from the input at
+// sum_i digit_i(q) * in_stride[i].  Used for permutes whose transpose plane
+// is too small to fill a tile; one cell is one W-byte word.
+struct StridedDesc {
+    char *dst;
+    const char *src;
+    int64_t in_stride[kMaxRank];  // bytes, per output axis
+    FastDiv div[kMaxRank];        // output extents, innermost last
+    int32_t nd;                   // output axes
+    uint32_t vec;                 // 1: 16 / W consecutive cells per thread, 16-byte stores
+    uint64_t n_cells;
+};
+
 struct InterlaceDesc {
     char *inter;                       // interlaced array (dst of interlace, src of de-interlace)
     char *planes[kInlineK];            // plane pointers when k <= kInlineK
@@ -165,6 +181,7 @@ struct OpDesc {
         CopyDesc copy;
         GatherDesc gather;
         InterlaceDesc inter;
+        StridedDesc strided;
     };
 };
 

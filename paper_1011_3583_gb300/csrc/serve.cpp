@@ -303,6 +303,7 @@ void Server::launch_batches(std::unique_lock<std::mutex> &)
             ready.pop_front();
             taken.push_back(r);
             if (op.units == 0) continue;  // zero-size op: done with the batch, no work
+            batch_form(op);
             ops.push_back(op);
             planes.push_back(extra ? pl : std::vector<char *>{});
             n_ptrs += extra;

@@ -3,6 +3,7 @@
 // the file named by the REARR_TUNE_TABLE environment variable is read on first
 // use, and rearr_tuning_load swaps in another file at run time.  Lines:
 //   min_grab <v> | max_grab <v> | grabs_per_cta <v>
+//   thin_tile_bytes <v> | thin_tile_cells <v> | thin_l2_bytes <v>
 //   rowb <E> <da_lo> <da_hi> <db_lo> <db_hi> <rowb> [<tile bytes>]
 // ("#" starts a comment line).  Plans compiled after a load use the new table.
 #include <cstdio>
@@ -31,6 +32,7 @@ struct RowbRule {
 
 struct Table {
     BatchTuning batch;
+    ThinTuning thin;
     std::vector<RowbRule> rowb;
 };
 
@@ -58,6 +60,9 @@ std::shared_ptr<const Table> parse(const char *path)
             if (!std::strcmp(key, "min_grab")) t->batch.min_grab = uint32_t(v);
             else if (!std::strcmp(key, "max_grab")) t->batch.max_grab = uint32_t(v);
             else if (!std::strcmp(key, "grabs_per_cta")) t->batch.grabs_per_cta = uint32_t(v);
+            else if (!std::strcmp(key, "thin_tile_bytes")) t->thin.tile_bytes = v;
+            else if (!std::strcmp(key, "thin_tile_cells")) t->thin.tile_cells = v;
+            else if (!std::strcmp(key, "thin_l2_bytes")) t->thin.l2_bytes = v;
         }
     }
     std::fclose(f);
@@ -82,6 +87,8 @@ std::shared_ptr<const Table> current()
 }  // namespace
 
 BatchTuning batch_tuning() { return current()->batch; }
+
+ThinTuning thin_tuning() { return current()->thin; }
 
 bool tuned_shape(int E, int64_t DA, int64_t DB, TileShape &shape)
 {

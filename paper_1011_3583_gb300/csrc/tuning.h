@@ -25,6 +25,18 @@ struct BatchTuning {
 
 BatchTuning batch_tuning();
 
+// When a tiled permute runs as an element-wise strided copy instead (thin
+// transpose planes): when its tiles would average fewer than tile_bytes of
+// payload, or, for ops of at most l2_bytes (whose scattered reads stay in the
+// L2), fewer than tile_cells cells.
+struct ThinTuning {
+    uint64_t tile_bytes = 1024;
+    uint64_t tile_cells = 1024;
+    uint64_t l2_bytes = uint64_t(32) << 20;
+};
+
+ThinTuning thin_tuning();
+
 // Shape of a fast tile: staged row bytes (128, 256 or 512) and payload bytes
 // (16384, or 8192 for the half tile).
 struct TileShape {

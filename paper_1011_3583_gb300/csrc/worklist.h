@@ -15,6 +15,12 @@ struct WorklistLayout {
     size_t off_prefix = 0, off_planes = 0, off_counter = 0, bytes = 0;
 };
 
+// Adapts a single-call op descriptor to the batched kernel: gathers get small
+// work units (2048 elements), so that the window of units in flight -- the
+// resident CTAs times the work grab -- keeps only a few random-read sources
+// in the L2 at a time instead of thrashing it.
+void batch_form(OpDesc &op);
+
 // Byte layout of a work list of n_ops descriptors and n_ptrs plane pointers:
 // descriptors | prefix sums (n_ops + 1) | plane pointers | work counter.
 WorklistLayout worklist_layout(size_t n_ops, size_t n_ptrs);

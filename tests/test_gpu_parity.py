@@ -411,7 +411,8 @@ def test_every_tile_shape(lr, orc, tmp_path):
             dims = [5, 7 * 16 * v // 4 + 3 * v, 9 * 16 * v // 4 + v]   # multiples of the vector width, ragged
             for rowb, tb in cands:
                 t = tmp_path / f"t{e}_{rowb}_{tb}.txt"
-                t.write_text(f"rowb {e} 1 2147483647 1 2147483647 {rowb} {tb}\n")
+                # the planes are small: switch the thin-plane rule off so the tile runs
+                t.write_text(f"rowb {e} 1 2147483647 1 2147483647 {rowb} {tb}\nthin_tile_bytes 1\nthin_tile_cells 1\n")
                 lr.tuning_load(str(t))
                 d = lr.describe_permute(e, dims, [0, 2, 1])
                 assert d["kind"] == "tile" and d["tile_a"] * e == rowb and d["tile_a"] * d["tile_b"] * e == tb, d
@@ -419,3 +420,47 @@ def test_every_tile_shape(lr, orc, tmp_path):
     finally:
         lr.tuning_load(None)
         lr.tuning_load(lr.DEFAULT_TUNE_TABLE)
+
+
+THIN = [  # (dims, perm): transpose planes far smaller than a tile
+    ([7, 122, 736, 2], [3, 2, 1, 0]),
+    ([5, 3, 401, 2], [3, 1, 2, 0]),
+    ([1000, 3, 2], [0, 2, 1]),
+    ([2, 3, 4, 5, 6, 7], [5, 3, 1, 4, 2, 0]),
+    ([3, 17, 2, 9], [1, 3, 0, 2]),
+    ([13, 2, 3], [2, 1, 0]),
+]
+
+
+@pytest.mark.parametrize("e", [1, 2, 4, 8, 16])
+def test_thin_planes_run_strided(lr, orc, e):
+    for t, (dims, perm) in enumerate(THIN):
+        d = lr.describe_permute(e, dims, perm)
+        assert d["kind"] == "strided", (dims, perm, d)
+        for off in (0, e if e < 16 else 0):  # aligned (16-byte stores) and unaligned destination
+            check_permute(lr, orc, 300 + t, e, dims, perm, src_off=off, dst_off=off)
+
+
+def test_strided_tail_and_unit_edges(lr, orc):
+    # cell counts around the unit size (256 threads x 16/E cells x 4 steps)
+    for e, n_b in ((4, 1023), (4, 1024), (4, 1025), (1, 4097), (8, 511)):
+        dims, perm = [n_b, 3, 2], [0, 2, 1]
+        assert lr.describe_permute(e, dims, perm)["kind"] == "strided"
+        check_permute(lr, orc, n_b, e, dims, perm)
+
+
+def test_batch_with_strided_ops(lr, orc):
+    ops = [dict(kind="permute", elem_bytes=[1, 2, 4, 8][i % 4], dims=dims, perm=perm, data_seed=i)
+           for i, (dims, perm) in enumerate(THIN * 4)]
+    ops += [dict(kind="permute", elem_bytes=4, dims=[64, 96], perm=[1, 0], data_seed=99)]  # a tile op
+    bufs = [make_op_buffers(op, offset=(i % 2) * 4) for i, op in enumerate(ops)]
+    plan = lr.Plan()
+    for op, b in zip(ops, bufs):
+        add_to_plan(plan, op, b)
+    plan.finalize()
+    plan.run()
+    sync()
+    for i, (op, b) in enumerate(zip(ops, bufs)):
+        for w, g in zip(oracle_of(orc, op, b), outputs_of(op, b)):
+            assert np.array_equal(g, w), (i, op)
+    plan.close()

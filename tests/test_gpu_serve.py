@@ -102,6 +102,24 @@ def test_each_result_same_alone_and_in_the_mix(rr, batching):
     srv.close()
 
 
+@pytest.mark.parametrize("batching", [True, False])
+def test_wide_interlaces_and_large_gathers_served(rr, batching):
+    """Interlaces with 5-8 planes (16-byte group path in single calls, the
+    generic body in batched launches) and reorders of several batched work
+    units, served together: every result matches the oracle."""
+    ops = []
+    for i, k in enumerate((5, 6, 7, 8, 6, 8)):
+        ops.append(dict(kind="interlace" if i % 2 == 0 else "deinterlace", elem_bytes=[4, 8, 2, 1][i % 4], k=k,
+                        n=4096 + 16 * i, data_seed=500 + i))
+    ops += [dict(kind="reorder", elem_bytes=e, n=n, data_seed=600 + n) for e, n in ((4, 10000), (8, 70001), (1, 33))]
+    srv = rr.Server(budget_bytes=256 << 20, n_streams=2, max_batch_ops=16, batching=batching)
+    outs, wants = serve_all(rr, srv, ops)
+    for i, (o, w) in enumerate(zip(outs, wants)):
+        for got, want in zip(o, w):
+            assert np.array_equal(got, want), (i, ops[i])
+    srv.close()
+
+
 def test_admission_waits_for_memory(rr):
     e, n = 4, (3 << 20) // 4                      # 3 MiB in + 3 MiB out per request
     op = dict(kind="permute", elem_bytes=e, dims=[n // 1024, 1024], perm=[1, 0])

@@ -67,6 +67,16 @@ def test_check_indices_validation(lr):
     assert librearr.check_indices(None, 0, 4, 0) == 0
 
 
+def test_thin_planes_classify_strided(lr):
+    from paper_1011_3583_gb300 import librearr
+    d = librearr.describe_permute(4, [7, 122, 736, 2], [3, 2, 1, 0])
+    assert d["kind"] == "strided" and d["vec_out"] == 16 and d["rank"] == 4
+    # the same reversal with a plane that fills tiles stays tiled
+    assert librearr.describe_permute(4, [512, 64, 64, 512], [3, 2, 1, 0])["kind"] == "tile"
+    # unaligned destination: scalar stores
+    assert librearr.describe_permute(4, [1000, 3, 2], [0, 2, 1], FAKE_DST + 4, FAKE_SRC)["vec_out"] == 4
+
+
 def test_status_strings(lr):
     assert [lr.status_str(i) for i in range(7)] == [
         "REARR_OK", "REARR_EINVAL", "REARR_ENOMEM", "REARR_ECUDA", "REARR_ERANGE", "REARR_ETIMEDOUT", "REARR_EBUSY"]
@@ -166,8 +176,11 @@ def test_describe_examples(lr):
     d = lr.describe_permute(4, [64, 128, 256, 64], [0, 1, 3, 2], FAKE_DST, FAKE_SRC)
     assert d["kind"] == "tile" and d["dims"] == [8192, 64, 256] and d["plane_a"] == 1
     # unmoved innermost axis folds into the cell
-    d = lr.describe_permute(4, [8, 16, 4], [1, 0, 2], FAKE_DST, FAKE_SRC)
+    d = lr.describe_permute(4, [64, 128, 4], [1, 0, 2], FAKE_DST, FAKE_SRC)
     assert d["cell_bytes"] == 16 and d["rank"] == 2 and d["kind"] == "tile"
+    # ... and a plane of 8 x 16 such cells is too thin for tiles
+    d = lr.describe_permute(4, [8, 16, 4], [1, 0, 2], FAKE_DST, FAKE_SRC)
+    assert d["cell_bytes"] == 16 and d["rank"] == 2 and d["kind"] == "strided"
     # long unmoved runs are copied as runs
     d = lr.describe_permute(4, [8, 16, 512], [1, 0, 2], FAKE_DST, FAKE_SRC)
     assert d["kind"] == "runs" and d["cell_bytes"] == 2048
