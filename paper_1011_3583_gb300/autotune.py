@@ -10,8 +10,11 @@ It measures, with CUDA events and the library's own kernels only:
   256 or 512 bytes; 16 KB tiles, or 8 KB half tiles for 2- and 4-byte
   elements) that moves a representative permute of that class fastest.  The representative case is a [nb, DB, DA] tensor permuted
   to [nb, DA, DB], nb chosen so that each call moves about 256 MiB;
-* the batched kernel's work grab (tiles taken per atomicAdd) on the first
-  1024 ops of the uneven mix.
+* the batched kernel's work grab (tiles taken per atomicAdd) on the 4096-op
+  uneven mix, with the tile rules just measured;
+* the thin-plane threshold (average cells per tile below which a permute runs
+  as an element-wise strided copy) on the permutes of the whole mix, batched
+  and as single calls (the sum of both times is minimised).
 
 The result is a text table read by rearr_tuning_load (see tuning.cpp).
 """
@@ -84,7 +87,7 @@ def tune_rowb(rr, torch, stream, tmpdir, log):
     return rules
 
 
-def tune_grab(rr, torch, stream, tmpdir, log, n_ops=1024):
+def tune_grab(rr, torch, stream, tmpdir, log, base_lines, n_ops=4096):
     import bench  # the mix's buffers and plan helpers
     import synth
     ops = synth.batch_mix(seed=1, n_ops=n_ops)
@@ -93,7 +96,7 @@ def tune_grab(rr, torch, stream, tmpdir, log, n_ops=1024):
     best = None
     for g in (1, 2, 4, 8, 16, 32):
         table = os.path.join(tmpdir, "grab.txt")
-        _write(table, [f"min_grab {g}", f"max_grab {g}"])
+        _write(table, base_lines + [f"min_grab {g}", f"max_grab {g}"])
         rr.tuning_load(table)
         plan = rr.Plan()
         for o, p in zip(ops, bufs):
@@ -107,6 +110,35 @@ def tune_grab(rr, torch, stream, tmpdir, log, n_ops=1024):
     rr.tuning_load(None)
     del pool
     return [f"min_grab {best[0]}", f"max_grab {best[0]}   # {nbytes / best[1] / 1e9:.0f} GB/s on the mix"]
+
+
+def tune_thin(rr, torch, stream, tmpdir, log, base_lines):
+    import bench
+    import synth
+    ops = [o for o in synth.batch_mix(seed=1, n_ops=4096) if o["kind"] == "permute"]
+    pool, bufs = bench.batch_buffers(torch, ops, torch.device("cuda"))
+    best = None
+    for cells in (256, 512, 1024, 2048, 4096):
+        table = os.path.join(tmpdir, "thin.txt")
+        _write(table, base_lines + [f"thin_tile_cells {cells}"])
+        rr.tuning_load(table)
+        plan = rr.Plan()
+        for o, p in zip(ops, bufs):
+            bench.add_to_plan(plan, o, p)
+        plan.finalize(stream)
+        tb = _time(torch, lambda: plan.run(stream), stream)
+        plan.close()
+
+        def plain():
+            for o, p in zip(ops, bufs):
+                rr.permute(p[1], p[0], o["elem_bytes"], o["dims"], o["perm"], stream)
+        tp = _time(torch, plain, stream, reps=3)
+        log(f"thin_tile_cells={cells:5d}: batched {tb * 1e3:7.3f} ms  single calls {tp * 1e3:7.3f} ms")
+        if best is None or tb + tp < best[1]:
+            best = (cells, tb + tp)
+    rr.tuning_load(None)
+    del pool
+    return [f"thin_tile_cells {best[0]}"]
 
 
 def main():
@@ -130,11 +162,13 @@ def main():
     t0 = time.time()
     with tempfile.TemporaryDirectory() as tmp:
         rules = tune_rowb(rr, torch, stream, tmp, log)
-        grab = tune_grab(rr, torch, stream, tmp, log)
+        base = [r.split("#")[0] for r in rules]
+        grab = tune_grab(rr, torch, stream, tmp, log, base)
+        thin = tune_thin(rr, torch, stream, tmp, log, base + [g.split("#")[0] for g in grab])
     head = [f"# librearr tuning table for {torch.cuda.get_device_name()} "
             f"(paper_1011_3583_gb300/autotune.py, {time.time() - t0:.0f} s)"]
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
-    _write(args.out, head + grab + rules + log_lines)
+    _write(args.out, head + grab + thin + rules + log_lines)
     print(f"wrote {args.out}: {len(rules)} tile rules")
 
 
