@@ -39,10 +39,34 @@ __device__ __forceinline__ char *const *planes_of(const InterlaceDesc &d)
 // of one op's units.  Separate functions get separate register allocations
 // (a single function holding every inlined variant overflows the register
 // file), and the call overhead is paid once per range, not once per tile.
+// Fast tiles are pipelined over the range: tile u+1 is copied (cp.async)
+// into the second half of the shared buffer while tile u is stored from the
+// first, so a CTA's next load latency hides behind its current stores (tiles
+// of the uneven mix are often partly filled and latency-bound).
 template <int E, int VI, int VO, int RB, int TBYTES = kTileBytes>
 __device__ __noinline__ void tile_range(const TileDesc &d, uint32_t u0, uint32_t u1, unsigned char *smem)
 {
-    for (uint32_t u = u0; u < u1; ++u) tile_fast_body<E, VI, VO, RB, TBYTES>(d, u, smem);
+    static_assert(2 * TBYTES <= kBatchSmemBytes, "two tile buffers must fit the batched kernel's shared memory");
+    if constexpr (VI < 4) {  // 1- and 2-byte loads: cp.async copies 4 bytes or more
+        for (uint32_t u = u0; u < u1; ++u) tile_fast_body<E, VI, VO, RB, TBYTES>(d, u, smem);
+    } else {
+        if (u0 >= u1) return;
+        tile_fast_issue<E, VI, VO, RB, TBYTES>(d, u0, smem);
+        for (uint32_t u = u0; u < u1; ++u) {
+            unsigned char *cur = smem + ((u - u0) & 1u) * TBYTES;
+            if (u + 1 < u1) {
+                // the other buffer's last reader was tile u-1, finished at the
+                // barrier that ended the previous iteration
+                tile_fast_issue<E, VI, VO, RB, TBYTES>(d, u + 1, smem + ((u + 1 - u0) & 1u) * TBYTES);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();
+            tile_fast_store<E, VI, VO, RB, TBYTES>(d, u, cur);
+            __syncthreads();
+        }
+    }
 }
 
 template <int W>
@@ -166,7 +190,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch(const OpDesc *__restrict_
                                                        const uint64_t *__restrict__ prefix, int n_ops,
                                                        unsigned long long *counter, uint32_t grab)
 {
-    __shared__ __align__(16) unsigned char smem[kSmemBytes > kInterStageBytes ? kSmemBytes : kInterStageBytes];
+    __shared__ __align__(16) unsigned char smem[kBatchSmemBytes];
     __shared__ unsigned long long s_start;
     const uint64_t total = prefix[n_ops];
     for (;;) {
@@ -321,6 +345,55 @@ rearr_status rearr_plan_finalize(rearr_plan *plan, rearr_stream_t stream)
     const size_t n = plan->ops.size();
     plan->finalized = true;
     if (n == 0) return REARR_OK;
+    // Ops are independent, so their order in the work list is free.  The
+    // batched kernel holds every body, and a mix that interleaves dozens of
+    // variants stalls on instruction fetch; a mix grouped by class runs its
+    // memory-bound and issue-bound classes one after the other instead of
+    // overlapping them.  So each class's ops are sorted by body variant and
+    // the classes are merged in proportion to their work units: the CTAs in
+    // flight run a few bodies, one current variant per class.
+    {
+        auto sub = [&](const OpDesc &o) -> uint64_t {
+            if (o.cls == OC_TILE) return o.tile.variant;
+            if (o.cls == OC_INTERLACE || o.cls == OC_DEINTERLACE)
+                return uint64_t(o.inter.fast) << 40 | uint64_t(o.inter.k) << 8 | o.inter.elem_bytes;
+            return o.word;
+        };
+        std::vector<std::vector<size_t>> groups(OC_COUNT);
+        std::vector<uint64_t> group_units(OC_COUNT, 0);
+        for (size_t i = 0; i < n; ++i) {
+            groups[plan->ops[i].cls].push_back(i);
+            group_units[plan->ops[i].cls] += plan->ops[i].units;
+        }
+        for (auto &g : groups)
+            std::stable_sort(g.begin(), g.end(),
+                             [&](size_t a, size_t b) { return sub(plan->ops[a]) < sub(plan->ops[b]); });
+        std::vector<size_t> order;
+        order.reserve(n);
+        std::vector<size_t> next(OC_COUNT, 0);
+        std::vector<uint64_t> done(OC_COUNT, 0);
+        while (order.size() < n) {
+            // the class furthest behind in its share of units goes next
+            int best = -1;
+            for (int c = 0; c < int(OC_COUNT); ++c) {
+                if (next[c] >= groups[c].size()) continue;
+                if (best < 0 || double(done[c]) / double(group_units[c]) <
+                                    double(done[best]) / double(group_units[best]))
+                    best = c;
+            }
+            const size_t i = groups[best][next[best]++];
+            done[best] += plan->ops[i].units;
+            order.push_back(i);
+        }
+        std::vector<OpDesc> ops(n);
+        std::vector<std::vector<char *>> lists(n);
+        for (size_t i = 0; i < n; ++i) {
+            ops[i] = plan->ops[order[i]];
+            lists[i] = std::move(plan->plane_lists[order[i]]);
+        }
+        plan->ops.swap(ops);
+        plan->plane_lists.swap(lists);
+    }
     // Host image of the device block.
     size_t n_ptrs = 0;
     for (auto &l : plan->plane_lists) n_ptrs += l.size();

@@ -168,6 +168,91 @@ __device__ __forceinline__ void tile_fast_body(const TileDesc &d, uint32_t t, un
     __syncthreads();
 }
 
+// The fast tile in two phases for pipelined ranges of tiles: tile_fast_issue
+// starts the tile's global -> shared copies as cp.async (no registers held,
+// 16-byte copies bypass the L1) into the same swizzled layout as
+// tile_fast_body, and commits them as one group; tile_fast_store runs the
+// store phase from shared memory once the group has landed (the caller waits
+// with cp.async.wait_group and a block barrier).  A CTA can so copy tile t+1
+// into a second buffer while it stores tile t.
+template <int N>
+__device__ __forceinline__ void cp_async(void *smem_dst, const void *gsrc)
+{
+    const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+    if constexpr (N == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gsrc), "n"(N) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory"); }
+
+template <int E, int VIN, int VOUT, int ROWB, int TBYTES = kTileBytes>
+__device__ __forceinline__ void tile_fast_issue(const TileDesc &d, uint32_t t, unsigned char *smem)
+{
+    constexpr int TA = FastTile<E, ROWB, TBYTES>::TA, TB = FastTile<E, ROWB, TBYTES>::TB;
+    constexpr int VB = VOUT / E;
+    constexpr int PPR = ROWB / VIN;
+    constexpr int NP = TB * PPR;
+    constexpr int PT = NP / kThreads;
+    static_assert(NP % kThreads == 0, "tile must split evenly over the CTA");
+    static_assert(VIN == 4 || VIN == 8 || VIN == 16, "cp.async copies 4, 8 or 16 bytes");
+    uint32_t a0, b0;
+    int64_t ioff, ooff;
+    tile_origin(d, t, a0, b0, ioff, ooff);
+    const uint32_t na = min(uint32_t(TA), d.DA - a0);
+    const uint32_t nbv = min(uint32_t(TB), d.DB - b0);
+    const char *in = d.src + ioff + int64_t(a0) * E + int64_t(b0) * d.sb_in;
+    const uint32_t row_valid_bytes = na * E;
+    const int tid = tid_x();
+#pragma unroll
+    for (int k = 0; k < PT; ++k) {
+        const int f = k * kThreads + tid;
+        const int row = f / PPR, x = (f % PPR) * VIN;
+        if (uint32_t(row) < nbv && uint32_t(x) < row_valid_bytes) {
+            const int sw = (row / VB) & 7;
+            cp_async<VIN>(smem + row * ROWB + (((x >> 4) ^ sw) << 4) + (x & 15), in + int64_t(row) * d.sb_in + x);
+        }
+    }
+    cp_async_commit();
+}
+
+template <int E, int VIN, int VOUT, int ROWB, int TBYTES = kTileBytes>
+__device__ __forceinline__ void tile_fast_store(const TileDesc &d, uint32_t t, const unsigned char *smem)
+{
+    constexpr int TA = FastTile<E, ROWB, TBYTES>::TA, TB = FastTile<E, ROWB, TBYTES>::TB;
+    constexpr int V = 16 / E;
+    constexpr int VB = VOUT / E;
+    uint32_t a0, b0;
+    int64_t ioff, ooff;
+    tile_origin(d, t, a0, b0, ioff, ooff);
+    const uint32_t na = min(uint32_t(TA), d.DA - a0);
+    const uint32_t nbv = min(uint32_t(TB), d.DB - b0);
+    char *out = d.dst + ooff + int64_t(a0) * d.sa_out + int64_t(b0) * E;
+    const int tid = tid_x();
+    constexpr int UB = TB / VB, UQ = TA / V, NU = UB * UQ;
+    static_assert(NU % kThreads == 0, "store units must split evenly");
+#pragma unroll
+    for (int u0 = 0; u0 < NU; u0 += kThreads) {
+        const int u = u0 + tid;
+        const int bq = u % UB, q = u / UB;
+        const int b = bq * VB;
+        if (uint32_t(b) < nbv) {
+            uint4 r[VB];
+#pragma unroll
+            for (int i = 0; i < VB; ++i) r[i] = lds<16>(smem + (b + i) * ROWB + ((q ^ (bq & 7)) << 4));
+#pragma unroll
+            for (int m = 0; m < V; ++m) {
+                const uint32_t a = uint32_t(q * V + m);
+                if (a < na) stg<VOUT>(out + int64_t(a) * d.sa_out + int64_t(b) * E, piece<E, VB>(r, m));
+            }
+        }
+    }
+}
+
 // Cells tile: each cell is c words of W bytes (any cell size; used for
 // element sizes that are not a power of two, unaligned element addresses and
 // permutes whose innermost axis is unmoved but short).  Rows are padded to a

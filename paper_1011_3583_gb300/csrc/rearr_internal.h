@@ -22,6 +22,11 @@ constexpr int kTileBytes = 16384;               // payload of one fast tile
 constexpr int kCellSmemBytes = 16384 + 4096;    // cells tile incl. padding
 constexpr int kSmemBytes = 20480;               // smem of any tile body
 constexpr int kInterStageBytes = kThreads / 32 * 8 * 32 * 16;  // interlace staging: K <= 8 chunks x 32 lanes per warp
+// Shared memory of the batched kernel: the largest of a cells tile, the
+// interlace staging and two fast tiles (pipelined ranges).
+constexpr int kBatchSmemBytes = kSmemBytes > kInterStageBytes
+                                    ? (kSmemBytes > 2 * kTileBytes ? kSmemBytes : 2 * kTileBytes)
+                                    : (kInterStageBytes > 2 * kTileBytes ? kInterStageBytes : 2 * kTileBytes);
 constexpr int kMaxRunsPerUnit = 256;            // run offsets staged in smem
 constexpr int kStridedSteps = 4;                // strided copy: thread steps per work unit
 
