@@ -331,7 +331,8 @@ __global__ void __launch_bounds__(kThreads) k_l2_partition(const L2Reorder p, ui
             p.sarr[g] = S.s_st[q];
             p.iarr[g] = S.i_st[q];
         }
-        for (uint32_t c = threadIdx.x; c < kWarps * kMaxChunks; c += kThreads) (&S.cnt[0][0])[c] = 0;
+        // only the C chunks in use need zeroing (not all kMaxChunks)
+        for (uint32_t x = threadIdx.x; x < kWarps * p.C; x += kThreads) S.cnt[x / p.C][x % p.C] = 0;
         __syncthreads();
         if (t + 1 < t1) {
 #pragma unroll
