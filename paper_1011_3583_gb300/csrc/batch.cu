@@ -345,55 +345,7 @@ rearr_status rearr_plan_finalize(rearr_plan *plan, rearr_stream_t stream)
     const size_t n = plan->ops.size();
     plan->finalized = true;
     if (n == 0) return REARR_OK;
-    // Ops are independent, so their order in the work list is free.  The
-    // batched kernel holds every body, and a mix that interleaves dozens of
-    // variants stalls on instruction fetch; a mix grouped by class runs its
-    // memory-bound and issue-bound classes one after the other instead of
-    // overlapping them.  So each class's ops are sorted by body variant and
-    // the classes are merged in proportion to their work units: the CTAs in
-    // flight run a few bodies, one current variant per class.
-    {
-        auto sub = [&](const OpDesc &o) -> uint64_t {
-            if (o.cls == OC_TILE) return o.tile.variant;
-            if (o.cls == OC_INTERLACE || o.cls == OC_DEINTERLACE)
-                return uint64_t(o.inter.fast) << 40 | uint64_t(o.inter.k) << 8 | o.inter.elem_bytes;
-            return o.word;
-        };
-        std::vector<std::vector<size_t>> groups(OC_COUNT);
-        std::vector<uint64_t> group_units(OC_COUNT, 0);
-        for (size_t i = 0; i < n; ++i) {
-            groups[plan->ops[i].cls].push_back(i);
-            group_units[plan->ops[i].cls] += plan->ops[i].units;
-        }
-        for (auto &g : groups)
-            std::stable_sort(g.begin(), g.end(),
-                             [&](size_t a, size_t b) { return sub(plan->ops[a]) < sub(plan->ops[b]); });
-        std::vector<size_t> order;
-        order.reserve(n);
-        std::vector<size_t> next(OC_COUNT, 0);
-        std::vector<uint64_t> done(OC_COUNT, 0);
-        while (order.size() < n) {
-            // the class furthest behind in its share of units goes next
-            int best = -1;
-            for (int c = 0; c < int(OC_COUNT); ++c) {
-                if (next[c] >= groups[c].size()) continue;
-                if (best < 0 || double(done[c]) / double(group_units[c]) <
-                                    double(done[best]) / double(group_units[best]))
-                    best = c;
-            }
-            const size_t i = groups[best][next[best]++];
-            done[best] += plan->ops[i].units;
-            order.push_back(i);
-        }
-        std::vector<OpDesc> ops(n);
-        std::vector<std::vector<char *>> lists(n);
-        for (size_t i = 0; i < n; ++i) {
-            ops[i] = plan->ops[order[i]];
-            lists[i] = std::move(plan->plane_lists[order[i]]);
-        }
-        plan->ops.swap(ops);
-        plan->plane_lists.swap(lists);
-    }
+    order_for_batch(plan->ops, plan->plane_lists);
     // Host image of the device block.
     size_t n_ptrs = 0;
     for (auto &l : plan->plane_lists) n_ptrs += l.size();
@@ -614,6 +566,57 @@ extern "C" rearr_status rearr_batch_noalloc(const rearr_plan *plan, rearr_stream
 // Work lists built and launched from host code (serving loop).
 
 namespace rearr {
+
+// Ops of a batch are independent, so their order in the work list is free.
+// The batched kernel holds every body, and a mix that interleaves dozens of
+// variants stalls on instruction fetch; a mix grouped by class runs its
+// memory-bound and issue-bound classes one after the other instead of
+// overlapping them.  So each class's ops are sorted by body variant and the
+// classes are merged in proportion to their work units: the CTAs in flight
+// run a few bodies, one current variant per class.
+void order_for_batch(std::vector<OpDesc> &all_ops, std::vector<std::vector<char *>> &plane_lists)
+{
+    const size_t n = all_ops.size();
+    auto sub = [&](const OpDesc &o) -> uint64_t {
+        if (o.cls == OC_TILE) return o.tile.variant;
+        if (o.cls == OC_INTERLACE || o.cls == OC_DEINTERLACE)
+            return uint64_t(o.inter.fast) << 40 | uint64_t(o.inter.k) << 8 | o.inter.elem_bytes;
+        return o.word;
+    };
+    std::vector<std::vector<size_t>> groups(OC_COUNT);
+    std::vector<uint64_t> group_units(OC_COUNT, 0);
+    for (size_t i = 0; i < n; ++i) {
+        groups[all_ops[i].cls].push_back(i);
+        group_units[all_ops[i].cls] += std::max<uint64_t>(all_ops[i].units, 1);
+    }
+    for (auto &g : groups)
+        std::stable_sort(g.begin(), g.end(), [&](size_t a, size_t b) { return sub(all_ops[a]) < sub(all_ops[b]); });
+    std::vector<size_t> order;
+    order.reserve(n);
+    std::vector<size_t> next(OC_COUNT, 0);
+    std::vector<uint64_t> done(OC_COUNT, 0);
+    while (order.size() < n) {
+        // the class furthest behind in its share of units goes next
+        int best = -1;
+        for (int c = 0; c < int(OC_COUNT); ++c) {
+            if (next[c] >= groups[c].size()) continue;
+            if (best < 0 ||
+                double(done[c]) / double(group_units[c]) < double(done[best]) / double(group_units[best]))
+                best = c;
+        }
+        const size_t i = groups[best][next[best]++];
+        done[best] += std::max<uint64_t>(all_ops[i].units, 1);
+        order.push_back(i);
+    }
+    std::vector<OpDesc> ops(n);
+    std::vector<std::vector<char *>> lists(n);
+    for (size_t i = 0; i < n; ++i) {
+        ops[i] = all_ops[order[i]];
+        lists[i] = std::move(plane_lists[order[i]]);
+    }
+    all_ops.swap(ops);
+    plane_lists.swap(lists);
+}
 
 void batch_form(OpDesc &op)
 {

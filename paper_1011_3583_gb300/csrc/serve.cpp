@@ -319,6 +319,7 @@ void Server::launch_batches(std::unique_lock<std::mutex> &)
             e = copy_inputs(*r, in_sz, s.stream);
         }
         if (!ops.empty() && e == cudaSuccess) {
+            order_for_batch(ops, planes);
             const uint64_t total = build_worklist(ops.data(), planes.data(), ops.size(), s.host_wl,
                                                   reinterpret_cast<uintptr_t>(s.dev_wl), lay);
             e = cudaMemcpyAsync(s.dev_wl, s.host_wl, lay.bytes, cudaMemcpyHostToDevice, s.stream);

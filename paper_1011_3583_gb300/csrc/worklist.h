@@ -21,6 +21,11 @@ struct WorklistLayout {
 // in the L2 at a time instead of thrashing it.
 void batch_form(OpDesc &op);
 
+// Reorders a batch's ops (and their plane lists) for the batched kernel: each
+// op class sorted by body variant, the classes merged in proportion to their
+// work units.  Ops of a batch are independent, so any order is correct.
+void order_for_batch(std::vector<OpDesc> &ops, std::vector<std::vector<char *>> &plane_lists);
+
 // Byte layout of a work list of n_ops descriptors and n_ptrs plane pointers:
 // descriptors | prefix sums (n_ops + 1) | plane pointers | work counter.
 WorklistLayout worklist_layout(size_t n_ops, size_t n_ptrs);
