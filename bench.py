@@ -662,11 +662,13 @@ def run_reference(args):
         total_t += time.perf_counter() - t0
         total_b += op_bytes(o)
     value = total_b / total_t / 1e9
-    return {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": 0,
+    # n_gpus is the launch's N (the oracle itself runs on one host thread of rank 0)
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s",
+            "n_gpus": int(os.environ.get("WORLD_SIZE", args.gpus)),
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_t / args.steps * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bytes (memcpy per element)",
             "data": "synthetic (seeded PCG64 random bit patterns)",
-            "config": {"workload": WORKLOAD, "parallelism": "single CPU thread"},
+            "config": {"workload": WORKLOAD, "parallelism": "single CPU thread (the oracle on the host)"},
             "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
                              "sample": "each step runs one op of: 512^3 fp32 (2,0,1); 64x128x256x64 (3,1,2,0) 4 B, "
                                        "(0,3,2,1) 8 B, (2,3,0,1) 2 B; reorder 2^28 fp32 random (rotating)",
