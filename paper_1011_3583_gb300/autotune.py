@@ -14,7 +14,9 @@ It measures, with CUDA events and the library's own kernels only:
   uneven mix, with the tile rules just measured;
 * the thin-plane threshold (average cells per tile below which a permute runs
   as an element-wise strided copy) on the permutes of the whole mix, batched
-  and as single calls (the sum of both times is minimised).
+  and as single calls (the sum of both times is minimised);
+* the longest run (128, 256 or 512 bytes) that is faster walked in input
+  order than in output order.
 
 The result is a text table read by rearr_tuning_load (see tuning.cpp).
 """
@@ -141,6 +143,30 @@ def tune_thin(rr, torch, stream, tmpdir, log, base_lines):
     return [f"thin_tile_cells {best[0]}"]
 
 
+def tune_runs_order(rr, torch, stream, tmpdir, log, base_lines):
+    """Largest run length (128, 256, 512 B) for which walking runs in input
+    order beats output order on a 1 GiB-class permute with that run length."""
+    best = 1
+    for e in (2, 4, 8):  # runs of 64 elements: 128, 256, 512 bytes
+        dims, perm = [64, 128, 256, 64], [2, 1, 0, 3]
+        n = int(np.prod(dims))
+        a = torch.empty(n * e, dtype=torch.uint8, device="cuda").random_()
+        b = torch.empty_like(a)
+        times = []
+        for mirror in (1, 64 * e):
+            table = os.path.join(tmpdir, "runs.txt")
+            _write(table, base_lines + [f"runs_mirror_bytes {mirror}"])
+            rr.tuning_load(table)
+            times.append(_time(torch, lambda: rr.permute(b, a, e, dims, perm, stream), stream))
+        log(f"runs of {64 * e:3d} B: output order {2 * n * e / times[0] / 1e9:7.1f} GB/s, "
+            f"input order {2 * n * e / times[1] / 1e9:7.1f} GB/s")
+        if times[1] < times[0]:
+            best = 64 * e
+        del a, b
+    rr.tuning_load(None)
+    return [f"runs_mirror_bytes {best}"]
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
@@ -165,10 +191,11 @@ def main():
         base = [r.split("#")[0] for r in rules]
         grab = tune_grab(rr, torch, stream, tmp, log, base)
         thin = tune_thin(rr, torch, stream, tmp, log, base + [g.split("#")[0] for g in grab])
+        runs = tune_runs_order(rr, torch, stream, tmp, log, base)
     head = [f"# librearr tuning table for {torch.cuda.get_device_name()} "
             f"(paper_1011_3583_gb300/autotune.py, {time.time() - t0:.0f} s)"]
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
-    _write(args.out, head + grab + thin + rules + log_lines)
+    _write(args.out, head + grab + thin + runs + rules + log_lines)
     print(f"wrote {args.out}: {len(rules)} tile rules")
 
 

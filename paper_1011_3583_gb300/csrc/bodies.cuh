@@ -375,6 +375,31 @@ __device__ __forceinline__ void runs_body(const RunsDesc &d, uint64_t unit, unsi
     const uint32_t total = nr * wpr;
     char *out = d.dst + int64_t(r0) * d.run_bytes;
     constexpr int U = W >= 16 ? 4 : 8;  // 64 bytes in flight per thread for 16-byte words (80 registers at U = 8)
+    if (d.mirror) {
+        // Runs walked in input order: the input is read contiguously and
+        // base[] holds each run's output offset (short runs: sequential reads
+        // keep DRAM rows open, the scattered writes are whole runs).
+        const char *in = d.src + int64_t(r0) * d.run_bytes;
+        for (uint32_t f0 = 0; f0 < total; f0 += kThreads * U) {
+            typename Word<W>::T v[U];
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const uint32_t f = f0 + k * kThreads + tid_x();
+                if (f < total) v[k] = ldg_stream<W>(in + int64_t(f) * W);
+            }
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const uint32_t f = f0 + k * kThreads + tid_x();
+                if (f < total) {
+                    uint32_t r, w;
+                    fdivmod(f, d.wpr_div, r, w);
+                    stg<W>(d.dst + base[r] + int64_t(w) * W, v[k]);
+                }
+            }
+        }
+        __syncthreads();
+        return;
+    }
     for (uint32_t f0 = 0; f0 < total; f0 += kThreads * U) {
         typename Word<W>::T v[U];
 #pragma unroll

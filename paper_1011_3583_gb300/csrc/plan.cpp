@@ -228,6 +228,32 @@ static rearr_status plan_axes(void *dst, const char *src, size_t elem_bytes, con
             r.cpr_div = make_fastdiv(1);
             r.runs_per_unit = uint32_t(std::min<int64_t>(kMaxRunsPerUnit, std::max<int64_t>(1, kRunUnitBytes / cell)));
             op.units = (n_runs + r.runs_per_unit - 1) / r.runs_per_unit;
+            // Short runs of a dense input may be walked in input order: the
+            // reads become sequential and each run is written whole.
+            if (uint64_t(cell) <= runs_mirror_max_bytes()) {
+                std::vector<int> by_in(R);
+                for (int i = 0; i < R; ++i) by_in[i] = i;
+                std::sort(by_in.begin(), by_in.end(), [&](int a, int b) { return ax[a].stride > ax[b].stride; });
+                bool dense = true;
+                int64_t expect = cell;
+                for (int k = R - 1; k >= 0; --k) {
+                    dense &= ax[by_in[k]].stride == expect;
+                    expect *= ax[by_in[k]].extent;
+                }
+                if (dense) {
+                    std::vector<int64_t> out_stride(R);
+                    int64_t os = cell;
+                    for (int i = R - 1; i >= 0; --i) {
+                        out_stride[i] = os;
+                        os *= ax[i].extent;
+                    }
+                    r.mirror = 1;
+                    for (int k = 0; k < kMaxRank; ++k) {
+                        r.in_stride[k] = k < R ? out_stride[by_in[k]] : 0;
+                        r.div[k] = make_fastdiv(k < R ? uint32_t(ax[by_in[k]].extent) : 1u);
+                    }
+                }
+            }
         }
         info.n_tiles = int64_t(op.units);
         return REARR_OK;

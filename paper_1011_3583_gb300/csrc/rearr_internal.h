@@ -126,6 +126,8 @@ struct RunsDesc {
     FastDiv wpr_div;              // words per run
     FastDiv cpr_div;              // chunks per run (> 1: long runs, one chunk per unit)
     uint32_t chunk_words;         // words per chunk of a long run
+    uint32_t mirror;              // 1: runs in input order -- run r is read at r * run_bytes
+                                  // and in_stride / div describe its output offset instead
 };
 
 struct CopyDesc {

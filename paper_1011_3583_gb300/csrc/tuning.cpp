@@ -4,6 +4,7 @@
 // use, and rearr_tuning_load swaps in another file at run time.  Lines:
 //   min_grab <v> | max_grab <v> | grabs_per_cta <v>
 //   thin_tile_bytes <v> | thin_tile_cells <v> | thin_l2_bytes <v>
+//   runs_mirror_bytes <v>   (1: never; runs of at most v bytes in input order)
 //   rowb <E> <da_lo> <da_hi> <db_lo> <db_hi> <rowb> [<tile bytes>]
 // ("#" starts a comment line).  Plans compiled after a load use the new table.
 #include <cstdio>
@@ -33,6 +34,7 @@ struct RowbRule {
 struct Table {
     BatchTuning batch;
     ThinTuning thin;
+    uint64_t runs_mirror_bytes = 0;
     std::vector<RowbRule> rowb;
 };
 
@@ -63,6 +65,7 @@ std::shared_ptr<const Table> parse(const char *path)
             else if (!std::strcmp(key, "thin_tile_bytes")) t->thin.tile_bytes = v;
             else if (!std::strcmp(key, "thin_tile_cells")) t->thin.tile_cells = v;
             else if (!std::strcmp(key, "thin_l2_bytes")) t->thin.l2_bytes = v;
+            else if (!std::strcmp(key, "runs_mirror_bytes")) t->runs_mirror_bytes = v;
         }
     }
     std::fclose(f);
@@ -89,6 +92,8 @@ std::shared_ptr<const Table> current()
 BatchTuning batch_tuning() { return current()->batch; }
 
 ThinTuning thin_tuning() { return current()->thin; }
+
+uint64_t runs_mirror_max_bytes() { return current()->runs_mirror_bytes; }
 
 bool tuned_shape(int E, int64_t DA, int64_t DB, TileShape &shape)
 {

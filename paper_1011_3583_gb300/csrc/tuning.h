@@ -35,6 +35,11 @@ struct ThinTuning {
     uint64_t l2_bytes = uint64_t(32) << 20;
 };
 
+// Runs of at most this many bytes are walked in input order (sequential
+// reads, whole runs written scattered) when the input is a dense array;
+// 0 keeps output order for every run length.
+uint64_t runs_mirror_max_bytes();
+
 ThinTuning thin_tuning();
 
 // Shape of a fast tile: staged row bytes (128, 256 or 512) and payload bytes

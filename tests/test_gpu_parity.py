@@ -464,3 +464,25 @@ def test_batch_with_strided_ops(lr, orc):
         for w, g in zip(oracle_of(orc, op, b), outputs_of(op, b)):
             assert np.array_equal(g, w), (i, op)
     plan.close()
+
+
+def test_runs_in_input_order(lr, orc, tmp_path):
+    """Short runs walked in input order (tuning knob runs_mirror_bytes) give
+    the oracle's bytes: dense permutes whose innermost axis is unmoved, any
+    element size, aligned and unaligned."""
+    t = tmp_path / "mirror.txt"
+    t.write_text(open(lr.DEFAULT_TUNE_TABLE).read() + "\nruns_mirror_bytes 4096\n")
+    cases = [([64, 128, 40, 64], [0, 2, 1, 3], 2), ([33, 17, 5, 64], [2, 1, 0, 3], 2), ([7, 9, 11, 32], [1, 2, 0, 3], 4),
+             ([5, 300, 16], [1, 0, 2], 8), ([3, 4, 5, 6, 16], [4, 3, 1, 0, 2], 12), ([100, 3, 128], [1, 0, 2], 1)]
+    try:
+        lr.tuning_load(str(t))
+        for i, (dims, perm, e) in enumerate(cases):
+            perm = list(perm)
+            if perm[-1] != len(dims) - 1:
+                continue
+            d = lr.describe_permute(e, dims, perm)
+            assert d["kind"] == "runs", (dims, perm, d)
+            for off in (0, 1 if e in (1, 12) else e):
+                check_permute(lr, orc, 700 + i, e, dims, perm, src_off=off, dst_off=off)
+    finally:
+        lr.tuning_load(lr.DEFAULT_TUNE_TABLE)
