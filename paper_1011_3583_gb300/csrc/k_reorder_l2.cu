@@ -31,6 +31,7 @@
 // another.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "bodies.cuh"
@@ -244,7 +245,7 @@ struct PartitionSmem {
     uint32_t warp_sums[kWarps];
 };
 
-__global__ void __launch_bounds__(kThreads) k_l2_partition(const L2Reorder p, uint32_t tiles_per_cta)
+__global__ void __launch_bounds__(kThreads, 3) k_l2_partition(const L2Reorder p, uint32_t tiles_per_cta)
 {
     if (!bucketed(p)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -555,17 +556,28 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
     const uint32_t tpc = (tiles + resident - 1) / resident;  // contiguous tiles per CTA
     const unsigned pgrid = unsigned((tiles + tpc - 1) / tpc);
     static bool smem_set[64] = {false};
+    static int part_per_sm[64] = {0};
     if (dev >= 0 && dev < 64 && !smem_set[dev]) {
         e = cudaFuncSetAttribute(k_l2_partition, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(PartitionSmem)));
         smem_set[dev] = e == cudaSuccess;
+        int per_sm = 0;
+        if (e == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_l2_partition, kThreads, sizeof(PartitionSmem)) ==
+                cudaSuccess)
+            part_per_sm[dev] = per_sm;
     }
+    // The partition runs one wave: every resident CTA takes a contiguous
+    // range of tiles (a second, partial wave would leave SMs idle).
+    const uint32_t part_resident = uint32_t(sms) * uint32_t(std::max(1, dev >= 0 && dev < 64 ? part_per_sm[dev] : 1));
+    const uint32_t part_tpc = (tiles + part_resident - 1) / part_resident;
+    const unsigned part_grid = unsigned((tiles + part_tpc - 1) / part_tpc);
     const unsigned pers = unsigned(sms) * 8;  // persistent grids of the gated passes
     const uint64_t dunits = (g.n + g.unit_elems - 1) / g.unit_elems;
     if (e == cudaSuccess) { k_l2_sample<<<kSampleRuns / (kThreads / 32), kThreads, 0, s>>>(p); e = cudaGetLastError(); }
     if (e == cudaSuccess) { k_l2_hist<<<pgrid, kThreads, 0, s>>>(p, tpc); e = cudaGetLastError(); }
     if (e == cudaSuccess) { k_l2_scan<<<1, 1024, 0, s>>>(p); e = cudaGetLastError(); }
     if (e == cudaSuccess) {
-        k_l2_partition<<<pgrid, kThreads, sizeof(PartitionSmem), s>>>(p, tpc);
+        k_l2_partition<<<part_grid, kThreads, sizeof(PartitionSmem), s>>>(p, part_tpc);
         e = cudaGetLastError();
     }
     if (!g.scatter) {
