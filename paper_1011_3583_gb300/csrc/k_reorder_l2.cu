@@ -555,20 +555,27 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
     const uint32_t resident = uint32_t(sms) * 4;
     const uint32_t tpc = (tiles + resident - 1) / resident;  // contiguous tiles per CTA
     const unsigned pgrid = unsigned((tiles + tpc - 1) / tpc);
+    // Per device, once: the partition's shared-memory opt-in and occupancy.
+    static std::mutex setup_mu;
     static bool smem_set[64] = {false};
     static int part_per_sm[64] = {0};
-    if (dev >= 0 && dev < 64 && !smem_set[dev]) {
-        e = cudaFuncSetAttribute(k_l2_partition, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(PartitionSmem)));
-        smem_set[dev] = e == cudaSuccess;
-        int per_sm = 0;
-        if (e == cudaSuccess &&
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_l2_partition, kThreads, sizeof(PartitionSmem)) ==
-                cudaSuccess)
-            part_per_sm[dev] = per_sm;
+    int per_sm_part = 1;
+    if (dev >= 0 && dev < 64) {
+        std::lock_guard<std::mutex> lock(setup_mu);
+        if (!smem_set[dev]) {
+            e = cudaFuncSetAttribute(k_l2_partition, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(sizeof(PartitionSmem)));
+            smem_set[dev] = e == cudaSuccess;
+            int per_sm = 0;
+            if (e == cudaSuccess && cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                        &per_sm, k_l2_partition, kThreads, sizeof(PartitionSmem)) == cudaSuccess)
+                part_per_sm[dev] = per_sm;
+        }
+        per_sm_part = std::max(1, part_per_sm[dev]);
     }
     // The partition runs one wave: every resident CTA takes a contiguous
     // range of tiles (a second, partial wave would leave SMs idle).
-    const uint32_t part_resident = uint32_t(sms) * uint32_t(std::max(1, dev >= 0 && dev < 64 ? part_per_sm[dev] : 1));
+    const uint32_t part_resident = uint32_t(sms) * uint32_t(per_sm_part);
     const uint32_t part_tpc = (tiles + part_resident - 1) / part_resident;
     const unsigned part_grid = unsigned((tiles + part_tpc - 1) / part_tpc);
     const unsigned pers = unsigned(sms) * 8;  // persistent grids of the gated passes
