@@ -86,7 +86,7 @@ rearr_status rearr_permute(void *dst, const void *src, size_t elem_bytes, int ra
  *   dst      : row-major over extents range[order[i]]:
  *       dst[j] = src[x],  x[a] = base[a] + (j_i if a == order[i] else 0).
  *   With rank_out == rank_in, base 0 and range dims it is rearr_permute; a
- *   rank-1 box is the "specified range" access of Sec. III.A.  When the box
+ *   rank-1 box is the access of a specified range of Sec. III.A.  When the box
  *   keeps no input-contiguous axis, reads cannot be coalesced (the paper notes
  *   the same) and the op runs as a gather of short runs.
  * ------------------------------------------------------------------------- */
@@ -113,7 +113,7 @@ rearr_status rearr_reorder(void *dst, const void *src, const uint32_t *idx, size
 
 /* ---------------------------------------------------------------------------
  * Other index-sequence forms (the scatter direction and 64-bit indices of the
- * reorder; Sec. III.A accesses "a specified set of indices"):
+ * reorder; Sec. III.A reads the elements at a given set of indices):
  *   rearr_scatter   : dst[idx[i]] = src[i], uint32 indices.
  *   rearr_reorder64 : dst[i] = src[idx[i]], uint64 indices (n may exceed 2^32).
  *   rearr_scatter64 : dst[idx[i]] = src[i], uint64 indices.
@@ -322,7 +322,7 @@ rearr_status rearr_plan_stats(const rearr_plan *plan, int64_t *n_ops, int64_t *n
  *
  * The plan compiler drops extent-1 axes, merges output axes that are adjacent
  * and in order in the input, folds an unmoved innermost run into a wider
- * element, and classifies the op (the "offset/striding approach" and the 2-D
+ * element, and classifies the op (the offset and stride computation and the 2-D
  * plane of Sec. III.B: the plane of the input's fastest and the output's
  * fastest dimension).
  * ------------------------------------------------------------------------- */

@@ -15,12 +15,12 @@
  *
  * Conventions (readings of the paper, Sec. III.B):
  *   - Storage is row-major: dims[0] is the slowest axis, dims[rank-1] the
- *     fastest (the paper's default "row major linearized storage").
+ *     fastest (the paper's default linearisation is row-major).
  *   - perm follows numpy's transpose: output axis i is input axis perm[i].
- *     The paper lists an "order" vector fastest-dimension-first; a paper order
+ *     The paper lists an order vector fastest-dimension-first; a paper order
  *     vector o converts to perm[i] = rank-1-o[rank-1-i].
  *   - Reorder by an index sequence is a gather, dst[i] = src[idx[i]], the
- *     "accessing specified set of indices" pattern of Sec. III.A.
+ *     access of a given set of indices of Sec. III.A.
  *   - Interlace joins k arrays of n elements each into one array of k*n
  *     elements, dst[i*k + j] = src_j[i]; de-interlace splits it back
  *     (Sec. III.C).

@@ -1,8 +1,9 @@
 // k_stencil.cu -- generic 2-D stencil kernels (Sec. III.D) for sm_103a.
 //
 // Every CTA of 256 threads computes 128 x 64 tiles of outputs from an input
-// box in shared memory (the "user managed cache" of Sec. III.D): the tile, r
-// halo rows above and below and 8 staged columns left and right.
+// box in shared memory (Sec. III.D uses shared memory as a cache the program
+// manages): the tile, r halo rows above and below and 8 staged columns left
+// and right.
 //
 // Staging.  When the grid's rows are 16-byte aligned the box arrives by ONE
 // TMA tensor copy (cp.async.bulk.tensor.2d) whose out-of-grid cells the copy

@@ -372,7 +372,7 @@ def nm_numpy(src_flat, e, dims, order, base, rng):
 def pin_reorder_nm(orc) -> List[str]:
     """N-to-M reorder (Sec. III.B) against numpy slicing + transpose, against a
     scatter-side brute force, and its special cases: full box = permute, and a
-    rank-1 box = a contiguous range copy (the "specified range" access of
+    rank-1 box = a contiguous range copy (the access of a specified range of
     Sec. III.A)."""
     fails = []
     g = synth.rng(21)
