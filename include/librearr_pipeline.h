@@ -40,13 +40,25 @@ typedef struct rearr_pipeline rearr_pipeline;
 rearr_status rearr_pipeline_create(size_t slot_bytes, int slots, rearr_pipeline **pipe);
 
 /* The ops: same arguments, layouts and validation as the librearr.h calls of
- * the same name, with host pointers.  Asynchronous: a call returns once the
- * op's copies and kernel are enqueued.  A CUDA failure is returned by the
+ * the same name, with host pointers.  The whole source array of an N-to-M
+ * reorder (every element of dims) is uploaded; its output is the box.  A
+ * scatter does not upload dst: with a permutation every element is written,
+ * otherwise the elements no index names come back undefined.
+ * Asynchronous: a call returns once the op's copies and kernel are enqueued.  A CUDA failure is returned by the
  * call that sees it and by every later call (the pipeline is then broken). */
 rearr_status rearr_pipeline_permute(rearr_pipeline *pipe, void *dst, const void *src, size_t elem_bytes,
                                     int rank, const int64_t *dims, const int *perm);
 rearr_status rearr_pipeline_reorder(rearr_pipeline *pipe, void *dst, const void *src, const uint32_t *idx,
                                     size_t n, size_t elem_bytes);
+rearr_status rearr_pipeline_reorder_nm(rearr_pipeline *pipe, void *dst, const void *src, size_t elem_bytes,
+                                       int rank_in, const int64_t *dims, int rank_out, const int *order,
+                                       const int64_t *base, const int64_t *range);
+rearr_status rearr_pipeline_scatter(rearr_pipeline *pipe, void *dst, const void *src, const uint32_t *idx,
+                                    size_t n, size_t elem_bytes);
+rearr_status rearr_pipeline_reorder64(rearr_pipeline *pipe, void *dst, const void *src, const uint64_t *idx,
+                                      size_t n, size_t elem_bytes);
+rearr_status rearr_pipeline_scatter64(rearr_pipeline *pipe, void *dst, const void *src, const uint64_t *idx,
+                                      size_t n, size_t elem_bytes);
 rearr_status rearr_pipeline_interlace(rearr_pipeline *pipe, void *dst, const void *const *srcs, int k,
                                       size_t n, size_t elem_bytes);
 rearr_status rearr_pipeline_deinterlace(rearr_pipeline *pipe, void *const *dsts, const void *src, int k,

@@ -135,6 +135,20 @@ size_t product(int rank, const int64_t *dims)
     return n;
 }
 
+// Gather / scatter with 4- or 8-byte indices.
+rearr_status pipeline_indexed(rearr_pipeline *pipe, const char *who, void *dst, const void *src,
+                              const void *idx, size_t n, size_t elem_bytes, int idx_bytes, bool scatter)
+{
+    return run_op(pipe, who, {{src, n * elem_bytes}, {idx, n * size_t(idx_bytes)}}, {{dst, n * elem_bytes}},
+                  [&](const SlotLayout &l, std::function<cudaError_t(cudaStream_t)> &go, std::string &err) {
+                      auto op = std::make_shared<OpDesc>();
+                      rearr_status st = plan_reorder(l.out[0], l.in[0], reinterpret_cast<const uint32_t *>(l.in[1]),
+                                                     n, elem_bytes, *op, err, idx_bytes, scatter);
+                      go = [op](cudaStream_t s) { return launch_single(*op, nullptr, s); };
+                      return st;
+                  });
+}
+
 }  // namespace
 
 extern "C" {
@@ -196,6 +210,46 @@ rearr_status rearr_pipeline_reorder(rearr_pipeline *pipe, void *dst, const void 
                       go = [op](cudaStream_t s) { return launch_single(*op, nullptr, s); };
                       return st;
                   });
+}
+
+rearr_status rearr_pipeline_reorder_nm(rearr_pipeline *pipe, void *dst, const void *src, size_t elem_bytes,
+                                       int rank_in, const int64_t *dims, int rank_out, const int *order,
+                                       const int64_t *base, const int64_t *range)
+{
+    const bool shape_ok = rank_in >= 1 && rank_in <= REARR_MAX_RANK && dims && rank_out >= 1 &&
+                          rank_out <= rank_in && order && range;
+    size_t in_bytes = shape_ok ? product(rank_in, dims) * elem_bytes : 0, out_bytes = 0;
+    if (shape_ok) {
+        out_bytes = elem_bytes;
+        for (int i = 0; i < rank_out; ++i)
+            out_bytes *= (order[i] >= 0 && order[i] < rank_in && range[order[i]] > 0) ? size_t(range[order[i]]) : 0;
+    }
+    return run_op(pipe, "rearr_pipeline_reorder_nm", {{src, in_bytes}}, {{dst, out_bytes}},
+                  [&](const SlotLayout &l, std::function<cudaError_t(cudaStream_t)> &go, std::string &err) {
+                      auto pl = std::make_shared<PermPlan>();
+                      rearr_status st = plan_reorder_nm(l.out[0], l.in[0], elem_bytes, rank_in, dims, rank_out,
+                                                        order, base, range, *pl, err);
+                      go = [pl](cudaStream_t s) { return launch_single(pl->op, nullptr, s); };
+                      return st;
+                  });
+}
+
+rearr_status rearr_pipeline_scatter(rearr_pipeline *pipe, void *dst, const void *src, const uint32_t *idx, size_t n,
+                                    size_t elem_bytes)
+{
+    return pipeline_indexed(pipe, "rearr_pipeline_scatter", dst, src, idx, n, elem_bytes, 4, true);
+}
+
+rearr_status rearr_pipeline_reorder64(rearr_pipeline *pipe, void *dst, const void *src, const uint64_t *idx, size_t n,
+                                      size_t elem_bytes)
+{
+    return pipeline_indexed(pipe, "rearr_pipeline_reorder64", dst, src, idx, n, elem_bytes, 8, false);
+}
+
+rearr_status rearr_pipeline_scatter64(rearr_pipeline *pipe, void *dst, const void *src, const uint64_t *idx, size_t n,
+                                      size_t elem_bytes)
+{
+    return pipeline_indexed(pipe, "rearr_pipeline_scatter64", dst, src, idx, n, elem_bytes, 8, true);
 }
 
 rearr_status rearr_pipeline_interlace(rearr_pipeline *pipe, void *dst, const void *const *srcs, int k, size_t n,

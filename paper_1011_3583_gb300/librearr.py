@@ -593,6 +593,10 @@ def _bind_pipeline():
         "rearr_pipeline_create": (st, [sz, ctypes.c_int, ctypes.POINTER(vp)]),
         "rearr_pipeline_permute": (st, [vp, vp, vp, sz, ctypes.c_int, i64p, ip]),
         "rearr_pipeline_reorder": (st, [vp, vp, vp, vp, sz, sz]),
+        "rearr_pipeline_reorder_nm": (st, [vp, vp, vp, sz, ctypes.c_int, i64p, ctypes.c_int, ip, i64p, i64p]),
+        "rearr_pipeline_scatter": (st, [vp, vp, vp, vp, sz, sz]),
+        "rearr_pipeline_reorder64": (st, [vp, vp, vp, vp, sz, sz]),
+        "rearr_pipeline_scatter64": (st, [vp, vp, vp, vp, sz, sz]),
         "rearr_pipeline_interlace": (st, [vp, vp, ctypes.POINTER(vp), ctypes.c_int, sz, sz]),
         "rearr_pipeline_deinterlace": (st, [vp, ctypes.POINTER(vp), vp, ctypes.c_int, sz, sz]),
         "rearr_pipeline_stencil2d_f32": (st, [vp, vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ip, ip,
@@ -643,6 +647,26 @@ class Pipeline:
     def reorder(self, dst, src, idx, n: int, elem_bytes: int) -> None:
         self._keep.append((dst, src, idx))
         _check(load().rearr_pipeline_reorder(self._h, _hptr(dst), _hptr(src), _hptr(idx), int(n), int(elem_bytes)))
+
+    def reorder_nm(self, dst, src, elem_bytes: int, dims: Sequence[int], order: Sequence[int],
+                   base: Sequence[int], rng: Sequence[int]) -> None:
+        rank_in, d, rank_out, o, b, r = _nm_args(dims, order, base, rng)
+        self._keep.append((dst, src))
+        _check(load().rearr_pipeline_reorder_nm(self._h, _hptr(dst), _hptr(src), int(elem_bytes), rank_in, d,
+                                                rank_out, o, b, r))
+
+    def _indexed(self, fn, dst, src, idx, n, elem_bytes):
+        self._keep.append((dst, src, idx))
+        _check(fn(self._h, _hptr(dst), _hptr(src), _hptr(idx), int(n), int(elem_bytes)))
+
+    def scatter(self, dst, src, idx, n: int, elem_bytes: int) -> None:
+        self._indexed(load().rearr_pipeline_scatter, dst, src, idx, n, elem_bytes)
+
+    def reorder64(self, dst, src, idx, n: int, elem_bytes: int) -> None:
+        self._indexed(load().rearr_pipeline_reorder64, dst, src, idx, n, elem_bytes)
+
+    def scatter64(self, dst, src, idx, n: int, elem_bytes: int) -> None:
+        self._indexed(load().rearr_pipeline_scatter64, dst, src, idx, n, elem_bytes)
 
     def interlace(self, dst, srcs, n: int, elem_bytes: int) -> None:
         arr = (ctypes.c_void_p * max(len(srcs), 1))(*[_hptr(x) for x in srcs])

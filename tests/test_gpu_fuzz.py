@@ -145,14 +145,42 @@ def one_batch(rr, orc, d, it):
 
 
 def one_pipeline(rr, orc, d, it):
-    e, dims, perm = d.permute()
-    n = int(np.prod(dims))
+    g = d.g
+    form = int(g.integers(0, 3))
+    if form == 0:
+        e, dims, perm = d.permute()
+        n = int(np.prod(dims))
+        src = synth.random_elements(it, n, e)
+        out = np.zeros(n * e, dtype=np.uint8)
+        with rr.Pipeline(slot_bytes=2 * n * e + 4096, slots=3) as pipe:
+            pipe.permute(out, src, e, dims, perm)
+            pipe.sync()
+        return "pipeline:permute", np.array_equal(out, orc.permute(src, e, dims, perm)), (e, dims, perm)
+    if form == 1:
+        e = int(g.choice(ELEMS))
+        rank = int(g.integers(1, 5))
+        dims = d.shape(rank)
+        base = [int(g.integers(0, x)) for x in dims]
+        rng = [int(g.integers(1, x - b + 1)) for x, b in zip(dims, base)]
+        order = [int(x) for x in g.permutation(rank)[:int(g.integers(1, rank + 1))]]
+        n, tot = int(np.prod(dims)), int(np.prod([rng[a] for a in order]))
+        src = synth.random_elements(it, n, e)
+        out = np.zeros(tot * e, dtype=np.uint8)
+        with rr.Pipeline(slot_bytes=(n + tot) * e + 4096, slots=3) as pipe:
+            pipe.reorder_nm(out, src, e, dims, order, base, rng)
+            pipe.sync()
+        return "pipeline:nm", np.array_equal(out, orc.reorder_nm(src, e, dims, order, base, rng)), (e, dims, order)
+    e, n = int(g.choice(ELEMS)), int(g.integers(1, 200000))
+    wide, scatter = bool(g.integers(0, 2)), bool(g.integers(0, 2))
     src = synth.random_elements(it, n, e)
+    idx = synth.random_permutation(it, n).astype(np.uint64 if wide else np.uint32)
     out = np.zeros(n * e, dtype=np.uint8)
-    with rr.Pipeline(slot_bytes=2 * n * e + 4096, slots=3) as pipe:
-        pipe.permute(out, src, e, dims, perm)
+    with rr.Pipeline(slot_bytes=n * (2 * e + 8) + 4096, slots=3) as pipe:
+        fn = {(False, False): pipe.reorder, (True, False): pipe.reorder64, (False, True): pipe.scatter,
+              (True, True): pipe.scatter64}[(wide, scatter)]
+        fn(out, src, idx, n, e)
         pipe.sync()
-    return "pipeline", np.array_equal(out, orc.permute(src, e, dims, perm)), (e, dims, perm)
+    return "pipeline:indexed", np.array_equal(out, orc.indexed(src, idx, e, scatter=scatter)), (e, n, wide, scatter)
 
 
 @pytest.mark.parametrize("seed", [11, 12])
@@ -167,4 +195,4 @@ def test_random_ops_match_oracle(rr, seed):
         if not ok:
             fails.append((name, what))
     assert not fails, (dict(stats), fails[:5])
-    assert all(stats[k] > 0 for k in ("nm", "interlace", "batch", "pipeline"))
+    assert all(stats[k] > 0 for k in ("nm", "interlace", "batch", "pipeline:permute", "pipeline:indexed"))

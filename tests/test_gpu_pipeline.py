@@ -130,3 +130,24 @@ def test_large_ops_stream_through(lr, orc):
             got = d.numpy().view(np.uint32)[lin].view(np.uint8)
             assert np.array_equal(got, want), p
     del torch
+
+
+def test_nm_scatter_and_wide_indices(lr, orc):
+    """The N-to-M reorder, the scatter and the 64-bit index forms on host buffers."""
+    with lr.Pipeline(slot_bytes=16 << 20, slots=3) as pipe:
+        dims, order, base, rng = [40, 50, 60], [2, 0], [3, 7, 5], [30, 1, 50]
+        src = synth.random_elements(1, int(np.prod(dims)), 4)
+        out_nm = np.zeros(50 * 30 * 4, dtype=np.uint8)
+        pipe.reorder_nm(out_nm, src, 4, dims, order, base, rng)
+        n, e = 77777, 8
+        s2 = synth.random_elements(2, n, e)
+        p = synth.random_permutation(3, n)
+        outs = {k: np.zeros(n * e, dtype=np.uint8) for k in ("scatter", "reorder64", "scatter64")}
+        pipe.scatter(outs["scatter"], s2, p, n, e)
+        pipe.reorder64(outs["reorder64"], s2, p.astype(np.uint64), n, e)
+        pipe.scatter64(outs["scatter64"], s2, p.astype(np.uint64), n, e)
+        pipe.sync()
+        assert np.array_equal(out_nm, orc.reorder_nm(src, 4, dims, order, base, rng))
+        assert np.array_equal(outs["scatter"], orc.indexed(s2, p, e, scatter=True))
+        assert np.array_equal(outs["scatter64"], orc.indexed(s2, p, e, scatter=True))
+        assert np.array_equal(outs["reorder64"], orc.reorder(s2, p, e))
