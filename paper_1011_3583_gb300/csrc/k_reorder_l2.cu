@@ -2,9 +2,12 @@
 // passes (dst[i] = src[idx[i]], arXiv:1011.3583 Sec. III.A indexed access).
 //
 // A direct gather from a source far larger than the L2 pays a whole DRAM
-// access (32-64 B) for every element it reads.  Here the source and the
-// destination are cut into chunks of about 16 MB (CS elements); element i
-// belongs to bucket (c, d) with c = idx[i] / CS and d = i / CS.  The passes:
+// access (32-64 B) for every element it reads.  Here the source is cut into
+// chunks of about 16 MB (CS elements) and the destination into chunks of DS
+// elements; element i belongs to bucket (c, d) with c = idx[i] / CS and
+// d = i / DS.  DS is 64 KB of elements (one CTA's shared memory) when the
+// bucket count C * D stays within a bound (the shared-memory scatter), and
+// CS otherwise (the L2 scatter).  The passes:
 //   K1 sample    : index locality on 4096 short runs of idx; if most
 //                  neighbours are close (|idx[j+1] - idx[j]| <= 16), the
 //                  direct gather is already streaming and K2..K6 do nothing,
@@ -17,8 +20,16 @@
 //                  index) and i-array (destination index), c-major.
 //   K5 gather    : v[k] = src[s[k]] walking k in order, so the CTAs in flight
 //                  read one ~16 MB source chunk at a time from L2.
-//   K6 scatter   : dst[i[k]] = v[k] walking the buckets d-major, so the CTAs
-//                  in flight complete one ~16 MB destination chunk in L2.
+//   K6 scatter   : shared-memory form: one CTA per 64 KB destination chunk
+//                  d reads the C buckets (c, d), places every value at its
+//                  slot of the chunk in shared memory and writes the chunk
+//                  out with coalesced stores.  L2 form: dst[i[k]] = v[k]
+//                  walking the buckets d-major, so the CTAs in flight
+//                  complete one ~16 MB destination chunk in L2.
+// Random global accesses cost one L1 request each (about one per clock per
+// SM, whatever the working set), random shared-memory accesses about a
+// twelfth of that: the shared-memory scatter leaves the gather as the one
+// pass bound by random requests.
 //   K7 direct    : the plain gather (when K1 found locality).
 // Traffic: 2 (idx) + 2 (s, i written) + 2 (s, i read) + 1 (src) + 2 (v) + 1
 // (dst) = 10 n-word passes of streaming access instead of n random accesses.
@@ -36,13 +47,16 @@
 
 #include "bodies.cuh"
 #include "launch.h"
+#include "tuning.h"
 
 namespace rearr {
 
 namespace {
 
 constexpr int kTile = 4096;        // elements per partition tile / scatter unit
-constexpr int kMaxChunks = 512;    // C, D <= 512
+constexpr int kMaxChunks = 512;    // C <= 512; D <= 512 for the L2 scatter
+constexpr int kScatterThreads = 512;
+constexpr uint32_t kScatterChunkBytes = 64u << 10;  // destination chunk of the shared-memory scatter
 constexpr int kSampleRuns = 4096;
 constexpr int kSampleLen = 64;
 constexpr uint32_t kNear = 16;
@@ -52,12 +66,14 @@ struct L2Reorder {
     char *dst;
     const uint32_t *idx;
     uint32_t n;
-    uint32_t cs_shift;             // chunk = 2^cs_shift elements
+    uint32_t cs_shift;             // source chunk = 2^cs_shift elements
+    uint32_t ds_shift;             // destination chunk = 2^ds_shift elements (>= log2 kTile)
     uint32_t C, D;                 // source / destination chunks
     unsigned long long *near;      // K1: close neighbour pairs in the sample
     unsigned int *ctr_gather;      // K5 / K6 work counters (units handed out in order)
     unsigned int *ctr_scatter;
     uint32_t *hist;                // [C*D] bucket sizes, c-major (b = c*D + d)
+    uint32_t *rowtot;              // [C] elements per source chunk
     uint32_t *base;                // [C*D] bucket starts, c-major
     uint32_t *cursor;              // [C*D] partition write cursors
     uint32_t *uprefix;             // [C*D + 1] d-major prefix of scatter units
@@ -77,7 +93,7 @@ __device__ __forceinline__ uint32_t chunk_of(const L2Reorder &p, uint32_t v)
 // a scatter has one (D = 1).
 __device__ __forceinline__ uint32_t dest_chunk(const L2Reorder &p, uint32_t i)
 {
-    return p.D == 1 ? 0u : i >> p.cs_shift;
+    return p.D == 1 ? 0u : i >> p.ds_shift;
 }
 
 __device__ __forceinline__ bool bucketed(const L2Reorder &p)
@@ -134,6 +150,7 @@ __global__ void __launch_bounds__(kThreads) k_l2_hist(const L2Reorder p, uint32_
     for (uint32_t c = threadIdx.x; c < kWarps * kMaxChunks; c += kThreads) (&sh[0][0])[c] = 0;
     __syncthreads();
     uint32_t cur_d = t0 < t1 ? dest_chunk(p, t0 * kTile) : 0;
+    uint32_t row[kMaxChunks / kThreads] = {};  // this CTA's count of chunks c = threadIdx.x + j * kThreads
     uint32_t v[kPer];
     if (t0 < t1) load_tile(p, t0 * kTile, min(uint32_t(kTile), p.n - t0 * kTile), v);
     for (uint32_t t = t0; t < t1; ++t) {
@@ -148,13 +165,17 @@ __global__ void __launch_bounds__(kThreads) k_l2_hist(const L2Reorder p, uint32_
         const uint32_t next_d = t + 1 < t1 ? dest_chunk(p, (t + 1) * kTile) : 0xFFFFFFFFu;
         if (next_d != cur_d) {
             __syncthreads();
-            for (uint32_t c = threadIdx.x; c < p.C; c += kThreads) {
+#pragma unroll
+            for (int j = 0; j < kMaxChunks / kThreads; ++j) {
+                const uint32_t c = threadIdx.x + j * kThreads;
+                if (c >= p.C) break;
                 uint32_t tot = 0;
 #pragma unroll
                 for (int x = 0; x < kWarps; ++x) {
                     tot += sh[x][c];
                     sh[x][c] = 0;
                 }
+                row[j] += tot;
                 if (tot) atomicAdd(&p.hist[c * p.D + cur_d], tot);
             }
             __syncthreads();
@@ -164,6 +185,11 @@ __global__ void __launch_bounds__(kThreads) k_l2_hist(const L2Reorder p, uint32_
 #pragma unroll
             for (int j = 0; j < kPer; ++j) v[j] = nxt[j];
         }
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxChunks / kThreads; ++j) {
+        const uint32_t c = threadIdx.x + j * kThreads;
+        if (c < p.C && row[j]) atomicAdd(&p.rowtot[c], row[j]);
     }
 }
 
@@ -230,22 +256,66 @@ __global__ void __launch_bounds__(1024) k_l2_scan(const L2Reorder p)
     if (threadIdx.x == 0) p.uprefix[nb] = carry;
 }
 
+// Bucket starts for the shared-memory scatter (C * D up to millions of
+// buckets): CTA c scans row c of the histogram, offset by the elements of
+// the rows before it.  Each thread sums kRowPer consecutive buckets.
+constexpr int kRowPer = 16;
+
+__global__ void __launch_bounds__(1024) k_l2_scan_rows(const L2Reorder p)
+{
+    if (!bucketed(p)) return;
+    __shared__ uint32_t warp_sums[32];
+    __shared__ uint32_t total;
+    const uint32_t c = blockIdx.x;
+    uint32_t part = 0;
+    for (uint32_t x = threadIdx.x; x < c; x += 1024) part += p.rowtot[x];
+    block_scan(part, warp_sums, &total);
+    uint32_t carry = total;  // elements of the rows before c
+    const uint32_t row = c * p.D;
+    for (uint32_t d0 = 0; d0 < p.D; d0 += 1024 * kRowPer) {
+        const uint32_t dt = d0 + threadIdx.x * kRowPer;
+        uint32_t v[kRowPer], sum = 0;
+#pragma unroll
+        for (int r = 0; r < kRowPer; ++r) {
+            v[r] = dt + r < p.D ? p.hist[row + dt + r] : 0u;
+            sum += v[r];
+        }
+        uint32_t run = carry + block_scan(sum, warp_sums, &total);
+#pragma unroll
+        for (int r = 0; r < kRowPer; ++r) {
+            if (dt + r < p.D) {
+                p.base[row + dt + r] = run;
+                p.cursor[row + dt + r] = run;
+            }
+            run += v[r];
+        }
+        carry += total;
+    }
+}
+
 // Partition: per tile, every warp ranks its 512 elements by source chunk in
-// its own counters; warp offsets and chunk segment offsets are prefix sums
-// over those counters; the tile is then staged in shared memory grouped by
-// chunk and written out as contiguous segments at ranges reserved with one
-// global atomic per chunk.  The next tile's indices load while this one is
-// sorted.
+// its own counters; thread t then owns chunks 2t and 2t + 1: it sums their
+// counts over the warps, and a block scan of those sums gives each chunk's
+// segment start in the tile.  The same thread turns its chunks' per-warp
+// counts into absolute slots and fixes the segment's global position: from
+// its own cursor when the CTA owns the tile's destination chunk (every tile
+// of that chunk is in the CTA's range, so the buckets (c, d) have no other
+// writer), else from one global atomic per chunk.  The tile is staged in
+// shared memory grouped by chunk (source index; tile index and chunk packed
+// in one word) and written out as contiguous segments.  The next tile's
+// indices load while this one is sorted.
 struct PartitionSmem {
-    uint32_t s_st[kTile], i_st[kTile];
-    uint16_t c_of[kTile];
-    uint32_t cnt[kWarps][kMaxChunks];   // per-warp counts, then per-warp offsets
-    uint32_t seg[kMaxChunks];           // segment start of each chunk in the tile
-    uint32_t gb[kMaxChunks];            // global start of each chunk's segment
+    uint32_t s_st[kTile];               // source index, grouped by chunk
+    uint32_t kc_st[kTile];              // tile index k | chunk << 12
+    uint32_t cnt[kWarps][kMaxChunks];   // per-warp counts, then per-warp slots
+    uint32_t delta[kMaxChunks];         // global position of tile slot 0 of the chunk's segment
+    uint32_t cur[kMaxChunks];           // owned destination chunk: next free slot of bucket (c, d)
     uint32_t warp_sums[kWarps];
 };
+static_assert(kTile <= 4096 && kMaxChunks <= (1 << 20), "tile index and chunk share one word");
 
-__global__ void __launch_bounds__(kThreads, 3) k_l2_partition(const L2Reorder p, uint32_t tiles_per_cta)
+__global__ void __launch_bounds__(kThreads, 3) k_l2_partition(const L2Reorder p, uint32_t tiles_per_cta,
+                                                              uint32_t own)
 {
     if (!bucketed(p)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -253,14 +323,22 @@ __global__ void __launch_bounds__(kThreads, 3) k_l2_partition(const L2Reorder p,
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t tiles = (p.n + kTile - 1) / kTile;
     const uint32_t t0 = blockIdx.x * tiles_per_cta, t1 = min(tiles, t0 + tiles_per_cta);
+    const uint32_t c0 = 2 * threadIdx.x;  // this thread's chunks: c0, c0 + 1
     for (uint32_t c = threadIdx.x; c < kWarps * kMaxChunks; c += kThreads) (&S.cnt[0][0])[c] = 0;
-    __syncthreads();
+    uint32_t cur_d = 0xFFFFFFFFu;
     uint32_t v[kPer];
     if (t0 < t1) load_tile(p, t0 * kTile, min(uint32_t(kTile), p.n - t0 * kTile), v);
+    __syncthreads();
     for (uint32_t t = t0; t < t1; ++t) {
         const uint32_t i0 = t * kTile;
         const uint32_t m = min(uint32_t(kTile), p.n - i0);
         const uint32_t d = dest_chunk(p, i0);
+        // an owned destination chunk starts: its buckets' first slots
+        uint32_t cb0 = 0, cb1 = 0;
+        if (own && d != cur_d) {
+            if (c0 < p.C) cb0 = p.base[c0 * p.D + d];
+            if (c0 + 1 < p.C) cb1 = p.base[(c0 + 1) * p.D + d];
+        }
         uint32_t nxt[kPer];
         if (t + 1 < t1) load_tile(p, (t + 1) * kTile, min(uint32_t(kTile), p.n - (t + 1) * kTile), nxt);
         uint32_t rk[kPer];
@@ -270,67 +348,79 @@ __global__ void __launch_bounds__(kThreads, 3) k_l2_partition(const L2Reorder p,
             rk[j] = k < m ? atomicAdd(&S.cnt[w][chunk_of(p, v[j])], 1u) : 0u;
         }
         __syncthreads();
-        // per chunk: tile total, exclusive offsets of the warps (in place)
-        for (uint32_t c = threadIdx.x; c < p.C; c += kThreads) {
-            uint32_t run = 0;
+        uint32_t a = 0, b = 0;
+        if (c0 < p.C) {
+#pragma unroll
+            for (int x = 0; x < kWarps; ++x) a += S.cnt[x][c0];
+        }
+        if (c0 + 1 < p.C) {
+#pragma unroll
+            for (int x = 0; x < kWarps; ++x) b += S.cnt[x][c0 + 1];
+        }
+        uint32_t xs = a + b;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, xs, o);
+            if (lane >= o) xs += y;
+        }
+        if (lane == 31) S.warp_sums[w] = xs;
+        __syncthreads();
+        uint32_t before = 0;
+#pragma unroll
+        for (int x = 0; x < kWarps; ++x) before += x < int(w) ? S.warp_sums[x] : 0u;
+        const uint32_t e0 = before + xs - (a + b), e1 = e0 + a;  // segment starts of c0, c0 + 1
+        if (c0 < p.C) {
+            uint32_t run = e0;
 #pragma unroll
             for (int x = 0; x < kWarps; ++x) {
-                const uint32_t q = S.cnt[x][c];
-                S.cnt[x][c] = run;
+                const uint32_t q = S.cnt[x][c0];
+                S.cnt[x][c0] = run;
                 run += q;
             }
-            S.seg[c] = run;  // tile count of chunk c, turned into a start below
+            uint32_t g = 0;
+            if (own) {
+                g = d != cur_d ? cb0 : S.cur[c0];
+                S.cur[c0] = g + a;
+            } else if (a) {
+                g = atomicAdd(&p.cursor[c0 * p.D + d], a);
+            }
+            S.delta[c0] = g - e0;
         }
-        __syncthreads();
-        // exclusive scan of the C chunk counts (C <= 512: two per thread)
-        {
-            const uint32_t c0 = 2 * threadIdx.x;
-            const uint32_t a = c0 < p.C ? S.seg[c0] : 0u, b = c0 + 1 < p.C ? S.seg[c0 + 1] : 0u;
-            uint32_t x = a + b;
+        if (c0 + 1 < p.C) {
+            uint32_t run = e1;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
+            for (int x = 0; x < kWarps; ++x) {
+                const uint32_t q = S.cnt[x][c0 + 1];
+                S.cnt[x][c0 + 1] = run;
+                run += q;
             }
-            if (lane == 31) S.warp_sums[w] = x;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                uint32_t acc = 0;
-                for (int x2 = 0; x2 < kWarps; ++x2) {
-                    const uint32_t q = S.warp_sums[x2];
-                    S.warp_sums[x2] = acc;
-                    acc += q;
-                }
+            uint32_t g = 0;
+            if (own) {
+                g = d != cur_d ? cb1 : S.cur[c0 + 1];
+                S.cur[c0 + 1] = g + b;
+            } else if (b) {
+                g = atomicAdd(&p.cursor[(c0 + 1) * p.D + d], b);
             }
-            __syncthreads();
-            const uint32_t e = S.warp_sums[w] + x - (a + b);
-            if (c0 < p.C) {
-                S.seg[c0] = e;
-                if (a) S.gb[c0] = atomicAdd(&p.cursor[c0 * p.D + d], a);
-            }
-            if (c0 + 1 < p.C) {
-                S.seg[c0 + 1] = e + a;
-                if (b) S.gb[c0 + 1] = atomicAdd(&p.cursor[(c0 + 1) * p.D + d], b);
-            }
+            S.delta[c0 + 1] = g - e1;
         }
+        cur_d = d;
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
             const uint32_t k = w * (kTile / kWarps) + j * 32 + lane;
             if (k < m) {
                 const uint32_t c = chunk_of(p, v[j]);
-                const uint32_t pos = S.seg[c] + S.cnt[w][c] + rk[j];
+                const uint32_t pos = S.cnt[w][c] + rk[j];
                 S.s_st[pos] = v[j];
-                S.i_st[pos] = i0 + k;
-                S.c_of[pos] = uint16_t(c);
+                S.kc_st[pos] = k | (c << 12);
             }
         }
         __syncthreads();
         for (uint32_t q = threadIdx.x; q < m; q += kThreads) {
-            const uint32_t c = S.c_of[q];
-            const uint32_t g = S.gb[c] + (q - S.seg[c]);
+            const uint32_t kc = S.kc_st[q];
+            const uint32_t g = S.delta[kc >> 12] + q;
             p.sarr[g] = S.s_st[q];
-            p.iarr[g] = S.i_st[q];
+            p.iarr[g] = i0 + (kc & (kTile - 1));
         }
         // only the C chunks in use need zeroing (not all kMaxChunks)
         for (uint32_t x = threadIdx.x; x < kWarps * p.C; x += kThreads) S.cnt[x / p.C][x % p.C] = 0;
@@ -441,6 +531,59 @@ __global__ void __launch_bounds__(kThreads) k_l2_scatter(const L2Reorder p)
     }
 }
 
+// K6, shared-memory form: CTA-sized destination chunks.  The warps split the
+// chunk's C buckets; each value goes to its slot of the chunk in shared
+// memory (i & dmask: every i of bucket (c, d) lies in chunk d by
+// construction, the mask only keeps a corrupt word inside the buffer), then
+// the CTA writes the chunk out, 16 bytes per lane when dst allows.
+template <int W>
+__global__ void __launch_bounds__(kScatterThreads) k_l2_scatter_smem(const L2Reorder p)
+{
+    if (!bucketed(p)) return;
+    using T = typename Word<W>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *chunk = reinterpret_cast<T *>(smem_raw);
+    const uint64_t first = l2_evict_first();
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr uint32_t kW = kScatterThreads / 32;
+    constexpr int U = 4;
+    const uint32_t dmask = (1u << p.ds_shift) - 1;
+    const bool vec = (reinterpret_cast<uintptr_t>(p.dst) & 15) == 0;
+    for (uint32_t d = blockIdx.x; d < p.D; d += gridDim.x) {
+        for (uint32_t c = warp; c < p.C; c += kW) {
+            const uint32_t b = c * p.D + d;
+            const uint32_t k1 = p.base[b] + p.hist[b];
+            uint32_t k = p.base[b] + lane;
+            for (; k + 32 * (U - 1) < k1; k += 32 * U) {
+                uint32_t di[U];
+                T val[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    di[u] = ldg_hint<4>(p.iarr + k + 32 * u, first);
+                    val[u] = ldg_hint<W>(p.varr + uint64_t(k + 32 * u) * W, first);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) chunk[di[u] & dmask] = val[u];
+            }
+            for (; k < k1; k += 32) chunk[ldg_hint<4>(p.iarr + k, first) & dmask] = ldg_hint<W>(p.varr + uint64_t(k) * W, first);
+        }
+        __syncthreads();
+        const uint64_t i0 = uint64_t(d) << p.ds_shift;
+        const uint32_t m = uint32_t(min(uint64_t(dmask) + 1, uint64_t(p.n) - i0));
+        char *out = p.dst + i0 * W;
+        uint32_t done = 0;
+        if (vec) {
+            const uint32_t nv = m * W / 16;
+            const uint4 *c16 = reinterpret_cast<const uint4 *>(smem_raw);
+            for (uint32_t q = threadIdx.x; q < nv; q += kScatterThreads)
+                reinterpret_cast<uint4 *>(out)[q] = c16[q];
+            done = nv * 16 / W;
+        }
+        for (uint32_t q = done + threadIdx.x; q < m; q += kScatterThreads) reinterpret_cast<T *>(out)[q] = chunk[q];
+        __syncthreads();
+    }
+}
+
 // Scatter form, last pass: dst[s[k]] = v[k] in k order (c-major: one
 // destination chunk at a time, L2-resident while its sectors are completed).
 template <int W>
@@ -516,17 +659,26 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
     p.dst = g.dst;
     p.idx = g.idx;
     p.n = uint32_t(g.n);
-    // ~16 MB chunks, at most kMaxChunks of them
+    // ~16 MB source chunks, at most kMaxChunks of them
     uint32_t shift = 0;
     while ((uint64_t(1) << shift) * W < (uint64_t(16) << 20)) ++shift;
     while (((uint64_t(g.n) + (uint64_t(1) << shift) - 1) >> shift) > kMaxChunks) ++shift;
     p.cs_shift = shift;
-    p.C = p.D = uint32_t((uint64_t(g.n) + (uint64_t(1) << shift) - 1) >> shift);
-    if (g.scatter) p.D = 1;  // buckets by destination chunk only
+    p.C = uint32_t((uint64_t(g.n) + (uint64_t(1) << shift) - 1) >> shift);
+    // destination chunks: CTA-sized (shared-memory scatter) while the bucket
+    // count stays within the tuned bound, else the source chunks' size
+    uint32_t dshift = 0;
+    while ((uint64_t(2) << dshift) * W <= kScatterChunkBytes) ++dshift;
+    const uint64_t d_small = (uint64_t(g.n) + (uint64_t(1) << dshift) - 1) >> dshift;
+    const bool smem_scatter =
+        !g.scatter && uint64_t(p.C) * d_small <= std::min<uint64_t>(reorder_smem_max_buckets(), uint64_t(1) << 24);
+    p.ds_shift = smem_scatter ? dshift : shift;
+    p.D = g.scatter ? 1u : smem_scatter ? uint32_t(d_small) : p.C;
     const uint32_t nb = p.C * p.D;
     auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-    const size_t off_hist = 256, off_base = off_hist + al(nb * 4), off_cur = off_base + al(nb * 4),
-                 off_up = off_cur + al(nb * 4), off_s = off_up + al((nb + 1) * 4), off_i = off_s + al(size_t(g.n) * 4),
+    const size_t off_hist = 256, off_row = off_hist + al(size_t(nb) * 4), off_base = off_row + al(size_t(p.C) * 4),
+                 off_cur = off_base + al(size_t(nb) * 4), off_up = off_cur + al(size_t(nb) * 4),
+                 off_s = off_up + al((size_t(nb) + 1) * 4), off_i = off_s + al(size_t(g.n) * 4),
                  off_v = off_i + al(size_t(g.n) * 4), bytes = off_v + al(size_t(g.n) * W);
     cudaMemPool_t pool;
     cudaError_t e = get_pool(pool);
@@ -538,6 +690,7 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
     p.ctr_gather = reinterpret_cast<unsigned int *>(scratch + 8);
     p.ctr_scatter = reinterpret_cast<unsigned int *>(scratch + 16);
     p.hist = reinterpret_cast<uint32_t *>(scratch + off_hist);
+    p.rowtot = reinterpret_cast<uint32_t *>(scratch + off_row);
     p.base = reinterpret_cast<uint32_t *>(scratch + off_base);
     p.cursor = reinterpret_cast<uint32_t *>(scratch + off_cur);
     p.uprefix = reinterpret_cast<uint32_t *>(scratch + off_up);
@@ -546,7 +699,7 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
     p.varr = scratch + off_v;
     const uint64_t pairs = uint64_t(kSampleRuns) * (kSampleLen - 1);
     p.near_threshold = pairs / 2;
-    e = cudaMemsetAsync(scratch, 0, off_base, s);  // near counter and histogram
+    e = cudaMemsetAsync(scratch, 0, off_base, s);  // near counter, histogram, row totals
 
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
@@ -558,38 +711,63 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
     // Per device, once: the partition's shared-memory opt-in and occupancy.
     static std::mutex setup_mu;
     static bool smem_set[64] = {false};
-    static int part_per_sm[64] = {0};
-    int per_sm_part = 1;
+    static int part_per_sm[64] = {0}, scat_per_sm[64] = {0};
+    int per_sm_part = 1, per_sm_scat = 1;
     if (dev >= 0 && dev < 64) {
         std::lock_guard<std::mutex> lock(setup_mu);
         if (!smem_set[dev]) {
             e = cudaFuncSetAttribute(k_l2_partition, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      int(sizeof(PartitionSmem)));
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_l2_scatter_smem<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(kScatterChunkBytes));
             smem_set[dev] = e == cudaSuccess;
             int per_sm = 0;
             if (e == cudaSuccess && cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                                         &per_sm, k_l2_partition, kThreads, sizeof(PartitionSmem)) == cudaSuccess)
                 part_per_sm[dev] = per_sm;
+            per_sm = 0;
+            if (e == cudaSuccess && cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                        &per_sm, k_l2_scatter_smem<W>, kScatterThreads, kScatterChunkBytes) ==
+                                        cudaSuccess)
+                scat_per_sm[dev] = per_sm;
         }
         per_sm_part = std::max(1, part_per_sm[dev]);
+        per_sm_scat = std::max(1, scat_per_sm[dev]);
     }
     // The partition runs one wave: every resident CTA takes a contiguous
     // range of tiles (a second, partial wave would leave SMs idle).
     const uint32_t part_resident = uint32_t(sms) * uint32_t(per_sm_part);
-    const uint32_t part_tpc = (tiles + part_resident - 1) / part_resident;
+    // With CTA-sized destination chunks every CTA takes whole chunks (a
+    // multiple of the chunk's tiles) and writes their buckets alone.
+    const uint32_t tpd = smem_scatter ? (1u << p.ds_shift) / kTile : 1u;
+    uint32_t part_tpc = (tiles + part_resident - 1) / part_resident;
+    part_tpc = (part_tpc + tpd - 1) / tpd * tpd;
     const unsigned part_grid = unsigned((tiles + part_tpc - 1) / part_tpc);
     const unsigned pers = unsigned(sms) * 8;  // persistent grids of the gated passes
     const uint64_t dunits = (g.n + g.unit_elems - 1) / g.unit_elems;
     if (e == cudaSuccess) { k_l2_sample<<<kSampleRuns / (kThreads / 32), kThreads, 0, s>>>(p); e = cudaGetLastError(); }
     if (e == cudaSuccess) { k_l2_hist<<<pgrid, kThreads, 0, s>>>(p, tpc); e = cudaGetLastError(); }
-    if (e == cudaSuccess) { k_l2_scan<<<1, 1024, 0, s>>>(p); e = cudaGetLastError(); }
     if (e == cudaSuccess) {
-        k_l2_partition<<<part_grid, kThreads, sizeof(PartitionSmem), s>>>(p, part_tpc);
+        if (smem_scatter) k_l2_scan_rows<<<p.C, 1024, 0, s>>>(p);
+        else k_l2_scan<<<1, 1024, 0, s>>>(p);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        k_l2_partition<<<part_grid, kThreads, sizeof(PartitionSmem), s>>>(p, part_tpc, smem_scatter ? 1u : 0u);
         e = cudaGetLastError();
     }
     if (!g.scatter) {
         if (e == cudaSuccess) { k_l2_gather<W><<<pers, kThreads, 0, s>>>(p); e = cudaGetLastError(); }
-        if (e == cudaSuccess) { k_l2_scatter<W><<<pers, kThreads, 0, s>>>(p); e = cudaGetLastError(); }
+        if (e == cudaSuccess) {
+            if (smem_scatter) {
+                const unsigned sgrid = unsigned(std::min<uint64_t>(p.D, uint64_t(sms) * per_sm_scat));
+                k_l2_scatter_smem<W><<<sgrid, kScatterThreads, kScatterChunkBytes, s>>>(p);
+            } else {
+                k_l2_scatter<W><<<pers, kThreads, 0, s>>>(p);
+            }
+            e = cudaGetLastError();
+        }
     } else {
         L2Reorder q = p;  // v[k] = src[i[k]]: gather by the source positions
         q.sarr = p.iarr;
@@ -597,7 +775,10 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
         if (e == cudaSuccess) { k_l2_scatter_linear<W><<<pers, kThreads, 0, s>>>(p); e = cudaGetLastError(); }
     }
     if (e == cudaSuccess) {
-        k_l2_direct<W><<<unsigned(std::min<uint64_t>(dunits, 0x7FFFFFFFull)), kThreads, 0, s>>>(p, g, dunits);
+        // two resident waves: when the bucketed passes ran, the grid exits at
+        // once; when it gathers, that is as fast as one CTA per unit
+        const uint64_t cap = uint64_t(sms) * 16;
+        k_l2_direct<W><<<unsigned(std::min<uint64_t>(dunits, cap)), kThreads, 0, s>>>(p, g, dunits);
         e = cudaGetLastError();
     }
     g_launches.fetch_add(7, std::memory_order_relaxed);

@@ -5,6 +5,7 @@
 //   min_grab <v> | max_grab <v> | grabs_per_cta <v>
 //   thin_tile_bytes <v> | thin_tile_cells <v> | thin_l2_bytes <v>
 //   runs_mirror_bytes <v>   (1: never; runs of at most v bytes in input order)
+//   reorder_smem_buckets <v> (bucket bound of the shared-memory scatter; 1: never)
 //   rowb <E> <da_lo> <da_hi> <db_lo> <db_hi> <rowb> [<tile bytes>]
 // ("#" starts a comment line).  Plans compiled after a load use the new table.
 #include <cstdio>
@@ -35,6 +36,7 @@ struct Table {
     BatchTuning batch;
     ThinTuning thin;
     uint64_t runs_mirror_bytes = 0;
+    uint64_t reorder_smem_buckets = uint64_t(1) << 22;
     std::vector<RowbRule> rowb;
 };
 
@@ -66,6 +68,7 @@ std::shared_ptr<const Table> parse(const char *path)
             else if (!std::strcmp(key, "thin_tile_cells")) t->thin.tile_cells = v;
             else if (!std::strcmp(key, "thin_l2_bytes")) t->thin.l2_bytes = v;
             else if (!std::strcmp(key, "runs_mirror_bytes")) t->runs_mirror_bytes = v;
+            else if (!std::strcmp(key, "reorder_smem_buckets")) t->reorder_smem_buckets = v;
         }
     }
     std::fclose(f);
@@ -94,6 +97,8 @@ BatchTuning batch_tuning() { return current()->batch; }
 ThinTuning thin_tuning() { return current()->thin; }
 
 uint64_t runs_mirror_max_bytes() { return current()->runs_mirror_bytes; }
+
+uint64_t reorder_smem_max_buckets() { return current()->reorder_smem_buckets; }
 
 bool tuned_shape(int E, int64_t DA, int64_t DB, TileShape &shape)
 {

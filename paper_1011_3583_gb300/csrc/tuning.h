@@ -42,6 +42,11 @@ uint64_t runs_mirror_max_bytes();
 
 ThinTuning thin_tuning();
 
+// A large random reorder scatters through CTA-sized destination chunks in
+// shared memory when its (source chunk, destination chunk) bucket count is at
+// most this; above it (or at 1) it scatters through ~16 MB chunks in the L2.
+uint64_t reorder_smem_max_buckets();
+
 // Shape of a fast tile: staged row bytes (128, 256 or 512) and payload bytes
 // (16384, or 8192 for the half tile).
 struct TileShape {

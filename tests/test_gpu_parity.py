@@ -398,6 +398,31 @@ def test_reorder_large_sources(lr, orc, e, kind):
     _l2_case(lr, orc, e, n, idx, seed=e * 100 + len(kind))
 
 
+@pytest.mark.parametrize("e,kind", [(4, "perm"), (8, "repeat"), (16, "perm")])
+def test_reorder_large_sources_l2_scatter(lr, orc, tmp_path, e, kind):
+    """The bucketed reorder with its last pass through ~16 MB destination
+    chunks in the L2 (the form taken when CTA-sized destination chunks would
+    need too many buckets), forced through the tuning table."""
+    n = (128 << 20) // e + 4099
+    idx = synth.random_permutation(17 + e, n) if kind == "perm" else synth.random_indices(18 + e, n, n)
+    t = tmp_path / "l2_scatter.txt"
+    t.write_text("reorder_smem_buckets 1\n")
+    try:
+        lr.tuning_load(str(t))
+        _l2_case(lr, orc, e, n, idx, seed=e * 10 + 3)
+    finally:
+        lr.tuning_load(None)
+        lr.tuning_load(lr.DEFAULT_TUNE_TABLE)
+
+
+def test_reorder_smem_scatter_chunk_edges(lr, orc):
+    """Sources just over 128 MiB whose last 64 KB destination chunk holds one
+    element, one tile, and one element short of a full chunk."""
+    for e, extra in ((4, 1), (4, 4096), (8, (64 << 10) // 8 - 1), (16, 3)):
+        n = (128 << 20) // e + extra
+        _l2_case(lr, orc, e, n, synth.random_permutation(extra + e, n), seed=e + extra)
+
+
 def test_every_tile_shape(lr, orc, tmp_path):
     """Each fast-tile shape (128/256/512-byte rows, 16 KB and 8 KB tiles),
     forced through the tuning table, gives the oracle's bytes on planes with
