@@ -679,7 +679,8 @@ def run_reference(args):
 def parse_case(spec: str):
     """Single-op case spec: permute:E:d0,d1,..:p0,p1,.. | reorder:E:n:random|block4096 |
     interlace:E:n:k | deinterlace:E:n:k | nm:E:dims:order:base:range (comma lists);
-    batch:N and stencil:TAPS:NY:NX[:BOUNDARY] are handled by their own runners."""
+    batch:N, stencil:TAPS:NY:NX[:BOUNDARY] and dist:E:dims:perm:P are handled by
+    their own runners."""
     parts = spec.split(":")
     kind, e = parts[0], int(parts[1])
     if kind == "permute":
@@ -753,6 +754,43 @@ def run_stencil_case(torch, rr, stream, dev, spec, args):
             "steps": args.steps}
 
 
+def run_dist_case(torch, rr, stream, dev, spec, args):
+    """dist:E:d0,d1,..:p0,p1,..:P -- the distributed permute's local steps for
+    P ranks emulated on one GPU: every rank's pack, the exchange (a device
+    permute of the P x P pieces standing in for the all-to-all) and every
+    rank's unpack, each timed on its own.  GB/s counts the read + write of all
+    P slabs."""
+    parts = spec.split(":")
+    e, P = int(parts[1]), int(parts[4])
+    dims, perm = [int(x) for x in parts[2].split(",")], [int(x) for x in parts[3].split(",")]
+    plan = rr.dist_permute_plan(e, dims, perm, P)
+    sb = plan.slab_bytes
+    glob = torch.empty(sb * P, dtype=torch.uint8, device=dev).random_()
+    send, recv, out = torch.empty_like(glob), torch.empty_like(glob), torch.empty_like(glob)
+    first = send if plan.exchange else out
+
+    def pack():
+        for r in range(P):
+            rr.dist_permute_pack(first[r * sb:(r + 1) * sb], glob[r * sb:(r + 1) * sb], plan, e, stream)
+
+    def exchange():
+        rr.permute(recv, send, 1, [P, P, plan.piece_bytes], [1, 0, 2], stream)
+
+    def unpack():
+        for r in range(P):
+            rr.dist_permute_unpack(out[r * sb:(r + 1) * sb], recv[r * sb:(r + 1) * sb], plan, e, stream)
+
+    nbytes = 2 * sb * P
+    res = {"case": spec, "bytes_per_step": nbytes, "exchange": bool(plan.exchange), "steps": args.steps,
+           "pack_permute": plan.pack(), "unpack_permute": plan.unpack() if plan.exchange else None}
+    for name, call in (("pack", pack), ("exchange", exchange), ("unpack", unpack)):
+        if name != "pack" and not plan.exchange:
+            continue
+        med, best = _time_calls(torch, stream, call, args.steps, args.warmup)
+        res[name] = {"median_ms": round(med * 1e3, 4), "gbs_median": round(nbytes / med / 1e9, 1)}
+    return res
+
+
 def run_case(args):
     """Time one op (used for profiling captures and sweeps): W untimed and K
     timed calls on one stream, CUDA events around each call."""
@@ -767,6 +805,8 @@ def run_case(args):
         return run_batch_case(torch, rr, stream, dev, int(args.case.split(":")[1]), args)
     if args.case.startswith("stencil:"):
         return run_stencil_case(torch, rr, stream, dev, args.case, args)
+    if args.case.startswith("dist:"):
+        return run_dist_case(torch, rr, stream, dev, args.case, args)
     o = parse_case(args.case)
     e = o["elem_bytes"]
     if o["kind"] == "nm":

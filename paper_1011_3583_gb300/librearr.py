@@ -73,6 +73,23 @@ def lib_path() -> str:
     return LIB
 
 
+class DistPlan(ctypes.Structure):
+    """rearr_dist_plan (include/librearr_dist.h)."""
+    _fields_ = [("nranks", ctypes.c_int), ("exchange", ctypes.c_int), ("slab_bytes", ctypes.c_uint64),
+                ("piece_bytes", ctypes.c_uint64),
+                ("pack_rank", ctypes.c_int), ("pack_dims", ctypes.c_int64 * 8), ("pack_perm", ctypes.c_int * 8),
+                ("unpack_rank", ctypes.c_int), ("unpack_dims", ctypes.c_int64 * 8),
+                ("unpack_perm", ctypes.c_int * 8)]
+
+    def pack(self):
+        """(dims, perm) of the pack permute."""
+        return list(self.pack_dims[:self.pack_rank]), list(self.pack_perm[:self.pack_rank])
+
+    def unpack(self):
+        """(dims, perm) of the unpack permute (exchange plans)."""
+        return list(self.unpack_dims[:self.unpack_rank]), list(self.unpack_perm[:self.unpack_rank])
+
+
 def load() -> ctypes.CDLL:
     """Load librearr.so (raises if it has not been built)."""
     global _lib
@@ -121,6 +138,9 @@ def load() -> ctypes.CDLL:
         "rearr_inject_wait_timeout": (st, [ctypes.c_int]),
         "rearr_check_indices": (st, [vp, sz, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), vp]),
         "rearr_reorder_checked": (st, [vp, vp, vp, sz, sz, vp]),
+        "rearr_dist_permute_plan": (st, [sz, ctypes.c_int, i64p, ip, ctypes.c_int, ctypes.POINTER(DistPlan)]),
+        "rearr_dist_permute_pack": (st, [vp, vp, ctypes.POINTER(DistPlan), sz, vp]),
+        "rearr_dist_permute_unpack": (st, [vp, vp, ctypes.POINTER(DistPlan), sz, vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -184,6 +204,27 @@ def permute(dst, src, elem_bytes: int, dims: Sequence[int], perm: Sequence[int],
     """rearr_permute: dst = src transposed by perm (numpy semantics, row-major)."""
     rank, d, p = _dims_perm(dims, perm)
     _check(load().rearr_permute(_ptr(dst), _ptr(src), int(elem_bytes), rank, d, p, _stream(stream)))
+
+
+def dist_permute_plan(elem_bytes: int, dims: Sequence[int], perm: Sequence[int], nranks: int) -> DistPlan:
+    """rearr_dist_permute_plan: the pack / unpack permutes of a permute of an
+    array sharded along its slowest axis over nranks ranks (host only)."""
+    rank, d, p = _dims_perm(dims, perm)
+    plan = DistPlan()
+    _check(load().rearr_dist_permute_plan(int(elem_bytes), rank, d, p, int(nranks), ctypes.byref(plan)))
+    return plan
+
+
+def dist_permute_pack(send, in_slab, plan: DistPlan, elem_bytes: int, stream=None) -> None:
+    """rearr_dist_permute_pack: send (or the output slab, plan.exchange == 0) <- in_slab."""
+    _check(load().rearr_dist_permute_pack(_ptr(send), _ptr(in_slab), ctypes.byref(plan), int(elem_bytes),
+                                          _stream(stream)))
+
+
+def dist_permute_unpack(out_slab, recv, plan: DistPlan, elem_bytes: int, stream=None) -> None:
+    """rearr_dist_permute_unpack: out_slab <- the received pieces."""
+    _check(load().rearr_dist_permute_unpack(_ptr(out_slab), _ptr(recv), ctypes.byref(plan), int(elem_bytes),
+                                            _stream(stream)))
 
 
 def _nm_args(dims, order, base, rng):
