@@ -33,10 +33,10 @@
 //   K7 direct    : the plain gather (when K1 found locality).
 // Traffic: 2 (idx) + 2 (s, i written) + 2 (s, i read) + 1 (src) + 2 (v) + 1
 // (dst) = 10 n-word passes of streaming access instead of n random accesses.
-// A scatter (dst[idx[i]] = src[i]) uses one destination dimension only
-// (D = 1, buckets by the chunk of idx[i]): the partition's source positions
-// are read back in order to gather v (reads local to each tile), and a linear
-// pass writes dst[s[k]] = v[k] with the destination chunk L2-resident.
+// A scatter (dst[idx[i]] = src[i]) uses one bucket dimension only (D = 1,
+// buckets by the destination chunk of idx[i]): the partition writes
+// (destination index, element) pairs, and a linear pass writes
+// dst[s[k]] = v[k] with the destination chunk L2-resident.
 // Scratch ((8 + E) n bytes) comes from a stream-ordered pool owned by the
 // library; the kernels are ordered on the caller's stream and none waits on
 // another.
@@ -313,13 +313,21 @@ struct PartitionSmem {
     uint32_t warp_sums[kWarps];
 };
 static_assert(kTile <= 4096 && kMaxChunks <= (1 << 20), "tile index and chunk share one word");
+static_assert(sizeof(PartitionSmem) % 16 == 0, "the scatter form's element buffer follows, 16-byte aligned");
 
+// SW = 0: gather form (s-array: source index, i-array: destination index).
+// SW = W: scatter form (s-array: destination index, v-array: the element
+// itself): the tile's source elements are copied into shared memory with
+// cp.async behind the index loads and written out beside their indices, so
+// the scatter needs no separate pass that reads the source by position.
+template <int SW>
 __global__ void __launch_bounds__(kThreads, 3) k_l2_partition(const L2Reorder p, uint32_t tiles_per_cta,
                                                               uint32_t own)
 {
     if (!bucketed(p)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PartitionSmem &S = *reinterpret_cast<PartitionSmem *>(smem_raw);
+    unsigned char *vals = smem_raw + sizeof(PartitionSmem);  // scatter form: kTile * SW bytes
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t tiles = (p.n + kTile - 1) / kTile;
     const uint32_t t0 = blockIdx.x * tiles_per_cta, t1 = min(tiles, t0 + tiles_per_cta);
@@ -338,6 +346,19 @@ __global__ void __launch_bounds__(kThreads, 3) k_l2_partition(const L2Reorder p,
         if (own && d != cur_d) {
             if (c0 < p.C) cb0 = p.base[c0 * p.D + d];
             if (c0 + 1 < p.C) cb1 = p.base[(c0 + 1) * p.D + d];
+        }
+        if constexpr (SW > 0) {
+            // the tile's source elements -> shared memory (waited for before the write-out)
+            const char *g = p.src + uint64_t(i0) * SW;
+            if ((reinterpret_cast<uintptr_t>(p.src) & 15) == 0) {
+                for (uint32_t x = threadIdx.x; x < m * SW / 16; x += kThreads)
+                    cp_async<16>(vals + 16 * x, g + 16 * x);
+                for (uint32_t k = m * SW / 16 * 16 / SW + threadIdx.x; k < m; k += kThreads)
+                    cp_async<SW>(vals + k * SW, g + uint64_t(k) * SW);
+            } else {
+                for (uint32_t k = threadIdx.x; k < m; k += kThreads) cp_async<SW>(vals + k * SW, g + uint64_t(k) * SW);
+            }
+            cp_async_commit();
         }
         uint32_t nxt[kPer];
         if (t + 1 < t1) load_tile(p, (t + 1) * kTile, min(uint32_t(kTile), p.n - (t + 1) * kTile), nxt);
@@ -415,12 +436,18 @@ __global__ void __launch_bounds__(kThreads, 3) k_l2_partition(const L2Reorder p,
                 S.kc_st[pos] = k | (c << 12);
             }
         }
+        if constexpr (SW > 0) cp_async_wait<0>();
         __syncthreads();
         for (uint32_t q = threadIdx.x; q < m; q += kThreads) {
             const uint32_t kc = S.kc_st[q];
             const uint32_t g = S.delta[kc >> 12] + q;
             p.sarr[g] = S.s_st[q];
-            p.iarr[g] = i0 + (kc & (kTile - 1));
+            if constexpr (SW > 0) {
+                using T = typename Word<SW>::T;
+                reinterpret_cast<T *>(p.varr)[g] = reinterpret_cast<const T *>(vals)[kc & (kTile - 1)];
+            } else {
+                p.iarr[g] = i0 + (kc & (kTile - 1));
+            }
         }
         // only the C chunks in use need zeroing (not all kMaxChunks)
         for (uint32_t x = threadIdx.x; x < kWarps * p.C; x += kThreads) S.cnt[x / p.C][x % p.C] = 0;
@@ -711,28 +738,36 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
     // Per device, once: the partition's shared-memory opt-in and occupancy.
     static std::mutex setup_mu;
     static bool smem_set[64] = {false};
-    static int part_per_sm[64] = {0}, scat_per_sm[64] = {0};
+    static int part_per_sm[64] = {0}, spart_per_sm[64] = {0}, scat_per_sm[64] = {0};
     int per_sm_part = 1, per_sm_scat = 1;
     if (dev >= 0 && dev < 64) {
         std::lock_guard<std::mutex> lock(setup_mu);
         if (!smem_set[dev]) {
-            e = cudaFuncSetAttribute(k_l2_partition, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(k_l2_partition<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      int(sizeof(PartitionSmem)));
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_l2_partition<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(sizeof(PartitionSmem) + kTile * W));
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(k_l2_scatter_smem<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(kScatterChunkBytes));
             smem_set[dev] = e == cudaSuccess;
             int per_sm = 0;
             if (e == cudaSuccess && cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                        &per_sm, k_l2_partition, kThreads, sizeof(PartitionSmem)) == cudaSuccess)
+                                        &per_sm, k_l2_partition<0>, kThreads, sizeof(PartitionSmem)) == cudaSuccess)
                 part_per_sm[dev] = per_sm;
+            per_sm = 0;
+            if (e == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_l2_partition<W>, kThreads,
+                                                              sizeof(PartitionSmem) + kTile * W) == cudaSuccess)
+                spart_per_sm[dev] = per_sm;
             per_sm = 0;
             if (e == cudaSuccess && cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                                         &per_sm, k_l2_scatter_smem<W>, kScatterThreads, kScatterChunkBytes) ==
                                         cudaSuccess)
                 scat_per_sm[dev] = per_sm;
         }
-        per_sm_part = std::max(1, part_per_sm[dev]);
+        per_sm_part = std::max(1, g.scatter ? spart_per_sm[dev] : part_per_sm[dev]);
         per_sm_scat = std::max(1, scat_per_sm[dev]);
     }
     // The partition runs one wave: every resident CTA takes a contiguous
@@ -754,7 +789,10 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        k_l2_partition<<<part_grid, kThreads, sizeof(PartitionSmem), s>>>(p, part_tpc, smem_scatter ? 1u : 0u);
+        if (g.scatter)
+            k_l2_partition<W><<<part_grid, kThreads, sizeof(PartitionSmem) + kTile * W, s>>>(p, part_tpc, 0u);
+        else
+            k_l2_partition<0><<<part_grid, kThreads, sizeof(PartitionSmem), s>>>(p, part_tpc, smem_scatter ? 1u : 0u);
         e = cudaGetLastError();
     }
     if (!g.scatter) {
@@ -769,9 +807,7 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
             e = cudaGetLastError();
         }
     } else {
-        L2Reorder q = p;  // v[k] = src[i[k]]: gather by the source positions
-        q.sarr = p.iarr;
-        if (e == cudaSuccess) { k_l2_gather<W><<<pers, kThreads, 0, s>>>(q); e = cudaGetLastError(); }
+        // the partition wrote (destination index, element) pairs
         if (e == cudaSuccess) { k_l2_scatter_linear<W><<<pers, kThreads, 0, s>>>(p); e = cudaGetLastError(); }
     }
     if (e == cudaSuccess) {
@@ -781,7 +817,7 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
         k_l2_direct<W><<<unsigned(std::min<uint64_t>(dunits, cap)), kThreads, 0, s>>>(p, g, dunits);
         e = cudaGetLastError();
     }
-    g_launches.fetch_add(7, std::memory_order_relaxed);
+    g_launches.fetch_add(g.scatter ? 6 : 7, std::memory_order_relaxed);
     cudaError_t e2 = cudaFreeAsync(scratch, s);
     return e != cudaSuccess ? e : e2;
 }
