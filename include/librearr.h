@@ -121,9 +121,10 @@ rearr_status rearr_reorder(void *dst, const void *src, const uint32_t *idx, size
  *   is undefined behaviour).  For a scatter whose indices repeat, a
  *   destination element receives one of the colliding source elements, which
  *   one is unspecified; with a permutation the result is unique.  idx must be
- *   aligned to its index size.  Large scatters with 4/8/16-byte elements and
- *   32-bit indices use the L2-resident passes of rearr_reorder (bucketed by
- *   destination chunk), with the same locality check and scratch pool.
+ *   aligned to its index size.  Large gathers and scatters with 4/8/16-byte
+ *   elements (either index size, n < 2^32) use the L2-resident passes of
+ *   rearr_reorder (a scatter's buckets by destination chunk), with the same
+ *   locality check and scratch pool.
  * ------------------------------------------------------------------------- */
 rearr_status rearr_scatter(void *dst, const void *src, const uint32_t *idx, size_t n,
                            size_t elem_bytes, rearr_stream_t stream);

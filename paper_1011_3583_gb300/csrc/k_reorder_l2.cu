@@ -1,5 +1,6 @@
 // k_reorder_l2.cu -- reorder by a large random index sequence with L2-resident
-// passes (dst[i] = src[idx[i]], arXiv:1011.3583 Sec. III.A indexed access).
+// passes (dst[i] = src[idx[i]], arXiv:1011.3583 Sec. III.A indexed access),
+// 32- or 64-bit indices, n < 2^32.
 //
 // A direct gather from a source far larger than the L2 pays a whole DRAM
 // access (32-64 B) for every element it reads.  Here the source is cut into
@@ -65,6 +66,7 @@ struct L2Reorder {
     const char *src;
     char *dst;
     const uint32_t *idx;
+    uint32_t idx64;                // 1: idx holds uint64 indices (every valid one < n < 2^32)
     uint32_t n;
     uint32_t cs_shift;             // source chunk = 2^cs_shift elements
     uint32_t ds_shift;             // destination chunk = 2^ds_shift elements (>= log2 kTile)
@@ -96,6 +98,13 @@ __device__ __forceinline__ uint32_t dest_chunk(const L2Reorder &p, uint32_t i)
     return p.D == 1 ? 0u : i >> p.ds_shift;
 }
 
+// Index i of the sequence, narrowed to 32 bits (an index >= n is undefined
+// behaviour for the caller either way).
+__device__ __forceinline__ uint32_t index_at(const L2Reorder &p, uint64_t i)
+{
+    return p.idx64 ? uint32_t(__ldg(reinterpret_cast<const unsigned long long *>(p.idx) + i)) : __ldg(p.idx + i);
+}
+
 __device__ __forceinline__ bool bucketed(const L2Reorder &p)
 {
     return *reinterpret_cast<volatile unsigned long long *>(p.near) < p.near_threshold;
@@ -110,7 +119,7 @@ __global__ void __launch_bounds__(kThreads) k_l2_sample(const L2Reorder p)
     uint32_t cnt = 0;
     if (r < kSampleRuns && p.n > kSampleLen) {
         const uint64_t start = uint64_t(r) * (p.n - kSampleLen) / kSampleRuns;
-        const uint32_t a = __ldg(p.idx + start + 2 * lane), b = __ldg(p.idx + start + 2 * lane + 1);
+        const uint32_t a = index_at(p, start + 2 * lane), b = index_at(p, start + 2 * lane + 1);
         const uint32_t next_a = __shfl_down_sync(0xffffffffu, a, 1);
         const uint32_t d1 = b > a ? b - a : a - b;
         const uint32_t d2 = next_a > b ? next_a - b : b - next_a;
@@ -133,7 +142,7 @@ __device__ __forceinline__ void load_tile(const L2Reorder &p, uint32_t i0, uint3
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
         const uint32_t k = w * (kTile / kWarps) + j * 32 + lane;
-        v[j] = k < m ? __ldg(p.idx + i0 + k) : 0xFFFFFFFFu;
+        v[j] = k < m ? index_at(p, i0 + k) : 0xFFFFFFFFu;
     }
 }
 
@@ -685,6 +694,7 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
     p.src = g.src;
     p.dst = g.dst;
     p.idx = g.idx;
+    p.idx64 = g.idx64;
     p.n = uint32_t(g.n);
     // ~16 MB source chunks, at most kMaxChunks of them
     uint32_t shift = 0;

@@ -514,7 +514,9 @@ rearr_status plan_reorder(void *dst, const void *src, const uint32_t *idx, size_
     // Sources much larger than the L2 go through the bucketed passes (which
     // fall back to this direct gather on the device if the indices turn out
     // to be local).
-    g.l2 = (g.vec && (W == 4 || W == 8 || W == 16) && bytes >= kReorderL2MinBytes && n <= 0xFFFFFFFFull) ? 1u : 0u;
+    // (64-bit indices too: every valid one is < n < 2^32)
+    const bool l2_ok = g.vec || (g.c == 1 && idx_bytes == 8 && contiguous % uint64_t(std::min(16, 4 * W)) == 0);
+    g.l2 = (l2_ok && (W == 4 || W == 8 || W == 16) && bytes >= kReorderL2MinBytes && n <= 0xFFFFFFFFull) ? 1u : 0u;
     return REARR_OK;
 }
 

@@ -166,3 +166,25 @@ def test_reorder_checked_leaves_dst_untouched(lr):
         lr.reorder_checked(d.ptr, s.ptr, ix.ptr, n, e)
     sync()
     assert np.all(d.download() == 0x33)
+
+
+@pytest.mark.parametrize("e,kind,scatter", [(4, "perm", False), (4, "perm", True), (4, "repeat", False),
+                                            (4, "block", False), (8, "perm", True), (16, "perm", False),
+                                            (16, "repeat", False)])
+def test_wide_indices_large_sources(lr, orc, e, kind, scatter):
+    """64-bit index sequences over sources of 128 MiB or more (the bucketed
+    passes read the 8-byte indices; the block-shuffled one keeps the direct
+    path): the same bytes as the oracle."""
+    n = (128 << 20) // e + 4099
+    if kind == "perm":
+        idx = synth.random_permutation(31 + e, n)
+    elif kind == "repeat":
+        idx = synth.random_indices(32 + e, n, n)
+    else:
+        m = n - n % 4096
+        idx = np.concatenate([synth.block_shuffled_permutation(33, m, 4096), np.arange(m, n, dtype=np.uint32)])
+    idx = idx.astype(np.uint64)
+    src = synth.random_elements(34 + e, n, e)
+    fn = lr.scatter64 if scatter else lr.reorder64
+    got = run(lr, fn, src, idx, e, n, fill=0)
+    assert np.array_equal(got, orc.indexed(src, idx, e, scatter=scatter)), (e, kind, scatter)
