@@ -97,6 +97,12 @@ __device__ __forceinline__ uint64_t l2_evict_last()
 
 // Loads (non-coherent, no L1 allocation) and stores with an L2 policy.
 template <int N> __device__ __forceinline__ typename Word<N>::T ldg_hint(const void *p, uint64_t pol);
+template <> __device__ __forceinline__ uint16_t ldg_hint<2>(const void *p, uint64_t pol)
+{
+    uint16_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+    return v;
+}
 template <> __device__ __forceinline__ uint32_t ldg_hint<4>(const void *p, uint64_t pol)
 {
     uint32_t v;

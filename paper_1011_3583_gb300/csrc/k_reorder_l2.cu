@@ -79,7 +79,8 @@ struct L2Reorder {
     uint32_t *base;                // [C*D] bucket starts, c-major
     uint32_t *cursor;              // [C*D] partition write cursors
     uint32_t *uprefix;             // [C*D + 1] d-major prefix of scatter units
-    uint32_t *sarr, *iarr;         // [n] source / destination indices, c-major
+    uint32_t *sarr, *iarr;         // [n] source / destination indices, c-major; with CTA-sized
+                                   // destination chunks the i-array holds uint16 offsets in the chunk
     char *varr;                    // [n] gathered values, c-major
     unsigned long long near_threshold;
 };
@@ -455,7 +456,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_l2_partition(const L2Reorder p,
                 using T = typename Word<SW>::T;
                 reinterpret_cast<T *>(p.varr)[g] = reinterpret_cast<const T *>(vals)[kc & (kTile - 1)];
             } else {
-                p.iarr[g] = i0 + (kc & (kTile - 1));
+                const uint32_t i = i0 + (kc & (kTile - 1));
+                if (own) reinterpret_cast<uint16_t *>(p.iarr)[g] = uint16_t(i & ((1u << p.ds_shift) - 1));
+                else p.iarr[g] = i;
             }
         }
         // only the C chunks in use need zeroing (not all kMaxChunks)
@@ -569,8 +572,8 @@ __global__ void __launch_bounds__(kThreads) k_l2_scatter(const L2Reorder p)
 
 // K6, shared-memory form: CTA-sized destination chunks.  The warps split the
 // chunk's C buckets; each value goes to its slot of the chunk in shared
-// memory (i & dmask: every i of bucket (c, d) lies in chunk d by
-// construction, the mask only keeps a corrupt word inside the buffer), then
+// memory (the partition stored i's 16-bit offset in chunk d; the mask only
+// keeps a corrupt word inside the buffer), then
 // the CTA writes the chunk out, 16 bytes per lane when dst allows.
 template <int W>
 __global__ void __launch_bounds__(kScatterThreads) k_l2_scatter_smem(const L2Reorder p)
@@ -590,18 +593,19 @@ __global__ void __launch_bounds__(kScatterThreads) k_l2_scatter_smem(const L2Reo
             const uint32_t b = c * p.D + d;
             const uint32_t k1 = p.base[b] + p.hist[b];
             uint32_t k = p.base[b] + lane;
+            const uint16_t *off = reinterpret_cast<const uint16_t *>(p.iarr);  // offsets in the chunk
             for (; k + 32 * (U - 1) < k1; k += 32 * U) {
                 uint32_t di[U];
                 T val[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    di[u] = ldg_hint<4>(p.iarr + k + 32 * u, first);
+                    di[u] = ldg_hint<2>(off + k + 32 * u, first);
                     val[u] = ldg_hint<W>(p.varr + uint64_t(k + 32 * u) * W, first);
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) chunk[di[u] & dmask] = val[u];
             }
-            for (; k < k1; k += 32) chunk[ldg_hint<4>(p.iarr + k, first) & dmask] = ldg_hint<W>(p.varr + uint64_t(k) * W, first);
+            for (; k < k1; k += 32) chunk[ldg_hint<2>(off + k, first) & dmask] = ldg_hint<W>(p.varr + uint64_t(k) * W, first);
         }
         __syncthreads();
         const uint64_t i0 = uint64_t(d) << p.ds_shift;
