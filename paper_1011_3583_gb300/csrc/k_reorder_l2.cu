@@ -331,7 +331,7 @@ static_assert(sizeof(PartitionSmem) % 16 == 0, "the scatter form's element buffe
 // cp.async behind the index loads and written out beside their indices, so
 // the scatter needs no separate pass that reads the source by position.
 template <int SW>
-__global__ void __launch_bounds__(kThreads, 3) k_l2_partition(const L2Reorder p, uint32_t tiles_per_cta,
+__global__ void __launch_bounds__(kThreads, 4) k_l2_partition(const L2Reorder p, uint32_t tiles_per_cta,
                                                               uint32_t own)
 {
     if (!bucketed(p)) return;
@@ -485,11 +485,11 @@ __device__ __forceinline__ uint32_t next_unit(unsigned int *ctr, uint32_t *slot)
     return *slot;
 }
 
-constexpr int kGatherUnit = 4096;  // elements per gather / scatter unit (16 per thread)
+constexpr int kGatherUnit = 2048;  // elements per gather / scatter unit (8 per thread)
 
 // K5: v[k] = src[s[k]] in k order; the source chunk being read is L2-resident.
 template <int W>
-__global__ void __launch_bounds__(kThreads) k_l2_gather(const L2Reorder p)
+__global__ void __launch_bounds__(kThreads, W == 4 ? 8 : W == 8 ? 6 : 4) k_l2_gather(const L2Reorder p)
 {
     if (!bucketed(p)) return;
     __shared__ uint32_t slot;
