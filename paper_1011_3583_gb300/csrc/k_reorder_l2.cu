@@ -13,12 +13,16 @@
 //                  neighbours are close (|idx[j+1] - idx[j]| <= 16), the
 //                  direct gather is already streaming and K2..K6 do nothing,
 //                  otherwise K7 does nothing.
-//   K2 histogram : bucket sizes.
-//   K3 scan      : bucket starts in c-major order, and the d-major work units
-//                  of the scatter pass.
+//   K2 histogram : bucket sizes, and the elements per source chunk.
+//   K3 scan      : bucket starts in c-major order (one CTA per source-chunk
+//                  row; the L2 scatter's single-CTA scan also lays out its
+//                  d-major work units).
 //   K4 partition : each 4096-element tile is counting-sorted by c in shared
 //                  memory and written as contiguous segments: s-array (source
-//                  index) and i-array (destination index), c-major.
+//                  index) and i-array (destination index; a 16-bit offset in
+//                  the chunk for the shared-memory scatter), c-major.  CTAs
+//                  that own whole destination chunks keep the bucket cursors
+//                  in shared memory.
 //   K5 gather    : v[k] = src[s[k]] walking k in order, so the CTAs in flight
 //                  read one ~16 MB source chunk at a time from L2.
 //   K6 scatter   : shared-memory form: one CTA per 64 KB destination chunk
@@ -27,20 +31,21 @@
 //                  out with coalesced stores.  L2 form: dst[i[k]] = v[k]
 //                  walking the buckets d-major, so the CTAs in flight
 //                  complete one ~16 MB destination chunk in L2.
-// Random global accesses cost one L1 request each (about one per clock per
-// SM, whatever the working set), random shared-memory accesses about a
-// twelfth of that: the shared-memory scatter leaves the gather as the one
-// pass bound by random requests.
 //   K7 direct    : the plain gather (when K1 found locality).
-// Traffic: 2 (idx) + 2 (s, i written) + 2 (s, i read) + 1 (src) + 2 (v) + 1
-// (dst) = 10 n-word passes of streaming access instead of n random accesses.
+// Random global accesses cost one L1 request each (about one per clock per
+// SM, whatever the working set); random shared-memory accesses run about
+// twelve times as fast.  The shared-memory scatter so leaves the gather as
+// the one pass bound by random requests.  Streaming traffic in index-sized
+// words per element: idx 2 (K2, K4), s 2, i 1 (two 16-bit offsets), src 1,
+// v 2, dst 1 = 9 passes instead of n random DRAM accesses (10 with the L2
+// scatter's 32-bit i-array).
 // A scatter (dst[idx[i]] = src[i]) uses one bucket dimension only (D = 1,
 // buckets by the destination chunk of idx[i]): the partition writes
 // (destination index, element) pairs, and a linear pass writes
 // dst[s[k]] = v[k] with the destination chunk L2-resident.
-// Scratch ((8 + E) n bytes) comes from a stream-ordered pool owned by the
-// library; the kernels are ordered on the caller's stream and none waits on
-// another.
+// Scratch ((8 + E) n bytes, plus 12 bytes per bucket) comes from a
+// stream-ordered pool owned by the library; the kernels are ordered on the
+// caller's stream and none waits on another.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -311,11 +316,11 @@ __global__ void __launch_bounds__(1024) k_l2_scan_rows(const L2Reorder p)
 // its own cursor when the CTA owns the tile's destination chunk (every tile
 // of that chunk is in the CTA's range, so the buckets (c, d) have no other
 // writer), else from one global atomic per chunk.  The tile is staged in
-// shared memory grouped by chunk (source index; tile index and chunk packed
-// in one word) and written out as contiguous segments.  The next tile's
+// shared memory grouped by chunk (the bucketed index; tile index and chunk
+// packed in one word) and written out as contiguous segments.  The next tile's
 // indices load while this one is sorted.
 struct PartitionSmem {
-    uint32_t s_st[kTile];               // source index, grouped by chunk
+    uint32_t s_st[kTile];               // the bucketed index (gather: source, scatter: destination), by chunk
     uint32_t kc_st[kTile];              // tile index k | chunk << 12
     uint32_t cnt[kWarps][kMaxChunks];   // per-warp counts, then per-warp slots
     uint32_t delta[kMaxChunks];         // global position of tile slot 0 of the chunk's segment
@@ -325,7 +330,8 @@ struct PartitionSmem {
 static_assert(kTile <= 4096 && kMaxChunks <= (1 << 20), "tile index and chunk share one word");
 static_assert(sizeof(PartitionSmem) % 16 == 0, "the scatter form's element buffer follows, 16-byte aligned");
 
-// SW = 0: gather form (s-array: source index, i-array: destination index).
+// SW = 0: gather form (s-array: source index, i-array: destination index, as
+// a 16-bit offset in its chunk when the CTA owns the destination chunks).
 // SW = W: scatter form (s-array: destination index, v-array: the element
 // itself): the tile's source elements are copied into shared memory with
 // cp.async behind the index loads and written out beside their indices, so
