@@ -13,7 +13,8 @@ Inputs are seeded random bit patterns (numpy PCG64), every op reads at least
 Throughput is effective GB/s = (bytes read + bytes written) / time, GB = 1e9,
 index reads of the reorders included.  The roofline denominators are a
 cudaMemcpyAsync device-to-device copy measured in the same run and the
-measured copy bandwidth in MEASURED_PEAKS.json.
+copy bandwidth recorded in MEASURED_PEAKS.json (a STREAM-style copy measured on
+the same GPU model).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun each rank runs the whole workload on its own GPU (independent

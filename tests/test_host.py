@@ -172,7 +172,7 @@ def test_describe_examples(lr):
     d = lr.describe_permute(4, [1024, 1024], [1, 0], FAKE_DST, FAKE_SRC)
     assert d["kind"] == "tile" and d["dims"] == [1024, 1024] and d["in_strides"] == [1, 1024]
     assert d["vec_in"] == 16 and d["vec_out"] == 16
-    # the survey's example: 64x128x256x64 with (0,1,3,2) is a batch of 8192 256x64 transposes
+    # 64x128x256x64 with (0,1,3,2) is a batch of 8192 transposes of 256 x 64
     d = lr.describe_permute(4, [64, 128, 256, 64], [0, 1, 3, 2], FAKE_DST, FAKE_SRC)
     assert d["kind"] == "tile" and d["dims"] == [8192, 64, 256] and d["plane_a"] == 1
     # unmoved innermost axis folds into the cell
