@@ -187,6 +187,48 @@ static rearr_status plan_axes(void *dst, const char *src, size_t elem_bytes, con
     for (int i = 0; i < R; ++i)
         if (ax[i].stride == cell) p = i;
 
+    // Every output cell copied on its own (one cell is one W-byte word), 16/W
+    // consecutive cells per thread written with one 16-byte store.
+    auto set_strided = [&](int W, uint64_t n_cells) {
+        StridedDesc sd;
+        std::memset(&sd, 0, sizeof(sd));
+        sd.dst = static_cast<char *>(dst);
+        sd.src = src;
+        sd.nd = R;
+        for (int i = 0; i < kMaxRank; ++i) {
+            sd.in_stride[i] = i < R ? ax[i].stride : 0;
+            sd.div[i] = make_fastdiv(i < R ? uint32_t(ax[i].extent) : 1u);
+        }
+        sd.n_cells = n_cells;
+        sd.vec = (da % 16 == 0) ? 1u : 0u;
+        const uint64_t per_unit = uint64_t(kThreads) * (16 / W) * kStridedSteps;
+        OpDesc &op = pl.op;
+        op.cls = OC_STRIDED;
+        op.word = uint32_t(W);
+        op.strided = sd;
+        op.units = (n_cells + per_unit - 1) / per_unit;
+        info.kind = REARR_KIND_STRIDED;
+        info.tile_a = info.tile_b = 0;
+        info.word_bytes = W;
+        info.vec_in = W;
+        info.vec_out = sd.vec ? 16 : W;
+        info.n_tiles = int64_t(op.units);
+    };
+
+    // A box with no input-contiguous axis and cells of one aligned word (the
+    // input's fastest axis dropped): every read is a scattered word, so each
+    // cell is gathered on its own and the output written 16 bytes at a time.
+    if (p < 0 && cell <= 16) {
+        const int W = pow2_align(da, sa, uint64_t(cell), strides_or);
+        const uint64_t n_cells = bytes / uint64_t(cell);
+        bool fits = n_cells < kMaxUnits;
+        for (int i = 0; i < R; ++i) fits &= ax[i].extent < int64_t(kMaxUnits);
+        if (W == cell && fits) {
+            set_strided(W, n_cells);
+            return REARR_OK;
+        }
+    }
+
     // Cells of 128 bytes or more are copied as runs, and so are boxes with no
     // input-contiguous axis (there both sides cannot be coalesced).
     if (cell >= kRunMinBytes || p < 0) {
@@ -352,28 +394,7 @@ static rearr_status plan_axes(void *dst, const char *src, size_t elem_bytes, con
     const ThinTuning thin = thin_tuning();
     const bool thin_plane =
         bytes < units * thin.tile_bytes || (bytes <= thin.l2_bytes && n_cells < units * thin.tile_cells);
-    if (W == cell && thin_plane && n_cells < kMaxUnits) {
-        StridedDesc sd;
-        std::memset(&sd, 0, sizeof(sd));
-        sd.dst = static_cast<char *>(dst);
-        sd.src = src;
-        sd.nd = R;
-        for (int i = 0; i < kMaxRank; ++i) {
-            sd.in_stride[i] = i < R ? ax[i].stride : 0;
-            sd.div[i] = make_fastdiv(i < R ? uint32_t(ax[i].extent) : 1u);
-        }
-        sd.n_cells = n_cells;
-        sd.vec = (da % 16 == 0) ? 1u : 0u;
-        const uint64_t per_unit = uint64_t(kThreads) * (16 / W) * kStridedSteps;
-        op.cls = OC_STRIDED;
-        op.strided = sd;
-        op.units = (n_cells + per_unit - 1) / per_unit;
-        info.kind = REARR_KIND_STRIDED;
-        info.tile_a = info.tile_b = 0;
-        info.vec_in = W;
-        info.vec_out = sd.vec ? 16 : W;
-        info.n_tiles = int64_t(op.units);
-    }
+    if (W == cell && thin_plane && n_cells < kMaxUnits) set_strided(W, n_cells);
     return REARR_OK;
 }
 

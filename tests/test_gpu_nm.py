@@ -54,7 +54,7 @@ def test_nm_special_cases(lr, orc):
     check_nm(lr, orc, 1, 4, [33, 70, 65], [2, 0, 1], [0, 0, 0], [33, 70, 65])
     # rank-1 range copy ("specified range" access)
     check_nm(lr, orc, 2, 4, [100003], [0], [517], [90001])
-    # the input's fastest axis dropped: no contiguous axis, runs of one element
+    # the input's fastest axis dropped: no contiguous axis, each element gathered on its own
     check_nm(lr, orc, 3, 4, [40, 50, 60], [1, 0], [3, 7, 11], [30, 40, 0])
     # inner axis kept but sliced: short runs of the kept part
     check_nm(lr, orc, 4, 2, [64, 80, 96], [0, 1, 2], [5, 6, 7], [50, 60, 70])
