@@ -336,7 +336,9 @@ typedef enum {
     REARR_KIND_STRIDED = 5      /* element-wise strided copy: a transpose plane
                                    too small to fill tiles (by default under
                                    1 KB of payload, or for ops up to 32 MiB
-                                   under 1024 cells, per tile on average)    */
+                                   under 1024 cells, per tile on average), or
+                                   a box with no input-contiguous axis and
+                                   one-word cells                            */
 } rearr_kind;
 
 typedef struct {
