@@ -360,6 +360,12 @@ rearr_status rearr_permute_describe(size_t elem_bytes, int rank, const int64_t *
                                     const int *perm, uintptr_t dst_addr, uintptr_t src_addr,
                                     rearr_permute_info *info);
 
+/* The same view of an N-to-M reorder (arguments and validation as
+ * rearr_reorder_nm; the box's base offset is added to src_addr). */
+rearr_status rearr_reorder_nm_describe(size_t elem_bytes, int rank_in, const int64_t *dims, int rank_out,
+                                      const int *order, const int64_t *base, const int64_t *range,
+                                      uintptr_t dst_addr, uintptr_t src_addr, rearr_permute_info *info);
+
 /* ---------------------------------------------------------------------------
  * Tuning table.  The paper chooses block and thread shapes per kernel by hand
  * (Sec. III); here the fast tile's staged row length per (element size,

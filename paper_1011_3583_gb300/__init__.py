@@ -8,6 +8,6 @@ from .librearr import (  # noqa: F401
     lib_path, load, memcpy_d2d, permute, reorder, reorder64, reorder_nm, scatter, scatter64, selftest_host,
     status_str, STENCIL_CLAMP, STENCIL_ZERO, describe_stencil, stencil2d, wait_timeouts, inject_wait_timeout,
     Pipeline, check_indices, reorder_checked, ERANGE,
-    DistPlan, dist_permute_plan, dist_permute_pack, dist_permute_unpack,
+    DistPlan, dist_permute_plan, dist_permute_pack, dist_permute_unpack, describe_reorder_nm,
 )
 from .dist import dist_permute  # noqa: F401

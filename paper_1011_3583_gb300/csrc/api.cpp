@@ -240,6 +240,22 @@ rearr_status rearr_permute_describe(size_t elem_bytes, int rank, const int64_t *
     return REARR_OK;
 }
 
+rearr_status rearr_reorder_nm_describe(size_t elem_bytes, int rank_in, const int64_t *dims, int rank_out,
+                                      const int *order, const int64_t *base, const int64_t *range,
+                                      uintptr_t dst_addr, uintptr_t src_addr, rearr_permute_info *info)
+{
+    if (!info) return fail(REARR_EINVAL, "rearr_reorder_nm_describe: info is NULL");
+    if (dst_addr == 0) dst_addr = uintptr_t(1) << 47;
+    if (src_addr == 0) src_addr = uintptr_t(1) << 46;
+    PermPlan pl;
+    std::string err;
+    rearr_status st = plan_reorder_nm(reinterpret_cast<void *>(dst_addr), reinterpret_cast<const void *>(src_addr),
+                                      elem_bytes, rank_in, dims, rank_out, order, base, range, pl, err);
+    if (st != REARR_OK) return fail(st, "rearr_reorder_nm_describe: " + err);
+    *info = pl.info;
+    return REARR_OK;
+}
+
 rearr_status rearr_memcpy_d2d(void *dst, const void *src, size_t bytes, rearr_stream_t stream)
 {
     if (bytes == 0) return REARR_OK;

@@ -125,6 +125,8 @@ def load() -> ctypes.CDLL:
         "rearr_plan_stats": (st, [vp, i64p, i64p]),
         "rearr_permute_describe": (st, [sz, ctypes.c_int, i64p, ip, ctypes.c_size_t, ctypes.c_size_t,
                                         ctypes.POINTER(PermuteInfo)]),
+        "rearr_reorder_nm_describe": (st, [sz, ctypes.c_int, i64p, ctypes.c_int, ip, i64p, i64p, ctypes.c_size_t,
+                                           ctypes.c_size_t, ctypes.POINTER(PermuteInfo)]),
         "rearr_memcpy_d2d": (st, [vp, vp, sz, vp]),
         "rearr_launch_count": (ctypes.c_uint64, []),
         "rearr_selftest_host": (st, []),
@@ -332,6 +334,16 @@ def describe_permute(elem_bytes: int, dims: Sequence[int], perm: Sequence[int], 
     info = PermuteInfo()
     _check(load().rearr_permute_describe(int(elem_bytes), rank, d, p, int(dst_addr), int(src_addr),
                                          ctypes.byref(info)))
+    return info.as_dict()
+
+
+def describe_reorder_nm(elem_bytes: int, dims: Sequence[int], order: Sequence[int], base: Sequence[int],
+                        rng: Sequence[int], dst_addr: int = 0, src_addr: int = 0) -> dict:
+    """rearr_reorder_nm_describe: the canonical plan of an N-to-M reorder (host only)."""
+    rank_in, d, rank_out, o, b, r = _nm_args(dims, order, base, rng)
+    info = PermuteInfo()
+    _check(load().rearr_reorder_nm_describe(int(elem_bytes), rank_in, d, rank_out, o, b, r, int(dst_addr),
+                                            int(src_addr), ctypes.byref(info)))
     return info.as_dict()
 
 

@@ -235,3 +235,26 @@ def test_collapsed_plan_equivalence(lr):
         if info["kind"] in ("tile", "tile_cells"):
             assert all(d > 1 for d in info["dims"])
             assert info["in_strides"][-1] != 1
+
+
+def test_reorder_nm_describe_routes_boxes(lr):
+    """N-to-M boxes through the plan compiler, host only: a box that drops the
+    input's fastest axis has no input-contiguous axis and, with one-word cells,
+    is gathered cell by cell (strided); wider cells stay runs; a kept inner
+    axis gives a tile or runs; the full box is the permute's plan."""
+    d = lr.describe_reorder_nm(4, [1024, 1024, 256], [0, 1], [0, 0, 5], [1024, 1024, 1])
+    assert d["kind"] == "strided" and d["word_bytes"] == 4 and d["vec_out"] == 16
+    d = lr.describe_reorder_nm(2, [40, 50, 60], [1, 0], [3, 7, 11], [30, 40, 1])
+    assert d["kind"] == "strided" and d["word_bytes"] == 2
+    # 12-byte cells are no single word: runs
+    assert lr.describe_reorder_nm(12, [40, 50, 60], [1, 0], [3, 7, 11], [30, 40, 1])["kind"] == "runs"
+    # unaligned source for 4-byte cells: no 4-byte word, runs
+    d = lr.describe_reorder_nm(4, [40, 50, 60], [1, 0], [3, 7, 11], [30, 40, 1], 0, FAKE_SRC + 2)
+    assert d["kind"] == "runs"
+    # inner axis kept: a transpose plane of the box
+    assert lr.describe_reorder_nm(4, [8, 256, 512], [2, 1], [3, 64, 128], [1, 128, 256])["kind"] == "tile"
+    # the full box in order (2, 0, 1) is the permute's plan
+    full = lr.describe_reorder_nm(4, [33, 70, 65], [2, 0, 1], [0, 0, 0], [33, 70, 65])
+    assert full == lr.describe_permute(4, [33, 70, 65], [2, 0, 1])
+    with pytest.raises(lr.RearrError):
+        lr.describe_reorder_nm(4, [10, 10], [0, 0], [0, 0], [5, 5])
