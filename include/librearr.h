@@ -151,6 +151,41 @@ rearr_status rearr_reorder_checked(void *dst, const void *src, const uint32_t *i
                                    size_t elem_bytes, rearr_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * rearr_reorder_describe: host-only view of how an index-sequence op runs
+ * (scatter 0: rearr_reorder / rearr_reorder64, 1: rearr_scatter /
+ * rearr_scatter64; idx_bytes 4 or 8; the addresses only steer the alignment
+ * decisions, 0 standing for a 256-byte-aligned buffer).  Validation as the
+ * op itself.  A form other than REARR_REORDER_DIRECT means the op is eligible
+ * for the L2-resident bucketed passes.  At run time the device still takes
+ * the direct path when its locality sample finds the indices local.  Then:
+ *   bucket_chunks, bucket_chunk_elems : chunks of the bucketed side (the
+ *                                       source of a gather, the destination
+ *                                       of a scatter), ~16 MB each;
+ *   dest_chunks, dest_chunk_elems     : the gather's destination chunks (64 KB
+ *                                       for the shared-memory scatter);
+ *                                       1 and 0 for a scatter;
+ *   scratch_bytes                     : scratch the call takes from the
+ *                                       library's pool while it runs.
+ * ------------------------------------------------------------------------- */
+typedef enum {
+    REARR_REORDER_DIRECT = 0,          /* one direct gather / scatter kernel         */
+    REARR_REORDER_SMEM_SCATTER = 1,    /* gather, last pass through shared memory    */
+    REARR_REORDER_L2_SCATTER = 2,      /* gather, last pass through ~16 MB L2 chunks */
+    REARR_REORDER_LINEAR_SCATTER = 3   /* scatter: (destination, element) pairs      */
+} rearr_reorder_form;
+
+typedef struct {
+    int form;                     /* rearr_reorder_form               */
+    int word_bytes;               /* access word (element size here) */
+    uint32_t bucket_chunks, dest_chunks;
+    uint64_t bucket_chunk_elems, dest_chunk_elems;
+    uint64_t scratch_bytes;
+} rearr_reorder_info;
+
+rearr_status rearr_reorder_describe(size_t n, size_t elem_bytes, int idx_bytes, int scatter, uintptr_t dst_addr,
+                                    uintptr_t src_addr, uintptr_t idx_addr, rearr_reorder_info *info);
+
+/* ---------------------------------------------------------------------------
  * rearr_interlace -- join k arrays into one interlaced array
  * (arXiv:1011.3583 Sec. III.C, Table 3):
  *       dst[i*k + j] = srcs[j][i],  0 <= i < n, 0 <= j < k.

@@ -9,5 +9,6 @@ from .librearr import (  # noqa: F401
     status_str, STENCIL_CLAMP, STENCIL_ZERO, describe_stencil, stencil2d, wait_timeouts, inject_wait_timeout,
     Pipeline, check_indices, reorder_checked, ERANGE,
     DistPlan, dist_permute_plan, dist_permute_pack, dist_permute_unpack, describe_reorder_nm,
+    describe_reorder,
 )
 from .dist import dist_permute  # noqa: F401

@@ -2,11 +2,14 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <cstring>
 #include <string>
 
 #include "../../include/librearr.h"
 #include "launch.h"
 #include "plan.h"
+#include "reorder_geometry.h"
+#include "tuning.h"
 #include "stencil.h"
 
 namespace rearr {
@@ -253,6 +256,38 @@ rearr_status rearr_reorder_nm_describe(size_t elem_bytes, int rank_in, const int
                                       elem_bytes, rank_in, dims, rank_out, order, base, range, pl, err);
     if (st != REARR_OK) return fail(st, "rearr_reorder_nm_describe: " + err);
     *info = pl.info;
+    return REARR_OK;
+}
+
+rearr_status rearr_reorder_describe(size_t n, size_t elem_bytes, int idx_bytes, int scatter, uintptr_t dst_addr,
+                                    uintptr_t src_addr, uintptr_t idx_addr, rearr_reorder_info *info)
+{
+    if (!info) return fail(REARR_EINVAL, "rearr_reorder_describe: info is NULL");
+    if (idx_bytes != 4 && idx_bytes != 8) return fail(REARR_EINVAL, "rearr_reorder_describe: idx_bytes must be 4 or 8");
+    if (dst_addr == 0) dst_addr = uintptr_t(1) << 47;
+    if (src_addr == 0) src_addr = uintptr_t(1) << 46;
+    if (idx_addr == 0) idx_addr = uintptr_t(1) << 45;
+    OpDesc op;
+    std::memset(&op, 0, sizeof(op));
+    std::string err;
+    rearr_status st = plan_reorder(reinterpret_cast<void *>(dst_addr), reinterpret_cast<const void *>(src_addr),
+                                   reinterpret_cast<const uint32_t *>(idx_addr), n, elem_bytes, op, err, idx_bytes,
+                                   scatter != 0);
+    if (st != REARR_OK) return fail(st, "rearr_reorder_describe: " + err);
+    rearr_reorder_info r;
+    std::memset(&r, 0, sizeof(r));
+    r.word_bytes = int(op.word);
+    if (op.cls == OC_GATHER && op.gather.l2) {
+        const ReorderGeometry gm = reorder_geometry(n, op.word, scatter != 0, reorder_smem_max_buckets());
+        r.form = scatter ? REARR_REORDER_LINEAR_SCATTER
+                         : gm.smem_scatter ? REARR_REORDER_SMEM_SCATTER : REARR_REORDER_L2_SCATTER;
+        r.bucket_chunks = gm.C;
+        r.bucket_chunk_elems = uint64_t(1) << gm.cs_shift;
+        r.dest_chunks = gm.D;
+        r.dest_chunk_elems = scatter ? 0 : uint64_t(1) << gm.ds_shift;
+        r.scratch_bytes = gm.bytes;
+    }
+    *info = r;
     return REARR_OK;
 }
 

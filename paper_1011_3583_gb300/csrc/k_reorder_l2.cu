@@ -53,6 +53,7 @@
 
 #include "bodies.cuh"
 #include "launch.h"
+#include "reorder_geometry.h"
 #include "tuning.h"
 
 namespace rearr {
@@ -60,9 +61,9 @@ namespace rearr {
 namespace {
 
 constexpr int kTile = 4096;        // elements per partition tile / scatter unit
-constexpr int kMaxChunks = 512;    // C <= 512; D <= 512 for the L2 scatter
+constexpr int kMaxChunks = int(kReorderMaxChunks);  // C <= 512; D <= 512 for the L2 scatter
 constexpr int kScatterThreads = 512;
-constexpr uint32_t kScatterChunkBytes = 64u << 10;  // destination chunk of the shared-memory scatter
+constexpr uint32_t kScatterChunkBytes = kReorderScatterChunkBytes;  // destination chunk of the shared-memory scatter
 constexpr int kSampleRuns = 4096;
 constexpr int kSampleLen = 64;
 constexpr uint32_t kNear = 16;
@@ -706,27 +707,16 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
     p.idx = g.idx;
     p.idx64 = g.idx64;
     p.n = uint32_t(g.n);
-    // ~16 MB source chunks, at most kMaxChunks of them
-    uint32_t shift = 0;
-    while ((uint64_t(1) << shift) * W < (uint64_t(16) << 20)) ++shift;
-    while (((uint64_t(g.n) + (uint64_t(1) << shift) - 1) >> shift) > kMaxChunks) ++shift;
-    p.cs_shift = shift;
-    p.C = uint32_t((uint64_t(g.n) + (uint64_t(1) << shift) - 1) >> shift);
-    // destination chunks: CTA-sized (shared-memory scatter) while the bucket
-    // count stays within the tuned bound, else the source chunks' size
-    uint32_t dshift = 0;
-    while ((uint64_t(2) << dshift) * W <= kScatterChunkBytes) ++dshift;
-    const uint64_t d_small = (uint64_t(g.n) + (uint64_t(1) << dshift) - 1) >> dshift;
-    const bool smem_scatter =
-        !g.scatter && uint64_t(p.C) * d_small <= std::min<uint64_t>(reorder_smem_max_buckets(), uint64_t(1) << 24);
-    p.ds_shift = smem_scatter ? dshift : shift;
-    p.D = g.scatter ? 1u : smem_scatter ? uint32_t(d_small) : p.C;
-    const uint32_t nb = p.C * p.D;
-    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-    const size_t off_hist = 256, off_row = off_hist + al(size_t(nb) * 4), off_base = off_row + al(size_t(p.C) * 4),
-                 off_cur = off_base + al(size_t(nb) * 4), off_up = off_cur + al(size_t(nb) * 4),
-                 off_s = off_up + al((size_t(nb) + 1) * 4), off_i = off_s + al(size_t(g.n) * 4),
-                 off_v = off_i + al(size_t(g.n) * 4), bytes = off_v + al(size_t(g.n) * W);
+    // ~16 MB source chunks; CTA-sized destination chunks (shared-memory
+    // scatter) while the bucket count stays within the tuned bound
+    const ReorderGeometry gm = reorder_geometry(g.n, W, g.scatter != 0, reorder_smem_max_buckets());
+    p.cs_shift = gm.cs_shift;
+    p.C = gm.C;
+    const bool smem_scatter = gm.smem_scatter;
+    p.ds_shift = gm.ds_shift;
+    p.D = gm.D;
+    const size_t off_hist = gm.off_hist, off_row = gm.off_row, off_base = gm.off_base, off_cur = gm.off_cur,
+                 off_up = gm.off_up, off_s = gm.off_s, off_i = gm.off_i, off_v = gm.off_v, bytes = gm.bytes;
     cudaMemPool_t pool;
     cudaError_t e = get_pool(pool);
     if (e != cudaSuccess) return e;

@@ -49,6 +49,22 @@ class PermuteInfo(ctypes.Structure):
                     tile_b=self.tile_b, n_tiles=self.n_tiles)
 
 
+REORDER_FORMS = {0: "direct", 1: "smem_scatter", 2: "l2_scatter", 3: "linear_scatter"}
+
+
+class ReorderInfo(ctypes.Structure):
+    """rearr_reorder_info (include/librearr.h)."""
+    _fields_ = [("form", ctypes.c_int), ("word_bytes", ctypes.c_int), ("bucket_chunks", ctypes.c_uint32),
+                ("dest_chunks", ctypes.c_uint32), ("bucket_chunk_elems", ctypes.c_uint64),
+                ("dest_chunk_elems", ctypes.c_uint64), ("scratch_bytes", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return dict(form=REORDER_FORMS.get(self.form, self.form), word_bytes=self.word_bytes,
+                    bucket_chunks=self.bucket_chunks, dest_chunks=self.dest_chunks,
+                    bucket_chunk_elems=self.bucket_chunk_elems, dest_chunk_elems=self.dest_chunk_elems,
+                    scratch_bytes=self.scratch_bytes)
+
+
 class StencilInfo(ctypes.Structure):
     _fields_ = [("shape", ctypes.c_int), ("body", ctypes.c_int), ("radius", ctypes.c_int), ("n_unique", ctypes.c_int),
                 ("tma", ctypes.c_int),
@@ -125,6 +141,8 @@ def load() -> ctypes.CDLL:
         "rearr_plan_stats": (st, [vp, i64p, i64p]),
         "rearr_permute_describe": (st, [sz, ctypes.c_int, i64p, ip, ctypes.c_size_t, ctypes.c_size_t,
                                         ctypes.POINTER(PermuteInfo)]),
+        "rearr_reorder_describe": (st, [sz, sz, ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_size_t,
+                                        ctypes.c_size_t, ctypes.POINTER(ReorderInfo)]),
         "rearr_reorder_nm_describe": (st, [sz, ctypes.c_int, i64p, ctypes.c_int, ip, i64p, i64p, ctypes.c_size_t,
                                            ctypes.c_size_t, ctypes.POINTER(PermuteInfo)]),
         "rearr_memcpy_d2d": (st, [vp, vp, sz, vp]),
@@ -334,6 +352,15 @@ def describe_permute(elem_bytes: int, dims: Sequence[int], perm: Sequence[int], 
     info = PermuteInfo()
     _check(load().rearr_permute_describe(int(elem_bytes), rank, d, p, int(dst_addr), int(src_addr),
                                          ctypes.byref(info)))
+    return info.as_dict()
+
+
+def describe_reorder(n: int, elem_bytes: int, idx_bytes: int = 4, scatter: bool = False, dst_addr: int = 0,
+                     src_addr: int = 0, idx_addr: int = 0) -> dict:
+    """rearr_reorder_describe: how an index-sequence op runs (host only)."""
+    info = ReorderInfo()
+    _check(load().rearr_reorder_describe(int(n), int(elem_bytes), int(idx_bytes), 1 if scatter else 0, int(dst_addr),
+                                         int(src_addr), int(idx_addr), ctypes.byref(info)))
     return info.as_dict()
 
 

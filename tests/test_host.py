@@ -258,3 +258,38 @@ def test_reorder_nm_describe_routes_boxes(lr):
     assert full == lr.describe_permute(4, [33, 70, 65], [2, 0, 1])
     with pytest.raises(lr.RearrError):
         lr.describe_reorder_nm(4, [10, 10], [0, 0], [0, 0], [5, 5])
+
+
+def test_reorder_describe_paths(lr, tmp_path):
+    """Which path an index-sequence op takes, host only: small sources and
+    unaligned words run the direct kernel; large ones the bucketed passes
+    with the shared-memory scatter, the L2 form (huge sources, or forced by
+    the tuning table), or the scatter's linear form."""
+    n = 1 << 28
+    d = lr.describe_reorder(n, 4)
+    assert d["form"] == "smem_scatter" and d["bucket_chunks"] == 64 and d["bucket_chunk_elems"] == 1 << 22
+    assert d["dest_chunks"] == n >> 14 and d["dest_chunk_elems"] == 1 << 14   # 64 KB of fp32
+    # scratch: s-, i- and v-arrays (12 bytes per element) plus the bucket tables
+    assert 12 * n < d["scratch_bytes"] < 12 * n + 20 * (64 * (n >> 14)) + (1 << 20)
+    assert lr.describe_reorder(n, 4, idx_bytes=8) == d                       # 64-bit indices: same passes
+    s = lr.describe_reorder(n, 4, scatter=True)
+    assert s["form"] == "linear_scatter" and s["dest_chunks"] == 1
+    assert lr.describe_reorder((128 << 20) // 4 - 1, 4)["form"] == "direct"  # below 128 MiB
+    assert lr.describe_reorder(n, 4, src_addr=FAKE_SRC + 2)["form"] == "direct"  # 2-byte words
+    assert lr.describe_reorder(n, 12)["form"] == "direct"                    # no 4/8/16-byte word
+    for e, dchunk in ((8, 1 << 13), (16, 1 << 12)):
+        d = lr.describe_reorder((256 << 20) // e, e)
+        assert d["form"] == "smem_scatter" and d["dest_chunk_elems"] == dchunk
+    huge = lr.describe_reorder(1 << 31, 4)                                   # 8 GB: too many buckets
+    assert huge["form"] == "l2_scatter" and huge["bucket_chunks"] == 512 == huge["dest_chunks"]
+    t = tmp_path / "l2.txt"
+    t.write_text("reorder_smem_buckets 1\n")
+    try:
+        lr.tuning_load(str(t))
+        assert lr.describe_reorder(n, 4)["form"] == "l2_scatter"
+    finally:
+        lr.tuning_load(None)
+        lr.tuning_load(lr.DEFAULT_TUNE_TABLE)
+    with pytest.raises(lr.RearrError) as ex:
+        lr.describe_reorder(n, 4, idx_bytes=2)
+    assert ex.value.status == lr.EINVAL
