@@ -43,6 +43,18 @@ int main(void)
     st = rearr_stencil2d_describe(4096, 4096, 5, dy, dx, w, REARR_STENCIL_ZERO, 0, 0, &si);
     printf("stencil %s shape %d radius %d\n", rearr_status_str(st), si.shape, si.radius);
 
+    /* a random reorder of 2^28 fp32: the bucketed passes, shared-memory scatter */
+    rearr_reorder_info ri;
+    st = rearr_reorder_describe((size_t)1 << 28, 4, 4, 0, 0, 0, 0, &ri);
+    printf("reorder %s form %d chunks %u %u\n", rearr_status_str(st), ri.form, ri.bucket_chunks, ri.dest_chunks);
+
+    /* a box that drops the input's fastest axis: one strided gather per cell */
+    const int64_t bd[3] = {40, 50, 60}, bb[3] = {3, 7, 11}, br[3] = {30, 40, 1};
+    const int bo[2] = {1, 0};
+    rearr_permute_info ni;
+    st = rearr_reorder_nm_describe(4, 3, bd, 2, bo, bb, br, 0, 0, &ni);
+    printf("nm %s kind %d\n", rearr_status_str(st), ni.kind);
+
     /* a pipeline of zero slots is rejected before any CUDA call */
     rearr_pipeline *pipe = (rearr_pipeline *)0;
     st = rearr_pipeline_create(1 << 20, 0, &pipe);

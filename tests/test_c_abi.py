@@ -55,3 +55,8 @@ def test_dist_plan(client):
 def test_stencil_and_selftest(client):
     assert client["stencil"] == ["REARR_OK", "shape", "1", "radius", "1"]  # a cross of radius 1
     assert client["selftest"] == ["REARR_OK"]
+
+
+def test_describe_reorder_and_box(client):
+    assert client["reorder"] == ["REARR_OK", "form", "1", "chunks", "64", "16384"]  # REARR_REORDER_SMEM_SCATTER
+    assert client["nm"] == ["REARR_OK", "kind", "5"]                                 # REARR_KIND_STRIDED
