@@ -364,9 +364,10 @@ def run_gpu(args):
         result = {
             "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bytes (u8/u16/u32/u64 words, bit-exact)",
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic (seeded PCG64 random bit patterns)",
             "config": {"workload": WORKLOAD, "ops_per_step": len(ops), "bytes_per_step": step_bytes,
+                       "elements": "2/4/8-byte elements moved as opaque bytes in 1-16-byte words, bit-exact",
                        "l2": "every operand >= 256 MiB, larger than the 129 MB L2; no flush",
                        "parallelism": f"replicas x{world}"},
             "memcpy_d2d_gbs": round(memcpy_gbs, 1), "frac_of_memcpy": round(value / world / memcpy_gbs, 4),
@@ -667,7 +668,7 @@ def run_reference(args):
     return {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s",
             "n_gpus": int(os.environ.get("WORLD_SIZE", args.gpus)),
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_t / args.steps * 1e3, 1),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bytes (memcpy per element)",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic (seeded PCG64 random bit patterns)",
             "config": {"workload": WORKLOAD, "parallelism": "single CPU thread (the oracle on the host)"},
             "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
