@@ -333,7 +333,10 @@ void rearr_plan_destroy(rearr_plan *plan);
  *
  *   plan   : a plan built with rearr_plan_add_* (finalized or not; only its
  *            host-side op list is read).  The caller still owns every input
- *            and output buffer the ops name.
+ *            and output buffer the ops name.  A finalized plan runs in the
+ *            work-list order rearr_plan_finalize chose (ops grouped by body);
+ *            a plan that was not finalized runs its ops in the order they were
+ *            added, with the same results.
  *   stream : the work list is copied and the kernel launched on this stream.
  *
  * The work list goes to a fixed 512 KiB device buffer compiled into the

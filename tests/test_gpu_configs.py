@@ -1,25 +1,32 @@
-"""The benchmark workloads at full size, checked against the oracle.
+"""The benchmark workloads at full size, compared with the oracle in full.
 
-At these sizes the oracle evaluates sampled output elements one by one
-(oracle_permute_sample, or the gather / interlace definitions on a subset of
-indices), and properties that hold at any size are checked on the whole
-output on the device: a permute followed by its inverse, interlace followed by
-de-interlace and a reorder followed by its inverse give back the input bit for
-bit.  The launch configuration is the one bench.py times (single calls on one
-stream).
+Every output byte of every full-size config is compared with the oracle's
+loop nest: the 1024^2 fp32 transpose, all 6 orders of 512^3 fp32, all 24
+orders of 64x128x256x64 at 2, 4 and 8 bytes, the 2^28 fp32 reorders, the
+complex64 split, the 4096^2 image planes and the AoS/SoA records.  The oracle
+is single-threaded C; independent oracle calls run on a few host threads at a
+time (the ctypes call releases the interpreter lock) while the GPU runs the
+next order.  Every output buffer is guarded (tests.gpu_util), so a write
+outside it fails too.  A permute followed by its inverse, a reorder by the
+inverse permutation and interlace followed by de-interlace are also checked
+to give back the input.  The launch configuration is the one bench.py times
+(single calls on one stream).
 """
+import collections
 import itertools
+import os
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 import pytest
 
 import oracle
 import synth
-from tests.gpu_util import sync
+from tests.gpu_util import DevBuf, sync, to_dev
 
 pytestmark = pytest.mark.gpu
 
-N_SAMPLES = 1 << 16
+ORACLE_THREADS = max(1, min(6, (os.cpu_count() or 2) - 2))
 
 
 @pytest.fixture(scope="module")
@@ -37,15 +44,17 @@ def orc():
     return oracle.get()
 
 
-def dev_from_np(a: np.ndarray):
-    import torch
-    return torch.from_numpy(np.ascontiguousarray(a).reshape(-1).view(np.uint8)).to("cuda")
-
-
-def sampled_equal(dev_out, e, lin: np.ndarray, want: np.ndarray) -> bool:
-    import torch
-    rows = dev_out.view(-1, e)[torch.from_numpy(lin).to("cuda")]
-    return np.array_equal(rows.cpu().numpy().reshape(-1), want)
+def in_order(calls, window=ORACLE_THREADS):
+    """Results of the callables in order, at most `window` running at once."""
+    with ThreadPoolExecutor(max_workers=window) as ex:
+        it = iter(calls)
+        pending = collections.deque(ex.submit(f) for f in itertools.islice(it, window))
+        while pending:
+            r = pending.popleft().result()
+            nxt = next(it, None)
+            if nxt is not None:
+                pending.append(ex.submit(nxt))
+            yield r
 
 
 def inverse(perm):
@@ -55,37 +64,41 @@ def inverse(perm):
     return inv
 
 
-def permute_all_orders(lr, orc, dims, e, seed, orders=None):
+def assert_same(got: np.ndarray, want: np.ndarray, what):
+    if not np.array_equal(got, want):
+        bad = np.flatnonzero(got != want)
+        raise AssertionError(f"{what}: {bad.size} bytes differ, first at byte {bad[0]}")
+
+
+def permute_all_orders(lr, orc, dims, e, seed):
     import torch
     n = int(np.prod(dims))
-    src_np = synth.random_elements(seed, n * 1, e)
-    src = dev_from_np(src_np)
-    out = torch.empty_like(src)
-    back = torch.empty_like(src)
-    g = synth.rng(seed + 1)
-    for perm in orders or itertools.permutations(range(len(dims))):
-        perm = list(perm)
-        out.fill_(0)
-        lr.permute(out, src, e, dims, perm)
-        lin = g.integers(0, n, size=N_SAMPLES, dtype=np.int64)
-        lin[:4] = [0, n - 1, n // 2, 1]
-        want = orc.permute_sample(src_np, e, dims, perm, lin)
+    src_np = synth.random_elements(seed, n, e)
+    src = to_dev(src_np)
+    out = DevBuf(n * e)
+    back = DevBuf(n * e)
+    perms = [list(p) for p in itertools.permutations(range(len(dims)))]
+    wants = in_order(lambda p=p: orc.permute(src_np, e, dims, p) for p in perms)
+    for perm, want in zip(perms, wants):
+        out.view.fill_(0xA5)
+        lr.permute(out.ptr, src.ptr, e, dims, perm)
         sync()
-        assert sampled_equal(out, e, lin, want), (dims, perm, e)
-        lr.permute(back, out, e, [dims[p] for p in perm], inverse(perm))
+        assert_same(out.download(), want, ("permute", dims, perm, e))
+        del want
+        lr.permute(back.ptr, out.ptr, e, [dims[p] for p in perm], inverse(perm))
         sync()
-        assert torch.equal(back, src), ("inverse round trip", dims, perm, e)
+        back.check_guards()
+        assert torch.equal(back.view, src.view), ("inverse round trip", dims, perm, e)
 
 
 def test_config_transpose_1024(lr, orc):
-    """1024 x 1024 fp32 transpose, compared in full."""
-    import torch
+    """1024 x 1024 fp32 transpose."""
     src_np = synth.random_elements(2024, 1024 * 1024, 4)
-    src = dev_from_np(src_np)
-    out = torch.empty_like(src)
-    lr.permute(out, src, 4, [1024, 1024], [1, 0])
+    src = to_dev(src_np)
+    out = DevBuf(src_np.size, fill=0)
+    lr.permute(out.ptr, src.ptr, 4, [1024, 1024], [1, 0])
     sync()
-    assert np.array_equal(out.cpu().numpy(), orc.permute(src_np, 4, [1024, 1024], [1, 0]))
+    assert_same(out.download(), orc.permute(src_np, 4, [1024, 1024], [1, 0]), "transpose 1024^2")
 
 
 def test_config_rank3_512_cubed(lr, orc):
@@ -104,82 +117,66 @@ def test_config_reorder_2p28(lr, orc, kind):
     src_np = synth.random_elements(28, n, 4)
     idx_np = (synth.random_permutation(29, n) if kind == "random"
               else synth.block_shuffled_permutation(30, n, 4096))
-    src, idx = dev_from_np(src_np), dev_from_np(idx_np)
-    out = torch.empty_like(src)
-    lr.reorder(out, src, idx, n, 4)
-    g = synth.rng(31)
-    lin = g.integers(0, n, size=N_SAMPLES, dtype=np.int64)
-    lin[:2] = [0, n - 1]
-    want = orc.reorder_sample(src_np, idx_np, 4, lin)
-    sync()
-    assert sampled_equal(out, 4, lin, want)
+    with ThreadPoolExecutor(max_workers=1) as ex:
+        want = ex.submit(orc.reorder, src_np, idx_np, 4)
+        src, idx = to_dev(src_np), to_dev(idx_np)
+        out = DevBuf(n * 4, fill=0x5A)
+        lr.reorder(out.ptr, src.ptr, idx.ptr, n, 4)
+        sync()
+        assert_same(out.download(), want.result(), ("reorder 2^28", kind))
     # reorder by the inverse permutation restores the input everywhere
-    inv = torch.empty_like(idx)
-    inv.view(torch.int32)[idx.view(torch.int32).long()] = torch.arange(n, dtype=torch.int32, device="cuda")
-    back = torch.empty_like(src)
-    lr.reorder(back, out, inv, n, 4)
+    inv_np = np.empty_like(idx_np)
+    inv_np[idx_np] = np.arange(n, dtype=np.uint32)
+    inv = to_dev(inv_np)
+    back = DevBuf(n * 4)
+    lr.reorder(back.ptr, out.ptr, inv.ptr, n, 4)
     sync()
-    assert torch.equal(back, src)
+    back.check_guards()
+    assert torch.equal(back.view, src.view)
 
 
-def interlace_roundtrip(lr, orc, k, n, e, seed):
+def interlace_both_ways(lr, orc, k, n, e, seed):
+    """Interlace k planes and de-interlace an independent interlaced array,
+    both compared with the oracle in full; then de-interlace the interlaced
+    result and get the planes back."""
     import torch
     planes_np = [synth.random_elements(seed + j, n, e) for j in range(k)]
-    planes = [dev_from_np(p) for p in planes_np]
-    inter = torch.empty(n * k * e, dtype=torch.uint8, device="cuda")
-    lr.interlace(inter, planes, n, e)
-    g = synth.rng(seed + 100)
-    rec = g.integers(0, n, size=N_SAMPLES // k, dtype=np.int64)
-    rec[:2] = [0, n - 1]
-    want = orc.interlace([p.reshape(n, e)[rec].reshape(-1) for p in planes_np], rec.size, e)
-    lin = (rec[:, None] * k + np.arange(k)[None, :]).reshape(-1)
-    sync()
-    assert sampled_equal(inter, e, lin, want), ("interlace", k, n, e)
-    outs = [torch.empty_like(p) for p in planes]
-    lr.deinterlace(outs, inter, n, e)
+    arr_np = synth.random_elements(seed + 100, n * k, e)
+    with ThreadPoolExecutor(max_workers=2) as ex:
+        want_i = ex.submit(orc.interlace, planes_np, n, e)
+        want_d = ex.submit(orc.deinterlace, arr_np, k, n, e)
+        planes = [to_dev(p) for p in planes_np]
+        inter = DevBuf(n * k * e, fill=0x33)
+        lr.interlace(inter.ptr, [p.ptr for p in planes], n, e)
+        sync()
+        assert_same(inter.download(), want_i.result(), ("interlace", k, n, e))
+        arr = to_dev(arr_np)
+        outs = [DevBuf(n * e, fill=0x44) for _ in range(k)]
+        lr.deinterlace([o.ptr for o in outs], arr.ptr, n, e)
+        sync()
+        for j, (o, w) in enumerate(zip(outs, want_d.result())):
+            assert_same(o.download(), w, ("de-interlace", k, n, e, j))
+    del arr, want_d
+    for o in outs:
+        o.view.fill_(0)
+    lr.deinterlace([o.ptr for o in outs], inter.ptr, n, e)
     sync()
     for o, p in zip(outs, planes):
-        assert torch.equal(o, p), ("de-interlace round trip", k, n, e)
+        o.check_guards()
+        assert torch.equal(o.view, p.view), ("de-interlace round trip", k, n, e)
 
 
 def test_config_complex_split_2p28(lr, orc):
     """complex64 of 2^28 elements <-> real and imaginary fp32 planes."""
-    import torch
-    n = 1 << 28
-    z_np = synth.random_elements(64, n, 8)
-    z = dev_from_np(z_np)
-    re, im = torch.empty(n * 4, dtype=torch.uint8, device="cuda"), torch.empty(n * 4, dtype=torch.uint8, device="cuda")
-    lr.deinterlace([re, im], z, n, 4)
-    g = synth.rng(65)
-    rec = g.integers(0, n, size=N_SAMPLES, dtype=np.int64)
-    sub = z_np.reshape(n, 8)[rec].reshape(-1)
-    w_re, w_im = orc.deinterlace(sub, 2, rec.size, 4)
-    sync()
-    assert sampled_equal(re, 4, rec, w_re) and sampled_equal(im, 4, rec, w_im)
-    back = torch.empty_like(z)
-    lr.interlace(back, [re, im], n, 4)
-    sync()
-    assert torch.equal(back, z)
+    interlace_both_ways(lr, orc, 2, 1 << 28, 4, seed=64)
 
 
 @pytest.mark.parametrize("k", [3, 4])
 def test_config_image_planes_4096(lr, orc, k):
-    """4096 x 4096 uint8 images, k planes, compared in full."""
-    import torch
-    n = 4096 * 4096
-    planes_np = [synth.random_elements(70 + j, n, 1) for j in range(k)]
-    planes = [dev_from_np(p) for p in planes_np]
-    inter = torch.empty(n * k, dtype=torch.uint8, device="cuda")
-    lr.interlace(inter, planes, n, 1)
-    sync()
-    assert np.array_equal(inter.cpu().numpy(), orc.interlace(planes_np, n, 1))
-    outs = [torch.empty_like(p) for p in planes]
-    lr.deinterlace(outs, inter, n, 1)
-    sync()
-    for o, p in zip(outs, planes_np):
-        assert np.array_equal(o.cpu().numpy(), p)
+    """4096 x 4096 uint8 images, k planes."""
+    interlace_both_ways(lr, orc, k, 4096 * 4096, 1, seed=70)
 
 
 @pytest.mark.parametrize("k", [2, 3, 4, 8])
 def test_config_aos_soa_2p26(lr, orc, k):
-    interlace_roundtrip(lr, orc, k, 1 << 26, 4, seed=80 + k)
+    interlace_both_ways(lr, orc, k, 1 << 26, 4, seed=80 + k)

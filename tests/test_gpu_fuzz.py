@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import synth
-from tests.gpu_util import DevBuf, sync, to_dev
+from tests.gpu_util import DevBuf, DevPool, sync, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -113,6 +113,7 @@ def one_interlace(rr, orc, d, it):
 def one_batch(rr, orc, d, it):
     g = d.g
     plan = rr.Plan()
+    pool = DevPool()
     checks = []
     for j in range(int(g.integers(1, 40))):
         t = int(g.integers(0, 3))
@@ -120,25 +121,26 @@ def one_batch(rr, orc, d, it):
             e, dims, perm = d.permute()
             n = int(np.prod(dims))
             src = synth.random_elements(it * 100 + j, n, e)
-            s, out = to_dev(src), DevBuf(n * e, 0, fill=0)
+            s, out = to_dev(src, 0, pool), DevBuf(n * e, 0, fill=0, pool=pool)
             plan.add_permute(out.ptr, s.ptr, e, dims, perm)
             checks.append((out, orc.permute(src, e, dims, perm), s))
         elif t == 1:
             e, n = int(g.choice([1, 2, 4, 8])), int(g.integers(1, 100000))
             src, idx = synth.random_elements(it * 100 + j, n, e), synth.random_permutation(j, n)
-            s, ix, out = to_dev(src), to_dev(idx), DevBuf(n * e, 0, fill=0)
+            s, ix, out = to_dev(src, 0, pool), to_dev(idx, 0, pool), DevBuf(n * e, 0, fill=0, pool=pool)
             plan.add_reorder(out.ptr, s.ptr, ix.ptr, n, e)
             checks.append((out, orc.reorder(src, idx, e), (s, ix)))
         else:
             e, k, n = int(g.choice([1, 2, 4, 8])), int(g.integers(1, 9)), int(g.integers(1, 50000))
             planes = [synth.random_elements(it * 100 + j + q, n, e) for q in range(k)]
-            pd = [to_dev(p) for p in planes]
-            iv = DevBuf(n * k * e, 0, fill=0)
+            pd = [to_dev(p, 0, pool) for p in planes]
+            iv = DevBuf(n * k * e, 0, fill=0, pool=pool)
             plan.add_interlace(iv.ptr, [p.ptr for p in pd], n, e)
             checks.append((iv, orc.interlace(planes, n, e), pd))
     plan.finalize()
     plan.run()
     sync()
+    pool.check()
     ok = all(np.array_equal(out.download(), want) for out, want, _ in checks)
     plan.close()
     return "batch", ok, (it, len(checks))

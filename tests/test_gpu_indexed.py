@@ -4,7 +4,7 @@ import pytest
 
 import oracle
 import synth
-from tests.gpu_util import DevBuf, sync, to_dev
+from tests.gpu_util import DevBuf, DevPool, sync, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -81,16 +81,18 @@ def test_gather64_with_repeats(lr, orc):
 
 def test_scatter_in_a_batch(lr, orc):
     plan = lr.Plan()
+    pool = DevPool()
     cases = []
     for t, (n, e) in enumerate([(1000, 4), (4099, 1), (77777, 8), (5, 16)]):
         src = synth.random_elements(70 + t, n, e)
         p = synth.random_permutation(80 + t, n)
-        s, ix, d = to_dev(src), to_dev(p), DevBuf(n * e, fill=0)
+        s, ix, d = to_dev(src, 0, pool), to_dev(p, 0, pool), DevBuf(n * e, fill=0, pool=pool)
         plan.add_scatter(d.ptr, s.ptr, ix.ptr, n, e)
         cases.append((src, p, e, s, ix, d))
     plan.finalize()
     plan.run()
     sync()
+    pool.check()
     for src, p, e, s, ix, d in cases:
         assert np.array_equal(d.download(), orc.indexed(src, p, e, scatter=True))
     plan.close()

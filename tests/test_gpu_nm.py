@@ -4,7 +4,7 @@ import pytest
 
 import oracle
 import synth
-from tests.gpu_util import DevBuf, sync, to_dev
+from tests.gpu_util import DevBuf, DevPool, sync, to_dev
 from tests.oracle_pins import random_box
 
 pytestmark = pytest.mark.gpu
@@ -87,19 +87,21 @@ def test_nm_in_a_batch(lr, orc):
     import torch
     g = synth.rng(66)
     cases, bufs = [], []
+    pool = DevPool()
     plan = lr.Plan()
     for t in range(40):
         dims, order, base, rng = random_box(g, int(g.integers(1, 6)), max_extent=24)
         e = ELEMS[t % len(ELEMS)]
         src = synth.random_elements(900 + t, int(np.prod(dims)), e)
         total = int(np.prod([rng[a] for a in order]))
-        s, d = to_dev(src), DevBuf(total * e, fill=0)
+        s, d = to_dev(src, 0, pool), DevBuf(total * e, fill=0, pool=pool)
         plan.add_reorder_nm(d.ptr, s.ptr, e, dims, order, base, rng)
         cases.append((src, e, dims, order, base, rng))
         bufs.append((s, d))
     plan.finalize()
     plan.run()
     sync()
+    pool.check()
     for (src, e, dims, order, base, rng), (s, d) in zip(cases, bufs):
         assert np.array_equal(d.download(), orc.reorder_nm(src, e, dims, order, base, rng))
     plan.close()

@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import synth
-from tests.gpu_util import DevBuf, sync, to_dev
+from tests.gpu_util import DevBuf, DevPool, sync, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -204,25 +204,28 @@ def test_interlace_many_planes_and_unaligned(lr, orc):
 # ---------------------------------------------------------------------------
 # batched execution
 
-def make_op_buffers(op, offset=0):
-    """Device inputs (from the op's data seed) and zeroed outputs for one op spec."""
+def make_op_buffers(op, offset=0, pool=None):
+    """Device inputs (from the op's data seed) and zeroed outputs for one op
+    spec, guarded, carved back to back from `pool` when one is given."""
     e = op["elem_bytes"]
     if op["kind"] == "permute":
         n = int(np.prod(op["dims"]))
         src = synth.random_elements(op["data_seed"], n, e)
-        return dict(src_np=src, src=to_dev(src, offset), dst=DevBuf(n * e, offset, fill=0))
+        return dict(src_np=src, src=to_dev(src, offset, pool), dst=DevBuf(n * e, offset, fill=0, pool=pool))
     if op["kind"] == "reorder":
         n = op["n"]
         src = synth.random_elements(op["data_seed"], n, e)
         idx = synth.random_permutation(op["data_seed"] ^ 1, n)
-        return dict(src_np=src, idx_np=idx, src=to_dev(src, offset), idx=to_dev(idx), dst=DevBuf(n * e, offset, fill=0))
+        return dict(src_np=src, idx_np=idx, src=to_dev(src, offset, pool), idx=to_dev(idx, 0, pool),
+                    dst=DevBuf(n * e, offset, fill=0, pool=pool))
     k, n = op["k"], op["n"]
     if op["kind"] == "interlace":
         planes = [synth.random_elements(op["data_seed"] + j, n, e) for j in range(k)]
-        return dict(planes_np=planes, planes=[to_dev(p, offset) for p in planes],
-                    dst=DevBuf(n * k * e, offset, fill=0))
+        return dict(planes_np=planes, planes=[to_dev(p, offset, pool) for p in planes],
+                    dst=DevBuf(n * k * e, offset, fill=0, pool=pool))
     arr = synth.random_elements(op["data_seed"], n * k, e)
-    return dict(src_np=arr, src=to_dev(arr, offset), dsts=[DevBuf(n * e, offset, fill=0) for _ in range(k)])
+    return dict(src_np=arr, src=to_dev(arr, offset, pool),
+                dsts=[DevBuf(n * e, offset, fill=0, pool=pool) for _ in range(k)])
 
 
 def add_to_plan(plan, op, b):
@@ -256,7 +259,8 @@ def outputs_of(op, b):
 
 def test_batch_mix_matches_oracle(lr, orc):
     ops = synth.batch_mix(seed=5, n_ops=160, hi_total=2 ** 15)
-    bufs = [make_op_buffers(op, offset=(i % 3) * 4) for i, op in enumerate(ops)]
+    pool = DevPool()
+    bufs = [make_op_buffers(op, offset=(i % 3) * 4, pool=pool) for i, op in enumerate(ops)]
     plan = lr.Plan()
     for op, b in zip(ops, bufs):
         add_to_plan(plan, op, b)
@@ -264,9 +268,10 @@ def test_batch_mix_matches_oracle(lr, orc):
     for rep in range(2):  # the second replay must give the same bytes
         for b in bufs:
             for out in ([b["dst"]] if "dst" in b else b["dsts"]):
-                out.t.fill_(0)
+                out.view.fill_(0)
         plan.run()
         sync()
+        pool.check()
         for i, (op, b) in enumerate(zip(ops, bufs)):
             want = oracle_of(orc, op, b)
             got = outputs_of(op, b)
@@ -295,8 +300,9 @@ def test_batch_rereads_inputs_on_replay(lr, orc):
 
 def test_batch_equals_single_calls(lr, orc):
     ops = synth.batch_mix(seed=9, n_ops=48, hi_total=2 ** 16)
-    b1 = [make_op_buffers(op) for op in ops]
-    b2 = [make_op_buffers(op) for op in ops]
+    p1, p2 = DevPool(), DevPool()
+    b1 = [make_op_buffers(op, pool=p1) for op in ops]
+    b2 = [make_op_buffers(op, pool=p2) for op in ops]
     plan = lr.Plan()
     for op, b in zip(ops, b1):
         add_to_plan(plan, op, b)
@@ -313,6 +319,8 @@ def test_batch_equals_single_calls(lr, orc):
         else:
             lr.deinterlace([d.ptr for d in b["dsts"]], b["src"].ptr, op["n"], e)
     sync()
+    p1.check()
+    p2.check()
     for op, x, y in zip(ops, b1, b2):
         for gx, gy in zip(outputs_of(op, x), outputs_of(op, y)):
             assert np.array_equal(gx, gy), op
@@ -332,7 +340,8 @@ def test_batch_interlace_next_to_shared_memory_bodies(lr, orc):
             ops.append(dict(kind="permute", elem_bytes=4, dims=[3 + i % 5, 9, 64], perm=[1, 0, 2], data_seed=i))
         else:
             ops.append(dict(kind="permute", elem_bytes=4, dims=[40, 33 + i % 4], perm=[1, 0], data_seed=i))
-    bufs = [make_op_buffers(op) for op in ops]
+    pool = DevPool()
+    bufs = [make_op_buffers(op, pool=pool) for op in ops]
     plan = lr.Plan()
     for op, b in zip(ops, bufs):
         add_to_plan(plan, op, b)
@@ -340,6 +349,7 @@ def test_batch_interlace_next_to_shared_memory_bodies(lr, orc):
     for rep in range(3):
         plan.run()
         sync()
+        pool.check()
         for i, (op, b) in enumerate(zip(ops, bufs)):
             for w, g in zip(oracle_of(orc, op, b), outputs_of(op, b)):
                 assert np.array_equal(g, w), (rep, i, op)
@@ -349,13 +359,15 @@ def test_batch_interlace_next_to_shared_memory_bodies(lr, orc):
 def test_batch_many_planes(lr, orc):
     op = dict(kind="interlace", elem_bytes=4, k=12, n=333, data_seed=3)
     op2 = dict(kind="deinterlace", elem_bytes=2, k=9, n=1001, data_seed=4)
-    b, b2 = make_op_buffers(op), make_op_buffers(op2)
+    pool = DevPool()
+    b, b2 = make_op_buffers(op, pool=pool), make_op_buffers(op2, pool=pool)
     plan = lr.Plan()
     add_to_plan(plan, op, b)
     add_to_plan(plan, op2, b2)
     plan.finalize()
     plan.run()
     sync()
+    pool.check()
     assert np.array_equal(outputs_of(op, b)[0], oracle_of(orc, op, b)[0])
     for g, w in zip(outputs_of(op2, b2), oracle_of(orc, op2, b2)):
         assert np.array_equal(g, w)
@@ -367,14 +379,12 @@ def test_batch_many_planes(lr, orc):
 # chosen on the device from the index locality)
 
 def _l2_case(lr, orc, e, n, idx, seed):
-    import torch
     src = synth.random_elements(seed, n, e)
-    s = torch.from_numpy(src).cuda()
-    ix = torch.from_numpy(idx.view(np.uint8)).cuda()
-    d = torch.empty_like(s).fill_(0x3C)
-    lr.reorder(d, s, ix, n, e)
+    s, ix = to_dev(src), to_dev(idx)
+    d = DevBuf(n * e, 0, fill=0x3C)
+    lr.reorder(d.ptr, s.ptr, ix.ptr, n, e)
     sync()
-    got = d.cpu().numpy()
+    got = d.download()
     want = orc.reorder(src, idx, e)
     assert np.array_equal(got, want), (e, n, seed)
 
@@ -478,13 +488,15 @@ def test_batch_with_strided_ops(lr, orc):
     ops = [dict(kind="permute", elem_bytes=[1, 2, 4, 8][i % 4], dims=dims, perm=perm, data_seed=i)
            for i, (dims, perm) in enumerate(THIN * 4)]
     ops += [dict(kind="permute", elem_bytes=4, dims=[64, 96], perm=[1, 0], data_seed=99)]  # a tile op
-    bufs = [make_op_buffers(op, offset=(i % 2) * 4) for i, op in enumerate(ops)]
+    pool = DevPool()
+    bufs = [make_op_buffers(op, offset=(i % 2) * 4, pool=pool) for i, op in enumerate(ops)]
     plan = lr.Plan()
     for op, b in zip(ops, bufs):
         add_to_plan(plan, op, b)
     plan.finalize()
     plan.run()
     sync()
+    pool.check()
     for i, (op, b) in enumerate(zip(ops, bufs)):
         for w, g in zip(oracle_of(orc, op, b), outputs_of(op, b)):
             assert np.array_equal(g, w), (i, op)

@@ -5,6 +5,7 @@ import pytest
 import oracle
 import synth
 from synth.stencils import fd_laplacian
+from tests.gpu_util import HostBuf
 
 pytestmark = pytest.mark.gpu
 
@@ -38,6 +39,13 @@ def test_mixed_ops_more_ops_than_slots(lr, orc, host):
     for i in range(10):
         kind = ["permute", "reorder", "interlace", "deinterlace", "stencil"][i % 5]
         ops.append((kind, i, g))
+    guarded = []
+
+    def out_buf(nbytes):
+        h = HostBuf(nbytes, offset=len(guarded) % 5)
+        guarded.append(h)
+        return h.body
+
     with lr.Pipeline(slot_bytes=8 << 20, slots=3) as pipe:
         checks = []
         for kind, i, _ in ops:
@@ -45,7 +53,7 @@ def test_mixed_ops_more_ops_than_slots(lr, orc, host):
             if kind == "permute":
                 dims, perm, e = [37, 64, 29], [2, 0, 1], 4
                 src = synth.random_elements(seed, int(np.prod(dims)), e)
-                dst = np.zeros(src.size, dtype=np.uint8)
+                dst = out_buf(src.size)
                 if host == "pinned":
                     s_t, d_t = pinned(src.size), pinned(dst.size)
                     s_t.numpy()[:] = src
@@ -58,19 +66,19 @@ def test_mixed_ops_more_ops_than_slots(lr, orc, host):
                 n, e = 100003, 8
                 src = synth.random_elements(seed, n, e)
                 idx = synth.random_indices(seed, n, n)
-                dst = np.zeros(n * e, dtype=np.uint8)
+                dst = out_buf(n * e)
                 pipe.reorder(dst, src, idx, n, e)
                 checks.append((lambda dst=dst: dst, orc.reorder(src, idx, e)))
             elif kind == "interlace":
                 n, k, e = 50001, 3, 2
                 planes = [synth.random_elements(seed + j, n, e) for j in range(k)]
-                dst = np.zeros(n * k * e, dtype=np.uint8)
+                dst = out_buf(n * k * e)
                 pipe.interlace(dst, planes, n, e)
                 checks.append((lambda dst=dst: dst, orc.interlace(planes, n, e)))
             elif kind == "deinterlace":
                 n, k, e = 40000, 4, 4
                 src = synth.random_elements(seed, n * k, e)
-                outs = [np.zeros(n * e, dtype=np.uint8) for _ in range(k)]
+                outs = [out_buf(n * e) for _ in range(k)]
                 pipe.deinterlace(outs, src, n, e)
                 want = orc.deinterlace(src, k, n, e)
                 checks.append((lambda outs=outs: np.concatenate(outs), np.concatenate(want)))
@@ -78,7 +86,7 @@ def test_mixed_ops_more_ops_than_slots(lr, orc, host):
                 ny, nx = 300, 260
                 grid = np.random.default_rng(seed).normal(size=(ny, nx)).astype(np.float32)
                 taps = [(dy, dx, float(np.float32(w))) for dy, dx, w in fd_laplacian(2)]
-                out = np.zeros((ny, nx), dtype=np.float32)
+                out = out_buf(ny * nx * 4).view(np.float32).reshape(ny, nx)
                 pipe.stencil2d(out, grid, ny, nx, taps, 1)
                 want = orc.stencil2d(grid, taps, 1)
                 s = orc.stencil2d(np.abs(grid), [(a, b, abs(w)) for a, b, w in taps], 1)
@@ -86,6 +94,8 @@ def test_mixed_ops_more_ops_than_slots(lr, orc, host):
                 checks.append((lambda out=out, want=want, tol=tol: np.abs(out.astype(np.float64) - want) <= tol,
                                np.ones((ny, nx), dtype=bool)))
         pipe.sync()
+        for h in guarded:
+            h.check_guards()
         for i, (got, want) in enumerate(checks):
             assert np.array_equal(got(), want), ops[i][0]
         st = pipe.stats()
@@ -137,16 +147,19 @@ def test_nm_scatter_and_wide_indices(lr, orc):
     with lr.Pipeline(slot_bytes=16 << 20, slots=3) as pipe:
         dims, order, base, rng = [40, 50, 60], [2, 0], [3, 7, 5], [30, 1, 50]
         src = synth.random_elements(1, int(np.prod(dims)), 4)
-        out_nm = np.zeros(50 * 30 * 4, dtype=np.uint8)
+        guarded = [HostBuf(50 * 30 * 4, 3)] + [HostBuf(77777 * 8, j) for j in range(3)]
+        out_nm = guarded[0].body
         pipe.reorder_nm(out_nm, src, 4, dims, order, base, rng)
         n, e = 77777, 8
         s2 = synth.random_elements(2, n, e)
         p = synth.random_permutation(3, n)
-        outs = {k: np.zeros(n * e, dtype=np.uint8) for k in ("scatter", "reorder64", "scatter64")}
+        outs = {k: h.body for k, h in zip(("scatter", "reorder64", "scatter64"), guarded[1:])}
         pipe.scatter(outs["scatter"], s2, p, n, e)
         pipe.reorder64(outs["reorder64"], s2, p.astype(np.uint64), n, e)
         pipe.scatter64(outs["scatter64"], s2, p.astype(np.uint64), n, e)
         pipe.sync()
+        for h in guarded:
+            h.check_guards()
         assert np.array_equal(out_nm, orc.reorder_nm(src, 4, dims, order, base, rng))
         assert np.array_equal(outs["scatter"], orc.indexed(s2, p, e, scatter=True))
         assert np.array_equal(outs["scatter64"], orc.indexed(s2, p, e, scatter=True))

@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import synth
-from tests.gpu_util import sync
+from tests.gpu_util import guard_pattern, sync
 
 pytestmark = pytest.mark.gpu
 
@@ -65,9 +65,29 @@ def download(rr, ptr, nbytes):
     return t.cpu().numpy()
 
 
+SENTINEL = dict(kind="permute", elem_bytes=1, dims=[256], perm=[0])
+
+
 def serve_all(rr, srv, ops):
-    """Reserve, fill and submit every op, then wait for all; returns outputs."""
+    """Reserve, fill and submit every op, then wait for all; returns outputs.
+
+    A sentinel reservation (256 bytes in, 256 out, filled with a seeded
+    pattern and never submitted) is made before the first request and after
+    every request.  The slab is first-fit and nothing is released until the
+    end, so every request's buffers lie between sentinel buffers; a write
+    outside a request's own buffers changes a sentinel and fails the test."""
+    sentinels = []
+
+    def sentinel():
+        t = srv.reserve(SENTINEL)
+        ins, outs = srv.buffers(t)
+        pat = guard_pattern(256, 2 + len(sentinels))
+        for p in ins + outs:
+            upload(rr, p, pat)
+        sentinels.append((t, ins + outs, pat))
+
     tickets, wants = [], []
+    sentinel()
     for op in ops:
         ins = op_inputs(op)
         t = srv.reserve(op)
@@ -75,6 +95,7 @@ def serve_all(rr, srv, ops):
         for p, h in zip(in_ptrs, ins):
             upload(rr, p, h)
         srv.submit(t)
+        sentinel()
         tickets.append(t)
         wants.append(oracle_outputs(op, ins))
     outs = []
@@ -83,6 +104,10 @@ def serve_all(rr, srv, ops):
         _, out_ptrs = srv.buffers(t)
         outs.append([download(rr, p, x.size) for p, x in zip(out_ptrs, w)])
         assert srv.latency(t) > 0
+        srv.release(t)
+    for t, ptrs, pat in sentinels:
+        for p in ptrs:
+            assert np.array_equal(download(rr, p, 256), pat), "a write landed outside a request's buffers"
         srv.release(t)
     return outs, wants
 
@@ -96,7 +121,8 @@ def test_each_result_same_alone_and_in_the_mix(rr, batching):
         for got, want in zip(o, w):
             assert np.array_equal(got, want), (i, ops[i])
     st = srv.stats()
-    assert st["completed"] == len(ops) and st["released"] == len(ops) and st["slab_used"] == 0
+    # every request and every sentinel (one more than the requests) was released
+    assert st["completed"] == len(ops) and st["released"] == 2 * len(ops) + 1 and st["slab_used"] == 0
     if batching:
         assert st["launches"] <= len(ops)
     srv.close()
