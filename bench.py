@@ -290,6 +290,9 @@ def run_gpu(args):
         step()
     torch.cuda.synchronize()
     memcpy_gbs, _ = measure_memcpy(torch, rr, stream)
+    # a device copy of each op's payload size, the same-size denominator
+    memcpy_same = {nb: measure_memcpy(torch, rr, stream, nbytes=nb)[0]
+                   for nb in sorted({op_out_bytes(o) for o in ops})}
 
     # timed region: K steps, one event between consecutive ops
     n_ev = len(ops) * args.steps + 1
@@ -348,6 +351,9 @@ def run_gpu(args):
     families = {f: {"gbs": round(fam_bytes[f] / fam_time[f] / 1e9, 1), "time_share": round(fam_time[f] / sum(fam_time.values()), 4),
                     "launches_per_step": fam_launch[f] // args.steps} for f in fam_time}
     per_op_gbs = [round(op_bytes(o) * args.steps / per_op[i] / 1e9, 1) for i, o in enumerate(ops)]
+    # payload bytes (R+W, index reads left out) per op against a copy of the same size
+    per_op_frac_same = [round(2 * op_out_bytes(o) * args.steps / per_op[i] / 1e9 / memcpy_same[op_out_bytes(o)], 4)
+                        for i, o in enumerate(ops)]
 
     # end to end through the public API with pinned host buffers
     t_e2e, e2e_steps, h2d, d2h = run_e2e(torch, rr, wl, ops, stream, args)
@@ -357,6 +363,7 @@ def run_gpu(args):
 
     batched = None if args.no_batched else run_batched(torch, rr, stream, device)
     serving = None if args.no_serving else run_serving(torch, rr, device)
+    configs = None if (args.no_configs or rank != 0) else measure_configs(torch, rr, device, stream, 10, 3)
 
     result = None
     if rank == 0:
@@ -371,10 +378,12 @@ def run_gpu(args):
                        "l2": "every operand >= 256 MiB, larger than the 129 MB L2; no flush",
                        "parallelism": f"replicas x{world}"},
             "memcpy_d2d_gbs": round(memcpy_gbs, 1), "frac_of_memcpy": round(value / world / memcpy_gbs, 4),
+            "memcpy_same_bytes_gbs": {str(k): round(v, 1) for k, v in memcpy_same.items()},
+            "per_op_frac_of_memcpy_same_bytes": per_op_frac_same,
             "frac_of_8tbs": round(value / world / 8000.0, 4),
             "roofline": roofline, "families": families, "per_op_gbs": per_op_gbs,
             "gpu_launches": int(launches), "clocks": clk.summary(), "e2e": e2e, "cpu_baseline": cpu,
-            "batched": batched, "serving": serving,
+            "batched": batched, "serving": serving, "configs": configs,
             "source_digest": source_digest(),
         }
     if world > 1:
@@ -481,7 +490,33 @@ def run_batched(torch, rr, stream, device, n_ops=4096, reps=5):
     t_batch = timed(lambda: plan.run(stream), reps)
     n_ops_plan, n_tiles = plan.stats()
     plan.close()
+
+    # the same kernel on each op class of the mix alone (one plan per class)
+    def op_class(o):
+        if o["kind"] == "permute":
+            return "permute:" + rr.describe_permute(o["elem_bytes"], o["dims"], o["perm"])["kind"]
+        return "reorder" if o["kind"] == "reorder" else "interlace/de-interlace"
+    classes = {}
+    for o, p in zip(ops, bufs):
+        classes.setdefault(op_class(o), []).append((o, p))
+    per_class = {}
+    for name, members in sorted(classes.items()):
+        cp = rr.Plan()
+        for o, p in members:
+            add_to_plan(cp, o, p)
+        cp.finalize(stream)
+        t = timed(lambda: cp.run(stream), reps)
+        cp.close()
+        nb = sum(synth.op_bytes(o) for o, _ in members)
+        per_class[name] = {"ops": len(members), "bytes": int(nb), "ms": round(t * 1e3, 3), "gbs": round(nb / t / 1e9, 1)}
     del pool
+    peak, peak_kind = measured_peak()
+    achieved = total_bytes / t_batch / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_batch (one persistent launch over the whole mix)",
+                "achieved": round(achieved, 1), "peak": peak,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)", "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "algorithmic_bytes_per_launch": int(total_bytes),
+                "traffic": None}
     return {"workload": f"{n_ops}-op uneven mix (seed 1): permute rank 2-5, reorder, interlace/de-interlace k 2-4; "
                         "elem 1/2/4/8 B; extents log-uniform [1,512]; op totals in [2^8, 2^22] elements",
             "bytes_per_batch": int(total_bytes), "tiles": int(n_tiles),
@@ -489,7 +524,8 @@ def run_batched(torch, rr, stream, device, n_ops=4096, reps=5):
             "batched_ops_per_s": round(n_ops / t_batch, 1), "plain_ops_per_s": round(n_ops / t_plain, 1),
             "batched_gbs": round(total_bytes / t_batch / 1e9, 1), "plain_gbs": round(total_bytes / t_plain / 1e9, 1),
             "speedup": round(t_plain / t_batch, 3), "plan_build_s": round(t_build, 3),
-            "launches_per_replay": 1, "kernels_per_plain_pass": n_ops}
+            "launches_per_replay": 1, "kernels_per_plain_pass": n_ops, "roofline": roofline,
+            "classes": per_class, "l2": "the mix's operands total about 6 GB per replay, far larger than the L2"}
 
 
 # ---------------------------------------------------------------------------
@@ -575,7 +611,7 @@ def run_e2e(torch, rr, wl, ops, stream, args):
             else:
                 pipe.permute(h_dst, h_src, o["elem_bytes"], o["dims"], o["perm"])
 
-    steps = max(1, min(args.steps, args.e2e_steps))
+    steps = args.steps if args.e2e_steps <= 0 else max(1, min(args.steps, args.e2e_steps))
     step()
     pipe.sync()
     torch.cuda.synchronize()
@@ -881,17 +917,14 @@ def _time_calls(torch, stream, call, steps, warmup, flush=None):
     return statistics.median(ts), min(ts)
 
 
-def run_configs(args):
-    """The single-op configs beside the bench step: the 1024^2 fp32 transpose
-    (warm and L2-flushed) and every interlace / de-interlace case of the
-    interlace config, each against a device copy of the same bytes timed the
-    same way.  GB/s counts bytes read + bytes written."""
-    import torch
-    from paper_1011_3583_gb300 import build as rbuild
-    rbuild.build()
-    import paper_1011_3583_gb300 as rr
-    dev = torch.device("cuda", 0)
-    stream = torch.cuda.Stream(dev)
+def measure_configs(torch, rr, dev, stream, steps, warmup):
+    """The single-op configs beside the bench step, each timed per call with
+    CUDA events against a device copy of the same bytes timed the same way
+    (L2 flushed before each call where the operands are comparable to the
+    L2): the 1024^2 fp32 transpose (warm and flushed), every interlace and
+    de-interlace case of the interlace config, and the 2-D stencil of Table 4
+    (4096^2 fp32 grid, finite-difference orders I-IV).  GB/s counts bytes
+    read + bytes written."""
     flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
     def flush():
@@ -902,11 +935,10 @@ def run_configs(args):
 
     def record(name, nbytes_moved, call, copy_bytes, flushed):
         fl = flush if flushed else None
-        med, best = _time_calls(torch, stream, call, args.steps, args.warmup, fl)
+        med, best = _time_calls(torch, stream, call, steps, warmup, fl)
         a = torch.empty(copy_bytes, dtype=torch.uint8, device=dev)
         b = torch.empty_like(a)
-        cmed, _ = _time_calls(torch, stream, lambda: rr.memcpy_d2d(b, a, copy_bytes, stream), args.steps,
-                              args.warmup, fl)
+        cmed, _ = _time_calls(torch, stream, lambda: rr.memcpy_d2d(b, a, copy_bytes, stream), steps, warmup, fl)
         del a, b
         out.append({"config": name, "l2": "flushed" if flushed else "warm", "bytes": nbytes_moved,
                     "median_us": round(med * 1e6, 2), "best_us": round(best * 1e6, 2),
@@ -934,6 +966,27 @@ def run_configs(args):
         record(name + " de-interlace", 2 * n * k * e, lambda: rr.deinterlace(planes, inter, n, e, stream),
                n * k * e, flushed)
         del planes, inter
+    # Table 4: the 2-D stencil on a 4096 x 4096 fp32 grid, orders I-IV
+    gen = torch.Generator(device=dev).manual_seed(5)
+    grid = torch.randn((4096, 4096), device=dev, generator=gen, dtype=torch.float32)
+    gout = torch.empty_like(grid)
+    for order in (1, 2, 3, 4):
+        taps = stencil_taps(f"fd{order}")
+        record(f"stencil 4096^2 fp32 FD order {order} (zero boundary)", 2 * grid.numel() * 4,
+               lambda: rr.stencil2d(gout, grid, 4096, 4096, taps, 0, stream), grid.numel() * 4, True)
+    del grid, gout, flush_buf
+    return out
+
+
+def run_configs(args):
+    """--configs: measure_configs alone, printed as one JSON line."""
+    import torch
+    from paper_1011_3583_gb300 import build as rbuild
+    rbuild.build()
+    import paper_1011_3583_gb300 as rr
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    out = measure_configs(torch, rr, dev, stream, args.steps, args.warmup)
     return {"configs": out, "steps": args.steps, "warmup": args.warmup, "timing": "CUDA events per call"}
 
 
@@ -970,10 +1023,11 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="librearr", choices=["librearr", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=0, help="e2e steps (0: the same as --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--case", default=None, help="time one op instead of the workload (see parse_case)")
     ap.add_argument("--configs", action="store_true", help="time the single-op configs (transpose, interlace)")
     args = ap.parse_args()

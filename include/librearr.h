@@ -340,7 +340,7 @@ void rearr_plan_destroy(rearr_plan *plan);
  *   stream : the work list is copied and the kernel launched on this stream.
  *
  * The work list goes to a fixed 512 KiB device buffer compiled into the
- * library (about 1400 ops; fewer when interlaces have more than 8 planes);
+ * library (about 1280 ops; fewer when interlaces have more than 8 planes);
  * every GPU that loads the library holds that buffer until the process exits.
  * A plan that does not fit returns REARR_EINVAL and launches nothing.  The
  * first call on a device looks up the buffer's address and the kernel's
@@ -390,6 +390,10 @@ typedef struct {
     int vec_in, vec_out;      /* global access widths in bytes (TILE)            */
     int tile_a, tile_b;       /* tile extents in cells (TILE, TILE_CELLS)        */
     int64_t n_tiles;          /* work units (tiles, runs or copy blocks)         */
+    int wide_a, wide_b;       /* TILE on a short plane: the output axis whose
+                                 planes the tile's A side (input rows) or B side
+                                 (output runs) also spans, -1: none; tile_a and
+                                 tile_b then count cells of the widened sides  */
 } rearr_permute_info;
 
 /* dst_addr / src_addr only steer the alignment decisions (0: 256-byte aligned);

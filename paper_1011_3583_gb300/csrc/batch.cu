@@ -72,7 +72,7 @@ __device__ __noinline__ void tile_range(const TileDesc &d, uint32_t u0, uint32_t
 template <int W>
 __device__ __noinline__ void cells_range(const TileDesc &d, uint32_t u0, uint32_t u1, unsigned char *smem)
 {
-    for (uint32_t u = u0; u < u1; ++u) tile_cells_body<W>(d, u, smem);
+    for (uint32_t u = u0; u < u1; ++u) tile_cells_any<W>(d, u, smem);
 }
 
 template <int W>
@@ -502,7 +502,7 @@ extern "C" rearr_status rearr_batch_noalloc(const rearr_plan *plan, rearr_stream
     if (need > kNoallocBytes) {
         return fail(REARR_EINVAL, "rearr_batch_noalloc: the plan's work list needs " + std::to_string(need) +
                                       " bytes, more than the fixed " + std::to_string(kNoallocBytes) +
-                                      "-byte buffer (about 1400 ops); use rearr_plan_finalize + rearr_batch");
+                                      "-byte buffer (about 1280 ops); use rearr_plan_finalize + rearr_batch");
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -620,6 +620,7 @@ void order_for_batch(std::vector<OpDesc> &all_ops, std::vector<std::vector<char 
 
 void batch_form(OpDesc &op)
 {
+    tile_to_single_width(op);
     if ((op.cls == OC_INTERLACE || op.cls == OC_DEINTERLACE) && op.inter.fast && op.inter.k > 4) {
         // The batched kernel instantiates the 16-byte group bodies for k <= 4
         // only: larger k runs the generic body (the fast path implies a

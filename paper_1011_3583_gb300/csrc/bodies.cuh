@@ -48,6 +48,22 @@ __device__ __forceinline__ void tile_origin(const TileDesc &d, uint32_t t, uint3
     }
 }
 
+// Input offset of row b of the (possibly widened) B axis, and output offset
+// of element a of the (possibly widened) A axis (TileDesc).
+__device__ __forceinline__ int64_t b_row_in(const TileDesc &d, uint32_t b)
+{
+    uint32_t hi, lo;
+    fdivmod(b, d.db_split, hi, lo);
+    return int64_t(lo) * d.sb_in + int64_t(hi) * d.sb1_in;
+}
+
+__device__ __forceinline__ int64_t a_col_out(const TileDesc &d, uint32_t a)
+{
+    uint32_t hi, lo;
+    fdivmod(a, d.da_split, hi, lo);
+    return int64_t(lo) * d.sa_out + int64_t(hi) * d.sa1_out;
+}
+
 // Output piece m of a register block: rows r[0..VB) of the staged tile, each
 // a 16-byte chunk of 16/E elements along A, give for element m of the chunk
 // the VB consecutive B-elements as one word of VB*E bytes.
@@ -115,8 +131,8 @@ __device__ __forceinline__ void tile_fast_body(const TileDesc &d, uint32_t t, un
     tile_origin(d, t, a0, b0, ioff, ooff);
     const uint32_t na = min(uint32_t(TA), d.DA - a0);
     const uint32_t nbv = min(uint32_t(TB), d.DB - b0);
-    const char *in = d.src + ioff + int64_t(a0) * E + int64_t(b0) * d.sb_in;
-    char *out = d.dst + ooff + int64_t(a0) * d.sa_out + int64_t(b0) * E;
+    const char *in = d.src + ioff + int64_t(a0) * E;
+    char *out = d.dst + ooff + int64_t(b0) * E;
     const int tid = tid_x();
     const uint32_t row_valid_bytes = na * E;
 
@@ -132,7 +148,7 @@ __device__ __forceinline__ void tile_fast_body(const TileDesc &d, uint32_t t, un
             const int f = (k0 + k) * kThreads + tid;
             const int row = f / PPR, x = (f % PPR) * VIN;
             if (uint32_t(row) < nbv && uint32_t(x) < row_valid_bytes)
-                buf[k] = ldg_stream<VIN>(in + int64_t(row) * d.sb_in + x);
+                buf[k] = ldg_stream<VIN>(in + b_row_in(d, b0 + uint32_t(row)) + x);
         }
 #pragma unroll
         for (int k = 0; k < PB; ++k) {
@@ -158,10 +174,13 @@ __device__ __forceinline__ void tile_fast_body(const TileDesc &d, uint32_t t, un
 #pragma unroll
             for (int i = 0; i < VB; ++i)
                 r[i] = lds<16>(smem + (b + i) * ROWB + ((q ^ (bq & 7)) << 4));
+            // the V elements of chunk q share their absorbed index (a widened
+            // A splits at a multiple of V)
+            char *col = out + a_col_out(d, a0 + uint32_t(q * V)) + int64_t(b) * E;
 #pragma unroll
             for (int m = 0; m < V; ++m) {
                 const uint32_t a = uint32_t(q * V + m);
-                if (a < na) stg<VOUT>(out + int64_t(a) * d.sa_out + int64_t(b) * E, piece<E, VB>(r, m));
+                if (a < na) stg<VOUT>(col + int64_t(m) * d.sa_out, piece<E, VB>(r, m));
             }
         }
     }
@@ -205,7 +224,7 @@ __device__ __forceinline__ void tile_fast_issue(const TileDesc &d, uint32_t t, u
     tile_origin(d, t, a0, b0, ioff, ooff);
     const uint32_t na = min(uint32_t(TA), d.DA - a0);
     const uint32_t nbv = min(uint32_t(TB), d.DB - b0);
-    const char *in = d.src + ioff + int64_t(a0) * E + int64_t(b0) * d.sb_in;
+    const char *in = d.src + ioff + int64_t(a0) * E;
     const uint32_t row_valid_bytes = na * E;
     const int tid = tid_x();
 #pragma unroll
@@ -214,7 +233,8 @@ __device__ __forceinline__ void tile_fast_issue(const TileDesc &d, uint32_t t, u
         const int row = f / PPR, x = (f % PPR) * VIN;
         if (uint32_t(row) < nbv && uint32_t(x) < row_valid_bytes) {
             const int sw = (row / VB) & 7;
-            cp_async<VIN>(smem + row * ROWB + (((x >> 4) ^ sw) << 4) + (x & 15), in + int64_t(row) * d.sb_in + x);
+            cp_async<VIN>(smem + row * ROWB + (((x >> 4) ^ sw) << 4) + (x & 15),
+                          in + b_row_in(d, b0 + uint32_t(row)) + x);
         }
     }
     cp_async_commit();
@@ -231,7 +251,7 @@ __device__ __forceinline__ void tile_fast_store(const TileDesc &d, uint32_t t, c
     tile_origin(d, t, a0, b0, ioff, ooff);
     const uint32_t na = min(uint32_t(TA), d.DA - a0);
     const uint32_t nbv = min(uint32_t(TB), d.DB - b0);
-    char *out = d.dst + ooff + int64_t(a0) * d.sa_out + int64_t(b0) * E;
+    char *out = d.dst + ooff + int64_t(b0) * E;
     const int tid = tid_x();
     constexpr int UB = TB / VB, UQ = TA / V, NU = UB * UQ;
     static_assert(NU % kThreads == 0, "store units must split evenly");
@@ -244,10 +264,11 @@ __device__ __forceinline__ void tile_fast_store(const TileDesc &d, uint32_t t, c
             uint4 r[VB];
 #pragma unroll
             for (int i = 0; i < VB; ++i) r[i] = lds<16>(smem + (b + i) * ROWB + ((q ^ (bq & 7)) << 4));
+            char *col = out + a_col_out(d, a0 + uint32_t(q * V)) + int64_t(b) * E;
 #pragma unroll
             for (int m = 0; m < V; ++m) {
                 const uint32_t a = uint32_t(q * V + m);
-                if (a < na) stg<VOUT>(out + int64_t(a) * d.sa_out + int64_t(b) * E, piece<E, VB>(r, m));
+                if (a < na) stg<VOUT>(col + int64_t(m) * d.sa_out, piece<E, VB>(r, m));
             }
         }
     }
@@ -311,6 +332,58 @@ __device__ __forceinline__ void tile_cells_body(const TileDesc &d, uint32_t t, u
         }
     }
     __syncthreads();
+}
+
+// Blocked runs (a cells tile with pitch 0): cells of 128 bytes or more -- an
+// unmoved inner run of the permute -- on the transpose plane, TA x TB cells
+// per tile, copied word for word without staging (a cell is at least one
+// whole 128-byte line, so each side is coalesced as it is).  Consecutive
+// words walk the tile's input rows, so a tile reads TB runs of TA * cell
+// contiguous bytes and writes TA runs of TB * cell contiguous bytes, where a
+// walk in output (or input) order reads (or writes) one cell per DRAM burst
+// run.  No shared memory is used.
+template <int W>
+__device__ __forceinline__ void tile_runs_body(const TileDesc &d, uint32_t t)
+{
+    uint32_t a0, b0;
+    int64_t ioff, ooff;
+    tile_origin(d, t, a0, b0, ioff, ooff);
+    const uint32_t c = d.c;
+    const uint32_t na = min(d.TA, d.DA - a0);
+    const uint32_t nbv = min(d.TB, d.DB - b0);
+    const char *in = d.src + ioff + int64_t(a0) * c * W + int64_t(b0) * d.sb_in;
+    char *out = d.dst + ooff + int64_t(a0) * d.sa_out + int64_t(b0) * c * W;
+    const uint32_t total = d.TB * d.rowwords_div.d;  // TB rows of TA * c words
+    const uint32_t rw_valid = na * c;
+    constexpr int U = W >= 16 ? 4 : 8;
+    for (uint32_t base = 0; base < total; base += kThreads * U) {
+        typename Word<W>::T v[U];
+        uint32_t row[U], w[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const uint32_t f = base + k * kThreads + tid_x();
+            fdivmod(f, d.rowwords_div, row[k], w[k]);
+            if (f < total && row[k] < nbv && w[k] < rw_valid)
+                v[k] = ldg_stream<W>(in + int64_t(row[k]) * d.sb_in + int64_t(w[k]) * W);
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const uint32_t f = base + k * kThreads + tid_x();
+            if (f < total && row[k] < nbv && w[k] < rw_valid) {
+                uint32_t a, ww;
+                fdivmod(w[k], d.c_div, a, ww);
+                stg<W>(out + int64_t(a) * d.sa_out + (int64_t(row[k]) * c + ww) * W, v[k]);
+            }
+        }
+    }
+}
+
+// A cells tile: staged in shared memory, or (pitch 0) blocked runs.
+template <int W>
+__device__ __forceinline__ void tile_cells_any(const TileDesc &d, uint32_t t, unsigned char *smem)
+{
+    if (d.pitch == 0) tile_runs_body<W>(d, t);
+    else tile_cells_body<W>(d, t, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -701,9 +774,36 @@ __device__ __forceinline__ void strided_body(const StridedDesc &d, uint64_t unit
                 T e[V];
             } v;
             v.u = make_uint4(0, 0, 0, 0);
+            // The thread's V consecutive cells: the first one's input offset
+            // from its multi-index (one division per axis), the next ones by
+            // stepping the multi-index like an odometer (an add per cell, a
+            // carry into the next axis when an extent is reached).
+            uint32_t digit[kMaxRank];
+            int64_t off = 0;
+            {
+                uint32_t q = uint32_t(base);
 #pragma unroll
-            for (int k = 0; k < V; ++k)
-                if (base + k < c1) v.e[k] = ldg_any<W>(d.src + strided_offset(d, uint32_t(base + k)));
+                for (int i = kMaxRank - 1; i >= 0; --i) {
+                    digit[i] = 0;
+                    if (i < d.nd) {
+                        fdivmod(q, d.div[i], q, digit[i]);
+                        off += int64_t(digit[i]) * d.in_stride[i];
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                if (base + k < c1) v.e[k] = ldg_any<W>(d.src + off);
+#pragma unroll
+                for (int i = kMaxRank - 1; i >= 0; --i) {
+                    if (i < d.nd) {
+                        off += d.in_stride[i];
+                        if (++digit[i] < d.div[i].d) break;
+                        off -= int64_t(d.div[i].d) * d.in_stride[i];
+                        digit[i] = 0;
+                    }
+                }
+            }
             if (base + V <= c1) {
                 stg<16>(d.dst + base * W, v.u);
             } else {

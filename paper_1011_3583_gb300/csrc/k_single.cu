@@ -26,6 +26,15 @@ __global__ void __launch_bounds__(kThreads) k_tile_cells(const __grid_constant__
     for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) tile_cells_body<W>(d, t, smem);
 }
 
+// Blocked runs (a cells tile with pitch 0) in a kernel of their own: no shared
+// memory and their own register allocation (the staged cells body needs
+// about twice the registers, which would halve the CTAs per SM).
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_tile_runs(const __grid_constant__ TileDesc d, uint32_t n)
+{
+    for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) tile_runs_body<W>(d, t);
+}
+
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_runs(const __grid_constant__ RunsDesc d, uint64_t n)
 {
@@ -96,16 +105,22 @@ cudaError_t go(K kernel, uint64_t units, const P &param, N n, cudaStream_t s)
     case tile_variant(E, VI, VO, RB, 8192):                                                       \
         return go(k_tile_fast<E, VI, VO, RB, 8192>, op.units, op.tile, uint32_t(op.units), s);
 
+#define RT_DOUBLE(E, VI, VO, RB)                                                              \
+    case tile_variant(E, VI, VO, RB, 32768):                                                      \
+        return go(k_tile_fast<E, VI, VO, RB, 32768>, op.units, op.tile, uint32_t(op.units), s);
+
 cudaError_t launch_tile_fast(const OpDesc &op, cudaStream_t s)
 {
     switch (op.tile.variant) {
         REARR_TILE_VARIANTS(RT_CASE)
         REARR_TILE_HALF_VARIANTS(RT_HALF)
+        REARR_TILE_DOUBLE_VARIANTS(RT_DOUBLE)
         default: return cudaErrorInvalidValue;
     }
 }
 #undef RT_CASE
 #undef RT_HALF
+#undef RT_DOUBLE
 
 template <template <int> class Fn, typename... A>
 cudaError_t by_word(int W, A &&...a)
@@ -123,6 +138,7 @@ cudaError_t by_word(int W, A &&...a)
 template <int W> struct RunCells {
     static cudaError_t run(const OpDesc &op, cudaStream_t s)
     {
+        if (op.tile.pitch == 0) return go(k_tile_runs<W>, op.units, op.tile, uint32_t(op.units), s);
         return go(k_tile_cells<W>, op.units, op.tile, uint32_t(op.units), s);
     }
 };

@@ -86,27 +86,94 @@ static TileShape choose_shape(int E, int64_t DA, int64_t DB)
         }
     }
     TileShape tuned;
-    if (tuned_shape(E, DA, DB, tuned) && (tuned.tbytes == kTileBytes || half_tile_vout(E))) return tuned;
+    if (tuned_shape(E, DA, DB, false, tuned) && (tuned.tbytes != kTileBytes / 2 || half_tile_vout(E))) return tuned;
     return best;
 }
 
-static void fill_tile_common(TileDesc &t, const std::vector<Axis> &ax, int p, int64_t cell, int64_t DA,
-                             int64_t DB, char *dst, const char *src)
+// The tile descriptor of plane (A = axis p, B = axis R-1) with the other
+// axes as batch.  qa / qb (-1: none) are the batch axes that A / B absorb
+// (a widened plane): A then spans DA * extent(qa) cells, B DB * extent(qb).
+// Tile shape of a widened plane (see choose_widening): the candidate that
+// fills the DA x DB plane (extents after widening) best, then the one whose
+// shorter side -- input rows of ROWB bytes or output runs of TB * E bytes,
+// each at most what the plane offers -- is longest (up to 512 bytes), then
+// the smaller tile.  32 KB tiles exist for the shapes of double_tile_ok().
+static TileShape choose_wide_shape(int E, int64_t DA0, int64_t DB0, int64_t DA, int64_t DB)
+{
+    TileShape tuned;
+    if (tuned_shape(E, DA0, DB0, true, tuned)) return tuned;
+    TileShape best{default_rowb(E), kTileBytes};
+    double best_util = -1.0;
+    int64_t best_run = -1;
+    for (int rowb : {128, 256, 512}) {
+        if (E == 1 && rowb == 512) continue;
+        for (int tbytes : {kTileBytes, 2 * kTileBytes}) {
+            if (tbytes > kTileBytes && !double_tile_ok(E, rowb)) continue;
+            const int64_t TA = rowb / E, TB = tbytes / rowb;
+            const double ua = double(DA) / double(((DA + TA - 1) / TA) * TA);
+            const double ub = double(DB) / double(((DB + TB - 1) / TB) * TB);
+            const double util = ua * ub;
+            const int64_t run = std::min<int64_t>({int64_t(rowb), DA * E, TB * E, DB * E, 512});
+            if (util > best_util + 0.01 || (util > best_util - 0.01 && run > best_run)) {
+                best = {rowb, tbytes};
+                best_util = std::max(best_util, util);
+                best_run = run;
+            }
+        }
+    }
+    return best;
+}
+
+// A transpose plane whose input rows (DA cells of A) or output runs (DB cells
+// of B) are short leaves DRAM with short bursts scattered far apart: every
+// tile reads DB rows of DA*E bytes at the stride of B and writes DA runs of
+// DB*E bytes at the stride of A.  Such a side is widened over the axis that
+// continues it -- A over the batch axis of input stride DA cells (the input
+// stays contiguous across the planes), B over the output axis just before it
+// (the output stays contiguous) -- so one tile spans several planes and both
+// its reads and its writes come in runs of up to 512 bytes.  Sides of at
+// least wide_min_bytes() are left alone; an axis that continues both sides
+// widens the shorter one.  Fast tiles only (one element per cell, 16-byte
+// loads, and A split at multiples of the 16-byte chunk).
+static void choose_widening(const std::vector<Axis> &ax, int p, int64_t cell, int &qa, int &qb)
+{
+    const int R = int(ax.size());
+    const uint64_t lim = wide_min_bytes();
+    qa = qb = -1;
+    if (R < 3) return;
+    const int64_t DA = ax[p].extent, DB = ax[R - 1].extent;
+    if (uint64_t(DA * cell) < lim && DA % (16 / cell) == 0)
+        for (int i = 0; i < R - 1; ++i)
+            if (i != p && ax[i].stride == DA * cell && DA * ax[i].extent <= kMaxExtent) qa = i;
+    if (uint64_t(DB * cell) < lim && R - 2 != p && DB * ax[R - 2].extent <= kMaxExtent) qb = R - 2;
+    if (qa >= 0 && qa == qb) {
+        if (DA <= DB) qb = -1;
+        else qa = -1;
+    }
+}
+
+static void fill_tile_common(TileDesc &t, const std::vector<Axis> &ax, int p, int64_t cell, int qa, int qb,
+                             char *dst, const char *src)
 {
     const int R = int(ax.size());
     // Output strides (cells) of the canonical output axes, row-major.
     std::vector<int64_t> os(R);
     os[R - 1] = 1;
     for (int i = R - 2; i >= 0; --i) os[i] = os[i + 1] * ax[i + 1].extent;
+    const int64_t DA = ax[p].extent, DB = ax[R - 1].extent;
     t.dst = dst;
     t.src = src;
     t.sb_in = ax[R - 1].stride;
     t.sa_out = os[p] * cell;
-    t.DA = uint32_t(DA);
-    t.DB = uint32_t(DB);
+    t.DA = uint32_t(qa >= 0 ? DA * ax[qa].extent : DA);
+    t.DB = uint32_t(qb >= 0 ? DB * ax[qb].extent : DB);
+    t.da_split = make_fastdiv(uint32_t(DA));
+    t.db_split = make_fastdiv(uint32_t(DB));
+    t.sa1_out = qa >= 0 ? os[qa] * cell : 0;
+    t.sb1_in = qb >= 0 ? ax[qb].stride : 0;
     int nb = 0;
     for (int i = 0; i < R; ++i) {
-        if (i == p || i == R - 1) continue;
+        if (i == p || i == R - 1 || i == qa || i == qb) continue;
         t.bin[nb] = ax[i].stride;
         t.bout[nb] = os[i] * cell;
         t.bdiv[nb] = make_fastdiv(uint32_t(ax[i].extent));
@@ -209,6 +276,7 @@ static rearr_status plan_axes(void *dst, const char *src, size_t elem_bytes, con
         op.units = (n_cells + per_unit - 1) / per_unit;
         info.kind = REARR_KIND_STRIDED;
         info.tile_a = info.tile_b = 0;
+        info.wide_a = info.wide_b = -1;
         info.word_bytes = W;
         info.vec_in = W;
         info.vec_out = sd.vec ? 16 : W;
@@ -230,8 +298,11 @@ static rearr_status plan_axes(void *dst, const char *src, size_t elem_bytes, con
     }
 
     // Cells of 128 bytes or more are copied as runs, and so are boxes with no
-    // input-contiguous axis (there both sides cannot be coalesced).
-    if (cell >= kRunMinBytes || p < 0) {
+    // input-contiguous axis (there both sides cannot be coalesced).  Runs
+    // shorter than runs_tile_max_bytes() on a transpose plane are copied in
+    // blocks of cells instead (tile_runs_body), for long runs on both sides.
+    const bool blocked_runs = p >= 0 && cell >= kRunMinBytes && uint64_t(cell) < runs_tile_max_bytes();
+    if ((cell >= kRunMinBytes && !blocked_runs) || p < 0) {
         const int W = pow2_align(da, sa, uint64_t(cell), strides_or);
         uint64_t n_runs = 1;
         for (int i = 0; i < R; ++i) n_runs *= uint64_t(ax[i].extent);
@@ -308,34 +379,44 @@ static rearr_status plan_axes(void *dst, const char *src, size_t elem_bytes, con
 
     OpDesc &op = pl.op;
     TileDesc &t = op.tile;
-    fill_tile_common(t, ax, p, cell, DA, DB, static_cast<char *>(dst), src);
     const int W = pow2_align(da, sa, uint64_t(cell), strides_or);
     info.word_bytes = W;
+    int vin = 0, vout = 0, qa = -1, qb = -1;
+    if (W == cell) {
+        const int E = int(cell);
+        // Widest legal global access on each side.  Input rows start at src
+        // plus sums of the (non-A) input strides; output rows start at
+        // multiples of DB*E bytes from dst.
+        uint64_t in_or = 0;
+        for (int i = 0; i < R; ++i)
+            if (i != p) in_or |= uint64_t(ax[i].stride);
+        const int vcap = tile_vector_bytes();
+        vin = E;
+        for (int v : {16, 4}) {
+            if (v > E && v <= vcap && (uint64_t(DA) * E) % v == 0 && sa % v == 0 && in_or % v == 0) { vin = v; break; }
+        }
+        vout = E;
+        const int vmax = std::min(std::min(16, 4 * E), vcap);
+        for (int v : {vmax, 4}) {
+            if (v > E && (uint64_t(DB) * E) % v == 0 && da % v == 0) { vout = v; break; }
+        }
+        if (vin == 16 && vout == std::min(16, 4 * E)) choose_widening(ax, p, cell, qa, qb);
+    }
+    fill_tile_common(t, ax, p, cell, qa, qb, static_cast<char *>(dst), src);
+    info.wide_a = qa;
+    info.wide_b = qb;
     uint64_t batch = 1;
     for (int i = 0; i < t.nb; ++i) batch *= t.bdiv[i].d;
 
     if (W == cell) {
         // Fast tile: one power-of-two element per cell.
         const int E = int(cell);
-        // Widest legal global access on each side.  Input rows start at src
-        // plus sums of the (non-A) input strides; output rows start at
-        // multiples of DB*E bytes from dst.
-        uint64_t in_or = uint64_t(t.sb_in);
-        for (int i = 0; i < t.nb; ++i) in_or |= uint64_t(t.bin[i]);
-        int vin = E;
-        for (int v : {16, 4}) {
-            if (v > E && (uint64_t(DA) * E) % v == 0 && sa % v == 0 && in_or % v == 0) { vin = v; break; }
-        }
-        int vout = E;
-        const int vmax = std::min(16, 4 * E);
-        for (int v : {vmax, 4}) {
-            if (v > E && (uint64_t(DB) * E) % v == 0 && da % v == 0) { vout = v; break; }
-        }
         // Tile shape: the default for the element size, or for the fully
-        // vectorised widths the shape that fills the plane best.
+        // vectorised widths the shape that fills the plane best (a widened
+        // plane: the shape with the longest runs on both sides).
         TileShape shape{default_rowb(E), kTileBytes};
         if (vin == 16 && vout == std::min(16, 4 * E)) {
-            shape = choose_shape(E, DA, DB);
+            shape = (qa >= 0 || qb >= 0) ? choose_wide_shape(E, DA, DB, t.DA, t.DB) : choose_shape(E, DA, DB);
             if (shape.tbytes < kTileBytes) vout = half_tile_vout(E);
         }
         t.TA = uint32_t(shape.rowb / E);
@@ -347,6 +428,22 @@ static rearr_status plan_axes(void *dst, const char *src, size_t elem_bytes, con
         t.c = 1;
         t.pitch = 0;
         op.cls = OC_TILE;
+    } else if (blocked_runs) {
+        const int64_t c = cell / W;
+        const int64_t side = std::max<int64_t>(int64_t(runs_tile_cells()), int64_t(runs_tile_side_bytes()) / cell);
+        const int64_t nbk = std::max<int64_t>(1, std::min<int64_t>(side, 64));
+        const int64_t TA = std::min<int64_t>(DA, nbk), TB = std::min<int64_t>(DB, nbk);
+        if (TB * TA * c > int64_t(kMaxUnits)) { err = "a runs block has 2^32 or more words"; return REARR_EINVAL; }
+        info.kind = REARR_KIND_TILE_CELLS;
+        t.TA = uint32_t(TA);
+        t.TB = uint32_t(TB);
+        t.c = uint32_t(c);
+        t.pitch = 0;  // no staging: blocked runs
+        t.rowwords_div = make_fastdiv(uint32_t(TA * c));
+        t.outwords_div = make_fastdiv(uint32_t(TB * c));
+        t.c_div = make_fastdiv(uint32_t(c));
+        t.variant = uint32_t(W);
+        op.cls = OC_TILE_CELLS;
     } else {
         const int64_t c = cell / W;
         int64_t TA = std::max<int64_t>(1, std::min<int64_t>(DA, 256 / cell));
@@ -372,8 +469,8 @@ static rearr_status plan_axes(void *dst, const char *src, size_t elem_bytes, con
     }
     info.tile_a = int(t.TA);
     info.tile_b = int(t.TB);
-    const uint64_t ta_tiles = (uint64_t(DA) + t.TA - 1) / t.TA;
-    const uint64_t tb_tiles = (uint64_t(DB) + t.TB - 1) / t.TB;
+    const uint64_t ta_tiles = (uint64_t(t.DA) + t.TA - 1) / t.TA;
+    const uint64_t tb_tiles = (uint64_t(t.DB) + t.TB - 1) / t.TB;
     const uint64_t units = ta_tiles * tb_tiles * batch;
     if (units > kMaxUnits || ta_tiles > kMaxUnits || tb_tiles > kMaxUnits) {
         err = "too many tiles";
@@ -390,10 +487,17 @@ static rearr_status plan_axes(void *dst, const char *src, size_t elem_bytes, con
     // payload on average -- a tile costs a whole load / store round trip
     // whatever its fill.  Decided after the tile plan so that the tile count
     // is the one the tile kernel would run; the thresholds are tuning knobs.
+    // A 32 KB tile halves the CTA count: small ops keep the 16 KB tile of the
+    // same row length so that they still fill the GPU.
+    if (op.cls == OC_TILE && bytes < double_tile_min_bytes()) {
+        tile_to_single_width(op);
+        info.tile_b = int(t.TB);
+        info.n_tiles = int64_t(op.units);
+    }
     const uint64_t n_cells = bytes / uint64_t(cell);
     const ThinTuning thin = thin_tuning();
-    const bool thin_plane =
-        bytes < units * thin.tile_bytes || (bytes <= thin.l2_bytes && n_cells < units * thin.tile_cells);
+    const bool thin_plane = bytes < op.units * thin.tile_bytes ||
+                            (bytes <= thin.l2_bytes && n_cells < op.units * thin.tile_cells);
     if (W == cell && thin_plane && n_cells < kMaxUnits) set_strided(W, n_cells);
     return REARR_OK;
 }
@@ -404,6 +508,7 @@ rearr_status plan_permute(void *dst, const void *src, size_t elem_bytes, int ran
     std::memset(&pl, 0, sizeof(pl));
     rearr_permute_info &info = pl.info;
     info.plane_a = -1;
+    info.wide_a = info.wide_b = -1;
     if (elem_bytes == 0) { err = "elem_bytes must be >= 1"; return REARR_EINVAL; }
     if (rank < 1 || rank > kMaxRank) { err = "rank must be in [1, 8]"; return REARR_EINVAL; }
     if (!dims || !perm) { err = "dims and perm must not be NULL"; return REARR_EINVAL; }
@@ -449,6 +554,7 @@ rearr_status plan_reorder_nm(void *dst, const void *src, size_t elem_bytes, int 
 {
     std::memset(&pl, 0, sizeof(pl));
     pl.info.plane_a = -1;
+    pl.info.wide_a = pl.info.wide_b = -1;
     if (elem_bytes == 0) { err = "elem_bytes must be >= 1"; return REARR_EINVAL; }
     if (rank_in < 1 || rank_in > kMaxRank) { err = "rank_in must be in [1, 8]"; return REARR_EINVAL; }
     if (rank_out < 1 || rank_out > rank_in) { err = "rank_out must be in [1, rank_in]"; return REARR_EINVAL; }
@@ -607,6 +713,25 @@ rearr_status plan_interlace(bool inter, char *interlaced, char *const *planes, i
         op.units = (uint64_t(n) + d.unit_groups - 1) / d.unit_groups;
     }
     return REARR_OK;
+}
+
+void tile_to_single_width(OpDesc &op)
+{
+    if (op.cls != OC_TILE) return;
+    TileDesc &t = op.tile;
+    const uint32_t v = t.variant;
+    const int tbytes = int((v >> 22) & 0xFu) * 8192;
+    if (tbytes <= kTileBytes) return;
+    const int E = int(v & 0x3Fu), vin = int((v >> 6) & 0x3Fu), vout = int((v >> 12) & 0x3Fu);
+    const int rowb = int((v >> 18) & 0xFu) * 128;
+    t.TB = uint32_t(kTileBytes / rowb);
+    t.variant = tile_variant(E, vin, vout, rowb, kTileBytes);
+    uint64_t batch = 1;
+    for (int i = 0; i < t.nb; ++i) batch *= t.bdiv[i].d;
+    const uint64_t ta_tiles = t.ta_div.d;
+    const uint64_t tb_tiles = (uint64_t(t.DB) + t.TB - 1) / t.TB;
+    t.tb_div = make_fastdiv(uint32_t(tb_tiles));
+    op.units = ta_tiles * tb_tiles * batch;
 }
 
 bool selftest_host(std::string &err)

@@ -37,6 +37,10 @@ rearr_status plan_reorder(void *dst, const void *src, const uint32_t *idx, size_
 rearr_status plan_interlace(bool inter, char *interlaced, char *const *planes, int k, size_t n,
                             size_t elem_bytes, InterlacePlan &pl, std::string &err);
 
+// A fast tile planned with the 32 KB payload re-planned with the 16 KB tile of
+// the same row length (the batched kernel holds two 16 KB tiles per CTA).
+void tile_to_single_width(OpDesc &op);
+
 // Largest power of two <= 16 dividing every argument.
 int pow2_align(uint64_t a, uint64_t b = 0, uint64_t c = 0, uint64_t d = 0);
 

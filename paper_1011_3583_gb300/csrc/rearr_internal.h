@@ -93,11 +93,24 @@ enum OpClass : uint32_t {
 // Plane of a tiled transpose: A = input-innermost axis (input stride one
 // cell), B = output-innermost axis (output stride one cell).  The remaining
 // collapsed axes are batch axes.  Strides are in bytes.
+//
+// A short plane may be widened (fast tiles only): A absorbs the batch axis
+// that continues it in the input (input stride DA cells), so input rows stay
+// contiguous over several planes, and B absorbs the batch axis that continues
+// it in the output (output stride DB cells).  Coordinate a of the widened A
+// is (a / da_split, a % da_split): output offset (a % da_split) * sa_out +
+// (a / da_split) * sa1_out; likewise row b of the widened B starts at input
+// offset (b % db_split) * sb_in + (b / db_split) * sb1_in.  An axis that is
+// not widened has a split larger than its extent and a zero second stride.
 struct TileDesc {
     char *dst;
     const char *src;
     int64_t sb_in;        // input stride of B
     int64_t sa_out;       // output stride of A
+    int64_t sa1_out;      // output stride of the axis A absorbed (0: none)
+    int64_t sb1_in;       // input stride of the axis B absorbed (0: none)
+    FastDiv da_split;     // extent of A before widening
+    FastDiv db_split;     // extent of B before widening
     int64_t bin[kMaxBatch], bout[kMaxBatch];
     FastDiv bdiv[kMaxBatch];   // batch extents, innermost batch axis last
     FastDiv ta_div, tb_div;    // tile counts along A and B

@@ -7,7 +7,9 @@
 //     requests, uploads their descriptors into the slot's own work-list
 //     buffer and launches the persistent batched kernel (continuous batching:
 //     requests that arrive while other batches run go out as soon as a slot
-//     frees up, so their work overlaps on the device);
+//     frees up, so their work overlaps on the device); a large request, or a
+//     request that is alone in the ready queue, runs as its single-op kernel
+//     in a slot of its own;
 //   plain mode: every ready request is launched at once as its own single-op
 //     kernel on one stream, in arrival order (the one-launch-per-call path).
 // Completion is found by polling CUDA events; the server never waits on the
@@ -263,8 +265,12 @@ void Server::launch_batches(std::unique_lock<std::mutex> &)
         std::vector<std::vector<char *>> planes;
         std::vector<Req *> taken;
         size_t n_ptrs = 0;
-        // A large request runs alone as its single-op kernel.
-        if (ready.front()->bytes >= cfg.large_bytes) {
+        // A large request runs alone as its single-op kernel, and so does a
+        // lone ready request: one op gains nothing from a work list, and its
+        // single-op kernel skips the work-list upload and the persistent
+        // kernel's set-up (light load keeps the plain path's latency; the
+        // batches take over as soon as requests queue up).
+        if (ready.front()->bytes >= cfg.large_bytes || ready.size() == 1) {
             Req *r = ready.front();
             ready.pop_front();
             OpDesc op;

@@ -40,7 +40,28 @@ struct ThinTuning {
 // 0 keeps output order for every run length.
 uint64_t runs_mirror_max_bytes();
 
+// Runs (cells of 128 bytes or more) shorter than runs_tile_max_bytes() on a
+// transpose plane are copied in square blocks of cells (tile_runs_body); 1
+// never.  A block side holds runs_tile_side_bytes() / cell cells, at least
+// runs_tile_cells().
+uint64_t runs_tile_max_bytes();
+uint64_t runs_tile_cells();
+uint64_t runs_tile_side_bytes();
+
+// Widest global access of a fast tile: 16 (the widest the alignment allows)
+// or 4 (loads and stores of at most 4 bytes; for measuring the choice).
+int tile_vector_bytes();
+
 ThinTuning thin_tuning();
+
+// A fast tile's plane side (input rows of DA * E bytes, output runs of
+// DB * E bytes) shorter than this is widened over the axis that continues it
+// (plan.cpp, choose_widening); 1 never widens.
+uint64_t wide_min_bytes();
+
+// Ops smaller than this run 32 KB fast tiles as 16 KB tiles of the same row
+// length (enough CTAs to fill the GPU).
+uint64_t double_tile_min_bytes();
 
 // A large random reorder scatters through CTA-sized destination chunks in
 // shared memory when its (source chunk, destination chunk) bucket count is at
@@ -48,14 +69,22 @@ ThinTuning thin_tuning();
 uint64_t reorder_smem_max_buckets();
 
 // Shape of a fast tile: staged row bytes (128, 256 or 512) and payload bytes
-// (16384, or 8192 for the half tile).
+// (16384; 8192 for the half tile; 32768 for the double tile of a widened
+// plane, where double_tile_ok).
 struct TileShape {
     int rowb;
     int tbytes;
 };
 
+// The 32 KB tile shapes that exist (variants.h).
+constexpr bool double_tile_ok(int E, int rowb)
+{
+    return E <= 2 ? (rowb == 128 || rowb == 256) : (E <= 16 && (rowb == 256 || rowb == 512));
+}
+
 // The shape the tuning table assigns to a fully vectorised fast tile of
-// element size E on a DA x DB plane; false if the table has no entry.
-bool tuned_shape(int E, int64_t DA, int64_t DB, TileShape &shape);
+// element size E on a DA x DB plane (extents before widening; `wide`: the
+// plane is widened); false if the table has no entry.
+bool tuned_shape(int E, int64_t DA, int64_t DB, bool wide, TileShape &shape);
 
 }  // namespace rearr

@@ -22,6 +22,14 @@
 // XH(E, VIN, VOUT, ROWB)
 #define REARR_TILE_HALF_VARIANTS(XH) XH(2, 16, 4, 128) XH(4, 16, 8, 128)
 
+// Double tiles (32 KB payload) for widened planes: long runs on both sides
+// (e.g. 256-byte input rows and 256-byte output runs of 2-byte elements).
+// Single calls only; the batched kernel runs the 16 KB shape instead.
+// XD(E, VIN, VOUT, ROWB)
+#define REARR_TILE_DOUBLE_VARIANTS(XD)                                                            \
+    XD(1, 16, 4, 128) XD(1, 16, 4, 256) XD(2, 16, 8, 128) XD(2, 16, 8, 256) XD(4, 16, 16, 256)    \
+    XD(4, 16, 16, 512) XD(8, 16, 16, 256) XD(8, 16, 16, 512) XD(16, 16, 16, 256) XD(16, 16, 16, 512)
+
 namespace rearr {
 
 // Default staged row length of an element size (used by the fallback widths).

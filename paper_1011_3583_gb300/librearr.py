@@ -39,14 +39,15 @@ class PermuteInfo(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("rank", ctypes.c_int), ("dims", ctypes.c_int64 * 8),
                 ("in_strides", ctypes.c_int64 * 8), ("cell_bytes", ctypes.c_int64), ("word_bytes", ctypes.c_int),
                 ("plane_a", ctypes.c_int), ("vec_in", ctypes.c_int), ("vec_out", ctypes.c_int),
-                ("tile_a", ctypes.c_int), ("tile_b", ctypes.c_int), ("n_tiles", ctypes.c_int64)]
+                ("tile_a", ctypes.c_int), ("tile_b", ctypes.c_int), ("n_tiles", ctypes.c_int64),
+                ("wide_a", ctypes.c_int), ("wide_b", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         r = self.rank
         return dict(kind=KIND_NAMES.get(self.kind, self.kind), rank=r, dims=list(self.dims[:r]),
                     in_strides=list(self.in_strides[:r]), cell_bytes=self.cell_bytes, word_bytes=self.word_bytes,
                     plane_a=self.plane_a, vec_in=self.vec_in, vec_out=self.vec_out, tile_a=self.tile_a,
-                    tile_b=self.tile_b, n_tiles=self.n_tiles)
+                    tile_b=self.tile_b, n_tiles=self.n_tiles, wide_a=self.wide_a, wide_b=self.wide_b)
 
 
 REORDER_FORMS = {0: "direct", 1: "smem_scatter", 2: "l2_scatter", 3: "linear_scatter"}

@@ -60,3 +60,23 @@ def test_stencil_and_selftest(client):
 def test_describe_reorder_and_box(client):
     assert client["reorder"] == ["REARR_OK", "form", "1", "chunks", "64", "16384"]  # REARR_REORDER_SMEM_SCATTER
     assert client["nm"] == ["REARR_OK", "kind", "5"]                                 # REARR_KIND_STRIDED
+
+
+@pytest.mark.gpu
+def test_device_permute_from_c(tmp_path):
+    """tests/c_abi/device_client.c: cudaMalloc'd buffers, one rearr_permute of
+    a 2 x 3 fp32 matrix, checked in C against the hand-written transpose."""
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not found")
+    rbuild.build()
+    from paper_1011_3583_gb300 import librearr
+    libdir = os.path.dirname(librearr.lib_path())
+    cuda = os.path.dirname(os.path.dirname(os.path.realpath(rbuild.nvcc())))
+    exe = str(tmp_path / "device_client")
+    cmd = ["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+           "-I", os.path.join(cuda, "include"), os.path.join(ROOT, "tests", "c_abi", "device_client.c"), "-o", exe,
+           "-L", libdir, "-lrearr", "-L", os.path.join(cuda, "lib64"), "-lcudart",
+           "-Wl,-rpath," + libdir, "-Wl,-rpath," + os.path.join(cuda, "lib64")]
+    subprocess.run(cmd, check=True, capture_output=True, text=True)
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0 and out.stdout.strip() == "device_permute OK", out.stdout + out.stderr

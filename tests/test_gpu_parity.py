@@ -471,7 +471,10 @@ THIN = [  # (dims, perm): transpose planes far smaller than a tile
 def test_thin_planes_run_strided(lr, orc, e):
     for t, (dims, perm) in enumerate(THIN):
         d = lr.describe_permute(e, dims, perm)
-        assert d["kind"] == "strided", (dims, perm, d)
+        # a thin plane runs strided, unless widening over its continuation
+        # axes turns it into a plane that fills tiles
+        widened = d["kind"] == "tile" and (d["wide_a"] >= 0 or d["wide_b"] >= 0)
+        assert d["kind"] == "strided" or widened, (dims, perm, d)
         for off in (0, e if e < 16 else 0):  # aligned (16-byte stores) and unaligned destination
             check_permute(lr, orc, 300 + t, e, dims, perm, src_off=off, dst_off=off)
 
@@ -508,7 +511,7 @@ def test_runs_in_input_order(lr, orc, tmp_path):
     the oracle's bytes: dense permutes whose innermost axis is unmoved, any
     element size, aligned and unaligned."""
     t = tmp_path / "mirror.txt"
-    t.write_text(open(lr.DEFAULT_TUNE_TABLE).read() + "\nruns_mirror_bytes 4096\n")
+    t.write_text(open(lr.DEFAULT_TUNE_TABLE).read() + "\nruns_mirror_bytes 4096\nruns_tile_max_bytes 1\n")
     cases = [([64, 128, 40, 64], [0, 2, 1, 3], 2), ([33, 17, 5, 64], [2, 1, 0, 3], 2), ([7, 9, 11, 32], [1, 2, 0, 3], 4),
              ([5, 300, 16], [1, 0, 2], 8), ([3, 4, 5, 6, 16], [4, 3, 1, 0, 2], 12), ([100, 3, 128], [1, 0, 2], 1)]
     try:
@@ -523,3 +526,136 @@ def test_runs_in_input_order(lr, orc, tmp_path):
                 check_permute(lr, orc, 700 + i, e, dims, perm, src_off=off, dst_off=off)
     finally:
         lr.tuning_load(lr.DEFAULT_TUNE_TABLE)
+
+
+# ---------------------------------------------------------------------------
+# widened planes: a short transpose plane spans several planes along the axis
+# that continues its input rows (A) and/or its output runs (B)
+
+WIDE = [  # (dims, perm, E, widened sides)
+    ([16, 24, 40, 16], [3, 2, 1, 0], 4, "ab"),
+    ([8, 5, 37, 32], [3, 2, 1, 0], 2, "ab"),      # ragged continuation extents
+    ([32, 12, 10, 16], [2, 1, 3, 0], 4, "a"),
+    ([16, 6, 10, 16], [2, 3, 1, 0], 4, "b"),
+    ([64, 32, 48, 32], [3, 2, 1, 0], 1, "ab"),
+    ([32, 9, 11, 32], [3, 2, 1, 0], 8, "ab"),
+    ([16, 7, 13, 16], [3, 2, 1, 0], 16, "ab"),
+    ([64, 33, 17, 64], [3, 2, 0, 1], 2, "a"),
+    ([3, 64, 20, 64], [0, 3, 2, 1], 2, "a"),
+    ([64, 6, 10, 64], [2, 3, 1, 0], 2, "b"),
+]
+
+
+def wide_sides(d):
+    return ("a" if d["wide_a"] >= 0 else "") + ("b" if d["wide_b"] >= 0 else "")
+
+
+@pytest.fixture
+def no_thin_rule(lr, tmp_path):
+    """The committed table with the thin-plane rule switched off, so that the
+    small test planes run as (widened) tiles whatever its thresholds."""
+    t = tmp_path / "no_thin.txt"
+    t.write_text(open(lr.DEFAULT_TUNE_TABLE).read() + "\nthin_tile_bytes 1\nthin_tile_cells 1\n")
+    lr.tuning_load(str(t))
+    yield
+    lr.tuning_load(None)
+    lr.tuning_load(lr.DEFAULT_TUNE_TABLE)
+
+
+@pytest.mark.parametrize("case", range(len(WIDE)))
+def test_widened_planes(lr, orc, case, no_thin_rule):
+    dims, perm, e, sides = WIDE[case]
+    d = lr.describe_permute(e, dims, perm)
+    assert d["kind"] == "tile" and wide_sides(d) == sides, d
+    check_permute(lr, orc, 800 + case, e, dims, perm)
+    # an unaligned destination keeps the plane as it is (no widening)
+    off = e if e < 16 else 4
+    check_permute(lr, orc, 850 + case, e, dims, perm, dst_off=off)
+
+
+def test_every_widened_tile_shape(lr, orc, tmp_path):
+    """Each 16 KB and 32 KB shape forced on widened planes through the tuning
+    table (rules for widened planes) gives the oracle's bytes."""
+    cases = {1: ([48, 7, 9, 64], [3, 2, 1, 0]), 2: ([32, 7, 9, 64], [3, 2, 1, 0]), 4: ([16, 7, 9, 32], [3, 2, 1, 0]),
+             8: ([16, 7, 9, 16], [3, 2, 1, 0]), 16: ([8, 7, 9, 8], [3, 2, 1, 0])}
+    try:
+        for e, (dims, perm) in cases.items():
+            for rowb in (128, 256, 512):
+                for tb in (16384, 32768):
+                    if (e == 1 and rowb == 512) or (tb == 32768 and not (rowb in (128, 256) if e <= 2 else rowb in (256, 512))):
+                        continue
+                    t = tmp_path / f"w{e}_{rowb}_{tb}.txt"
+                    t.write_text(f"rowb {e} 1 2147483647 1 2147483647 {rowb} {tb} 1\nthin_tile_bytes 1\nthin_tile_cells 1\n"
+                                 "double_tile_min_bytes 1\n")
+                    lr.tuning_load(str(t))
+                    d = lr.describe_permute(e, dims, perm)
+                    assert d["kind"] == "tile" and wide_sides(d) == "ab", d
+                    assert d["tile_a"] * e == rowb and d["tile_a"] * d["tile_b"] * e == tb, d
+                    check_permute(lr, orc, 31 * e + rowb + tb, e, dims, perm)
+    finally:
+        lr.tuning_load(None)
+        lr.tuning_load(lr.DEFAULT_TUNE_TABLE)
+
+
+def test_widened_planes_in_a_batch(lr, orc):
+    """Widened planes (32 KB tiles in single calls) run in the batched kernel
+    with the 16 KB tile of the same row length."""
+    ops = [dict(kind="permute", elem_bytes=e, dims=dims, perm=perm, data_seed=900 + i)
+           for i, (dims, perm, e, _) in enumerate(WIDE)]
+    ops += [dict(kind="permute", elem_bytes=2, dims=[64, 16, 24, 64], perm=[3, 2, 1, 0], data_seed=999)]
+    pool = DevPool()
+    bufs = [make_op_buffers(op, offset=0, pool=pool) for op in ops]
+    plan = lr.Plan()
+    for op, b in zip(ops, bufs):
+        add_to_plan(plan, op, b)
+    plan.finalize()
+    for rep in range(2):
+        plan.run()
+        sync()
+        pool.check()
+        for i, (op, b) in enumerate(zip(ops, bufs)):
+            for w, g in zip(oracle_of(orc, op, b), outputs_of(op, b)):
+                assert np.array_equal(g, w), (rep, i, op)
+    plan.close()
+
+
+# blocked runs: unmoved inner runs of 128 bytes up to 1 KB on a transpose
+# plane, copied in blocks of cells (no shared memory)
+BLOCKED = [  # (dims, perm, E)
+    ([64, 128, 40, 64], [2, 1, 0, 3], 2),
+    ([33, 17, 5, 64], [2, 1, 0, 3], 2),       # ragged blocks
+    ([7, 9, 11, 32], [1, 2, 0, 3], 4),
+    ([5, 300, 16], [1, 0, 2], 8),
+    ([3, 4, 5, 6, 16], [4, 3, 1, 0, 2], 12),   # 12-byte elements, 4-byte words
+    ([100, 3, 128], [1, 0, 2], 1),
+    ([30, 20, 3, 96], [1, 0, 2, 3], 4),       # 1152-byte runs (3 x 96 x 4): the runs kernel
+    ([40, 50, 7, 48], [2, 1, 0, 3], 4),       # 192-byte runs
+]
+
+
+@pytest.mark.parametrize("case", range(len(BLOCKED)))
+def test_blocked_runs(lr, orc, case):
+    dims, perm, e = BLOCKED[case]
+    d = lr.describe_permute(e, dims, perm)
+    for off in (0, 1 if e in (1, 12) else e):
+        check_permute(lr, orc, 950 + case, e, dims, perm, src_off=off, dst_off=off)
+    if perm[-1] == len(dims) - 1:  # an unmoved inner run: blocked below 1 KB, the runs kernel above
+        assert d["kind"] == ("tile_cells" if 128 <= d["cell_bytes"] < 1024 else "runs"), d
+
+
+def test_blocked_runs_in_a_batch(lr, orc):
+    ops = [dict(kind="permute", elem_bytes=e, dims=dims, perm=perm, data_seed=960 + i)
+           for i, (dims, perm, e) in enumerate(BLOCKED)]
+    pool = DevPool()
+    bufs = [make_op_buffers(op, offset=4 * (i % 2), pool=pool) for i, op in enumerate(ops)]
+    plan = lr.Plan()
+    for op, b in zip(ops, bufs):
+        add_to_plan(plan, op, b)
+    plan.finalize()
+    plan.run()
+    sync()
+    pool.check()
+    for i, (op, b) in enumerate(zip(ops, bufs)):
+        for w, g in zip(oracle_of(orc, op, b), outputs_of(op, b)):
+            assert np.array_equal(g, w), (i, op)
+    plan.close()

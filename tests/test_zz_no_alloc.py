@@ -22,8 +22,8 @@ import synth
 from tests.gpu_util import DevBuf, DevPool, sync
 from tests.test_gpu_parity import add_to_plan, make_op_buffers, oracle_of, outputs_of
 
-# The fixed work-list buffer holds about 1400 ops (the documented capacity).
-DOCUMENTED_CAPACITY_OPS = 1400
+# The fixed work-list buffer holds about 1280 ops (the documented capacity).
+DOCUMENTED_CAPACITY_OPS = 1280
 
 pytestmark = pytest.mark.gpu
 
