@@ -24,7 +24,9 @@ def client(tmp_path_factory):
            os.path.join(ROOT, "tests", "c_abi", "client.c"), "-o", exe, "-L", libdir, "-lrearr",
            "-Wl,-rpath," + libdir]
     subprocess.run(cmd, check=True, capture_output=True, text=True)
-    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    # the client reads the same tuning table as the Python binding
+    env = dict(os.environ, REARR_TUNE_TABLE=librearr.DEFAULT_TUNE_TABLE)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True, env=env).stdout
     return {ln.split()[0]: ln.split()[1:] for ln in out.splitlines()}
 
 

@@ -659,3 +659,4 @@ def test_blocked_runs_in_a_batch(lr, orc):
         for w, g in zip(oracle_of(orc, op, b), outputs_of(op, b)):
             assert np.array_equal(g, w), (i, op)
     plan.close()
+

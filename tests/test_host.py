@@ -175,8 +175,9 @@ def test_describe_examples(lr):
     # 64x128x256x64 with (0,1,3,2) is a batch of 8192 transposes of 256 x 64
     d = lr.describe_permute(4, [64, 128, 256, 64], [0, 1, 3, 2], FAKE_DST, FAKE_SRC)
     assert d["kind"] == "tile" and d["dims"] == [8192, 64, 256] and d["plane_a"] == 1
-    # unmoved innermost axis folds into the cell
-    d = lr.describe_permute(4, [64, 128, 4], [1, 0, 2], FAKE_DST, FAKE_SRC)
+    # unmoved innermost axis folds into the cell (an op past the L2 bound of
+    # the thin-plane rule, so that it stays a tile whatever the table says)
+    d = lr.describe_permute(4, [2048, 2048, 4], [1, 0, 2], FAKE_DST, FAKE_SRC)
     assert d["cell_bytes"] == 16 and d["rank"] == 2 and d["kind"] == "tile"
     # ... and a plane of 8 x 16 such cells is too thin for tiles
     d = lr.describe_permute(4, [8, 16, 4], [1, 0, 2], FAKE_DST, FAKE_SRC)
@@ -193,7 +194,7 @@ def test_describe_examples(lr):
     d = lr.describe_permute(4, [64, 64], [1, 0], FAKE_DST + 4, FAKE_SRC)
     assert d["kind"] == "tile" and d["vec_out"] == 4 and d["vec_in"] == 16
     # ragged extents lower the vector widths, never the correctness
-    d = lr.describe_permute(4, [37, 211], [1, 0], FAKE_DST, FAKE_SRC)
+    d = lr.describe_permute(4, [3701, 4219], [1, 0], FAKE_DST, FAKE_SRC)
     assert d["kind"] == "tile" and d["vec_in"] == 4 and d["vec_out"] == 4
 
 
