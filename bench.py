@@ -294,35 +294,48 @@ def run_gpu(args):
     memcpy_same = {nb: measure_memcpy(torch, rr, stream, nbytes=nb)[0]
                    for nb in sorted({op_out_bytes(o) for o in ops})}
 
-    # timed region: K steps, one event between consecutive ops
-    n_ev = len(ops) * args.steps + 1
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
+    # timed region: K steps back to back, events only at its two ends (an
+    # event between two kernels would stop the next one from launching while
+    # the previous drains)
     try:
         gpu_id = str(torch.cuda.get_device_properties(device).uuid)
         gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
     except Exception:
         gpu_id = None
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = rr.launch_count()
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(gpu_id) as clk:
-        evs[0].record(stream)
-        k = 1
+        ev0.record(stream)
         for _ in range(args.steps):
             for o in ops:
                 wl.run_op(rr, o, stream)
-                evs[k].record(stream)
-                k += 1
+        ev1.record(stream)
         torch.cuda.synchronize()
     barrier()
     launches = rr.launch_count() - launches0
-    elapsed = max_over_ranks(evs[0].elapsed_time(evs[-1]) / 1e3, world, device)
+    elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, world, device)
+
+    # per-op times (families, roofline, per-op rates): separate steps after the
+    # timed region, one event between consecutive ops
+    op_steps = max(1, min(args.steps, 5))
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(ops) * op_steps + 1)]
+    evs[0].record(stream)
+    k = 1
+    for _ in range(op_steps):
+        for o in ops:
+            wl.run_op(rr, o, stream)
+            evs[k].record(stream)
+            k += 1
+    torch.cuda.synchronize()
     per_op = np.zeros(len(ops))
     k = 1
-    for _ in range(args.steps):
+    for _ in range(op_steps):
         for i in range(len(ops)):
             per_op[i] += evs[k - 1].elapsed_time(evs[k]) / 1e3
             k += 1
+    per_op *= args.steps / op_steps  # per-op totals over as many steps as the timed region ran
     value = replica_value(world, step_bytes, args.steps, elapsed)
 
     # roofline of the dominant kernel family

@@ -67,9 +67,8 @@ typedef struct {
 /* ---------------------------------------------------------------------------
  * Server.
  * In batching mode, requests moving at least large_bytes (read + write) run as
- * their own single-op launch in a stream slot, on a stream of the device's
- * highest priority, and so does a request that is alone in the ready queue
- * when a slot frees up (on the slot's normal stream); the others are grouped.
+ * their own single-op launch in a stream slot, and so does a request that is
+ * alone in the ready queue when a slot frees up; the others are grouped.
  *   budget_bytes     : size of the device slab holding every request buffer
  *                      (one cudaMalloc at create).
  *   n_streams        : batches in flight at once (1..8); each has its stream

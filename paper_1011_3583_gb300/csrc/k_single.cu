@@ -12,9 +12,25 @@ namespace rearr {
 
 std::atomic<uint64_t> g_launches{0};
 
+// Programmatic dependent launch.  Every single-op kernel is launched with
+// programmatic stream serialisation: when the kernel before it on the stream
+// is also one of these, it may be launched while that one drains, its CTAs
+// taking SM slots as they free up.  Each kernel therefore first waits for
+// the grid it depends on to complete and its writes to be visible
+// (griddepcontrol.wait; a no-op when nothing is pending), and then allows
+// the next kernel to launch (griddepcontrol.launch_dependents; that launch
+// happens once every CTA of this grid has started or exited).  No memory is
+// touched before the wait, so ordering on the stream is as without it.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <int E, int VIN, int VOUT, int ROWB, int TBYTES = kTileBytes>
 __global__ void __launch_bounds__(kThreads) k_tile_fast(const __grid_constant__ TileDesc d, uint32_t n)
 {
+    pdl_enter();
     __shared__ __align__(16) unsigned char smem[TBYTES];
     for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) tile_fast_body<E, VIN, VOUT, ROWB, TBYTES>(d, t, smem);
 }
@@ -22,6 +38,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_fast(const __grid_constant__ 
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_tile_cells(const __grid_constant__ TileDesc d, uint32_t n)
 {
+    pdl_enter();
     __shared__ __align__(16) unsigned char smem[kSmemBytes];
     for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) tile_cells_body<W>(d, t, smem);
 }
@@ -32,12 +49,14 @@ __global__ void __launch_bounds__(kThreads) k_tile_cells(const __grid_constant__
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_tile_runs(const __grid_constant__ TileDesc d, uint32_t n)
 {
+    pdl_enter();
     for (uint32_t t = blockIdx.x; t < n; t += gridDim.x) tile_runs_body<W>(d, t);
 }
 
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_runs(const __grid_constant__ RunsDesc d, uint64_t n)
 {
+    pdl_enter();
     __shared__ __align__(16) unsigned char smem[kMaxRunsPerUnit * 8];
     for (uint64_t u = blockIdx.x; u < n; u += gridDim.x) runs_body<W>(d, u, smem);
 }
@@ -45,18 +64,21 @@ __global__ void __launch_bounds__(kThreads) k_runs(const __grid_constant__ RunsD
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_copy(const __grid_constant__ CopyDesc d, uint64_t n)
 {
+    pdl_enter();
     for (uint64_t u = blockIdx.x; u < n; u += gridDim.x) copy_body<W>(d, u);
 }
 
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_gather(const __grid_constant__ GatherDesc d, uint64_t n)
 {
+    pdl_enter();
     for (uint64_t u = blockIdx.x; u < n; u += gridDim.x) gather_body<W>(d, u);
 }
 
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_strided(const __grid_constant__ StridedDesc d, uint64_t n)
 {
+    pdl_enter();
     for (uint64_t u = blockIdx.x; u < n; u += gridDim.x) strided_body<W>(d, u);
 }
 
@@ -69,6 +91,7 @@ struct InterlaceParams {
 template <int E, int K, bool INTER>
 __global__ void __launch_bounds__(kThreads) k_inter_fast(const __grid_constant__ InterlaceParams p, uint64_t n)
 {
+    pdl_enter();
     __shared__ __align__(16) unsigned char smem[kThreads / 32 * K * 32 * 16];
     for (uint64_t u = blockIdx.x; u < n; u += gridDim.x) {
         if constexpr (INTER) interlace_fast_body<E, K>(p.d, p.planes, u, n, smem);
@@ -79,6 +102,7 @@ __global__ void __launch_bounds__(kThreads) k_inter_fast(const __grid_constant__
 template <int W, bool INTER>
 __global__ void __launch_bounds__(kThreads) k_inter_generic(const __grid_constant__ InterlaceParams p, uint64_t n)
 {
+    pdl_enter();
     for (uint64_t u = blockIdx.x; u < n; u += gridDim.x) interlace_generic_body<W>(p.d, p.planes, u, INTER);
 }
 
@@ -89,12 +113,22 @@ inline unsigned grid_for(uint64_t units)
     return unsigned(units < 0x7FFFFFFFull ? units : 0x7FFFFFFFull);
 }
 
-template <typename K, typename P, typename N>
-cudaError_t go(K kernel, uint64_t units, const P &param, N n, cudaStream_t s)
+template <typename P, typename N>
+cudaError_t go(void (*kernel)(P, N), uint64_t units, const P &param, N n, cudaStream_t s)
 {
-    kernel<<<grid_for(units), kThreads, 0, s>>>(param, n);
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid_for(units));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, param, n);
+    if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+    return e;
 }
 
 #define RT_CASE(E, VI, VO, RB)                                                                \

@@ -149,7 +149,6 @@ rearr_status plan_request(const Req &r, OpDesc &op, std::vector<char *> &planes,
 
 struct Slot {
     cudaStream_t stream = nullptr;
-    cudaStream_t stream_hi = nullptr;  // higher-priority stream for large requests (batching mode)
     cudaEvent_t done = nullptr;
     void *dev_wl = nullptr;          // device work-list buffer
     unsigned char *host_wl = nullptr;  // pinned staging of the same size
@@ -206,7 +205,6 @@ Server::~Server()
 {
     for (Slot &s : slots) {
         if (s.stream) cudaStreamDestroy(s.stream);
-        if (s.stream_hi) cudaStreamDestroy(s.stream_hi);
         if (s.done) cudaEventDestroy(s.done);
         if (s.dev_wl) cudaFree(s.dev_wl);
         if (s.host_wl) cudaFreeHost(s.host_wl);
@@ -280,13 +278,9 @@ void Server::launch_batches(std::unique_lock<std::mutex> &)
             std::string err;
             std::vector<size_t> in_sz, out_sz;
             buffer_sizes(r->spec, in_sz, out_sz, err);
-            // A large request goes on the slot's higher-priority stream: the
-            // block scheduler hands it the SMs first, so the small batches
-            // that overlap it fill in around it instead of stretching it.
-            cudaStream_t ls = (r->bytes >= cfg.large_bytes && s.stream_hi) ? s.stream_hi : s.stream;
-            cudaError_t e = copy_inputs(*r, in_sz, ls);
-            if (e == cudaSuccess && plan_request(*r, op, pl, err) == REARR_OK) e = launch_single(op, pl.data(), ls);
-            if (e == cudaSuccess) e = cudaEventRecord(s.done, ls);
+            cudaError_t e = copy_inputs(*r, in_sz, s.stream);
+            if (e == cudaSuccess && plan_request(*r, op, pl, err) == REARR_OK) e = launch_single(op, pl.data(), s.stream);
+            if (e == cudaSuccess) e = cudaEventRecord(s.done, s.stream);
             if (e != cudaSuccess) worker_error = std::string("launch failed: ") + cudaGetErrorString(e);
             r->state = RUNNING;
             s.reqs = {r};
@@ -440,11 +434,6 @@ rearr_status rearr_server_create(const rearr_server_config *config, rearr_server
     S.slots.resize(size_t(c.n_streams));
     for (Slot &s : S.slots) {
         e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
-        if (e == cudaSuccess && c.batching) {
-            int least = 0, greatest = 0;
-            e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
-            if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s.stream_hi, cudaStreamNonBlocking, greatest);
-        }
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
         if (e == cudaSuccess && c.batching) {
             s.wl_bytes = lay.bytes;
