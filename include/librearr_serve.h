@@ -67,8 +67,10 @@ typedef struct {
 /* ---------------------------------------------------------------------------
  * Server.
  * In batching mode, requests moving at least large_bytes (read + write) run as
- * their own single-op launch in a stream slot, and so does a request that is
- * alone in the ready queue when a slot frees up; the others are grouped.
+ * their own single-op launch, and so does a request that is alone in the
+ * ready queue; those go out in arrival order on one stream of their own (at
+ * light load the server then behaves as the plain path), the others are
+ * grouped into batches on the stream slots.
  *   budget_bytes     : size of the device slab holding every request buffer
  *                      (one cudaMalloc at create).
  *   n_streams        : batches in flight at once (1..8); each has its stream

@@ -9,7 +9,7 @@
 //     requests that arrive while other batches run go out as soon as a slot
 //     frees up, so their work overlaps on the device); a large request, or a
 //     request that is alone in the ready queue, runs as its single-op kernel
-//     in a slot of its own;
+//     on the single-op lane, one stream in arrival order;
 //   plain mode: every ready request is launched at once as its own single-op
 //     kernel on one stream, in arrival order (the one-launch-per-call path).
 // Completion is found by polling CUDA events; the server never waits on the
@@ -173,9 +173,11 @@ struct Server {
     uint64_t next_ticket = 1;
     std::deque<uint64_t> admit_q;      // reservations waiting for their turn / memory
     std::deque<Req *> ready;           // submitted, not launched
+    std::deque<Req *> ready_large;     // batching mode: submitted large requests, not launched
     std::unordered_map<uint64_t, std::unique_ptr<Req>> reqs;
     std::vector<Slot> slots;
-    std::deque<Req *> plain_inflight;  // plain mode: launched, not yet complete
+    std::deque<Req *> plain_inflight;  // single-op launches in stream order, not yet complete
+    cudaStream_t lane = nullptr;       // batching mode: the stream of single-op launches
     std::vector<cudaEvent_t> event_pool;
     bool stop = false;
     std::thread worker;
@@ -189,6 +191,14 @@ struct Server {
     void run();
     void launch_batches(std::unique_lock<std::mutex> &lk);
     void launch_plain(std::unique_lock<std::mutex> &lk);
+    void launch_on_lane(Req *r, cudaStream_t stream);
+    // Queues a submitted request (large ones apart in batching mode).
+    void enqueue(Req *r)
+    {
+        if (cfg.batching && r->bytes >= cfg.large_bytes) ready_large.push_back(r);
+        else ready.push_back(r);
+    }
+    bool pending() const { return !ready.empty() || !ready_large.empty(); }
     bool poll_completions();
     bool inflight() const;
 };
@@ -209,6 +219,7 @@ Server::~Server()
         if (s.dev_wl) cudaFree(s.dev_wl);
         if (s.host_wl) cudaFreeHost(s.host_wl);
     }
+    if (lane) cudaStreamDestroy(lane);
     for (cudaEvent_t e : event_pool) cudaEventDestroy(e);
     for (auto &kv : reqs)
         if (kv.second->ev) cudaEventDestroy(kv.second->ev);
@@ -257,7 +268,24 @@ bool Server::poll_completions()
 
 void Server::launch_batches(std::unique_lock<std::mutex> &)
 {
+    // A large request runs as its own single-op kernel on the single-op lane
+    // as soon as it is ready: large requests never wait for a slot, and run
+    // back to back in arrival order.
+    while (!ready_large.empty()) {
+        Req *r = ready_large.front();
+        ready_large.pop_front();
+        launch_on_lane(r, lane);
+    }
     for (Slot &s : slots) {
+        // A lone ready request also runs as its single-op kernel on the lane
+        // (one op gains nothing from a work list): at light load the server
+        // then behaves as the plain path does; batches take over as soon as
+        // requests queue up.
+        if (ready.size() == 1) {
+            Req *r = ready.front();
+            ready.pop_front();
+            launch_on_lane(r, lane);
+        }
         if (ready.empty()) return;
         if (s.busy) continue;
         // Take ready requests in FIFO order while the slot's work list has room.
@@ -265,33 +293,9 @@ void Server::launch_batches(std::unique_lock<std::mutex> &)
         std::vector<std::vector<char *>> planes;
         std::vector<Req *> taken;
         size_t n_ptrs = 0;
-        // A large request runs alone as its single-op kernel, and so does a
-        // lone ready request: one op gains nothing from a work list, and its
-        // single-op kernel skips the work-list upload and the persistent
-        // kernel's set-up (light load keeps the plain path's latency; the
-        // batches take over as soon as requests queue up).
-        if (ready.front()->bytes >= cfg.large_bytes || ready.size() == 1) {
-            Req *r = ready.front();
-            ready.pop_front();
-            OpDesc op;
-            std::vector<char *> pl;
-            std::string err;
-            std::vector<size_t> in_sz, out_sz;
-            buffer_sizes(r->spec, in_sz, out_sz, err);
-            cudaError_t e = copy_inputs(*r, in_sz, s.stream);
-            if (e == cudaSuccess && plan_request(*r, op, pl, err) == REARR_OK) e = launch_single(op, pl.data(), s.stream);
-            if (e == cudaSuccess) e = cudaEventRecord(s.done, s.stream);
-            if (e != cudaSuccess) worker_error = std::string("launch failed: ") + cudaGetErrorString(e);
-            r->state = RUNNING;
-            s.reqs = {r};
-            s.busy = true;
-            s.t_launch = now_s();
-            ++st.launches;
-            continue;
-        }
         while (!ready.empty() && int(taken.size()) < cfg.max_batch_ops) {
             Req *r = ready.front();
-            if (r->bytes >= cfg.large_bytes) break;  // goes alone into the next free slot
+            if (r->bytes >= cfg.large_bytes) break;  // goes to the single-op lane
             OpDesc op;
             std::vector<char *> pl;
             std::string err;
@@ -341,39 +345,45 @@ void Server::launch_batches(std::unique_lock<std::mutex> &)
     }
 }
 
+// One request as its single-op kernel on `stream`; its completion event
+// joins plain_inflight (requests on one stream complete in order).
+void Server::launch_on_lane(Req *r, cudaStream_t stream)
+{
+    OpDesc op;
+    std::vector<char *> pl;
+    std::string err;
+    std::vector<size_t> in_sz, out_sz;
+    buffer_sizes(r->spec, in_sz, out_sz, err);
+    cudaError_t e = copy_inputs(*r, in_sz, stream);
+    if (e != cudaSuccess) {
+        worker_error = std::string("input copy failed: ") + cudaGetErrorString(e);
+    } else if (plan_request(*r, op, pl, err) == REARR_OK) {
+        e = launch_single(op, pl.data(), stream);
+    } else {
+        worker_error = "plan failed in the server: " + err;
+    }
+    if (event_pool.empty()) {
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) event_pool.push_back(ev);
+    }
+    if (!event_pool.empty()) {
+        r->ev = event_pool.back();
+        event_pool.pop_back();
+        if (e == cudaSuccess) e = cudaEventRecord(r->ev, stream);
+    }
+    if (e != cudaSuccess) worker_error = std::string("single-op launch failed: ") + cudaGetErrorString(e);
+    r->state = RUNNING;
+    if (r->ev) plain_inflight.push_back(r);
+    else { r->state = DONE; r->t_done = now_s(); ++st.completed; }
+    ++st.launches;
+}
+
 void Server::launch_plain(std::unique_lock<std::mutex> &)
 {
-    Slot &s = slots[0];
     while (!ready.empty()) {
         Req *r = ready.front();
         ready.pop_front();
-        OpDesc op;
-        std::vector<char *> pl;
-        std::string err;
-        std::vector<size_t> in_sz, out_sz;
-        buffer_sizes(r->spec, in_sz, out_sz, err);
-        cudaError_t e = copy_inputs(*r, in_sz, s.stream);
-        if (e != cudaSuccess) {
-            worker_error = std::string("input copy failed: ") + cudaGetErrorString(e);
-        } else if (plan_request(*r, op, pl, err) == REARR_OK) {
-            e = launch_single(op, pl.data(), s.stream);
-        } else {
-            worker_error = "plan failed in the server: " + err;
-        }
-        if (event_pool.empty()) {
-            cudaEvent_t ev;
-            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) event_pool.push_back(ev);
-        }
-        if (!event_pool.empty()) {
-            r->ev = event_pool.back();
-            event_pool.pop_back();
-            if (e == cudaSuccess) e = cudaEventRecord(r->ev, s.stream);
-        }
-        if (e != cudaSuccess) worker_error = std::string("plain launch failed: ") + cudaGetErrorString(e);
-        r->state = RUNNING;
-        if (r->ev) plain_inflight.push_back(r);
-        else { r->state = DONE; r->t_done = now_s(); ++st.completed; }
-        ++st.launches;
+        launch_on_lane(r, slots[0].stream);
     }
 }
 
@@ -386,11 +396,11 @@ void Server::run()
         if (cfg.batching) launch_batches(lk);
         else launch_plain(lk);
         if (completed) cv.notify_all();
-        if (stop && ready.empty() && !inflight()) break;
+        if (stop && !pending() && !inflight()) break;
         if (inflight()) {
             cv.wait_for(lk, std::chrono::microseconds(cfg.poll_interval_us));
         } else {
-            cv.wait(lk, [&] { return stop || !ready.empty(); });
+            cv.wait(lk, [&] { return stop || pending(); });
         }
     }
     cv.notify_all();
@@ -443,6 +453,13 @@ rearr_status rearr_server_create(const rearr_server_config *config, rearr_server
         if (e != cudaSuccess) {
             delete out;
             return cuda_fail(e, "rearr_server_create: stream slot");
+        }
+    }
+    if (c.batching) {
+        e = cudaStreamCreateWithFlags(&S.lane, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete out;
+            return cuda_fail(e, "rearr_server_create: single-op lane");
         }
     }
     S.worker = std::thread([&S] { S.run(); });
@@ -561,7 +578,7 @@ rearr_status rearr_server_submit(rearr_server *server, uint64_t ticket)
     if (!r) return fail(REARR_EINVAL, "rearr_server_submit: unknown ticket");
     if (r->state != RESERVED) return fail(REARR_EBUSY, "rearr_server_submit: request already submitted");
     r->state = QUEUED;
-    S.ready.push_back(r);
+    S.enqueue(r);
     S.cv.notify_all();
     return REARR_OK;
 }
@@ -577,7 +594,7 @@ rearr_status rearr_server_submit_from(rearr_server *server, uint64_t ticket, con
     if (size_t(n_srcs) > r->ins.size()) return fail(REARR_EINVAL, "rearr_server_submit_from: more sources than inputs");
     r->in_src.assign(srcs, srcs + n_srcs);
     r->state = QUEUED;
-    S.ready.push_back(r);
+    S.enqueue(r);
     S.cv.notify_all();
     return REARR_OK;
 }
@@ -664,7 +681,7 @@ rearr_status rearr_server_destroy(rearr_server *server, int64_t timeout_us)
     Server &S = server->s;
     {
         std::unique_lock<std::mutex> lk(S.mu);
-        auto idle = [&] { return S.ready.empty() && !S.inflight(); };
+        auto idle = [&] { return !S.pending() && !S.inflight(); };
         if (timeout_us < 0) S.cv.wait(lk, idle);
         else if (!S.cv.wait_for(lk, std::chrono::microseconds(timeout_us), idle))
             return fail(REARR_ETIMEDOUT, "rearr_server_destroy: work still in flight");
