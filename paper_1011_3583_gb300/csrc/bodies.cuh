@@ -135,6 +135,8 @@ __device__ __forceinline__ void tile_fast_body(const TileDesc &d, uint32_t t, un
     char *out = d.dst + ooff + int64_t(b0) * E;
     const int tid = tid_x();
     const uint32_t row_valid_bytes = na * E;
+    // a widened A whose planes end inside 16-byte chunks
+    const bool fine_split = d.sa1_out != 0 && (d.da_split.d & uint32_t(V - 1)) != 0;
 
     // Loads are issued in batches of up to 8 per thread before their shared
     // stores, which keeps narrow-width variants within the register budget.
@@ -174,13 +176,22 @@ __device__ __forceinline__ void tile_fast_body(const TileDesc &d, uint32_t t, un
 #pragma unroll
             for (int i = 0; i < VB; ++i)
                 r[i] = lds<16>(smem + (b + i) * ROWB + ((q ^ (bq & 7)) << 4));
-            // the V elements of chunk q share their absorbed index (a widened
-            // A splits at a multiple of V)
-            char *col = out + a_col_out(d, a0 + uint32_t(q * V)) + int64_t(b) * E;
+            if (fine_split) {
+                // a widened A that splits inside a chunk: each element's own
+                // output row
 #pragma unroll
-            for (int m = 0; m < V; ++m) {
-                const uint32_t a = uint32_t(q * V + m);
-                if (a < na) stg<VOUT>(col + int64_t(m) * d.sa_out, piece<E, VB>(r, m));
+                for (int m = 0; m < V; ++m) {
+                    const uint32_t a = uint32_t(q * V + m);
+                    if (a < na) stg<VOUT>(out + a_col_out(d, a0 + a) + int64_t(b) * E, piece<E, VB>(r, m));
+                }
+            } else {
+                // the V elements of chunk q share their absorbed index
+                char *col = out + a_col_out(d, a0 + uint32_t(q * V)) + int64_t(b) * E;
+#pragma unroll
+                for (int m = 0; m < V; ++m) {
+                    const uint32_t a = uint32_t(q * V + m);
+                    if (a < na) stg<VOUT>(col + int64_t(m) * d.sa_out, piece<E, VB>(r, m));
+                }
             }
         }
     }
@@ -253,6 +264,8 @@ __device__ __forceinline__ void tile_fast_store(const TileDesc &d, uint32_t t, c
     const uint32_t nbv = min(uint32_t(TB), d.DB - b0);
     char *out = d.dst + ooff + int64_t(b0) * E;
     const int tid = tid_x();
+    // a widened A whose planes end inside 16-byte chunks
+    const bool fine_split = d.sa1_out != 0 && (d.da_split.d & uint32_t(V - 1)) != 0;
     constexpr int UB = TB / VB, UQ = TA / V, NU = UB * UQ;
     static_assert(NU % kThreads == 0, "store units must split evenly");
 #pragma unroll
@@ -264,11 +277,19 @@ __device__ __forceinline__ void tile_fast_store(const TileDesc &d, uint32_t t, c
             uint4 r[VB];
 #pragma unroll
             for (int i = 0; i < VB; ++i) r[i] = lds<16>(smem + (b + i) * ROWB + ((q ^ (bq & 7)) << 4));
-            char *col = out + a_col_out(d, a0 + uint32_t(q * V)) + int64_t(b) * E;
+            if (fine_split) {
 #pragma unroll
-            for (int m = 0; m < V; ++m) {
-                const uint32_t a = uint32_t(q * V + m);
-                if (a < na) stg<VOUT>(col + int64_t(m) * d.sa_out, piece<E, VB>(r, m));
+                for (int m = 0; m < V; ++m) {
+                    const uint32_t a = uint32_t(q * V + m);
+                    if (a < na) stg<VOUT>(out + a_col_out(d, a0 + a) + int64_t(b) * E, piece<E, VB>(r, m));
+                }
+            } else {
+                char *col = out + a_col_out(d, a0 + uint32_t(q * V)) + int64_t(b) * E;
+#pragma unroll
+                for (int m = 0; m < V; ++m) {
+                    const uint32_t a = uint32_t(q * V + m);
+                    if (a < na) stg<VOUT>(col + int64_t(m) * d.sa_out, piece<E, VB>(r, m));
+                }
             }
         }
     }

@@ -133,8 +133,9 @@ static TileShape choose_wide_shape(int E, int64_t DA0, int64_t DB0, int64_t DA, 
 // (the output stays contiguous) -- so one tile spans several planes and both
 // its reads and its writes come in runs of up to 512 bytes.  Sides of at
 // least wide_min_bytes() are left alone; an axis that continues both sides
-// widens the shorter one.  Fast tiles only (one element per cell, 16-byte
-// loads, and A split at multiples of the 16-byte chunk).
+// widens the shorter one.  Fast tiles only (one element per cell).  When DA
+// is not a multiple of a 16-byte chunk's elements, the store phase splits
+// every element's coordinate on its own (tile_fast_body).
 static void choose_widening(const std::vector<Axis> &ax, int p, int64_t cell, int &qa, int &qb)
 {
     const int R = int(ax.size());
@@ -142,7 +143,7 @@ static void choose_widening(const std::vector<Axis> &ax, int p, int64_t cell, in
     qa = qb = -1;
     if (R < 3) return;
     const int64_t DA = ax[p].extent, DB = ax[R - 1].extent;
-    if (uint64_t(DA * cell) < lim && DA % (16 / cell) == 0)
+    if (uint64_t(DA * cell) < lim)
         for (int i = 0; i < R - 1; ++i)
             if (i != p && ax[i].stride == DA * cell && DA * ax[i].extent <= kMaxExtent) qa = i;
     if (uint64_t(DB * cell) < lim && R - 2 != p && DB * ax[R - 2].extent <= kMaxExtent) qb = R - 2;
@@ -385,22 +386,25 @@ static rearr_status plan_axes(void *dst, const char *src, size_t elem_bytes, con
     if (W == cell) {
         const int E = int(cell);
         // Widest legal global access on each side.  Input rows start at src
-        // plus sums of the (non-A) input strides; output rows start at
-        // multiples of DB*E bytes from dst.
+        // plus sums of the input strides of the axes other than A (and other
+        // than the axis a widened A absorbs: the widened row is contiguous
+        // over DA * extent(qa) cells, so the load width follows that row
+        // length); output rows start at multiples of DB*E bytes from dst.
+        choose_widening(ax, p, cell, qa, qb);
         uint64_t in_or = 0;
         for (int i = 0; i < R; ++i)
-            if (i != p) in_or |= uint64_t(ax[i].stride);
+            if (i != p && i != qa) in_or |= uint64_t(ax[i].stride);
+        const int64_t DAw = qa >= 0 ? DA * ax[qa].extent : DA;
         const int vcap = tile_vector_bytes();
         vin = E;
         for (int v : {16, 4}) {
-            if (v > E && v <= vcap && (uint64_t(DA) * E) % v == 0 && sa % v == 0 && in_or % v == 0) { vin = v; break; }
+            if (v > E && v <= vcap && (uint64_t(DAw) * E) % v == 0 && sa % v == 0 && in_or % v == 0) { vin = v; break; }
         }
         vout = E;
         const int vmax = std::min(std::min(16, 4 * E), vcap);
         for (int v : {vmax, 4}) {
             if (v > E && (uint64_t(DB) * E) % v == 0 && da % v == 0) { vout = v; break; }
         }
-        if (vin == 16 && vout == std::min(16, 4 * E)) choose_widening(ax, p, cell, qa, qb);
     }
     fill_tile_common(t, ax, p, cell, qa, qb, static_cast<char *>(dst), src);
     info.wide_a = qa;

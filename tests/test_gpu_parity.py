@@ -543,6 +543,14 @@ WIDE = [  # (dims, perm, E, widened sides)
     ([64, 33, 17, 64], [3, 2, 0, 1], 2, "a"),
     ([3, 64, 20, 64], [0, 3, 2, 1], 2, "a"),
     ([64, 6, 10, 64], [2, 3, 1, 0], 2, "b"),
+    # A's extent not a multiple of a 16-byte chunk's elements: the store
+    # phase splits every element's coordinate on its own
+    ([9, 10, 11, 7], [3, 2, 1, 0], 4, "ab"),      # 4-byte loads (77-element rows)
+    ([9, 10, 4, 7], [3, 2, 1, 0], 4, "ab"),       # 16-byte loads (28-element rows)
+    ([5, 6, 13, 3], [3, 2, 1, 0], 2, "ab"),
+    ([5, 6, 13, 3], [3, 2, 1, 0], 1, "ab"),
+    ([5, 6, 13, 3], [3, 2, 1, 0], 8, "ab"),
+    ([40, 3, 25, 5], [3, 1, 2, 0], 4, "a"),
 ]
 
 
