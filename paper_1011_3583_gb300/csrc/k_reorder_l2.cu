@@ -112,6 +112,14 @@ __device__ __forceinline__ uint32_t index_at(const L2Reorder &p, uint64_t i)
     return p.idx64 ? uint32_t(__ldg(reinterpret_cast<const unsigned long long *>(p.idx) + i)) : __ldg(p.idx + i);
 }
 
+// The same with the index width fixed at compile time (I64: 64-bit indices).
+template <bool I64>
+__device__ __forceinline__ uint32_t index_at_t(const L2Reorder &p, uint64_t i)
+{
+    if constexpr (I64) return uint32_t(__ldg(reinterpret_cast<const unsigned long long *>(p.idx) + i));
+    else return __ldg(p.idx + i);
+}
+
 __device__ __forceinline__ bool bucketed(const L2Reorder &p)
 {
     return *reinterpret_cast<volatile unsigned long long *>(p.near) < p.near_threshold;
@@ -143,19 +151,31 @@ __global__ void __launch_bounds__(kThreads) k_l2_sample(const L2Reorder p)
 constexpr int kWarps = kThreads / 32;
 constexpr int kPer = kTile / kThreads;  // 16
 
+// Tile index k of this thread's element j.
+__device__ __forceinline__ uint32_t tile_k(int j)
+{
+    return (threadIdx.x >> 5) * (kTile / kWarps) + uint32_t(j) * 32 + (threadIdx.x & 31);
+}
+
+template <bool I64>
 __device__ __forceinline__ void load_tile(const L2Reorder &p, uint32_t i0, uint32_t m, uint32_t (&v)[kPer])
 {
-    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (m == kTile) {  // a full tile: no bounds test per element
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-        const uint32_t k = w * (kTile / kWarps) + j * 32 + lane;
-        v[j] = k < m ? index_at(p, i0 + k) : 0xFFFFFFFFu;
+        for (int j = 0; j < kPer; ++j) v[j] = index_at_t<I64>(p, i0 + tile_k(j));
+    } else {
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const uint32_t k = tile_k(j);
+            v[j] = k < m ? index_at_t<I64>(p, i0 + k) : 0xFFFFFFFFu;
+        }
     }
 }
 
 // Each CTA walks a contiguous range of tiles with per-warp shared counters
 // (the only contention is among the lanes of one warp) and flushes them to
 // the global histogram whenever the destination chunk changes.
+template <bool I64>
 __global__ void __launch_bounds__(kThreads) k_l2_hist(const L2Reorder p, uint32_t tiles_per_cta)
 {
     if (!bucketed(p)) return;
@@ -168,15 +188,18 @@ __global__ void __launch_bounds__(kThreads) k_l2_hist(const L2Reorder p, uint32_
     uint32_t cur_d = t0 < t1 ? dest_chunk(p, t0 * kTile) : 0;
     uint32_t row[kMaxChunks / kThreads] = {};  // this CTA's count of chunks c = threadIdx.x + j * kThreads
     uint32_t v[kPer];
-    if (t0 < t1) load_tile(p, t0 * kTile, min(uint32_t(kTile), p.n - t0 * kTile), v);
+    if (t0 < t1) load_tile<I64>(p, t0 * kTile, min(uint32_t(kTile), p.n - t0 * kTile), v);
     for (uint32_t t = t0; t < t1; ++t) {
         uint32_t nxt[kPer];
-        if (t + 1 < t1) load_tile(p, (t + 1) * kTile, min(uint32_t(kTile), p.n - (t + 1) * kTile), nxt);
+        if (t + 1 < t1) load_tile<I64>(p, (t + 1) * kTile, min(uint32_t(kTile), p.n - (t + 1) * kTile), nxt);
         const uint32_t m = min(uint32_t(kTile), p.n - t * kTile);
+        if (m == kTile) {
 #pragma unroll
-        for (int j = 0; j < kPer; ++j) {
-            const uint32_t k = w * (kTile / kWarps) + j * 32 + (threadIdx.x & 31);
-            if (k < m) atomicAdd(&sh[w][chunk_of(p, v[j])], 1u);
+            for (int j = 0; j < kPer; ++j) atomicAdd(&sh[w][chunk_of(p, v[j])], 1u);
+        } else {
+#pragma unroll
+            for (int j = 0; j < kPer; ++j)
+                if (tile_k(j) < m) atomicAdd(&sh[w][chunk_of(p, v[j])], 1u);
         }
         const uint32_t next_d = t + 1 < t1 ? dest_chunk(p, (t + 1) * kTile) : 0xFFFFFFFFu;
         if (next_d != cur_d) {
@@ -317,18 +340,17 @@ __global__ void __launch_bounds__(1024) k_l2_scan_rows(const L2Reorder p)
 // its own cursor when the CTA owns the tile's destination chunk (every tile
 // of that chunk is in the CTA's range, so the buckets (c, d) have no other
 // writer), else from one global atomic per chunk.  The tile is staged in
-// shared memory grouped by chunk (the bucketed index; tile index and chunk
-// packed in one word) and written out as contiguous segments.  The next tile's
-// indices load while this one is sorted.
+// shared memory grouped by chunk (the bucketed index and the tile index
+// packed in one 64-bit word; the chunk is recomputed from the index) and
+// written out as contiguous segments.  The next tile's indices load while this
+// one is sorted.
 struct PartitionSmem {
-    uint32_t s_st[kTile];               // the bucketed index (gather: source, scatter: destination), by chunk
-    uint32_t kc_st[kTile];              // tile index k | chunk << 12
+    unsigned long long sk[kTile];       // bucketed index (gather: source, scatter: destination) | tile index << 32
     uint32_t cnt[kWarps][kMaxChunks];   // per-warp counts, then per-warp slots
     uint32_t delta[kMaxChunks];         // global position of tile slot 0 of the chunk's segment
     uint32_t cur[kMaxChunks];           // owned destination chunk: next free slot of bucket (c, d)
     uint32_t warp_sums[kWarps];
 };
-static_assert(kTile <= 4096 && kMaxChunks <= (1 << 20), "tile index and chunk share one word");
 static_assert(sizeof(PartitionSmem) % 16 == 0, "the scatter form's element buffer follows, 16-byte aligned");
 
 // SW = 0: gather form (s-array: source index, i-array: destination index, as
@@ -337,7 +359,7 @@ static_assert(sizeof(PartitionSmem) % 16 == 0, "the scatter form's element buffe
 // itself): the tile's source elements are copied into shared memory with
 // cp.async behind the index loads and written out beside their indices, so
 // the scatter needs no separate pass that reads the source by position.
-template <int SW>
+template <int SW, bool I64>
 __global__ void __launch_bounds__(kThreads, 4) k_l2_partition(const L2Reorder p, uint32_t tiles_per_cta,
                                                               uint32_t own)
 {
@@ -352,7 +374,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_l2_partition(const L2Reorder p,
     for (uint32_t c = threadIdx.x; c < kWarps * kMaxChunks; c += kThreads) (&S.cnt[0][0])[c] = 0;
     uint32_t cur_d = 0xFFFFFFFFu;
     uint32_t v[kPer];
-    if (t0 < t1) load_tile(p, t0 * kTile, min(uint32_t(kTile), p.n - t0 * kTile), v);
+    if (t0 < t1) load_tile<I64>(p, t0 * kTile, min(uint32_t(kTile), p.n - t0 * kTile), v);
     __syncthreads();
     for (uint32_t t = t0; t < t1; ++t) {
         const uint32_t i0 = t * kTile;
@@ -378,12 +400,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_l2_partition(const L2Reorder p,
             cp_async_commit();
         }
         uint32_t nxt[kPer];
-        if (t + 1 < t1) load_tile(p, (t + 1) * kTile, min(uint32_t(kTile), p.n - (t + 1) * kTile), nxt);
+        if (t + 1 < t1) load_tile<I64>(p, (t + 1) * kTile, min(uint32_t(kTile), p.n - (t + 1) * kTile), nxt);
         uint32_t rk[kPer];
+        if (m == kTile) {
 #pragma unroll
-        for (int j = 0; j < kPer; ++j) {
-            const uint32_t k = w * (kTile / kWarps) + j * 32 + lane;
-            rk[j] = k < m ? atomicAdd(&S.cnt[w][chunk_of(p, v[j])], 1u) : 0u;
+            for (int j = 0; j < kPer; ++j) rk[j] = atomicAdd(&S.cnt[w][chunk_of(p, v[j])], 1u);
+        } else {
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) rk[j] = tile_k(j) < m ? atomicAdd(&S.cnt[w][chunk_of(p, v[j])], 1u) : 0u;
         }
         __syncthreads();
         uint32_t a = 0, b = 0;
@@ -445,25 +469,24 @@ __global__ void __launch_bounds__(kThreads, 4) k_l2_partition(const L2Reorder p,
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
-            const uint32_t k = w * (kTile / kWarps) + j * 32 + lane;
-            if (k < m) {
-                const uint32_t c = chunk_of(p, v[j]);
-                const uint32_t pos = S.cnt[w][c] + rk[j];
-                S.s_st[pos] = v[j];
-                S.kc_st[pos] = k | (c << 12);
+            const uint32_t k = tile_k(j);
+            if (m == kTile || k < m) {
+                const uint32_t pos = S.cnt[w][chunk_of(p, v[j])] + rk[j];
+                S.sk[pos] = (unsigned long long)v[j] | ((unsigned long long)k << 32);
             }
         }
         if constexpr (SW > 0) cp_async_wait<0>();
         __syncthreads();
         for (uint32_t q = threadIdx.x; q < m; q += kThreads) {
-            const uint32_t kc = S.kc_st[q];
-            const uint32_t g = S.delta[kc >> 12] + q;
-            p.sarr[g] = S.s_st[q];
+            const unsigned long long x = S.sk[q];
+            const uint32_t sv = uint32_t(x), k = uint32_t(x >> 32);
+            const uint32_t g = S.delta[chunk_of(p, sv)] + q;
+            p.sarr[g] = sv;
             if constexpr (SW > 0) {
                 using T = typename Word<SW>::T;
-                reinterpret_cast<T *>(p.varr)[g] = reinterpret_cast<const T *>(vals)[kc & (kTile - 1)];
+                reinterpret_cast<T *>(p.varr)[g] = reinterpret_cast<const T *>(vals)[k];
             } else {
-                const uint32_t i = i0 + (kc & (kTile - 1));
+                const uint32_t i = i0 + k;
                 if (own) reinterpret_cast<uint16_t *>(p.iarr)[g] = uint16_t(i & ((1u << p.ds_shift) - 1));
                 else p.iarr[g] = i;
             }
@@ -753,10 +776,16 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
     if (dev >= 0 && dev < 64) {
         std::lock_guard<std::mutex> lock(setup_mu);
         if (!smem_set[dev]) {
-            e = cudaFuncSetAttribute(k_l2_partition<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(k_l2_partition<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      int(sizeof(PartitionSmem)));
             if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k_l2_partition<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                e = cudaFuncSetAttribute(k_l2_partition<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(sizeof(PartitionSmem)));
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_l2_partition<W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(sizeof(PartitionSmem) + kTile * W));
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_l2_partition<W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(sizeof(PartitionSmem) + kTile * W));
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(k_l2_scatter_smem<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -764,11 +793,11 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
             smem_set[dev] = e == cudaSuccess;
             int per_sm = 0;
             if (e == cudaSuccess && cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                        &per_sm, k_l2_partition<0>, kThreads, sizeof(PartitionSmem)) == cudaSuccess)
+                                        &per_sm, k_l2_partition<0, false>, kThreads, sizeof(PartitionSmem)) == cudaSuccess)
                 part_per_sm[dev] = per_sm;
             per_sm = 0;
             if (e == cudaSuccess &&
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_l2_partition<W>, kThreads,
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_l2_partition<W, false>, kThreads,
                                                               sizeof(PartitionSmem) + kTile * W) == cudaSuccess)
                 spart_per_sm[dev] = per_sm;
             per_sm = 0;
@@ -792,17 +821,23 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
     const unsigned pers = unsigned(sms) * 8;  // persistent grids of the gated passes
     const uint64_t dunits = (g.n + g.unit_elems - 1) / g.unit_elems;
     if (e == cudaSuccess) { k_l2_sample<<<kSampleRuns / (kThreads / 32), kThreads, 0, s>>>(p); e = cudaGetLastError(); }
-    if (e == cudaSuccess) { k_l2_hist<<<pgrid, kThreads, 0, s>>>(p, tpc); e = cudaGetLastError(); }
+    if (e == cudaSuccess) {
+        if (p.idx64) k_l2_hist<true><<<pgrid, kThreads, 0, s>>>(p, tpc);
+        else k_l2_hist<false><<<pgrid, kThreads, 0, s>>>(p, tpc);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) {
         if (smem_scatter) k_l2_scan_rows<<<p.C, 1024, 0, s>>>(p);
         else k_l2_scan<<<1, 1024, 0, s>>>(p);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        if (g.scatter)
-            k_l2_partition<W><<<part_grid, kThreads, sizeof(PartitionSmem) + kTile * W, s>>>(p, part_tpc, 0u);
-        else
-            k_l2_partition<0><<<part_grid, kThreads, sizeof(PartitionSmem), s>>>(p, part_tpc, smem_scatter ? 1u : 0u);
+        const size_t sm_part = sizeof(PartitionSmem) + (g.scatter ? size_t(kTile) * W : 0);
+        const uint32_t own = !g.scatter && smem_scatter ? 1u : 0u;
+        if (g.scatter && p.idx64) k_l2_partition<W, true><<<part_grid, kThreads, sm_part, s>>>(p, part_tpc, own);
+        else if (g.scatter) k_l2_partition<W, false><<<part_grid, kThreads, sm_part, s>>>(p, part_tpc, own);
+        else if (p.idx64) k_l2_partition<0, true><<<part_grid, kThreads, sm_part, s>>>(p, part_tpc, own);
+        else k_l2_partition<0, false><<<part_grid, kThreads, sm_part, s>>>(p, part_tpc, own);
         e = cudaGetLastError();
     }
     if (!g.scatter) {
