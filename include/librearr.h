@@ -371,12 +371,15 @@ typedef enum {
     REARR_KIND_TILE = 2,        /* shared-memory tiled transpose, 1 word/cell   */
     REARR_KIND_TILE_CELLS = 3,  /* tiled transpose of multi-word cells          */
     REARR_KIND_RUNS = 4,        /* copy of long contiguous runs                 */
-    REARR_KIND_STRIDED = 5      /* element-wise strided copy: a transpose plane
-                                   too small to fill tiles (by default under
-                                   1 KB of payload, or for ops up to 32 MiB
-                                   under 1024 cells, per tile on average), or
-                                   a box with no input-contiguous axis and
-                                   one-word cells                            */
+    REARR_KIND_STRIDED = 5,     /* element-wise strided copy: a transpose plane
+                                   too small to fill tiles (by the tuning
+                                   table's thin-plane rule) whose box (below)
+                                   would have short runs, or a box with no
+                                   input-contiguous axis and one-word cells  */
+    REARR_KIND_BOX = 6          /* a thin transpose plane staged as boxes of
+                                   several whole axes (Sec. III.B, generic
+                                   reorder): runs of tile_a cells read, runs of
+                                   tile_b cells written, one-word cells       */
 } rearr_kind;
 
 typedef struct {
@@ -387,8 +390,9 @@ typedef struct {
     int64_t cell_bytes;       /* bytes per cell after folding                    */
     int word_bytes;           /* access word size (power of two, <= 16)          */
     int plane_a;              /* output axis that is input-innermost (-1: none)  */
-    int vec_in, vec_out;      /* global access widths in bytes (TILE)            */
-    int tile_a, tile_b;       /* tile extents in cells (TILE, TILE_CELLS)        */
+    int vec_in, vec_out;      /* global access widths in bytes (TILE, BOX)       */
+    int tile_a, tile_b;       /* tile extents in cells (TILE, TILE_CELLS); BOX:
+                                 cells of an input run and of an output run     */
     int64_t n_tiles;          /* work units (tiles, runs or copy blocks)         */
     int wide_a, wide_b;       /* TILE on a short plane: the output axis whose
                                  planes the tile's A side (input rows) or B side
@@ -428,7 +432,9 @@ rearr_status rearr_tuning_load(const char *path);
  *   rearr_launch_count : number of kernels this library has launched in this
  *                        process (graph replays count the kernels they run).
  *   rearr_selftest_host: host-only checks of the plan compiler's integer
- *                        helpers; returns REARR_OK when they all pass.
+ *                        helpers, and box plans of pseudo-random permutes run
+ *                        on the host against the permute written out;
+ *                        returns REARR_OK when they all pass.
  * ------------------------------------------------------------------------- */
 rearr_status rearr_memcpy_d2d(void *dst, const void *src, size_t bytes, rearr_stream_t stream);
 uint64_t rearr_launch_count(void);

@@ -26,8 +26,10 @@ It measures, with CUDA events and the library's own kernels only:
 * the batched kernel's work grab (tiles taken per atomicAdd) on the 4096-op
   uneven mix, with the tile rules just measured;
 * the thin-plane threshold (average cells per tile below which a permute runs
-  as an element-wise strided copy) on the permutes of the whole mix, batched
-  and as single calls (the sum of both times is minimised);
+  as staged boxes of whole axes or an element-wise strided copy), then the
+  largest cell size that runs as boxes and the shortest box run worth it, on
+  the permutes of the whole mix, batched and as single calls (the sum of both
+  times is minimised);
 * the longest run (128, 256 or 512 bytes) that is faster walked in input
   order than in output order.
 
@@ -238,33 +240,65 @@ def tune_grab(rr, torch, stream, tmpdir, log, base_lines, n_ops=4096):
     return [f"min_grab {best[0]}", f"max_grab {best[0]}   # {nbytes / best[1] / 1e9:.0f} GB/s on the mix"]
 
 
-def tune_thin(rr, torch, stream, tmpdir, log, base_lines):
+def _mix_permutes(torch):
     import bench
     import synth
     ops = [o for o in synth.batch_mix(seed=1, n_ops=4096) if o["kind"] == "permute"]
     pool, bufs = bench.batch_buffers(torch, ops, torch.device("cuda"))
+    return ops, pool, bufs
+
+
+def _time_mix(rr, torch, stream, table, ops, bufs):
+    """(batched replay, one call per op) times of the mix's permutes under a table."""
+    import bench
+    rr.tuning_load(table)
+    plan = rr.Plan()
+    for o, p in zip(ops, bufs):
+        bench.add_to_plan(plan, o, p)
+    plan.finalize(stream)
+    tb = _time(torch, lambda: plan.run(stream), stream)
+    plan.close()
+
+    def plain():
+        for o, p in zip(ops, bufs):
+            rr.permute(p[1], p[0], o["elem_bytes"], o["dims"], o["perm"], stream)
+    tp = _time(torch, plain, stream, reps=3)
+    return tb, tp
+
+
+def tune_thin(rr, torch, stream, tmpdir, log, base_lines):
+    ops, pool, bufs = _mix_permutes(torch)
     best = None
     for cells in (256, 512, 1024, 2048, 4096):
         table = os.path.join(tmpdir, "thin.txt")
         _write(table, base_lines + [f"thin_tile_cells {cells}"])
-        rr.tuning_load(table)
-        plan = rr.Plan()
-        for o, p in zip(ops, bufs):
-            bench.add_to_plan(plan, o, p)
-        plan.finalize(stream)
-        tb = _time(torch, lambda: plan.run(stream), stream)
-        plan.close()
-
-        def plain():
-            for o, p in zip(ops, bufs):
-                rr.permute(p[1], p[0], o["elem_bytes"], o["dims"], o["perm"], stream)
-        tp = _time(torch, plain, stream, reps=3)
+        tb, tp = _time_mix(rr, torch, stream, table, ops, bufs)
         log(f"thin_tile_cells={cells:5d}: batched {tb * 1e3:7.3f} ms  single calls {tp * 1e3:7.3f} ms")
         if best is None or tb + tp < best[1]:
             best = (cells, tb + tp)
     rr.tuning_load(None)
     del pool
     return [f"thin_tile_cells {best[0]}"]
+
+
+def tune_box(rr, torch, stream, tmpdir, log, base_lines):
+    """Thin planes as staged boxes: the largest cell size that runs as boxes
+    (0: none) and the shortest run for which a box beats the strided copy,
+    on the mix's permutes (batched plus single calls)."""
+    ops, pool, bufs = _mix_permutes(torch)
+    best = None
+    for cell in (0, 1, 2, 4, 16):
+        for min_run in ((16,) if cell == 0 else (16, 64)):
+            table = os.path.join(tmpdir, "box.txt")
+            _write(table, base_lines + [f"box_max_cell_bytes {cell}", f"box_min_run_bytes {min_run}"])
+            tb, tp = _time_mix(rr, torch, stream, table, ops, bufs)
+            log(f"box_max_cell_bytes={cell:2d} box_min_run_bytes={min_run:3d}: batched {tb * 1e3:7.3f} ms  "
+                f"single calls {tp * 1e3:7.3f} ms")
+            if best is None or tb + tp < best[2]:
+                best = (cell, min_run, tb + tp)
+    rr.tuning_load(None)
+    del pool
+    return [f"box_max_cell_bytes {best[0]}", f"box_min_run_bytes {best[1]}"]
 
 
 def tune_runs_order(rr, torch, stream, tmpdir, log, base_lines):
@@ -318,12 +352,14 @@ def main():
         blocks = tune_runs_blocks(rr, torch, stream, tmp, log, base)
         base += blocks
         grab = tune_grab(rr, torch, stream, tmp, log, base)
-        thin = tune_thin(rr, torch, stream, tmp, log, base + [g.split("#")[0] for g in grab])
+        base += [g.split("#")[0] for g in grab]
+        thin = tune_thin(rr, torch, stream, tmp, log, base)
+        box = tune_box(rr, torch, stream, tmp, log, base + thin)
         runs = tune_runs_order(rr, torch, stream, tmp, log, base + ["runs_tile_max_bytes 1"])
     head = [f"# librearr tuning table for {torch.cuda.get_device_name()} "
             f"(paper_1011_3583_gb300/autotune.py, {time.time() - t0:.0f} s)"]
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
-    _write(args.out, head + grab + thin + runs + blocks + vec + rules + log_lines)
+    _write(args.out, head + grab + thin + box + runs + blocks + vec + rules + log_lines)
     print(f"wrote {args.out}: {len(rules)} tile rules")
 
 

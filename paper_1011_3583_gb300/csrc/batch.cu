@@ -93,6 +93,23 @@ __device__ __noinline__ void strided_range(const StridedDesc &d, uint64_t u0, ui
     for (uint64_t u = u0; u < u1; ++u) strided_body<W>(d, u);
 }
 
+template <int W, int NU>
+__device__ __noinline__ void box_range_nu(const BoxDesc &d, uint64_t u0, uint64_t u1, unsigned char *smem)
+{
+    for (uint64_t u = u0; u < u1; ++u) box_body<W, NU>(d, u, smem);
+}
+
+template <int W>
+__device__ __forceinline__ void box_range(const BoxDesc &d, uint64_t u0, uint64_t u1, unsigned char *smem)
+{
+    switch (d.nu) {
+        case 1: box_range_nu<W, 1>(d, u0, u1, smem); return;
+        case 2: box_range_nu<W, 2>(d, u0, u1, smem); return;
+        case 3: box_range_nu<W, 3>(d, u0, u1, smem); return;
+        default: box_range_nu<W, 4>(d, u0, u1, smem); return;
+    }
+}
+
 template <int W>
 __device__ __noinline__ void gather_range(const GatherDesc &d, uint64_t u0, uint64_t u1)
 {
@@ -140,6 +157,7 @@ __device__ __forceinline__ void run_word_class(const OpDesc &d, uint64_t u0, uin
         case OC_RUNS: runs_range<W>(d.runs, u0, u1, smem); return;
         case OC_COPY: copy_range<W>(d.copy, u0, u1); return;
         case OC_STRIDED: strided_range<W>(d.strided, u0, u1); return;
+        case OC_BOX: box_range<W>(d.box, u0, u1, smem); return;
         case OC_GATHER: gather_range<W>(d.gather, u0, u1); return;
         case OC_INTERLACE: igen_range<W>(d.inter, u0, u1, true); return;
         case OC_DEINTERLACE: igen_range<W>(d.inter, u0, u1, false); return;

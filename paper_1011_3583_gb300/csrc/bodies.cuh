@@ -839,6 +839,189 @@ __device__ __forceinline__ void strided_body(const StridedDesc &d, uint64_t unit
     }
 }
 
+// Box permute (OC_BOX): one unit is the sub-box U of its unit index (see
+// BoxDesc).  Every full unit has the same shape, so a thread visits the same
+// cells of each: its first cell's digits (U in input order for the loads, in
+// output order for the stores) come from one decomposition, and each next
+// cell of the thread (kThreads loads or stores further on) from adding the
+// digits of that stride with carries -- no division per cell.
+// Load phase: VL bytes per load (a load never spans two runs of the input
+// chain), stored densely in input order in shared memory.  Store phase:
+// V = VO / E consecutive cells of an output run per thread, each read from its
+// shared-memory slot (stepping the output digits like an odometer), written
+// with one VO-byte store.  Cells whose partial-axis index is past the axis'
+// end (its last range) are neither read nor written; that unit moves single
+// cells on both sides.
+
+// Digits of n over the first NU extents (fastest first).
+template <int NU>
+__device__ __forceinline__ void box_digits(uint32_t n, const FastDiv *ext, uint32_t (&dig)[NU])
+{
+#pragma unroll
+    for (int i = 0; i < NU; ++i) fdivmod(n, ext[i], n, dig[i]);
+}
+
+// dig += step in the mixed radix of the extents (every step digit is below
+// its extent, so each digit wraps at most once).
+template <int NU>
+__device__ __forceinline__ void box_advance(uint32_t (&dig)[NU], const uint32_t (&step)[NU], const uint32_t (&ext)[NU])
+{
+    uint32_t carry = 0;
+#pragma unroll
+    for (int i = 0; i < NU; ++i) {
+        const uint32_t v = dig[i] + step[i] + carry;
+        carry = v >= ext[i];
+        dig[i] = carry ? v - ext[i] : v;
+    }
+}
+
+template <int E, int VL, int NU>
+__device__ __forceinline__ void box_load(const BoxDesc &d, const char *in, uint32_t keff, unsigned char *smem)
+{
+    constexpr int B = VL >= 8 ? 4 : 8;  // loads in flight per thread (a unit is at most 4 16-byte loads per thread)
+    constexpr uint32_t CV = VL / E;     // cells per load
+    const uint32_t cells = d.cells;
+    const uint32_t c0 = uint32_t(tid_x()) * CV;
+    uint32_t dig[NU], step[NU], ext[NU];
+    box_digits<NU>(c0, d.iext, dig);
+    box_digits<NU>(uint32_t(kThreads) * CV, d.iext, step);
+#pragma unroll
+    for (int i = 0; i < NU; ++i) ext[i] = d.iext[i].d;
+    for (uint32_t c = c0; c < cells; c += uint32_t(kThreads) * CV * B) {
+        typename Word<VL>::T r[B];
+        bool ok[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const uint32_t cj = c + uint32_t(j) * kThreads * CV;
+            ok[j] = false;
+            if (cj < cells) {
+                int64_t off = 0;
+                uint32_t kd = 0;
+#pragma unroll
+                for (int i = 0; i < NU; ++i) {
+                    off += int64_t(dig[i]) * d.iin[i];
+                    if (i == d.kin) kd = dig[i];
+                }
+                if (kd < keff) {
+                    r[j] = ldg_stream<VL>(in + off);
+                    ok[j] = true;
+                }
+                box_advance<NU>(dig, step, ext);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < B; ++j)
+            if (ok[j]) sts<VL>(smem + (c + uint32_t(j) * kThreads * CV) * E, r[j]);
+    }
+}
+
+template <int E, int VO, int NU>
+__device__ __forceinline__ void box_store(const BoxDesc &d, char *out, uint32_t keff, const unsigned char *smem)
+{
+    constexpr int V = VO / E;
+    const uint32_t cells = d.cells;
+    const uint32_t y0 = uint32_t(tid_x()) * V;
+    uint32_t dig[NU], step[NU], ext[NU], sms[NU];
+    box_digits<NU>(y0, d.oext, dig);
+    box_digits<NU>(uint32_t(kThreads) * V, d.oext, step);
+#pragma unroll
+    for (int i = 0; i < NU; ++i) {
+        ext[i] = d.oext[i].d;
+        sms[i] = d.osm[i];
+    }
+    for (uint32_t y = y0; y < cells; y += uint32_t(kThreads) * V) {
+        uint32_t sm = 0, kd = 0;
+        int64_t off = 0;
+#pragma unroll
+        for (int i = 0; i < NU; ++i) {
+            sm += dig[i] * sms[i];
+            off += int64_t(dig[i]) * d.oout[i];
+            if (i == d.kout) kd = dig[i];
+        }
+        if (kd < keff) {
+            union {
+                typename Word<VO>::T v;
+                typename Word<E>::T e[V];
+            } u;
+            uint32_t dd[NU];
+#pragma unroll
+            for (int i = 0; i < NU; ++i) dd[i] = dig[i];
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                u.e[k] = lds<E>(smem + sm);
+                if (k + 1 < V) {
+#pragma unroll
+                    for (int i = 0; i < NU; ++i) {
+                        sm += sms[i];
+                        if (++dd[i] < ext[i]) break;
+                        sm -= ext[i] * sms[i];
+                        dd[i] = 0;
+                    }
+                }
+            }
+            stg<VO>(out + off, u.v);
+        }
+        box_advance<NU>(dig, step, ext);
+    }
+}
+
+template <int E, int NU>
+__device__ __forceinline__ void box_phases(const BoxDesc &d, const char *in, char *out, uint32_t keff,
+                                           unsigned char *smem)
+{
+    // the partial axis' last range: single cells (a wider access could cross its end)
+    const uint32_t vin = keff < d.K ? uint32_t(E) : d.vin, vout = keff < d.K ? uint32_t(E) : d.vout;
+    switch (vin) {
+        case 16: box_load<E, 16, NU>(d, in, keff, smem); break;
+        case 8: if constexpr (E <= 8) box_load<E, 8, NU>(d, in, keff, smem); break;
+        case 4: if constexpr (E <= 4) box_load<E, 4, NU>(d, in, keff, smem); break;
+        case 2: if constexpr (E <= 2) box_load<E, 2, NU>(d, in, keff, smem); break;
+        default: if constexpr (E == 1) box_load<E, 1, NU>(d, in, keff, smem); break;
+    }
+    __syncthreads();
+    switch (vout) {
+        case 16: box_store<E, 16, NU>(d, out, keff, smem); break;
+        case 8: if constexpr (E <= 8) box_store<E, 8, NU>(d, out, keff, smem); break;
+        case 4: if constexpr (E <= 4) box_store<E, 4, NU>(d, out, keff, smem); break;
+        case 2: if constexpr (E <= 2) box_store<E, 2, NU>(d, out, keff, smem); break;
+        default: if constexpr (E == 1) box_store<E, 1, NU>(d, out, keff, smem); break;
+    }
+    __syncthreads();
+}
+
+// Input / output offsets of a unit and its partial-axis extent.  Not inlined:
+// inlined into a kernel's unit loop, the descriptor fields it reads would be
+// hoisted out of that loop and held in registers across both phases.
+struct BoxUnit {
+    int64_t in, out;
+    uint32_t keff;
+};
+
+static __device__ __noinline__ BoxUnit box_unit(const BoxDesc &d, uint32_t q)
+{
+    BoxUnit b{0, 0, d.K};
+#pragma unroll
+    for (int i = kMaxBoxOuter - 1; i >= 0; --i) {
+        if (i < d.no) {
+            uint32_t dig;
+            fdivmod(q, d.udiv[i], q, dig);
+            b.in += int64_t(dig) * d.uin[i];
+            b.out += int64_t(dig) * d.uout[i];
+            if (i == d.kunit) b.keff = min(d.K, d.kfull - dig * d.K);
+        }
+    }
+    return b;
+}
+
+// One unit of a box permute with NU axes in the box (one kernel per (E, NU):
+// the phases' register needs grow with NU).
+template <int E, int NU>
+__device__ __forceinline__ void box_body(const BoxDesc &d, uint64_t unit, unsigned char *smem)
+{
+    const BoxUnit b = box_unit(d, uint32_t(unit));
+    box_phases<E, NU>(d, d.src + b.in, d.dst + b.out, b.keff, smem);
+}
+
 // Fast interlace / de-interlace.  A warp handles 32 consecutive 16-byte groups
 // per step, one per lane, reading (interlace) or writing (de-interlace) one
 // 16-byte vector per plane per lane -- 512 contiguous bytes per instruction on

@@ -82,6 +82,14 @@ __global__ void __launch_bounds__(kThreads) k_strided(const __grid_constant__ St
     for (uint64_t u = blockIdx.x; u < n; u += gridDim.x) strided_body<W>(d, u);
 }
 
+template <int W, int NU>
+__global__ void __launch_bounds__(kThreads, 3) k_box(const __grid_constant__ BoxDesc d, uint32_t n)
+{
+    pdl_enter();
+    __shared__ __align__(16) unsigned char smem[kBoxBytes];
+    for (uint32_t u = blockIdx.x; u < n; u += gridDim.x) box_body<W, NU>(d, u, smem);
+}
+
 // Interlace kernels take every plane pointer by value.
 struct InterlaceParams {
     InterlaceDesc d;
@@ -188,6 +196,18 @@ template <int W> struct RunStrided {
         return go(k_strided<W>, op.units, op.strided, op.units, s);
     }
 };
+template <int W> struct RunBox {
+    static cudaError_t run(const OpDesc &op, cudaStream_t s)
+    {
+        switch (op.box.nu) {
+            case 1: return go(k_box<W, 1>, op.units, op.box, uint32_t(op.units), s);
+            case 2: return go(k_box<W, 2>, op.units, op.box, uint32_t(op.units), s);
+            case 3: return go(k_box<W, 3>, op.units, op.box, uint32_t(op.units), s);
+            case 4: return go(k_box<W, 4>, op.units, op.box, uint32_t(op.units), s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+};
 template <int W> struct RunGather {
     static cudaError_t run(const OpDesc &op, cudaStream_t s)
     {
@@ -245,6 +265,7 @@ cudaError_t launch_single(const OpDesc &op, char *const *planes_all, cudaStream_
         case OC_RUNS: return by_word<RunRuns>(int(op.word), op, s);
         case OC_COPY: return by_word<RunCopy>(int(op.word), op, s);
         case OC_STRIDED: return by_word<RunStrided>(int(op.word), op, s);
+        case OC_BOX: return by_word<RunBox>(int(op.word), op, s);
         case OC_GATHER:
             if (op.gather.l2) return launch_reorder_l2(op, s);
             return by_word<RunGather>(int(op.word), op, s);

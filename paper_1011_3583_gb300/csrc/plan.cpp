@@ -188,6 +188,175 @@ static void fill_tile_common(TileDesc &t, const std::vector<Axis> &ax, int p, in
     t.nb = nb;
 }
 
+// Box plan of a thin-plane permute with cells of one aligned E-byte word (see
+// BoxDesc).  The unit's sub-box U grows from the input-innermost and the
+// output-innermost axes: each step takes the axis that continues the shorter
+// of the two runs (the input chain's next axis has an input stride equal to
+// the chain's length, the output chain's an output stride equal to its),
+// else the other side's, whole while the unit fits kBoxBytes.  When neither
+// fits whole, the first becomes the partial axis over K indices (the last
+// step).  Growth stops once both runs reach box_run_bytes() and the unit holds
+// half a tile.  False when the box needs more axes than the descriptor holds,
+// a run stays shorter than box_min_run_bytes(), or its stores would be
+// narrower than 4 bytes.
+static bool plan_box(const std::vector<Axis> &ax, int64_t E, uintptr_t da, uintptr_t sa, char *dst,
+                     const char *src, OpDesc &op, rearr_permute_info &info)
+{
+    const int R = int(ax.size());
+    std::vector<int64_t> os(R);  // output strides in bytes
+    os[R - 1] = E;
+    for (int i = R - 2; i >= 0; --i) os[i] = os[i + 1] * ax[i + 1].extent;
+    const int64_t cap = kBoxBytes / E;
+    std::vector<int> U;
+    int kax = -1;
+    int64_t K = 1, prod = 1;
+    auto in_u = [&](int i) { return std::find(U.begin(), U.end(), i) != U.end(); };
+    // One side's chain: its run in bytes, the axes on it and the next axis (-1: none).
+    auto chain = [&](bool input, int64_t &run, std::vector<int> &on, int &next) {
+        run = E;
+        on.clear();
+        next = -1;
+        for (;;) {
+            int hit = -1;
+            for (int i = 0; i < R; ++i)
+                if ((input ? ax[i].stride : os[i]) == run) hit = i;
+            if (hit < 0) return;
+            if (!in_u(hit)) {
+                next = hit;
+                return;
+            }
+            on.push_back(hit);
+            if (hit == kax) {
+                run *= K;
+                return;
+            }
+            run *= ax[hit].extent;
+        }
+    };
+    int64_t rin = E, rout = E;
+    std::vector<int> on_in, on_out;
+    const int64_t target = int64_t(box_run_bytes());
+    for (;;) {
+        int nin, nout;
+        chain(true, rin, on_in, nin);
+        chain(false, rout, on_out, nout);
+        if (kax >= 0 || int(U.size()) == kMaxBoxAxes) break;
+        if (rin >= target && rout >= target && 2 * prod * E >= kBoxBytes) break;
+        const int first = rin <= rout ? (nin >= 0 ? nin : nout) : (nout >= 0 ? nout : nin);
+        const int second = first == nin ? nout : nin;
+        if (first < 0) break;
+        if (prod * ax[first].extent <= cap) {
+            U.push_back(first);
+            prod *= ax[first].extent;
+            continue;
+        }
+        if (second >= 0 && prod * ax[second].extent <= cap) {
+            U.push_back(second);
+            prod *= ax[second].extent;
+            continue;
+        }
+        int64_t k = cap / prod;
+        // range starts stay 16-byte aligned on both sides where K allows
+        const int64_t m = std::max(16 / std::min<int64_t>(16, ax[first].stride & -ax[first].stride),
+                                   16 / std::min<int64_t>(16, os[first] & -os[first]));
+        if (k >= 2 * m) k -= k % m;
+        if (k < 2) break;
+        U.push_back(first);
+        kax = first;
+        K = k;
+        prod *= k;
+    }
+    if (rin < int64_t(box_min_run_bytes()) || rout < int64_t(box_min_run_bytes())) return false;
+    // unit-index axes: the others in output order, the partial axis as its range index
+    struct Slot {
+        int64_t ext, in, out;
+    };
+    std::vector<Slot> outer;
+    int kunit = -1;
+    for (int i = 0; i < R; ++i) {
+        if (i == kax) {
+            kunit = int(outer.size());
+            outer.push_back({(ax[i].extent + K - 1) / K, K * ax[i].stride, K * os[i]});
+        } else if (!in_u(i)) {
+            outer.push_back({ax[i].extent, ax[i].stride, os[i]});
+        }
+    }
+    if (int(outer.size()) > kMaxBoxOuter) return false;
+    uint64_t units = 1;
+    for (const Slot &o : outer) units *= uint64_t(o.ext);
+    if (units >= kMaxUnits) return false;
+    // widest loads / stores: within a run, and every run start aligned
+    auto width = [&](bool input) {
+        const std::vector<int> &on = input ? on_in : on_out;
+        uint64_t bits = uint64_t(input ? rin : rout) | uint64_t(input ? sa : da) | 16;
+        for (int i : U)
+            if (std::find(on.begin(), on.end(), i) == on.end()) bits |= uint64_t(input ? ax[i].stride : os[i]);
+        for (const Slot &o : outer) bits |= uint64_t(input ? o.in : o.out);
+        const uint64_t v = bits & (~bits + 1);
+        return uint32_t(std::max<uint64_t>(v, uint64_t(E)));
+    };
+    BoxDesc b;
+    std::memset(&b, 0, sizeof(b));
+    b.dst = dst;
+    b.src = src;
+    std::vector<int> by_in = U, by_out = U;
+    std::sort(by_in.begin(), by_in.end(), [&](int x, int y) { return ax[x].stride < ax[y].stride; });
+    std::sort(by_out.begin(), by_out.end(), [&](int x, int y) { return os[x] < os[y]; });
+    const int nu = int(U.size());
+    std::vector<int64_t> sm(R, 0);  // shared-memory strides, dense in input order
+    int64_t acc = E;
+    for (int j = 0; j < nu; ++j) {
+        const int i = by_in[j];
+        const int64_t ext = i == kax ? K : ax[i].extent;
+        b.iext[j] = make_fastdiv(uint32_t(ext));
+        b.iin[j] = ax[i].stride;
+        sm[i] = acc;
+        acc *= ext;
+    }
+    for (int j = 0; j < nu; ++j) {
+        const int i = by_out[j];
+        b.oext[j] = make_fastdiv(uint32_t(i == kax ? K : ax[i].extent));
+        b.oout[j] = os[i];
+        b.osm[j] = uint32_t(sm[i]);
+    }
+    for (int j = nu; j < kMaxBoxAxes; ++j) b.iext[j] = b.oext[j] = make_fastdiv(1);
+    const int no = int(outer.size());
+    for (int j = 0; j < kMaxBoxOuter; ++j) {
+        b.udiv[j] = make_fastdiv(j < no ? uint32_t(outer[j].ext) : 1u);
+        b.uin[j] = j < no ? outer[j].in : 0;
+        b.uout[j] = j < no ? outer[j].out : 0;
+    }
+    b.nu = int8_t(nu);
+    b.no = int8_t(no);
+    b.kin = b.kout = -1;
+    for (int j = 0; j < nu; ++j) {
+        if (by_in[j] == kax) b.kin = int8_t(j);
+        if (by_out[j] == kax) b.kout = int8_t(j);
+    }
+    b.kunit = int8_t(kunit);
+    b.K = uint32_t(K);
+    b.kfull = uint32_t(kax >= 0 ? ax[kax].extent : 1);
+    b.vin = width(true);
+    b.vout = width(false);
+    // byte or 2-byte stores of short cells: the strided copy writes its
+    // contiguous output 16 bytes at a time instead
+    if (b.vout < 4) return false;
+    b.cells = uint32_t(prod);
+    op.cls = OC_BOX;
+    op.word = uint32_t(E);
+    op.box = b;
+    op.units = units;
+    info.kind = REARR_KIND_BOX;
+    info.word_bytes = int(E);
+    info.tile_a = int(rin / E);
+    info.tile_b = int(rout / E);
+    info.vec_in = int(b.vin);
+    info.vec_out = int(b.vout);
+    info.wide_a = info.wide_b = -1;
+    info.n_tiles = int64_t(units);
+    return true;
+}
+
 // Plans a gather of `total` elements of elem_bytes whose output axes are
 // given in order (slowest first) with their input byte strides; src already
 // points at the element of output index 0.  The output is contiguous.
@@ -502,7 +671,9 @@ static rearr_status plan_axes(void *dst, const char *src, size_t elem_bytes, con
     const ThinTuning thin = thin_tuning();
     const bool thin_plane = bytes < op.units * thin.tile_bytes ||
                             (bytes <= thin.l2_bytes && n_cells < op.units * thin.tile_cells);
-    if (W == cell && thin_plane && n_cells < kMaxUnits) set_strided(W, n_cells);
+    if (W == cell && thin_plane && n_cells < kMaxUnits &&
+        !(uint64_t(cell) <= box_max_cell_bytes() && plan_box(ax, cell, da, sa, static_cast<char *>(dst), src, op, info)))
+        set_strided(W, n_cells);
     return REARR_OK;
 }
 
@@ -738,6 +909,182 @@ void tile_to_single_width(OpDesc &op)
     op.units = ta_tiles * tb_tiles * batch;
 }
 
+// Host run of a box descriptor over the cells the device body visits
+// (box_body), checking what the body relies on: every load and store inside
+// its buffer and aligned to its width, the cells of one load (store)
+// consecutive in the input (output) and inside the partial axis' range, every
+// shared-memory access inside the unit, and the odometer's slot equal to the
+// one decomposed from the cell's index.  Shared memory is poisoned before
+// each unit.
+static bool box_emulate(const OpDesc &op, const char *src0, size_t src_bytes, char *dst0, size_t dst_bytes, int E,
+                        std::string &err)
+{
+    const BoxDesc &d = op.box;
+    std::vector<unsigned char> smem(kBoxBytes);
+    auto in_cell = [&](uint32_t c, int64_t &off, uint32_t &kd) {
+        off = 0;
+        kd = 0;
+        for (int i = 0; i < d.nu; ++i) {
+            uint32_t dig;
+            fdivmod(c, d.iext[i], c, dig);
+            off += int64_t(dig) * d.iin[i];
+            if (i == d.kin) kd = dig;
+        }
+    };
+    auto out_cell = [&](uint32_t c, uint32_t *dig, uint32_t &sm, int64_t &off, uint32_t &kd) {
+        sm = 0;
+        off = 0;
+        kd = 0;
+        for (int i = 0; i < d.nu; ++i) {
+            fdivmod(c, d.oext[i], c, dig[i]);
+            sm += dig[i] * d.osm[i];
+            off += int64_t(dig[i]) * d.oout[i];
+            if (i == d.kout) kd = dig[i];
+        }
+    };
+    if (uint64_t(d.cells) * E > uint64_t(kBoxBytes)) { err = "box unit larger than its shared memory"; return false; }
+    for (uint64_t unit = 0; unit < op.units; ++unit) {
+        std::memset(smem.data(), 0xCD, smem.size());
+        uint32_t q = uint32_t(unit), keff = d.K;
+        int64_t bin = 0, bout = 0;
+        for (int i = d.no - 1; i >= 0; --i) {
+            uint32_t dig;
+            fdivmod(q, d.udiv[i], q, dig);
+            bin += int64_t(dig) * d.uin[i];
+            bout += int64_t(dig) * d.uout[i];
+            if (i == d.kunit) keff = std::min(d.K, d.kfull - dig * d.K);
+        }
+        const uint32_t vin = keff < d.K ? uint32_t(E) : d.vin, vout = keff < d.K ? uint32_t(E) : d.vout;
+        for (uint32_t x = 0; x < d.cells * uint32_t(E); x += vin) {
+            int64_t off;
+            uint32_t kd;
+            in_cell(x / E, off, kd);
+            if (kd >= keff) continue;
+            const char *g = d.src + bin + off;
+            if (uintptr_t(g) % vin) { err = "box load misaligned"; return false; }
+            if (g < src0 || g + vin > src0 + src_bytes) { err = "box load outside the source"; return false; }
+            for (uint32_t k = 1; k < vin / uint32_t(E); ++k) {
+                int64_t o2;
+                uint32_t k2;
+                in_cell(x / E + k, o2, k2);
+                if (o2 != off + int64_t(k) * E || k2 >= keff) { err = "box load spans two runs"; return false; }
+            }
+            std::memcpy(&smem[x], g, vin);
+        }
+        const uint32_t V = vout / uint32_t(E);
+        for (uint32_t y = 0; y < d.cells; y += V) {
+            uint32_t dig[kMaxBoxAxes], sm, kd;
+            int64_t off;
+            out_cell(y, dig, sm, off, kd);
+            if (kd >= keff) continue;
+            char *g = d.dst + bout + off;
+            if (uintptr_t(g) % vout) { err = "box store misaligned"; return false; }
+            if (g < dst0 || g + vout > dst0 + dst_bytes) { err = "box store outside the destination"; return false; }
+            for (uint32_t k = 0; k < V; ++k) {
+                uint32_t dig2[kMaxBoxAxes], sm2, kd2;
+                int64_t off2;
+                out_cell(y + k, dig2, sm2, off2, kd2);
+                if (sm2 != sm || off2 != off + int64_t(k) * E || kd2 >= keff) { err = "box store spans two runs"; return false; }
+                if (uint64_t(sm) + E > uint64_t(d.cells) * E) { err = "box slot outside the unit"; return false; }
+                std::memcpy(g + k * E, &smem[sm], E);
+                for (int i = 0; i < d.nu; ++i) {  // the device body's odometer step
+                    sm += d.osm[i];
+                    if (++dig[i] < d.oext[i].d) break;
+                    sm -= d.oext[i].d * d.osm[i];
+                    dig[i] = 0;
+                }
+            }
+        }
+    }
+    return true;
+}
+
+// Box plans of pseudo-random permutes (ranks 2-6, extents up to a few
+// thousand, cells of 1-16 bytes, aligned and unaligned pointers) run on the
+// host by box_emulate and compared with the permute written out directly.
+static bool selftest_box(std::string &err)
+{
+    uint64_t x = 0x2545F4914F6CDD1Dull;
+    auto rnd = [&](uint64_t n) {
+        x ^= x << 13; x ^= x >> 7; x ^= x << 17;
+        return x % n;
+    };
+    int boxes = 0, partial = 0;
+    for (int t = 0; t < 2000 && boxes < 300; ++t) {
+        const int rank = 2 + int(rnd(5));
+        const int E = 1 << rnd(5);
+        int64_t dims[kMaxRank];
+        uint64_t total = 1;
+        for (int i = 0; i < rank; ++i) {
+            dims[i] = rnd(4) == 0 ? 1 + int64_t(rnd(3000)) : 1 + int64_t(rnd(rnd(2) ? 12 : 60));
+            total *= uint64_t(dims[i]);
+        }
+        if (total > (uint64_t(1) << 17) || total < 2) continue;
+        int perm[kMaxRank];
+        for (int i = 0; i < rank; ++i) perm[i] = i;
+        for (int i = rank - 1; i > 0; --i) std::swap(perm[i], perm[rnd(uint64_t(i) + 1)]);
+        const size_t bytes = size_t(total) * E;
+        const int so = rnd(3) == 0 ? E : 0, dof = rnd(3) == 0 ? E : 0;
+        std::vector<char> sbuf(bytes + 64), dbuf(bytes + 64), want(bytes);
+        char *src = sbuf.data() + ((16 - uintptr_t(sbuf.data()) % 16) % 16) + so;
+        char *dst = dbuf.data() + ((16 - uintptr_t(dbuf.data()) % 16) % 16) + dof;
+        for (size_t i = 0; i < bytes; ++i) src[i] = char(rnd(256));
+        // the permute written out: output cell o (row-major over dims[perm])
+        int64_t s[kMaxRank];
+        s[rank - 1] = E;
+        for (int i = rank - 2; i >= 0; --i) s[i] = s[i + 1] * dims[i + 1];
+        for (uint64_t o = 0; o < total; ++o) {
+            uint64_t r = o;
+            int64_t in = 0;
+            for (int i = rank - 1; i >= 0; --i) {
+                const int64_t ext = dims[perm[i]];
+                in += int64_t(r % uint64_t(ext)) * s[perm[i]];
+                r /= uint64_t(ext);
+            }
+            std::memcpy(&want[o * E], src + in, E);
+        }
+        // canonical axes as plan_axes forms them
+        std::vector<Axis> ax;
+        for (int i = 0; i < rank; ++i) {
+            const Axis cur{dims[perm[i]], s[perm[i]]};
+            if (cur.extent == 1) continue;
+            if (!ax.empty() && ax.back().stride == cur.stride * cur.extent) {
+                ax.back().extent *= cur.extent;
+                ax.back().stride = cur.stride;
+            } else {
+                ax.push_back(cur);
+            }
+        }
+        if (ax.size() < 2 || ax.back().stride == E) continue;  // a copy or an unmoved inner axis
+        bool has_a = false;
+        for (const Axis &a : ax) has_a |= a.stride == E;
+        if (!has_a) continue;
+        OpDesc op;
+        std::memset(&op, 0, sizeof(op));
+        rearr_permute_info info;
+        std::memset(&info, 0, sizeof(info));
+        if (!plan_box(ax, E, uintptr_t(dst), uintptr_t(src), dst, src, op, info)) continue;
+        ++boxes;
+        partial += op.box.kunit >= 0;
+        std::memset(dst, 0, bytes);
+        if (!box_emulate(op, src, bytes, dst, bytes, E, err)) return false;
+        if (std::memcmp(dst, want.data(), bytes) != 0) {
+            char buf[160];
+            std::snprintf(buf, sizeof buf, "box plan of a rank-%d permute of %d-byte cells differs from the permute",
+                          rank, E);
+            err = buf;
+            return false;
+        }
+    }
+    if (boxes < 100 || partial < 10) {
+        char buf[96];
+        std::snprintf(buf, sizeof buf, "box self-test planned only %d boxes (%d partial)", boxes, partial);
+        err = buf;
+        return false;
+    }
+    return true;
+}
+
 bool selftest_host(std::string &err)
 {
     // Fast division against the hardware divide on divisors and dividends
@@ -791,7 +1138,7 @@ bool selftest_host(std::string &err)
         err = "pow2_align";
         return false;
     }
-    return true;
+    return selftest_box(err);
 }
 
 }  // namespace rearr

@@ -87,7 +87,8 @@ enum OpClass : uint32_t {
     OC_INTERLACE = 5,    // dst[i*k+j] = src_j[i]
     OC_DEINTERLACE = 6,  // dst_j[i] = src[i*k+j]
     OC_STRIDED = 7,      // element-wise strided copy (permutes of thin planes)
-    OC_COUNT = 8
+    OC_BOX = 8,          // staged box of several whole axes (permutes of thin planes)
+    OC_COUNT = 9
 };
 
 // Plane of a tiled transpose: A = input-innermost axis (input stride one
@@ -177,6 +178,37 @@ struct StridedDesc {
     uint64_t n_cells;
 };
 
+// Box permute: a work unit is a sub-box U of the index space -- a few whole
+// axes, and at most one more axis (the partial axis) over a range of K
+// indices -- that fits one shared-memory tile.  U is read in input order:
+// its axes sorted by input stride, the first ones (the input chain) dense in
+// the input, so the unit's input is runs of chain cells copied vin bytes at a
+// time into shared memory laid out densely in that order.  It is written in
+// output order: runs along the output chain, vout bytes per store, each cell
+// read from shared memory.  The remaining axes (and the partial axis' range
+// index) make up the unit index.  Strides are in bytes.
+constexpr int kMaxBoxAxes = 4;
+constexpr int kMaxBoxOuter = 4;
+constexpr int kBoxBytes = 16384;  // shared memory of a box unit
+
+struct BoxDesc {
+    char *dst;
+    const char *src;
+    FastDiv iext[kMaxBoxAxes];      // U extents in input order, fastest first (K for the partial axis)
+    int64_t iin[kMaxBoxAxes];       // their input strides
+    FastDiv oext[kMaxBoxAxes];      // U extents in output order, fastest first
+    int64_t oout[kMaxBoxAxes];      // their output strides
+    uint32_t osm[kMaxBoxAxes];      // their strides in shared memory (dense in input order)
+    FastDiv udiv[kMaxBoxOuter];     // unit index digits: extents of the other axes, innermost last
+    int64_t uin[kMaxBoxOuter], uout[kMaxBoxOuter];
+    int8_t nu, no;                  // U axes, unit-index axes
+    int8_t kin, kout;               // slot of the partial axis in input / output order (-1: none)
+    int8_t kunit;                   // slot of its range index among the unit-index axes (-1: none)
+    uint32_t K, kfull;              // partial axis: indices per unit (1: none), full extent
+    uint32_t vin, vout;             // load / store widths in bytes (multiples of the cell)
+    uint32_t cells;                 // cells per unit (product of the U extents)
+};
+
 struct InterlaceDesc {
     char *inter;                       // interlaced array (dst of interlace, src of de-interlace)
     char *planes[kInlineK];            // plane pointers when k <= kInlineK
@@ -202,8 +234,10 @@ struct OpDesc {
         GatherDesc gather;
         InterlaceDesc inter;
         StridedDesc strided;
+        BoxDesc box;
     };
 };
+static_assert(sizeof(BoxDesc) <= sizeof(TileDesc), "the box descriptor must not grow the work list");
 
 // Fast-tile variant ids: E in {1,2,4,8,16} x VIN x VOUT x staged row bytes x
 // tile payload bytes.

@@ -15,6 +15,12 @@
 //   wide_bytes <v>          (fast-tile plane sides shorter than v bytes are
 //                            widened over the axis that continues them; 1: never)
 //   reorder_smem_buckets <v> (bucket bound of the shared-memory scatter; 1: never)
+//   box_min_run_bytes <v>   (thin planes run as staged boxes when both runs of
+//                            the box reach v bytes, else as strided copies;
+//                            a v above 16 KB: never)
+//   box_run_bytes <v>       (a box stops growing once both runs reach v bytes
+//                            and it holds half a tile)
+//   box_max_cell_bytes <v>  (boxes only for cells of at most v bytes; 0: never)
 //   rowb <E> <da_lo> <da_hi> <db_lo> <db_hi> <rowb> [<tile bytes> [<wide>]]
 //                           (wide 1: the rule applies to widened planes, keyed
 //                            by their extents before widening; 0: to the others)
@@ -55,6 +61,9 @@ struct Table {
     uint64_t runs_tile_side_bytes = 2048;
     uint64_t tile_vector_bytes = 16;
     uint64_t reorder_smem_buckets = uint64_t(1) << 22;
+    uint64_t box_min_run_bytes = 16;
+    uint64_t box_run_bytes = 512;
+    uint64_t box_max_cell_bytes = 2;
     std::vector<RowbRule> rowb;
 };
 
@@ -81,6 +90,8 @@ std::shared_ptr<const Table> parse(const char *path)
             const bool ok_tb = r.tbytes == 16384 || (r.tbytes == 8192 && r.rowb == 128) ||
                                (r.tbytes == 32768 && double_tile_ok(r.E, r.rowb));
             if (ok_rowb && ok_tb && (r.wide == 0 || r.wide == 1)) t->rowb.push_back(r);
+        } else if (std::sscanf(line, "%31s %lu", key, &v) == 2 && !std::strcmp(key, "box_max_cell_bytes")) {
+            t->box_max_cell_bytes = v;
         } else if (std::sscanf(line, "%31s %lu", key, &v) == 2 && v >= 1) {
             if (!std::strcmp(key, "min_grab")) t->batch.min_grab = uint32_t(v);
             else if (!std::strcmp(key, "max_grab")) t->batch.max_grab = uint32_t(v);
@@ -96,6 +107,8 @@ std::shared_ptr<const Table> parse(const char *path)
             else if (!std::strcmp(key, "runs_tile_side_bytes")) t->runs_tile_side_bytes = v;
             else if (!std::strcmp(key, "tile_vector_bytes")) t->tile_vector_bytes = v < 16 ? 4 : 16;
             else if (!std::strcmp(key, "reorder_smem_buckets")) t->reorder_smem_buckets = v;
+            else if (!std::strcmp(key, "box_min_run_bytes")) t->box_min_run_bytes = v;
+            else if (!std::strcmp(key, "box_run_bytes")) t->box_run_bytes = v;
         }
     }
     std::fclose(f);
@@ -138,6 +151,12 @@ uint64_t runs_tile_side_bytes() { return current()->runs_tile_side_bytes; }
 int tile_vector_bytes() { return int(current()->tile_vector_bytes); }
 
 uint64_t reorder_smem_max_buckets() { return current()->reorder_smem_buckets; }
+
+uint64_t box_min_run_bytes() { return current()->box_min_run_bytes; }
+
+uint64_t box_run_bytes() { return current()->box_run_bytes; }
+
+uint64_t box_max_cell_bytes() { return current()->box_max_cell_bytes; }
 
 bool tuned_shape(int E, int64_t DA, int64_t DB, bool wide, TileShape &shape)
 {

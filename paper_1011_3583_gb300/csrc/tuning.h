@@ -68,6 +68,14 @@ uint64_t double_tile_min_bytes();
 // most this; above it (or at 1) it scatters through ~16 MB chunks in the L2.
 uint64_t reorder_smem_max_buckets();
 
+// Thin planes of cells of at most box_max_cell_bytes() (0: none) run as
+// staged boxes (OC_BOX) when the box's input and output runs both reach
+// box_min_run_bytes(), else as strided copies.  A box grows until both runs
+// reach box_run_bytes() and it holds half a tile.
+uint64_t box_min_run_bytes();
+uint64_t box_run_bytes();
+uint64_t box_max_cell_bytes();
+
 // Shape of a fast tile: staged row bytes (128, 256 or 512) and payload bytes
 // (16384; 8192 for the half tile; 32768 for the double tile of a widened
 // plane, where double_tile_ok).

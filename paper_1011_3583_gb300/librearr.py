@@ -26,7 +26,7 @@ DEFAULT_TUNE_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "t
 STATUS = {0: "REARR_OK", 1: "REARR_EINVAL", 2: "REARR_ENOMEM", 3: "REARR_ECUDA", 4: "REARR_ERANGE",
           5: "REARR_ETIMEDOUT", 6: "REARR_EBUSY"}
 OK, EINVAL, ENOMEM, ECUDA, ERANGE, ETIMEDOUT, EBUSY = range(7)
-KIND_NAMES = {0: "noop", 1: "copy", 2: "tile", 3: "tile_cells", 4: "runs", 5: "strided"}
+KIND_NAMES = {0: "noop", 1: "copy", 2: "tile", 3: "tile_cells", 4: "runs", 5: "strided", 6: "box"}
 
 
 class RearrError(RuntimeError):

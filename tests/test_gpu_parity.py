@@ -467,19 +467,57 @@ THIN = [  # (dims, perm): transpose planes far smaller than a tile
 ]
 
 
+def _table_with(lr, tmp_path, name, extra):
+    t = tmp_path / name
+    t.write_text(open(lr.DEFAULT_TUNE_TABLE).read() + "\n" + extra + "\n")
+    lr.tuning_load(str(t))
+
+
+@pytest.fixture
+def no_box(lr, tmp_path):
+    """The committed table with boxes switched off: thin planes run strided."""
+    _table_with(lr, tmp_path, "nobox.txt", "box_max_cell_bytes 0")
+    yield
+    lr.tuning_load(None)
+    lr.tuning_load(lr.DEFAULT_TUNE_TABLE)
+
+
+@pytest.fixture
+def all_thin(lr, tmp_path):
+    """The committed table with every fast-tile plan counted thin and boxes on,
+    so that any plane with long enough runs on both sides runs as boxes."""
+    _table_with(lr, tmp_path, "allthin.txt", "thin_tile_bytes 1000000000\nthin_tile_cells 1000000000\n"
+                                             "thin_l2_bytes 1000000000000\nbox_min_run_bytes 16\n"
+                                             "box_max_cell_bytes 16")
+    yield
+    lr.tuning_load(None)
+    lr.tuning_load(lr.DEFAULT_TUNE_TABLE)
+
+
 @pytest.mark.parametrize("e", [1, 2, 4, 8, 16])
-def test_thin_planes_run_strided(lr, orc, e):
+def test_thin_planes(lr, orc, e):
     for t, (dims, perm) in enumerate(THIN):
         d = lr.describe_permute(e, dims, perm)
-        # a thin plane runs strided, unless widening over its continuation
-        # axes turns it into a plane that fills tiles
+        # a thin plane runs as boxes or strided (as the table decides), unless
+        # widening over its continuation axes turns it into a plane that
+        # fills tiles
         widened = d["kind"] == "tile" and (d["wide_a"] >= 0 or d["wide_b"] >= 0)
-        assert d["kind"] == "strided" or widened, (dims, perm, d)
+        assert d["kind"] in ("box", "strided") or widened, (dims, perm, d)
         for off in (0, e if e < 16 else 0):  # aligned (16-byte stores) and unaligned destination
             check_permute(lr, orc, 300 + t, e, dims, perm, src_off=off, dst_off=off)
 
 
-def test_strided_tail_and_unit_edges(lr, orc):
+@pytest.mark.parametrize("e", [1, 2, 4, 8, 16])
+def test_thin_planes_run_strided(lr, orc, e, no_box):
+    for t, (dims, perm) in enumerate(THIN):
+        d = lr.describe_permute(e, dims, perm)
+        widened = d["kind"] == "tile" and (d["wide_a"] >= 0 or d["wide_b"] >= 0)
+        assert d["kind"] == "strided" or widened, (dims, perm, d)
+        for off in (0, e if e < 16 else 0):
+            check_permute(lr, orc, 300 + t, e, dims, perm, src_off=off, dst_off=off)
+
+
+def test_strided_tail_and_unit_edges(lr, orc, no_box):
     # cell counts around the unit size (256 threads x 16/E cells x 4 steps)
     for e, n_b in ((4, 1023), (4, 1024), (4, 1025), (1, 4097), (8, 511)):
         dims, perm = [n_b, 3, 2], [0, 2, 1]
@@ -487,9 +525,62 @@ def test_strided_tail_and_unit_edges(lr, orc):
         check_permute(lr, orc, n_b, e, dims, perm)
 
 
-def test_batch_with_strided_ops(lr, orc):
+# boxes of whole axes (thin planes): contiguous batches of whole planes, a
+# partial axis with a ragged last range, short runs on one side, ranks 2-5
+BOX = [  # (dims, perm)
+    ([1000, 3, 2], [0, 2, 1]),
+    ([64, 3, 5000], [0, 2, 1]),          # NCHW -> NHWC with 3 channels: partial axis, ragged end
+    ([3, 20011], [1, 0]),                # one thin transpose, ragged partial axis
+    ([20011, 5], [1, 0]),
+    ([7, 122, 736, 2], [3, 2, 1, 0]),
+    ([2, 10, 7, 74, 3], [4, 2, 1, 0, 3]),
+    ([56, 5, 84, 3, 7], [2, 0, 4, 3, 1]),
+    ([111, 2, 108, 81], [3, 2, 0, 1]),
+    ([5, 2, 425, 25, 2], [0, 2, 3, 1, 4]),
+    ([95, 14, 5, 58], [3, 0, 2, 1]),
+    ([182, 4, 122], [1, 2, 0]),
+    ([8, 234], [1, 0]),
+    ([40, 5, 188, 24], [1, 3, 2, 0]),
+]
+
+
+@pytest.mark.parametrize("e", [1, 2, 4, 8, 16])
+def test_box_planes(lr, orc, e, all_thin):
+    n_box = 0
+    for t, (dims, perm) in enumerate(BOX):
+        d = lr.describe_permute(e, dims, perm)
+        n_box += d["kind"] == "box"
+        for so, do in ((0, 0), (e, 0), (0, e), (4 if e < 4 else 0, 8 if e < 8 else 0)):
+            if e == 16 and (so or do):
+                continue
+            check_permute(lr, orc, 700 + t, e, dims, perm, src_off=so, dst_off=do)
+    assert n_box >= len(BOX) // 2, n_box
+
+
+def test_box_random_shapes(lr, orc, all_thin):
+    """Random permutes of ranks 2-6 with every tile plan counted thin: boxes
+    (and strided copies where a box's runs stay short) against the oracle."""
+    g = synth.rng(404)
+    kinds = {}
+    for t in range(120):
+        rank = int(g.integers(2, 7))
+        e = ELEMS[t % len(ELEMS)]
+        dims = [int(g.integers(1, 3000)) if g.random() < 0.25 else int(g.integers(1, 40)) for _ in range(rank)]
+        while int(np.prod(dims)) * e > (2 << 20):
+            dims[int(np.argmax(dims))] //= 2
+        perm = [int(v) for v in g.permutation(rank)]
+        k = lr.describe_permute(e, dims, perm)["kind"]
+        kinds[k] = kinds.get(k, 0) + 1
+        off = (0, 0) if t % 3 else (e % 16, (2 * e) % 16)
+        check_permute(lr, orc, 4000 + t, e, dims, perm, src_off=off[0], dst_off=off[1])
+    assert kinds.get("box", 0) >= 30, kinds
+
+
+def _batch_of_thin_ops(lr, orc):
     ops = [dict(kind="permute", elem_bytes=[1, 2, 4, 8][i % 4], dims=dims, perm=perm, data_seed=i)
            for i, (dims, perm) in enumerate(THIN * 4)]
+    ops += [dict(kind="permute", elem_bytes=[1, 2, 4, 8, 16][i % 5], dims=dims, perm=perm, data_seed=50 + i)
+            for i, (dims, perm) in enumerate(BOX) if int(np.prod(dims)) <= 1 << 18]
     ops += [dict(kind="permute", elem_bytes=4, dims=[64, 96], perm=[1, 0], data_seed=99)]  # a tile op
     pool = DevPool()
     bufs = [make_op_buffers(op, offset=(i % 2) * 4, pool=pool) for i, op in enumerate(ops)]
@@ -497,13 +588,22 @@ def test_batch_with_strided_ops(lr, orc):
     for op, b in zip(ops, bufs):
         add_to_plan(plan, op, b)
     plan.finalize()
-    plan.run()
-    sync()
-    pool.check()
-    for i, (op, b) in enumerate(zip(ops, bufs)):
-        for w, g in zip(oracle_of(orc, op, b), outputs_of(op, b)):
-            assert np.array_equal(g, w), (i, op)
+    for rep in range(2):
+        plan.run()
+        sync()
+        pool.check()
+        for i, (op, b) in enumerate(zip(ops, bufs)):
+            for w, g in zip(oracle_of(orc, op, b), outputs_of(op, b)):
+                assert np.array_equal(g, w), (rep, i, op)
     plan.close()
+
+
+def test_batch_with_box_ops(lr, orc, all_thin):
+    _batch_of_thin_ops(lr, orc)
+
+
+def test_batch_with_strided_ops(lr, orc, no_box):
+    _batch_of_thin_ops(lr, orc)
 
 
 def test_runs_in_input_order(lr, orc, tmp_path):

@@ -67,14 +67,51 @@ def test_check_indices_validation(lr):
     assert librearr.check_indices(None, 0, 4, 0) == 0
 
 
-def test_thin_planes_classify_strided(lr):
+def test_thin_planes_classify(lr, tmp_path):
     from paper_1011_3583_gb300 import librearr
+    # boxes on for every cell size
+    t = tmp_path / "box16.txt"
+    t.write_text(open(librearr.DEFAULT_TUNE_TABLE).read() + "\nbox_max_cell_bytes 16\nbox_min_run_bytes 16\n")
+    librearr.tuning_load(str(t))
+    # a thin plane runs as boxes of whole axes: (2 x 7) planes, the box also
+    # spans the 122-axis whole and two indices of the 736-axis (16-byte input
+    # runs, 1708 x 4 cells written in one run)
     d = librearr.describe_permute(4, [7, 122, 736, 2], [3, 2, 1, 0])
-    assert d["kind"] == "strided" and d["vec_out"] == 16 and d["rank"] == 4
+    assert d["kind"] == "box" and d["rank"] == 4, d
+    assert (d["tile_a"], d["tile_b"], d["vec_in"], d["vec_out"], d["n_tiles"]) == (4, 1708, 16, 16, 368), d
+    # a batch of whole 3 x 2 planes: 682 planes per box, contiguous on both sides
+    d = librearr.describe_permute(4, [1000, 3, 2], [0, 2, 1])
+    assert d["kind"] == "box" and (d["tile_a"], d["tile_b"], d["n_tiles"]) == (4092, 4092, 2), d
     # the same reversal with a plane that fills tiles stays tiled
     assert librearr.describe_permute(4, [512, 64, 64, 512], [3, 2, 1, 0])["kind"] == "tile"
-    # unaligned destination: scalar stores
+    # unaligned destination: 4-byte stores
     assert librearr.describe_permute(4, [1000, 3, 2], [0, 2, 1], FAKE_DST + 4, FAKE_SRC)["vec_out"] == 4
+    # ... a cells tile of 16-byte cells: one box
+    d = lr.describe_permute(4, [8, 16, 4], [1, 0, 2], FAKE_DST, FAKE_SRC)
+    assert d["cell_bytes"] == 16 and d["rank"] == 2 and d["kind"] == "box" and d["n_tiles"] == 1
+    # boxes switched off (runs must reach more than a tile, or no cell size
+    # allowed): strided copies
+    for extra in ("box_min_run_bytes 1000000", "box_max_cell_bytes 0"):
+        t = tmp_path / "nobox.txt"
+        t.write_text(open(librearr.DEFAULT_TUNE_TABLE).read() + "\n" + extra + "\n")
+        try:
+            librearr.tuning_load(str(t))
+            d = librearr.describe_permute(4, [7, 122, 736, 2], [3, 2, 1, 0])
+            assert d["kind"] == "strided" and d["vec_out"] == 16 and d["rank"] == 4
+            assert librearr.describe_permute(4, [1000, 3, 2], [0, 2, 1], FAKE_DST + 4, FAKE_SRC)["vec_out"] == 4
+        finally:
+            librearr.tuning_load(None)
+            librearr.tuning_load(librearr.DEFAULT_TUNE_TABLE)
+    # boxes for cells of at most box_max_cell_bytes
+    t = tmp_path / "box2.txt"
+    t.write_text(open(librearr.DEFAULT_TUNE_TABLE).read() + "\nbox_max_cell_bytes 2\nbox_min_run_bytes 16\n")
+    try:
+        librearr.tuning_load(str(t))
+        assert librearr.describe_permute(2, [1000, 3, 2], [0, 2, 1])["kind"] == "box"
+        assert librearr.describe_permute(4, [1000, 3, 2], [0, 2, 1])["kind"] == "strided"
+    finally:
+        librearr.tuning_load(None)
+        librearr.tuning_load(librearr.DEFAULT_TUNE_TABLE)
 
 
 def test_status_strings(lr):
@@ -181,7 +218,7 @@ def test_describe_examples(lr):
     assert d["cell_bytes"] == 16 and d["rank"] == 2 and d["kind"] == "tile"
     # ... and a plane of 8 x 16 such cells is too thin for tiles
     d = lr.describe_permute(4, [8, 16, 4], [1, 0, 2], FAKE_DST, FAKE_SRC)
-    assert d["cell_bytes"] == 16 and d["rank"] == 2 and d["kind"] == "strided"
+    assert d["cell_bytes"] == 16 and d["rank"] == 2 and d["kind"] in ("strided", "box")
     # long unmoved runs are copied as runs
     d = lr.describe_permute(4, [8, 16, 512], [1, 0, 2], FAKE_DST, FAKE_SRC)
     assert d["kind"] == "runs" and d["cell_bytes"] == 2048
