@@ -13,11 +13,24 @@
  * finished (ordered on the GPU with events; submitting never blocks the host
  * except inside the CUDA runtime for pageable host memory).
  *
+ * Direct ops: where the GPU reaches host memory through the host's own page
+ * tables (a coherent link such as NVLink-C2C; the pipeline's default there),
+ * a permute, interlace or de-interlace whose host buffers are page-locked and
+ * whose plan streams through them (copy, tiles, runs, boxes, interlace
+ * kernels) runs its kernel on the host buffers directly, with no staging:
+ * every byte still crosses the host link once, but reads and writes share it
+ * in both directions inside one kernel.  Other ops, and every op on pageable
+ * memory, are staged as above.  A direct op starts after everything
+ * submitted before it and everything submitted after it waits for it, so the
+ * ops act on host memory in submission order whichever way each one runs.
+ * rearr_pipeline_set_direct turns direct ops on or off.
+ *
  * Conventions are those of librearr.h, except that every data pointer here is
  * a HOST pointer.  Page-locked (pinned) host memory gives full copy speed;
  * pageable memory works but its uploads are staged by the driver.  The caller
  * must not modify an op's inputs or read its outputs until rearr_pipeline_sync
- * returns.  Each op's inputs and outputs, each rounded up to 256 bytes, must
+ * returns.  Ops of one pipeline may feed each other through host memory: an
+ * op whose input overlaps an earlier op's output reads that output.  Each op's inputs and outputs, each rounded up to 256 bytes, must
  * fit in one slot (REARR_EINVAL otherwise; nothing is enqueued).  A pipeline
  * is used by one host thread at a time.
  */
@@ -70,7 +83,15 @@ rearr_status rearr_pipeline_stencil2d_f32(rearr_pipeline *pipe, float *dst, cons
 /* Waits until every submitted op's outputs are in host memory. */
 rearr_status rearr_pipeline_sync(rearr_pipeline *pipe);
 
-/* Ops submitted and bytes copied host-to-device / device-to-host so far. */
+/* mode 1: run eligible ops directly on page-locked host buffers (see above);
+ * 0: stage every op.  Applies to ops submitted afterwards. */
+rearr_status rearr_pipeline_set_direct(rearr_pipeline *pipe, int mode);
+
+/* Ops that ran directly on host buffers so far, and the current mode. */
+rearr_status rearr_pipeline_direct_ops(const rearr_pipeline *pipe, uint64_t *direct_ops, int *mode);
+
+/* Ops submitted and bytes moved host-to-device / device-to-host so far (by
+ * copies, or across the host link by the kernels of direct ops). */
 rearr_status rearr_pipeline_stats(const rearr_pipeline *pipe, uint64_t *ops, uint64_t *h2d_bytes,
                                   uint64_t *d2h_bytes);
 

@@ -8,7 +8,20 @@
 //                     record computed[s]
 //   download stream : wait computed[s]; copy outputs out; record out_done[s]
 // so consecutive ops overlap their uploads, kernels and downloads, and a slot
-// is never overwritten while its previous op is still being read.
+// is never overwritten while its previous op is still being read.  An upload
+// that reads host memory an op still in flight writes also waits for that
+// op's download, so an op may consume an earlier op's output.
+//
+// Direct ops.  With direct access on (the default where the GPU reaches host
+// memory through the system's page tables, as over NVLink-C2C), a permute or
+// (de-)interlace whose host buffers are page-locked and whose plan streams
+// (copy, tiles, runs, boxes, interlace kernels) runs its kernel on the host
+// buffers themselves: each byte crosses the host link once, as with the
+// copies, but reads and writes share the link in both directions within one
+// kernel instead of relying on the overlap of separate copies.  A direct op
+// runs on the kernel stream after everything enqueued before it on the three
+// streams, and everything enqueued after it waits for it, so host memory sees
+// the ops in submission order whichever way each runs.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -37,8 +50,11 @@ struct rearr_pipeline {
     cudaStream_t up = nullptr, comp = nullptr, down = nullptr;
     std::vector<cudaEvent_t> in_ready, computed, out_done;
     std::vector<bool> used;
+    std::vector<std::vector<std::pair<uintptr_t, size_t>>> wrote;  // host ranges the slot's last op writes
+    cudaEvent_t up_tail = nullptr, down_tail = nullptr, direct_done = nullptr;
+    int direct = 0;
     cudaError_t broken = cudaSuccess;
-    uint64_t ops = 0, h2d = 0, d2h = 0;
+    uint64_t ops = 0, h2d = 0, d2h = 0, direct_ops = 0;
 };
 
 namespace {
@@ -82,6 +98,47 @@ rearr_status layout(rearr_pipeline *p, int slot, const std::vector<HostRange> &i
     return REARR_OK;
 }
 
+// Device-visible addresses of the ranges when every non-empty one starts and
+// ends in page-locked host memory the device can address.
+bool device_views(const std::vector<HostRange> &ins, const std::vector<HostOut> &outs, SlotLayout &lay)
+{
+    auto view = [](const void *h, size_t bytes, char *&d) {
+        if (bytes == 0) {
+            d = nullptr;
+            return true;
+        }
+        cudaPointerAttributes a, b;
+        if (cudaPointerGetAttributes(&a, h) != cudaSuccess ||
+            cudaPointerGetAttributes(&b, static_cast<const char *>(h) + bytes - 1) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
+            return false;
+        d = static_cast<char *>(a.devicePointer);
+        return static_cast<char *>(b.devicePointer) == d + bytes - 1;
+    };
+    for (const HostRange &r : ins) {
+        char *d;
+        if (!view(r.host, r.bytes, d)) return false;
+        lay.in.push_back(d);
+    }
+    for (const HostOut &r : outs) {
+        char *d;
+        if (!view(r.host, r.bytes, d)) return false;
+        lay.out.push_back(d);
+    }
+    return true;
+}
+
+// Plans whose kernels stream through their buffers (every byte read and
+// written about once, in runs): the ones a direct op may run on host memory.
+bool streams(uint32_t cls)
+{
+    return cls == OC_COPY || cls == OC_TILE || cls == OC_TILE_CELLS || cls == OC_RUNS || cls == OC_BOX ||
+           cls == OC_INTERLACE || cls == OC_DEINTERLACE;
+}
+
 template <class Launch>
 rearr_status run_op(rearr_pipeline *p, const char *who, const std::vector<HostRange> &ins,
                     const std::vector<HostOut> &outs, Launch &&launch)
@@ -92,6 +149,35 @@ rearr_status run_op(rearr_pipeline *p, const char *who, const std::vector<HostRa
         if (r.bytes && !r.host) return fail(REARR_EINVAL, std::string(who) + ": NULL host input");
     for (const HostOut &r : outs)
         if (r.bytes && !r.host) return fail(REARR_EINVAL, std::string(who) + ": NULL host output");
+    if (p->direct) {
+        SlotLayout dl;
+        if (device_views(ins, outs, dl)) {
+            std::string err;
+            std::function<cudaError_t(cudaStream_t)> go;
+            uint32_t cls = OC_COUNT;
+            rearr_status st = launch(dl, go, err, cls);
+            if (st != REARR_OK) return fail(st, std::string(who) + ": " + err);
+            if (streams(cls)) {
+                cudaError_t e = cudaEventRecord(p->up_tail, p->up);
+                if (e == cudaSuccess) e = cudaEventRecord(p->down_tail, p->down);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(p->comp, p->up_tail, 0);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(p->comp, p->down_tail, 0);
+                if (e == cudaSuccess) e = go(p->comp);
+                if (e == cudaSuccess) e = cudaEventRecord(p->direct_done, p->comp);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(p->up, p->direct_done, 0);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(p->down, p->direct_done, 0);
+                if (e != cudaSuccess) {
+                    p->broken = e;
+                    return cuda_fail(e, who);
+                }
+                p->ops += 1;
+                p->direct_ops += 1;
+                for (const HostRange &r : ins) p->h2d += r.bytes;
+                for (const HostOut &r : outs) p->d2h += r.bytes;
+                return REARR_OK;
+            }
+        }
+    }
     const int s = p->next;
     SlotLayout lay;
     rearr_status st = layout(p, s, ins, outs, lay, who);
@@ -100,11 +186,22 @@ rearr_status run_op(rearr_pipeline *p, const char *who, const std::vector<HostRa
     // anything is enqueued.
     std::string err;
     std::function<cudaError_t(cudaStream_t)> go;
-    st = launch(lay, go, err);
+    uint32_t cls = OC_COUNT;
+    st = launch(lay, go, err, cls);
     if (st != REARR_OK) return fail(st, std::string(who) + ": " + err);
 
     cudaError_t e = cudaSuccess;
     if (p->used[s]) e = cudaStreamWaitEvent(p->up, p->out_done[s], 0);
+    // an input that an earlier op still in flight writes: upload after that
+    // op's download (ops older than the slot ring were waited for above)
+    for (int o = 0; o < p->slots && e == cudaSuccess; ++o) {
+        if (o == s || !p->used[o]) continue;
+        bool hit = false;
+        for (const HostRange &r : ins)
+            for (const auto &w : p->wrote[o])
+                hit |= r.bytes && uintptr_t(r.host) < w.first + w.second && w.first < uintptr_t(r.host) + r.bytes;
+        if (hit) e = cudaStreamWaitEvent(p->up, p->out_done[o], 0);
+    }
     for (size_t i = 0; i < ins.size() && e == cudaSuccess; ++i)
         if (ins[i].bytes) e = cudaMemcpyAsync(lay.in[i], ins[i].host, ins[i].bytes, cudaMemcpyHostToDevice, p->up);
     if (e == cudaSuccess) e = cudaEventRecord(p->in_ready[s], p->up);
@@ -121,6 +218,9 @@ rearr_status run_op(rearr_pipeline *p, const char *who, const std::vector<HostRa
         return cuda_fail(e, who);
     }
     p->used[s] = true;
+    p->wrote[s].clear();
+    for (const HostOut &r : outs)
+        if (r.bytes) p->wrote[s].push_back({uintptr_t(r.host), r.bytes});
     p->next = (s + 1) % p->slots;
     p->ops += 1;
     for (const HostRange &r : ins) p->h2d += r.bytes;
@@ -140,7 +240,7 @@ rearr_status pipeline_indexed(rearr_pipeline *pipe, const char *who, void *dst, 
                               const void *idx, size_t n, size_t elem_bytes, int idx_bytes, bool scatter)
 {
     return run_op(pipe, who, {{src, n * elem_bytes}, {idx, n * size_t(idx_bytes)}}, {{dst, n * elem_bytes}},
-                  [&](const SlotLayout &l, std::function<cudaError_t(cudaStream_t)> &go, std::string &err) {
+                  [&](const SlotLayout &l, std::function<cudaError_t(cudaStream_t)> &go, std::string &err, uint32_t &cls) {
                       auto op = std::make_shared<OpDesc>();
                       rearr_status st = plan_reorder(l.out[0], l.in[0], reinterpret_cast<const uint32_t *>(l.in[1]),
                                                      n, elem_bytes, *op, err, idx_bytes, scatter);
@@ -174,9 +274,18 @@ rearr_status rearr_pipeline_create(size_t slot_bytes, int slots, rearr_pipeline 
     p->computed.assign(slots, nullptr);
     p->out_done.assign(slots, nullptr);
     p->used.assign(slots, false);
+    p->wrote.assign(slots, {});
     for (int i = 0; i < slots && e == cudaSuccess; ++i)
         for (cudaEvent_t *ev : {&p->in_ready[i], &p->computed[i], &p->out_done[i]})
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    for (cudaEvent_t *ev : {&p->up_tail, &p->down_tail, &p->direct_done})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    // direct ops by default where the device uses the host's page tables
+    // (coherent host access, as over NVLink-C2C)
+    int dev = 0, ats = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ats, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev);
+    p->direct = ats ? 1 : 0;
     if (e != cudaSuccess) {
         rearr_pipeline_destroy(p);
         return cuda_fail(e, "rearr_pipeline_create");
@@ -190,9 +299,10 @@ rearr_status rearr_pipeline_permute(rearr_pipeline *pipe, void *dst, const void 
 {
     const size_t bytes = (rank >= 1 && rank <= REARR_MAX_RANK && dims) ? product(rank, dims) * elem_bytes : 0;
     return run_op(pipe, "rearr_pipeline_permute", {{src, bytes}}, {{dst, bytes}},
-                  [&](const SlotLayout &l, std::function<cudaError_t(cudaStream_t)> &go, std::string &err) {
+                  [&](const SlotLayout &l, std::function<cudaError_t(cudaStream_t)> &go, std::string &err, uint32_t &cls) {
                       auto pl = std::make_shared<PermPlan>();
                       rearr_status st = plan_permute(l.out[0], l.in[0], elem_bytes, rank, dims, perm, *pl, err);
+                      cls = pl->info.kind == REARR_KIND_NOOP ? uint32_t(OC_COPY) : pl->op.cls;
                       go = [pl](cudaStream_t s) { return launch_single(pl->op, nullptr, s); };
                       return st;
                   });
@@ -203,7 +313,7 @@ rearr_status rearr_pipeline_reorder(rearr_pipeline *pipe, void *dst, const void 
 {
     return run_op(pipe, "rearr_pipeline_reorder", {{src, n * elem_bytes}, {idx, n * sizeof(uint32_t)}},
                   {{dst, n * elem_bytes}},
-                  [&](const SlotLayout &l, std::function<cudaError_t(cudaStream_t)> &go, std::string &err) {
+                  [&](const SlotLayout &l, std::function<cudaError_t(cudaStream_t)> &go, std::string &err, uint32_t &cls) {
                       auto op = std::make_shared<OpDesc>();
                       rearr_status st = plan_reorder(l.out[0], l.in[0], reinterpret_cast<const uint32_t *>(l.in[1]),
                                                      n, elem_bytes, *op, err);
@@ -225,7 +335,7 @@ rearr_status rearr_pipeline_reorder_nm(rearr_pipeline *pipe, void *dst, const vo
             out_bytes *= (order[i] >= 0 && order[i] < rank_in && range[order[i]] > 0) ? size_t(range[order[i]]) : 0;
     }
     return run_op(pipe, "rearr_pipeline_reorder_nm", {{src, in_bytes}}, {{dst, out_bytes}},
-                  [&](const SlotLayout &l, std::function<cudaError_t(cudaStream_t)> &go, std::string &err) {
+                  [&](const SlotLayout &l, std::function<cudaError_t(cudaStream_t)> &go, std::string &err, uint32_t &cls) {
                       auto pl = std::make_shared<PermPlan>();
                       rearr_status st = plan_reorder_nm(l.out[0], l.in[0], elem_bytes, rank_in, dims, rank_out,
                                                         order, base, range, *pl, err);
@@ -260,12 +370,13 @@ rearr_status rearr_pipeline_interlace(rearr_pipeline *pipe, void *dst, const voi
         for (int j = 0; j < k; ++j) ins.push_back({srcs[j], n * elem_bytes});
     const size_t out = ins.empty() ? 0 : n * elem_bytes * size_t(k);
     return run_op(pipe, "rearr_pipeline_interlace", ins, {{dst, out}},
-                  [&](const SlotLayout &l, std::function<cudaError_t(cudaStream_t)> &go, std::string &err) {
+                  [&](const SlotLayout &l, std::function<cudaError_t(cudaStream_t)> &go, std::string &err, uint32_t &cls) {
                       auto pl = std::make_shared<InterlacePlan>();
                       std::vector<char *> planes(l.in.begin(), l.in.end());
                       rearr_status st = plan_interlace(true, l.out.empty() ? nullptr : l.out[0],
                                                        planes.empty() ? nullptr : planes.data(), k, n, elem_bytes,
                                                        *pl, err);
+                      cls = pl->op.cls;
                       go = [pl](cudaStream_t s) { return launch_single(pl->op, pl->planes.data(), s); };
                       return st;
                   });
@@ -279,11 +390,12 @@ rearr_status rearr_pipeline_deinterlace(rearr_pipeline *pipe, void *const *dsts,
         for (int j = 0; j < k; ++j) outs.push_back({dsts[j], n * elem_bytes});
     const size_t in = outs.empty() ? 0 : n * elem_bytes * size_t(k);
     return run_op(pipe, "rearr_pipeline_deinterlace", {{src, in}}, outs,
-                  [&](const SlotLayout &l, std::function<cudaError_t(cudaStream_t)> &go, std::string &err) {
+                  [&](const SlotLayout &l, std::function<cudaError_t(cudaStream_t)> &go, std::string &err, uint32_t &cls) {
                       auto pl = std::make_shared<InterlacePlan>();
                       std::vector<char *> planes(l.out.begin(), l.out.end());
                       rearr_status st = plan_interlace(false, l.in[0], planes.empty() ? nullptr : planes.data(), k,
                                                        n, elem_bytes, *pl, err);
+                      cls = pl->op.cls;
                       go = [pl](cudaStream_t s) { return launch_single(pl->op, pl->planes.data(), s); };
                       return st;
                   });
@@ -294,7 +406,7 @@ rearr_status rearr_pipeline_stencil2d_f32(rearr_pipeline *pipe, float *dst, cons
 {
     const size_t bytes = (ny > 0 && nx > 0) ? size_t(ny) * size_t(nx) * sizeof(float) : 0;
     return run_op(pipe, "rearr_pipeline_stencil2d_f32", {{src, bytes}}, {{dst, bytes}},
-                  [&](const SlotLayout &l, std::function<cudaError_t(cudaStream_t)> &go, std::string &err) {
+                  [&](const SlotLayout &l, std::function<cudaError_t(cudaStream_t)> &go, std::string &err, uint32_t &cls) {
                       auto pl = std::make_shared<StencilPlan>();
                       rearr_status st = plan_stencil2d(reinterpret_cast<float *>(l.out[0]),
                                                        reinterpret_cast<const float *>(l.in[0]), ny, nx, ntaps, dy,
@@ -320,6 +432,22 @@ rearr_status rearr_pipeline_sync(rearr_pipeline *pipe)
     return REARR_OK;
 }
 
+rearr_status rearr_pipeline_set_direct(rearr_pipeline *pipe, int mode)
+{
+    if (!pipe) return fail(REARR_EINVAL, "rearr_pipeline_set_direct: pipeline is NULL");
+    if (mode != 0 && mode != 1) return fail(REARR_EINVAL, "rearr_pipeline_set_direct: mode must be 0 or 1");
+    pipe->direct = mode;
+    return REARR_OK;
+}
+
+rearr_status rearr_pipeline_direct_ops(const rearr_pipeline *pipe, uint64_t *direct_ops, int *mode)
+{
+    if (!pipe) return fail(REARR_EINVAL, "rearr_pipeline_direct_ops: pipeline is NULL");
+    if (direct_ops) *direct_ops = pipe->direct_ops;
+    if (mode) *mode = pipe->direct;
+    return REARR_OK;
+}
+
 rearr_status rearr_pipeline_stats(const rearr_pipeline *pipe, uint64_t *ops, uint64_t *h2d_bytes, uint64_t *d2h_bytes)
 {
     if (!pipe) return fail(REARR_EINVAL, "rearr_pipeline_stats: pipeline is NULL");
@@ -337,6 +465,8 @@ void rearr_pipeline_destroy(rearr_pipeline *pipe)
     for (auto *v : {&pipe->in_ready, &pipe->computed, &pipe->out_done})
         for (cudaEvent_t ev : *v)
             if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : {pipe->up_tail, pipe->down_tail, pipe->direct_done})
+        if (ev) cudaEventDestroy(ev);
     for (cudaStream_t s : {pipe->up, pipe->comp, pipe->down})
         if (s) cudaStreamDestroy(s);
     if (pipe->dev) cudaFree(pipe->dev);

@@ -683,6 +683,8 @@ def _bind_pipeline():
         "rearr_pipeline_stencil2d_f32": (st, [vp, vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ip, ip,
                                               ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
         "rearr_pipeline_sync": (st, [vp]),
+        "rearr_pipeline_set_direct": (st, [vp, ctypes.c_int]),
+        "rearr_pipeline_direct_ops": (st, [vp, u64p, ctypes.POINTER(ctypes.c_int)]),
         "rearr_pipeline_stats": (st, [vp, u64p, u64p, u64p]),
         "rearr_pipeline_destroy": (None, [vp]),
     }
@@ -711,7 +713,8 @@ def _hptr(x) -> int | None:
 
 class Pipeline:
     """rearr_pipeline_*: ops on HOST buffers, staged through device slots with
-    uploads, kernels and downloads overlapped on three streams."""
+    uploads, kernels and downloads overlapped on three streams, or run directly
+    on page-locked host buffers where the device reaches host memory coherently."""
 
     def __init__(self, slot_bytes: int, slots: int = 3):
         L = _bind_pipeline()
@@ -768,6 +771,16 @@ class Pipeline:
     def sync(self) -> None:
         _check(load().rearr_pipeline_sync(self._h))
         self._keep.clear()
+
+    def set_direct(self, mode: int) -> None:
+        """1: run eligible ops directly on page-locked host buffers; 0: stage every op."""
+        _check(load().rearr_pipeline_set_direct(self._h, int(mode)))
+
+    def direct(self) -> dict:
+        n = ctypes.c_uint64()
+        m = ctypes.c_int()
+        _check(load().rearr_pipeline_direct_ops(self._h, ctypes.byref(n), ctypes.byref(m)))
+        return {"direct_ops": n.value, "mode": m.value}
 
     def stats(self) -> dict:
         ops, h2d, d2h = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()

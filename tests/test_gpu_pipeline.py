@@ -164,3 +164,78 @@ def test_nm_scatter_and_wide_indices(lr, orc):
         assert np.array_equal(outs["scatter"], orc.indexed(s2, p, e, scatter=True))
         assert np.array_equal(outs["scatter64"], orc.indexed(s2, p, e, scatter=True))
         assert np.array_equal(outs["reorder64"], orc.reorder(s2, p, e))
+
+
+def pinned_guarded(nbytes, off=0):
+    """A page-locked buffer with guard bands before and after its body."""
+    from tests.gpu_util import GUARD, guard_pattern
+    t = pinned(GUARD + off + nbytes + GUARD)
+    a = t.numpy()
+    a[:GUARD + off] = guard_pattern(GUARD + off, 0)
+    a[GUARD + off + nbytes:] = guard_pattern(GUARD, 1)
+    return t, a[GUARD + off: GUARD + off + nbytes]
+
+
+def guards_intact(t, nbytes, off=0):
+    from tests.gpu_util import GUARD, guard_pattern
+    a = t.numpy()
+    return (np.array_equal(a[:GUARD + off], guard_pattern(GUARD + off, 0)) and
+            np.array_equal(a[GUARD + off + nbytes:], guard_pattern(GUARD, 1)))
+
+
+@pytest.mark.parametrize("mode", [1, 0])
+def test_direct_ops_keep_submission_order(lr, orc, mode):
+    """A chain through page-locked host buffers mixing ops that run directly on
+    them (permutes planned as tiles and boxes, interlaces) and a staged op (a
+    reorder): each op reads what the op before it wrote, so the
+    results match the oracle's chain only if host memory sees the ops in
+    submission order.  Mode 0 stages everything; both give the same bytes and
+    no op writes outside its output."""
+    e4, dims, perm = 4, [61, 47, 33], [2, 0, 1]
+    n = int(np.prod(dims))
+    src = synth.random_elements(71, n, e4)
+    idx = synth.random_indices(72, n, n)
+    bufs = {}
+    for name, nb, off in (("src", n * e4, 0), ("a", n * e4, 4), ("b", n * e4, 0), ("c", n * e4, 8),
+                          ("u8", 16 * 3 * 4099, 0), ("u8t", 16 * 3 * 4099, 1), ("il", 2 * n * e4, 0),
+                          ("d0", n * e4, 0), ("d1", n * e4, 0)):
+        bufs[name] = (pinned_guarded(nb, off), nb, off)
+    body = {k: v[0][1] for k, v in bufs.items()}
+    body["src"][:] = src
+    img = synth.random_elements(73, 16 * 3 * 4099, 1)
+    body["u8"][:] = img
+    with lr.Pipeline(slot_bytes=8 << 20, slots=3) as pipe:
+        pipe.set_direct(mode)
+        t = {k: v[0][0] for k, v in bufs.items()}
+        off = {k: v[2] for k, v in bufs.items()}
+        from tests.gpu_util import GUARD
+
+        def ptr(k):
+            return t[k].data_ptr() + GUARD + off[k]
+
+        pipe.permute(ptr("a"), ptr("src"), e4, dims, perm)                 # tile
+        pipe.reorder(ptr("b"), ptr("a"), idx, n, e4)                       # staged, reads a
+        pipe.permute(ptr("c"), ptr("b"), e4, [61, 47 * 33], [1, 0])        # reads b
+        pipe.permute(ptr("u8t"), ptr("u8"), 1, [16, 3, 4099], [0, 2, 1])  # a box of 1-byte cells
+        pipe.interlace(ptr("il"), [ptr("c"), ptr("a")], n, e4)             # reads c and a
+        pipe.deinterlace([ptr("d0"), ptr("d1")], ptr("il"), n, e4)         # reads il
+        pipe.sync()
+        d = pipe.direct()
+        # direct ops: the permutes whose plans stream, the interlace and the
+        # de-interlace (the reorder is always staged)
+        streaming = sum(lr.describe_permute(e, dm, pm, ptr(o), ptr(i))["kind"] in ("copy", "tile", "tile_cells",
+                                                                                     "runs", "box")
+                        for o, i, e, dm, pm in (("a", "src", e4, dims, perm), ("c", "b", e4, [61, 47 * 33], [1, 0]),
+                                                ("u8t", "u8", 1, [16, 3, 4099], [0, 2, 1])))
+        assert d["mode"] == mode
+        assert d["direct_ops"] == (streaming + 2 if mode else 0), (d, streaming)
+    a = orc.permute(src, e4, dims, perm)
+    b = orc.reorder(a, idx, e4)
+    c = orc.permute(b, e4, [61, 47 * 33], [1, 0])
+    il = orc.interlace([c, a], n, e4)
+    d0, d1 = orc.deinterlace(il, 2, n, e4)
+    for k, want in (("a", a), ("b", b), ("c", c), ("il", il), ("d0", d0), ("d1", d1),
+                    ("u8t", orc.permute(img, 1, [16, 3, 4099], [0, 2, 1]))):
+        assert np.array_equal(body[k], want), k
+    for k, (tb, nb, o) in bufs.items():
+        assert guards_intact(tb[0], nb, o), k
