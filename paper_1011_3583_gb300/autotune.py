@@ -269,7 +269,7 @@ def _time_mix(rr, torch, stream, table, ops, bufs):
 def tune_thin(rr, torch, stream, tmpdir, log, base_lines):
     ops, pool, bufs = _mix_permutes(torch)
     best = None
-    for cells in (256, 512, 1024, 2048, 4096):
+    for cells in (256, 512, 1024, 2048, 4096, 8192, 16384):
         table = os.path.join(tmpdir, "thin.txt")
         _write(table, base_lines + [f"thin_tile_cells {cells}"])
         tb, tp = _time_mix(rr, torch, stream, table, ops, bufs)

@@ -87,10 +87,22 @@ __device__ __noinline__ void copy_range(const CopyDesc &d, uint64_t u0, uint64_t
     for (uint64_t u = u0; u < u1; ++u) copy_body<W>(d, u);
 }
 
-template <int W>
-__device__ __noinline__ void strided_range(const StridedDesc &d, uint64_t u0, uint64_t u1)
+template <int W, int ND>
+__device__ __noinline__ void strided_range_nd(const StridedDesc &d, uint64_t u0, uint64_t u1)
 {
-    for (uint64_t u = u0; u < u1; ++u) strided_body<W>(d, u);
+    for (uint64_t u = u0; u < u1; ++u) strided_body<W, ND>(d, u);
+}
+
+template <int W>
+__device__ __forceinline__ void strided_range(const StridedDesc &d, uint64_t u0, uint64_t u1)
+{
+    switch (d.nd) {  // the usual ranks after collapsing, then any
+        case 2: strided_range_nd<W, 2>(d, u0, u1); return;
+        case 3: strided_range_nd<W, 3>(d, u0, u1); return;
+        case 4: strided_range_nd<W, 4>(d, u0, u1); return;
+        case 5: strided_range_nd<W, 5>(d, u0, u1); return;
+        default: strided_range_nd<W, 0>(d, u0, u1); return;
+    }
 }
 
 template <int W, int NU>

@@ -765,12 +765,16 @@ __device__ __forceinline__ void interlace_tail(const InterlaceDesc &d, char *con
 // from its index; the writes are coalesced (consecutive cells per thread,
 // 16-byte stores when aligned) and the reads hit the L1 / L2 wherever
 // neighbouring cells share sectors.
+// ND > 0: the number of output axes fixed at compile time (no per-axis test);
+// ND = 0: read from the descriptor.
+template <int ND>
 __device__ __forceinline__ int64_t strided_offset(const StridedDesc &d, uint32_t q)
 {
+    constexpr int R = ND > 0 ? ND : kMaxRank;
     int64_t off = 0;
 #pragma unroll
-    for (int i = kMaxRank - 1; i >= 0; --i) {
-        if (i < d.nd) {
+    for (int i = R - 1; i >= 0; --i) {
+        if (ND > 0 || i < d.nd) {
             uint32_t r;
             fdivmod(q, d.div[i], q, r);
             off += int64_t(r) * d.in_stride[i];
@@ -779,10 +783,11 @@ __device__ __forceinline__ int64_t strided_offset(const StridedDesc &d, uint32_t
     return off;
 }
 
-template <int W>
+template <int W, int ND = 0>
 __device__ __forceinline__ void strided_body(const StridedDesc &d, uint64_t unit)
 {
     constexpr int V = 16 / W;  // cells per 16-byte store
+    constexpr int R = ND > 0 ? ND : kMaxRank;
     using T = typename Word<W>::T;
     const uint64_t per_unit = uint64_t(kThreads) * V * kStridedSteps;
     const uint64_t c0 = unit * per_unit;
@@ -799,14 +804,14 @@ __device__ __forceinline__ void strided_body(const StridedDesc &d, uint64_t unit
             // from its multi-index (one division per axis), the next ones by
             // stepping the multi-index like an odometer (an add per cell, a
             // carry into the next axis when an extent is reached).
-            uint32_t digit[kMaxRank];
+            uint32_t digit[R];
             int64_t off = 0;
             {
                 uint32_t q = uint32_t(base);
 #pragma unroll
-                for (int i = kMaxRank - 1; i >= 0; --i) {
+                for (int i = R - 1; i >= 0; --i) {
                     digit[i] = 0;
-                    if (i < d.nd) {
+                    if (ND > 0 || i < d.nd) {
                         fdivmod(q, d.div[i], q, digit[i]);
                         off += int64_t(digit[i]) * d.in_stride[i];
                     }
@@ -816,8 +821,8 @@ __device__ __forceinline__ void strided_body(const StridedDesc &d, uint64_t unit
             for (int k = 0; k < V; ++k) {
                 if (base + k < c1) v.e[k] = ldg_any<W>(d.src + off);
 #pragma unroll
-                for (int i = kMaxRank - 1; i >= 0; --i) {
-                    if (i < d.nd) {
+                for (int i = R - 1; i >= 0; --i) {
+                    if (ND > 0 || i < d.nd) {
                         off += d.in_stride[i];
                         if (++digit[i] < d.div[i].d) break;
                         off -= int64_t(d.div[i].d) * d.in_stride[i];
@@ -835,7 +840,7 @@ __device__ __forceinline__ void strided_body(const StridedDesc &d, uint64_t unit
         }
     } else {
         for (uint64_t q = c0 + tid; q < c1; q += kThreads)
-            stg<W>(d.dst + q * W, ldg_any<W>(d.src + strided_offset(d, uint32_t(q))));
+            stg<W>(d.dst + q * W, ldg_any<W>(d.src + strided_offset<ND>(d, uint32_t(q))));
     }
 }
 

@@ -75,11 +75,11 @@ __global__ void __launch_bounds__(kThreads) k_gather(const __grid_constant__ Gat
     for (uint64_t u = blockIdx.x; u < n; u += gridDim.x) gather_body<W>(d, u);
 }
 
-template <int W>
+template <int W, int ND>
 __global__ void __launch_bounds__(kThreads) k_strided(const __grid_constant__ StridedDesc d, uint64_t n)
 {
     pdl_enter();
-    for (uint64_t u = blockIdx.x; u < n; u += gridDim.x) strided_body<W>(d, u);
+    for (uint64_t u = blockIdx.x; u < n; u += gridDim.x) strided_body<W, ND>(d, u);
 }
 
 template <int W, int NU>
@@ -193,7 +193,13 @@ template <int W> struct RunCopy {
 template <int W> struct RunStrided {
     static cudaError_t run(const OpDesc &op, cudaStream_t s)
     {
-        return go(k_strided<W>, op.units, op.strided, op.units, s);
+        switch (op.strided.nd) {  // the usual ranks after collapsing, then any
+            case 2: return go(k_strided<W, 2>, op.units, op.strided, op.units, s);
+            case 3: return go(k_strided<W, 3>, op.units, op.strided, op.units, s);
+            case 4: return go(k_strided<W, 4>, op.units, op.strided, op.units, s);
+            case 5: return go(k_strided<W, 5>, op.units, op.strided, op.units, s);
+            default: return go(k_strided<W, 0>, op.units, op.strided, op.units, s);
+        }
     }
 };
 template <int W> struct RunBox {

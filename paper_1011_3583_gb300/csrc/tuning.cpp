@@ -63,7 +63,7 @@ struct Table {
     uint64_t reorder_smem_buckets = uint64_t(1) << 22;
     uint64_t box_min_run_bytes = 16;
     uint64_t box_run_bytes = 512;
-    uint64_t box_max_cell_bytes = 2;
+    uint64_t box_max_cell_bytes = 0;
     std::vector<RowbRule> rowb;
 };
 

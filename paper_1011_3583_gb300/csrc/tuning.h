@@ -68,8 +68,8 @@ uint64_t double_tile_min_bytes();
 // most this; above it (or at 1) it scatters through ~16 MB chunks in the L2.
 uint64_t reorder_smem_max_buckets();
 
-// Thin planes of cells of at most box_max_cell_bytes() (0: none) run as
-// staged boxes (OC_BOX) when the box's input and output runs both reach
+// Thin planes of cells of at most box_max_cell_bytes() (0, the default: none)
+// run as staged boxes (OC_BOX) when the box's input and output runs both reach
 // box_min_run_bytes(), else as strided copies.  A box grows until both runs
 // reach box_run_bytes() and it holds half a tile.
 uint64_t box_min_run_bytes();
