@@ -669,8 +669,11 @@ static rearr_status plan_axes(void *dst, const char *src, size_t elem_bytes, con
     }
     const uint64_t n_cells = bytes / uint64_t(cell);
     const ThinTuning thin = thin_tuning();
+    // (a threshold above what a tile holds means: every under-filled tile;
+    // ops whose tiles are all full stay tiles)
+    const uint64_t cells_rule = std::min<uint64_t>(thin.tile_cells, uint64_t(t.TA) * t.TB);
     const bool thin_plane = bytes < op.units * thin.tile_bytes ||
-                            (bytes <= thin.l2_bytes && n_cells < op.units * thin.tile_cells);
+                            (bytes <= thin.l2_bytes && n_cells < op.units * cells_rule);
     if (W == cell && thin_plane && n_cells < kMaxUnits &&
         !(uint64_t(cell) <= box_max_cell_bytes() && plan_box(ax, cell, da, sa, static_cast<char *>(dst), src, op, info)))
         set_strided(W, n_cells);

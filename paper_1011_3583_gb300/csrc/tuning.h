@@ -28,7 +28,8 @@ BatchTuning batch_tuning();
 // When a tiled permute runs as an element-wise strided copy instead (thin
 // transpose planes): when its tiles would average fewer than tile_bytes of
 // payload, or, for ops of at most l2_bytes (whose scattered reads stay in the
-// L2), fewer than tile_cells cells.
+// L2), fewer than tile_cells cells (capped at the cells a full tile holds, so
+// an op whose tiles are all full stays tiled).
 struct ThinTuning {
     uint64_t tile_bytes = 1024;
     uint64_t tile_cells = 1024;
