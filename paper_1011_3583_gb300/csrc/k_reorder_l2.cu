@@ -4,46 +4,45 @@
 //
 // A direct gather from a source far larger than the L2 pays a whole DRAM
 // access (32-64 B) for every element it reads.  Here the source is cut into
-// chunks of about 16 MB (CS elements) and the destination into chunks of DS
-// elements; element i belongs to bucket (c, d) with c = idx[i] / CS and
-// d = i / DS.  DS is 64 KB of elements (one CTA's shared memory) when the
-// bucket count C * D stays within a bound (the shared-memory scatter), and
-// CS otherwise (the L2 scatter).  The passes:
-//   K1 sample    : index locality on 4096 short runs of idx; if most
-//                  neighbours are close (|idx[j+1] - idx[j]| <= 16), the
-//                  direct gather is already streaming and K2..K6 do nothing,
-//                  otherwise K7 does nothing.
-//   K2 histogram : bucket sizes, and the elements per source chunk.
-//   K3 scan      : bucket starts in c-major order (one CTA per source-chunk
-//                  row; the L2 scatter's single-CTA scan also lays out its
-//                  d-major work units).
-//   K4 partition : each 4096-element tile is counting-sorted by c in shared
-//                  memory and written as contiguous segments: s-array (source
-//                  index) and i-array (destination index; a 16-bit offset in
-//                  the chunk for the shared-memory scatter), c-major.  CTAs
-//                  that own whole destination chunks keep the bucket cursors
-//                  in shared memory.
-//   K5 gather    : v[k] = src[s[k]] walking k in order, so the CTAs in flight
-//                  read one ~16 MB source chunk at a time from L2.
-//   K6 scatter   : shared-memory form: one CTA per 64 KB destination chunk
-//                  d reads the C buckets (c, d), places every value at its
-//                  slot of the chunk in shared memory and writes the chunk
-//                  out with coalesced stores.  L2 form: dst[i[k]] = v[k]
-//                  walking the buckets d-major, so the CTAs in flight
-//                  complete one ~16 MB destination chunk in L2.
-//   K7 direct    : the plain gather (when K1 found locality).
-// Random global accesses cost one L1 request each (about one per clock per
-// SM, whatever the working set); random shared-memory accesses run about
-// twelve times as fast.  The shared-memory scatter so leaves the gather as
-// the one pass bound by random requests.  Streaming traffic in index-sized
-// words per element: idx 2 (K2, K4), s 2, i 1 (two 16-bit offsets), src 1,
-// v 2, dst 1 = 9 passes instead of n random DRAM accesses (10 with the L2
-// scatter's 32-bit i-array).
+// chunks of about 16 MB (CS elements, C chunks), and the passes make the
+// gather read one chunk at a time, L2-resident.  K1 first samples the index
+// locality on 4096 short runs of idx: if most neighbours are close
+// (|idx[j+1] - idx[j]| <= 16), the direct gather (K7) is already streaming
+// and every other pass returns at once; otherwise K7 returns at once.
+//
+// Tile-local form (gathers whose destination splits into CTA-sized chunks of
+// DS = 64 KB of elements, the usual case):
+//   partition : each 4096-index tile is counting-sorted by source chunk in
+//               shared memory and written back in place -- s-array (source
+//               index) and i-array (16-bit offset of the destination in its
+//               DS chunk) at the tile's own positions -- with the tile's
+//               C + 1 segment starts in a small table.  No pass over the
+//               whole sequence comes first.
+//   gather    : for each source chunk c in turn, v = src[s] over the
+//               c-segment of every tile, written at the same positions, so
+//               the CTAs in flight read one ~16 MB chunk at a time from L2.
+//   scatter   : one CTA per destination chunk reads the chunk's tiles in
+//               order, places each value at its offset in shared memory and
+//               writes the chunk out with coalesced stores.
+// L2 form (more than reorder_smem_max_buckets() (C, DS-chunk) buckets, or
+// forced by the tuning table): destination chunks of CS elements, element i
+// in bucket (c, d), d = i / CS; a histogram of the buckets and a scan give
+// c-major bucket starts; the partition writes each tile's c-segments at the
+// buckets' cursors (s-array, 32-bit i-array); the gather walks the s-array in
+// order; the scatter writes dst[i] = v walking the buckets d-major, so the
+// CTAs in flight complete one ~16 MB destination chunk in L2.
 // A scatter (dst[idx[i]] = src[i]) uses one bucket dimension only (D = 1,
 // buckets by the destination chunk of idx[i]): the partition writes
 // (destination index, element) pairs, and a linear pass writes
 // dst[s[k]] = v[k] with the destination chunk L2-resident.
-// Scratch ((8 + E) n bytes, plus 12 bytes per bucket) comes from a
+// Random global accesses cost one L1 request each (about one per clock per
+// SM, whatever the working set); random shared-memory accesses run about
+// twelve times as fast, so in the tile-local form the gather is the one pass
+// bound by random requests.  Its streaming traffic in index-sized words per
+// element: idx 1, s 2, i 1 (two 16-bit offsets), src 1, v 2, dst 1 = 8
+// passes instead of n random DRAM accesses.
+// Scratch ((8 + E) n bytes, plus 12 bytes per bucket and 2 (C + 1) bytes per
+// 4096-index tile) comes from a
 // stream-ordered pool owned by the library; the kernels are ordered on the
 // caller's stream and none waits on another.
 #include <cuda_runtime.h>
@@ -88,6 +87,8 @@ struct L2Reorder {
     uint32_t *sarr, *iarr;         // [n] source / destination indices, c-major; with CTA-sized
                                    // destination chunks the i-array holds uint16 offsets in the chunk
     char *varr;                    // [n] gathered values, c-major
+    uint16_t *st;                  // tile-local form: [tiles][C + 1] segment starts per tile
+    uint32_t tiles;                // 4096-index tiles of the sequence
     unsigned long long near_threshold;
 };
 
@@ -295,51 +296,12 @@ __global__ void __launch_bounds__(1024) k_l2_scan(const L2Reorder p)
     if (threadIdx.x == 0) p.uprefix[nb] = carry;
 }
 
-// Bucket starts for the shared-memory scatter (C * D up to millions of
-// buckets): CTA c scans row c of the histogram, offset by the elements of
-// the rows before it.  Each thread sums kRowPer consecutive buckets.
-constexpr int kRowPer = 16;
-
-__global__ void __launch_bounds__(1024) k_l2_scan_rows(const L2Reorder p)
-{
-    if (!bucketed(p)) return;
-    __shared__ uint32_t warp_sums[32];
-    __shared__ uint32_t total;
-    const uint32_t c = blockIdx.x;
-    uint32_t part = 0;
-    for (uint32_t x = threadIdx.x; x < c; x += 1024) part += p.rowtot[x];
-    block_scan(part, warp_sums, &total);
-    uint32_t carry = total;  // elements of the rows before c
-    const uint32_t row = c * p.D;
-    for (uint32_t d0 = 0; d0 < p.D; d0 += 1024 * kRowPer) {
-        const uint32_t dt = d0 + threadIdx.x * kRowPer;
-        uint32_t v[kRowPer], sum = 0;
-#pragma unroll
-        for (int r = 0; r < kRowPer; ++r) {
-            v[r] = dt + r < p.D ? p.hist[row + dt + r] : 0u;
-            sum += v[r];
-        }
-        uint32_t run = carry + block_scan(sum, warp_sums, &total);
-#pragma unroll
-        for (int r = 0; r < kRowPer; ++r) {
-            if (dt + r < p.D) {
-                p.base[row + dt + r] = run;
-                p.cursor[row + dt + r] = run;
-            }
-            run += v[r];
-        }
-        carry += total;
-    }
-}
-
 // Partition: per tile, every warp ranks its 512 elements by source chunk in
 // its own counters; thread t then owns chunks 2t and 2t + 1: it sums their
 // counts over the warps, and a block scan of those sums gives each chunk's
 // segment start in the tile.  The same thread turns its chunks' per-warp
-// counts into absolute slots and fixes the segment's global position: from
-// its own cursor when the CTA owns the tile's destination chunk (every tile
-// of that chunk is in the CTA's range, so the buckets (c, d) have no other
-// writer), else from one global atomic per chunk.  The tile is staged in
+// counts into absolute slots and takes the segment's global position with
+// one global atomic per chunk on the bucket's cursor.  The tile is staged in
 // shared memory grouped by chunk (the bucketed index and the tile index
 // packed in one 64-bit word; the chunk is recomputed from the index) and
 // written out as contiguous segments.  The next tile's indices load while this
@@ -348,20 +310,18 @@ struct PartitionSmem {
     unsigned long long sk[kTile];       // bucketed index (gather: source, scatter: destination) | tile index << 32
     uint32_t cnt[kWarps][kMaxChunks];   // per-warp counts, then per-warp slots
     uint32_t delta[kMaxChunks];         // global position of tile slot 0 of the chunk's segment
-    uint32_t cur[kMaxChunks];           // owned destination chunk: next free slot of bucket (c, d)
     uint32_t warp_sums[kWarps];
 };
 static_assert(sizeof(PartitionSmem) % 16 == 0, "the scatter form's element buffer follows, 16-byte aligned");
 
-// SW = 0: gather form (s-array: source index, i-array: destination index, as
-// a 16-bit offset in its chunk when the CTA owns the destination chunks).
+// SW = 0: gather form with ~16 MB destination chunks (s-array: source index,
+// i-array: destination index).
 // SW = W: scatter form (s-array: destination index, v-array: the element
 // itself): the tile's source elements are copied into shared memory with
 // cp.async behind the index loads and written out beside their indices, so
 // the scatter needs no separate pass that reads the source by position.
 template <int SW, bool I64>
-__global__ void __launch_bounds__(kThreads, 4) k_l2_partition(const L2Reorder p, uint32_t tiles_per_cta,
-                                                              uint32_t own)
+__global__ void __launch_bounds__(kThreads, 4) k_l2_partition(const L2Reorder p, uint32_t tiles_per_cta)
 {
     if (!bucketed(p)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -372,7 +332,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_l2_partition(const L2Reorder p,
     const uint32_t t0 = blockIdx.x * tiles_per_cta, t1 = min(tiles, t0 + tiles_per_cta);
     const uint32_t c0 = 2 * threadIdx.x;  // this thread's chunks: c0, c0 + 1
     for (uint32_t c = threadIdx.x; c < kWarps * kMaxChunks; c += kThreads) (&S.cnt[0][0])[c] = 0;
-    uint32_t cur_d = 0xFFFFFFFFu;
     uint32_t v[kPer];
     if (t0 < t1) load_tile<I64>(p, t0 * kTile, min(uint32_t(kTile), p.n - t0 * kTile), v);
     __syncthreads();
@@ -380,12 +339,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_l2_partition(const L2Reorder p,
         const uint32_t i0 = t * kTile;
         const uint32_t m = min(uint32_t(kTile), p.n - i0);
         const uint32_t d = dest_chunk(p, i0);
-        // an owned destination chunk starts: its buckets' first slots
-        uint32_t cb0 = 0, cb1 = 0;
-        if (own && d != cur_d) {
-            if (c0 < p.C) cb0 = p.base[c0 * p.D + d];
-            if (c0 + 1 < p.C) cb1 = p.base[(c0 + 1) * p.D + d];
-        }
         if constexpr (SW > 0) {
             // the tile's source elements -> shared memory (waited for before the write-out)
             const char *g = p.src + uint64_t(i0) * SW;
@@ -439,13 +392,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_l2_partition(const L2Reorder p,
                 S.cnt[x][c0] = run;
                 run += q;
             }
-            uint32_t g = 0;
-            if (own) {
-                g = d != cur_d ? cb0 : S.cur[c0];
-                S.cur[c0] = g + a;
-            } else if (a) {
-                g = atomicAdd(&p.cursor[c0 * p.D + d], a);
-            }
+            const uint32_t g = a ? atomicAdd(&p.cursor[c0 * p.D + d], a) : 0u;
             S.delta[c0] = g - e0;
         }
         if (c0 + 1 < p.C) {
@@ -456,16 +403,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_l2_partition(const L2Reorder p,
                 S.cnt[x][c0 + 1] = run;
                 run += q;
             }
-            uint32_t g = 0;
-            if (own) {
-                g = d != cur_d ? cb1 : S.cur[c0 + 1];
-                S.cur[c0 + 1] = g + b;
-            } else if (b) {
-                g = atomicAdd(&p.cursor[(c0 + 1) * p.D + d], b);
-            }
+            const uint32_t g = b ? atomicAdd(&p.cursor[(c0 + 1) * p.D + d], b) : 0u;
             S.delta[c0 + 1] = g - e1;
         }
-        cur_d = d;
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
@@ -486,12 +426,114 @@ __global__ void __launch_bounds__(kThreads, 4) k_l2_partition(const L2Reorder p,
                 using T = typename Word<SW>::T;
                 reinterpret_cast<T *>(p.varr)[g] = reinterpret_cast<const T *>(vals)[k];
             } else {
-                const uint32_t i = i0 + k;
-                if (own) reinterpret_cast<uint16_t *>(p.iarr)[g] = uint16_t(i & ((1u << p.ds_shift) - 1));
-                else p.iarr[g] = i;
+                p.iarr[g] = i0 + k;
             }
         }
         // only the C chunks in use need zeroing (not all kMaxChunks)
+        for (uint32_t x = threadIdx.x; x < kWarps * p.C; x += kThreads) S.cnt[x / p.C][x % p.C] = 0;
+        __syncthreads();
+        if (t + 1 < t1) {
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) v[j] = nxt[j];
+        }
+    }
+}
+
+// Tile-local form (a gather with CTA-sized destination chunks): no pass over
+// the whole index sequence has to come before the partition.  Each 4096-index
+// tile is counting-sorted by source chunk as above and written back IN PLACE
+// (s-array: source index, i-array: 16-bit offset of the destination in its
+// chunk, both at the tile's own positions), with the tile's C + 1 segment
+// starts in st.  The gather then walks, for each source chunk c in turn, the
+// c-segment of every tile, and writes each value at its element's position;
+// the scatter reads one destination chunk's tiles in order.
+template <bool I64>
+__global__ void __launch_bounds__(kThreads, 4) k_l2_partition_local(const L2Reorder p, uint32_t tiles_per_cta)
+{
+    if (!bucketed(p)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PartitionSmem &S = *reinterpret_cast<PartitionSmem *>(smem_raw);
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t t0 = blockIdx.x * tiles_per_cta, t1 = min(p.tiles, t0 + tiles_per_cta);
+    const uint32_t c0 = 2 * threadIdx.x;  // this thread's chunks: c0, c0 + 1
+    const uint32_t dmask = (1u << p.ds_shift) - 1;
+    for (uint32_t c = threadIdx.x; c < kWarps * kMaxChunks; c += kThreads) (&S.cnt[0][0])[c] = 0;
+    uint32_t v[kPer];
+    if (t0 < t1) load_tile<I64>(p, t0 * kTile, min(uint32_t(kTile), p.n - t0 * kTile), v);
+    __syncthreads();
+    for (uint32_t t = t0; t < t1; ++t) {
+        const uint32_t i0 = t * kTile;
+        const uint32_t m = min(uint32_t(kTile), p.n - i0);
+        uint32_t nxt[kPer];
+        if (t + 1 < t1) load_tile<I64>(p, (t + 1) * kTile, min(uint32_t(kTile), p.n - (t + 1) * kTile), nxt);
+        uint32_t rk[kPer];
+        if (m == kTile) {
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) rk[j] = atomicAdd(&S.cnt[w][chunk_of(p, v[j])], 1u);
+        } else {
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) rk[j] = tile_k(j) < m ? atomicAdd(&S.cnt[w][chunk_of(p, v[j])], 1u) : 0u;
+        }
+        __syncthreads();
+        uint32_t a = 0, b = 0;
+        if (c0 < p.C) {
+#pragma unroll
+            for (int x = 0; x < kWarps; ++x) a += S.cnt[x][c0];
+        }
+        if (c0 + 1 < p.C) {
+#pragma unroll
+            for (int x = 0; x < kWarps; ++x) b += S.cnt[x][c0 + 1];
+        }
+        uint32_t xs = a + b;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, xs, o);
+            if (lane >= o) xs += y;
+        }
+        if (lane == 31) S.warp_sums[w] = xs;
+        __syncthreads();
+        uint32_t before = 0;
+#pragma unroll
+        for (int x = 0; x < kWarps; ++x) before += x < int(w) ? S.warp_sums[x] : 0u;
+        const uint32_t e0 = before + xs - (a + b), e1 = e0 + a;  // segment starts of c0, c0 + 1
+        uint16_t *row = p.st + size_t(t) * (p.C + 1);
+        if (c0 < p.C) {
+            uint32_t run = e0;
+#pragma unroll
+            for (int x = 0; x < kWarps; ++x) {
+                const uint32_t q = S.cnt[x][c0];
+                S.cnt[x][c0] = run;
+                run += q;
+            }
+            row[c0] = uint16_t(e0);
+        }
+        if (c0 + 1 < p.C) {
+            uint32_t run = e1;
+#pragma unroll
+            for (int x = 0; x < kWarps; ++x) {
+                const uint32_t q = S.cnt[x][c0 + 1];
+                S.cnt[x][c0 + 1] = run;
+                run += q;
+            }
+            row[c0 + 1] = uint16_t(e1);
+        }
+        if (threadIdx.x == 0) row[p.C] = uint16_t(m);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const uint32_t k = tile_k(j);
+            if (m == kTile || k < m) {
+                const uint32_t pos = S.cnt[w][chunk_of(p, v[j])] + rk[j];
+                S.sk[pos] = (unsigned long long)v[j] | ((unsigned long long)k << 32);
+            }
+        }
+        __syncthreads();
+        uint16_t *ioff = reinterpret_cast<uint16_t *>(p.iarr) + i0;
+        for (uint32_t q = threadIdx.x; q < m; q += kThreads) {
+            const unsigned long long x = S.sk[q];
+            p.sarr[i0 + q] = uint32_t(x);
+            ioff[q] = uint16_t((i0 + uint32_t(x >> 32)) & dmask);
+        }
         for (uint32_t x = threadIdx.x; x < kWarps * p.C; x += kThreads) S.cnt[x / p.C][x % p.C] = 0;
         __syncthreads();
         if (t + 1 < t1) {
@@ -551,6 +593,116 @@ __global__ void __launch_bounds__(kThreads, W == 4 ? 8 : W == 8 ? 6 : 4) k_l2_ga
     }
 }
 
+// Gather over the tile-local form: unit (c, g) takes source chunk c's
+// segment in each of the kWarps * S tiles of group g; a warp walks the
+// segments of S tiles together, J elements of each per lane in flight,
+// reading s and writing v at the same positions.  S grows with C (segments
+// shrink as 4096 / C), so that a unit stays about 2048 elements, and 32 J
+// covers a segment's mean length plus three standard deviations, so that
+// one round usually finishes it.  Units go out in c-major order, so the CTAs
+// in flight read about one ~16 MB source chunk at a time from the L2.
+template <int W, int S, int J>
+__global__ void __launch_bounds__(kThreads, W == 4 ? 6 : W == 8 ? 5 : 4) k_l2_gather_local(const L2Reorder p)
+{
+    if (!bucketed(p)) return;
+    constexpr uint32_t kUnitTiles = kWarps * S;
+    __shared__ uint32_t slot;
+    using T = typename Word<W>::T;
+    const uint64_t first = l2_evict_first(), last = l2_evict_last();
+    const uint32_t groups = (p.tiles + kUnitTiles - 1) / kUnitTiles;
+    const uint32_t units = p.C * groups;
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        const uint32_t u = next_unit(p.ctr_gather, &slot);
+        if (u >= units) break;
+        const uint32_t c = u / groups, g = u - c * groups;
+        uint32_t beg[S], end[S], len = 0;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const uint32_t t = g * kUnitTiles + w * S + s;
+            beg[s] = end[s] = 0;
+            if (t < p.tiles) {
+                const uint16_t *row = p.st + size_t(t) * (p.C + 1);
+                beg[s] = t * kTile + row[c];
+                end[s] = t * kTile + row[c + 1];
+                len = max(len, end[s] - beg[s]);
+            }
+        }
+        for (uint32_t off = 0; off < len; off += 32 * J) {
+            uint32_t sv[S][J];
+            T val[S][J];
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const uint32_t k = beg[s] + off + uint32_t(j) * 32 + lane;
+                    sv[s][j] = k < end[s] ? ldg_hint<4>(p.sarr + k, first) : 0u;
+                }
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const uint32_t k = beg[s] + off + uint32_t(j) * 32 + lane;
+                    if (k < end[s]) val[s][j] = ldg_hint<W>(p.src + uint64_t(sv[s][j]) * W, last);
+                }
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const uint32_t k = beg[s] + off + uint32_t(j) * 32 + lane;
+                    if (k < end[s]) stg_hint<W>(p.varr + uint64_t(k) * W, val[s][j], first);
+                }
+        }
+    }
+}
+
+// Scatter over the tile-local form: one CTA per destination chunk d reads the
+// chunk's i- and v-arrays in order (its own tiles), places each value at its
+// offset of the chunk in shared memory and writes the chunk out with
+// coalesced stores, 16 bytes per lane when dst allows.
+template <int W>
+__global__ void __launch_bounds__(kScatterThreads) k_l2_scatter_local(const L2Reorder p)
+{
+    if (!bucketed(p)) return;
+    using T = typename Word<W>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *chunk = reinterpret_cast<T *>(smem_raw);
+    const uint64_t first = l2_evict_first();
+    constexpr int U = 4;
+    const uint32_t dmask = (1u << p.ds_shift) - 1;
+    const bool vec = (reinterpret_cast<uintptr_t>(p.dst) & 15) == 0;
+    const uint16_t *off = reinterpret_cast<const uint16_t *>(p.iarr);
+    for (uint32_t d = blockIdx.x; d < p.D; d += gridDim.x) {
+        const uint64_t i0 = uint64_t(d) << p.ds_shift;
+        const uint32_t m = uint32_t(min(uint64_t(dmask) + 1, uint64_t(p.n) - i0));
+        uint32_t q = threadIdx.x;
+        for (; q + (U - 1) * kScatterThreads < m; q += U * kScatterThreads) {
+            uint32_t di[U];
+            T val[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                di[u] = ldg_hint<2>(off + i0 + q + u * kScatterThreads, first);
+                val[u] = ldg_hint<W>(p.varr + (i0 + q + u * kScatterThreads) * W, first);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) chunk[di[u] & dmask] = val[u];
+        }
+        for (; q < m; q += kScatterThreads)
+            chunk[ldg_hint<2>(off + i0 + q, first) & dmask] = ldg_hint<W>(p.varr + (i0 + q) * W, first);
+        __syncthreads();
+        char *out = p.dst + i0 * W;
+        uint32_t done = 0;
+        if (vec) {
+            const uint32_t nv = m * W / 16;
+            const uint4 *c16 = reinterpret_cast<const uint4 *>(smem_raw);
+            for (uint32_t x = threadIdx.x; x < nv; x += kScatterThreads) reinterpret_cast<uint4 *>(out)[x] = c16[x];
+            done = nv * 16 / W;
+        }
+        for (uint32_t x = done + threadIdx.x; x < m; x += kScatterThreads) reinterpret_cast<T *>(out)[x] = chunk[x];
+        __syncthreads();
+    }
+}
+
 // K6: dst[i[k]] = v[k] walking the buckets d-major; the destination chunk
 // being written is L2-resident, so its sectors are completed there.
 template <int W>
@@ -597,60 +749,6 @@ __global__ void __launch_bounds__(kThreads) k_l2_scatter(const L2Reorder p)
             const uint32_t k = k0 + j * kThreads + threadIdx.x;
             if (k < k1) stg_hint<W>(p.dst + uint64_t(di[j]) * W, val[j], last);
         }
-    }
-}
-
-// K6, shared-memory form: CTA-sized destination chunks.  The warps split the
-// chunk's C buckets; each value goes to its slot of the chunk in shared
-// memory (the partition stored i's 16-bit offset in chunk d; the mask only
-// keeps a corrupt word inside the buffer), then
-// the CTA writes the chunk out, 16 bytes per lane when dst allows.
-template <int W>
-__global__ void __launch_bounds__(kScatterThreads) k_l2_scatter_smem(const L2Reorder p)
-{
-    if (!bucketed(p)) return;
-    using T = typename Word<W>::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *chunk = reinterpret_cast<T *>(smem_raw);
-    const uint64_t first = l2_evict_first();
-    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr uint32_t kW = kScatterThreads / 32;
-    constexpr int U = 4;
-    const uint32_t dmask = (1u << p.ds_shift) - 1;
-    const bool vec = (reinterpret_cast<uintptr_t>(p.dst) & 15) == 0;
-    for (uint32_t d = blockIdx.x; d < p.D; d += gridDim.x) {
-        for (uint32_t c = warp; c < p.C; c += kW) {
-            const uint32_t b = c * p.D + d;
-            const uint32_t k1 = p.base[b] + p.hist[b];
-            uint32_t k = p.base[b] + lane;
-            const uint16_t *off = reinterpret_cast<const uint16_t *>(p.iarr);  // offsets in the chunk
-            for (; k + 32 * (U - 1) < k1; k += 32 * U) {
-                uint32_t di[U];
-                T val[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    di[u] = ldg_hint<2>(off + k + 32 * u, first);
-                    val[u] = ldg_hint<W>(p.varr + uint64_t(k + 32 * u) * W, first);
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) chunk[di[u] & dmask] = val[u];
-            }
-            for (; k < k1; k += 32) chunk[ldg_hint<2>(off + k, first) & dmask] = ldg_hint<W>(p.varr + uint64_t(k) * W, first);
-        }
-        __syncthreads();
-        const uint64_t i0 = uint64_t(d) << p.ds_shift;
-        const uint32_t m = uint32_t(min(uint64_t(dmask) + 1, uint64_t(p.n) - i0));
-        char *out = p.dst + i0 * W;
-        uint32_t done = 0;
-        if (vec) {
-            const uint32_t nv = m * W / 16;
-            const uint4 *c16 = reinterpret_cast<const uint4 *>(smem_raw);
-            for (uint32_t q = threadIdx.x; q < nv; q += kScatterThreads)
-                reinterpret_cast<uint4 *>(out)[q] = c16[q];
-            done = nv * 16 / W;
-        }
-        for (uint32_t q = done + threadIdx.x; q < m; q += kScatterThreads) reinterpret_cast<T *>(out)[q] = chunk[q];
-        __syncthreads();
     }
 }
 
@@ -739,7 +837,8 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
     p.ds_shift = gm.ds_shift;
     p.D = gm.D;
     const size_t off_hist = gm.off_hist, off_row = gm.off_row, off_base = gm.off_base, off_cur = gm.off_cur,
-                 off_up = gm.off_up, off_s = gm.off_s, off_i = gm.off_i, off_v = gm.off_v, bytes = gm.bytes;
+                 off_up = gm.off_up, off_s = gm.off_s, off_i = gm.off_i, off_v = gm.off_v, off_st = gm.off_st,
+                 bytes = gm.bytes;
     cudaMemPool_t pool;
     cudaError_t e = get_pool(pool);
     if (e != cudaSuccess) return e;
@@ -757,6 +856,8 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
     p.sarr = reinterpret_cast<uint32_t *>(scratch + off_s);
     p.iarr = reinterpret_cast<uint32_t *>(scratch + off_i);
     p.varr = scratch + off_v;
+    p.st = reinterpret_cast<uint16_t *>(scratch + off_st);
+    p.tiles = uint32_t((g.n + kTile - 1) / kTile);
     const uint64_t pairs = uint64_t(kSampleRuns) * (kSampleLen - 1);
     p.near_threshold = pairs / 2;
     e = cudaMemsetAsync(scratch, 0, off_base, s);  // near counter, histogram, row totals
@@ -785,11 +886,17 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
                 e = cudaFuncSetAttribute(k_l2_partition<W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(sizeof(PartitionSmem) + kTile * W));
             if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_l2_partition_local<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(sizeof(PartitionSmem)));
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_l2_partition_local<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(sizeof(PartitionSmem)));
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_l2_scatter_local<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(kScatterChunkBytes));
+            if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(k_l2_partition<W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(sizeof(PartitionSmem) + kTile * W));
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(k_l2_scatter_smem<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(kScatterChunkBytes));
             smem_set[dev] = e == cudaSuccess;
             int per_sm = 0;
             if (e == cudaSuccess && cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -802,7 +909,7 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
                 spart_per_sm[dev] = per_sm;
             per_sm = 0;
             if (e == cudaSuccess && cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                        &per_sm, k_l2_scatter_smem<W>, kScatterThreads, kScatterChunkBytes) ==
+                                        &per_sm, k_l2_scatter_local<W>, kScatterThreads, kScatterChunkBytes) ==
                                         cudaSuccess)
                 scat_per_sm[dev] = per_sm;
         }
@@ -812,45 +919,55 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
     // The partition runs one wave: every resident CTA takes a contiguous
     // range of tiles (a second, partial wave would leave SMs idle).
     const uint32_t part_resident = uint32_t(sms) * uint32_t(per_sm_part);
-    // With CTA-sized destination chunks every CTA takes whole chunks (a
-    // multiple of the chunk's tiles) and writes their buckets alone.
-    const uint32_t tpd = smem_scatter ? (1u << p.ds_shift) / kTile : 1u;
-    uint32_t part_tpc = (tiles + part_resident - 1) / part_resident;
-    part_tpc = (part_tpc + tpd - 1) / tpd * tpd;
+    const uint32_t part_tpc = (tiles + part_resident - 1) / part_resident;
     const unsigned part_grid = unsigned((tiles + part_tpc - 1) / part_tpc);
     const unsigned pers = unsigned(sms) * 8;  // persistent grids of the gated passes
     const uint64_t dunits = (g.n + g.unit_elems - 1) / g.unit_elems;
     if (e == cudaSuccess) { k_l2_sample<<<kSampleRuns / (kThreads / 32), kThreads, 0, s>>>(p); e = cudaGetLastError(); }
-    if (e == cudaSuccess) {
+    // A gather with CTA-sized destination chunks runs the tile-local form:
+    // partition in place, gather over the tiles' segments, scatter per chunk.
+    const bool local = smem_scatter && !g.scatter;
+    if (local) {
+        if (e == cudaSuccess) {
+            if (p.idx64) k_l2_partition_local<true><<<part_grid, kThreads, sizeof(PartitionSmem), s>>>(p, part_tpc);
+            else k_l2_partition_local<false><<<part_grid, kThreads, sizeof(PartitionSmem), s>>>(p, part_tpc);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            // segments of 4096 / C elements: tiles per warp so that a unit is ~2048 elements
+            // (wider elements take fewer per lane, within the register budget)
+            constexpr int J1 = W == 16 ? 8 : 10, J2 = W == 16 ? 4 : 6, J4 = W == 4 ? 3 : 2;
+            if (p.C <= 16) k_l2_gather_local<W, 1, J1><<<pers, kThreads, 0, s>>>(p);
+            else if (p.C <= 32) k_l2_gather_local<W, 2, J2><<<pers, kThreads, 0, s>>>(p);
+            else if (p.C <= 64) k_l2_gather_local<W, 4, J4><<<pers, kThreads, 0, s>>>(p);
+            else k_l2_gather_local<W, 4, 2><<<pers, kThreads, 0, s>>>(p);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            const unsigned sgrid = unsigned(std::min<uint64_t>(p.D, uint64_t(sms) * per_sm_scat));
+            k_l2_scatter_local<W><<<sgrid, kScatterThreads, kScatterChunkBytes, s>>>(p);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess && !local) {
         if (p.idx64) k_l2_hist<true><<<pgrid, kThreads, 0, s>>>(p, tpc);
         else k_l2_hist<false><<<pgrid, kThreads, 0, s>>>(p, tpc);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) {
-        if (smem_scatter) k_l2_scan_rows<<<p.C, 1024, 0, s>>>(p);
-        else k_l2_scan<<<1, 1024, 0, s>>>(p);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && !local) { k_l2_scan<<<1, 1024, 0, s>>>(p); e = cudaGetLastError(); }
+    if (e == cudaSuccess && !local) {
         const size_t sm_part = sizeof(PartitionSmem) + (g.scatter ? size_t(kTile) * W : 0);
-        const uint32_t own = !g.scatter && smem_scatter ? 1u : 0u;
-        if (g.scatter && p.idx64) k_l2_partition<W, true><<<part_grid, kThreads, sm_part, s>>>(p, part_tpc, own);
-        else if (g.scatter) k_l2_partition<W, false><<<part_grid, kThreads, sm_part, s>>>(p, part_tpc, own);
-        else if (p.idx64) k_l2_partition<0, true><<<part_grid, kThreads, sm_part, s>>>(p, part_tpc, own);
-        else k_l2_partition<0, false><<<part_grid, kThreads, sm_part, s>>>(p, part_tpc, own);
+        if (g.scatter && p.idx64) k_l2_partition<W, true><<<part_grid, kThreads, sm_part, s>>>(p, part_tpc);
+        else if (g.scatter) k_l2_partition<W, false><<<part_grid, kThreads, sm_part, s>>>(p, part_tpc);
+        else if (p.idx64) k_l2_partition<0, true><<<part_grid, kThreads, sm_part, s>>>(p, part_tpc);
+        else k_l2_partition<0, false><<<part_grid, kThreads, sm_part, s>>>(p, part_tpc);
         e = cudaGetLastError();
     }
-    if (!g.scatter) {
+    if (local) {
+        // done above
+    } else if (!g.scatter) {
         if (e == cudaSuccess) { k_l2_gather<W><<<pers, kThreads, 0, s>>>(p); e = cudaGetLastError(); }
-        if (e == cudaSuccess) {
-            if (smem_scatter) {
-                const unsigned sgrid = unsigned(std::min<uint64_t>(p.D, uint64_t(sms) * per_sm_scat));
-                k_l2_scatter_smem<W><<<sgrid, kScatterThreads, kScatterChunkBytes, s>>>(p);
-            } else {
-                k_l2_scatter<W><<<pers, kThreads, 0, s>>>(p);
-            }
-            e = cudaGetLastError();
-        }
+        if (e == cudaSuccess) { k_l2_scatter<W><<<pers, kThreads, 0, s>>>(p); e = cudaGetLastError(); }
     } else {
         // the partition wrote (destination index, element) pairs
         if (e == cudaSuccess) { k_l2_scatter_linear<W><<<pers, kThreads, 0, s>>>(p); e = cudaGetLastError(); }
@@ -862,7 +979,7 @@ cudaError_t run_l2(const GatherDesc &g, cudaStream_t s)
         k_l2_direct<W><<<unsigned(std::min<uint64_t>(dunits, cap)), kThreads, 0, s>>>(p, g, dunits);
         e = cudaGetLastError();
     }
-    g_launches.fetch_add(g.scatter ? 6 : 7, std::memory_order_relaxed);
+    g_launches.fetch_add(local ? 5 : g.scatter ? 6 : 7, std::memory_order_relaxed);
     cudaError_t e2 = cudaFreeAsync(scratch, s);
     return e != cudaSuccess ? e : e2;
 }

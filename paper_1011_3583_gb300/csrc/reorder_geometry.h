@@ -23,7 +23,7 @@ struct ReorderGeometry {
     uint32_t C, D;       // source / destination chunks (D = 1 for a scatter)
     bool smem_scatter;   // the gather's last pass through shared memory
     // scratch layout: byte offsets of the arrays and the total
-    size_t off_hist, off_row, off_base, off_cur, off_up, off_s, off_i, off_v, bytes;
+    size_t off_hist, off_row, off_base, off_cur, off_up, off_s, off_i, off_v, off_st, bytes;
 };
 
 // n elements of W bytes; scatter: buckets by destination chunk only;
@@ -52,7 +52,10 @@ inline ReorderGeometry reorder_geometry(uint64_t n, uint32_t W, bool scatter, ui
     g.off_s = g.off_up + al((nb + 1) * 4);
     g.off_i = g.off_s + al(size_t(n) * 4);
     g.off_v = g.off_i + al(size_t(n) * 4);
-    g.bytes = g.off_v + al(size_t(n) * W);
+    g.off_st = g.off_v + al(size_t(n) * W);
+    // tile-local form: C + 1 segment starts (uint16) per 4096-index tile
+    const size_t tiles = size_t((n + 4095) / 4096);
+    g.bytes = g.off_st + al(tiles * (size_t(g.C) + 1) * 2);
     return g;
 }
 

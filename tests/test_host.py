@@ -307,8 +307,9 @@ def test_reorder_describe_paths(lr, tmp_path):
     d = lr.describe_reorder(n, 4)
     assert d["form"] == "smem_scatter" and d["bucket_chunks"] == 64 and d["bucket_chunk_elems"] == 1 << 22
     assert d["dest_chunks"] == n >> 14 and d["dest_chunk_elems"] == 1 << 14   # 64 KB of fp32
-    # scratch: s-, i- and v-arrays (12 bytes per element) plus the bucket tables
-    assert 12 * n < d["scratch_bytes"] < 12 * n + 20 * (64 * (n >> 14)) + (1 << 20)
+    # scratch: s-, i- and v-arrays (12 bytes per element) plus the bucket
+    # tables and the per-tile segment starts (65 x 2 bytes per 4096 indices)
+    assert 12 * n < d["scratch_bytes"] < 12 * n + 20 * (64 * (n >> 14)) + 130 * (n >> 12) + (1 << 20)
     assert lr.describe_reorder(n, 4, idx_bytes=8) == d                       # 64-bit indices: same passes
     s = lr.describe_reorder(n, 4, scatter=True)
     assert s["form"] == "linear_scatter" and s["dest_chunks"] == 1
