@@ -169,7 +169,9 @@ rearr_status rearr_reorder_checked(void *dst, const void *src, const uint32_t *i
  * ------------------------------------------------------------------------- */
 typedef enum {
     REARR_REORDER_DIRECT = 0,          /* one direct gather / scatter kernel         */
-    REARR_REORDER_SMEM_SCATTER = 1,    /* gather, last pass through shared memory    */
+    REARR_REORDER_SMEM_SCATTER = 1,    /* gather, tile-local passes: partition in
+                                          place, gather per source chunk, scatter
+                                          through shared memory per 64 KB chunk  */
     REARR_REORDER_L2_SCATTER = 2,      /* gather, last pass through ~16 MB L2 chunks */
     REARR_REORDER_LINEAR_SCATTER = 3   /* scatter: (destination, element) pairs      */
 } rearr_reorder_form;
